@@ -1,0 +1,201 @@
+"""FP64 CPU oracle for the GS / WGS / OSPR hologram generators.
+
+TEST INFRASTRUCTURE ONLY: the tests, ``__graft_entry__.smoke()`` and the
+CPU-baseline leg of ``bench.py`` use it; the product path never imports it.
+It shares no code with the CUDA path.  The arithmetic lives in
+``hologen_oracle.c`` (plain C, double precision); this module compiles it
+with gcc on first use and wraps it with ctypes, returning numpy arrays.
+
+Every function cites the passage of arXiv:2008.12214 (HoloGen) it follows in
+the C source's header.  Parity status: the FFT, quantiser, GS step, replay and
+Philox are pinned by ``tests/test_oracle.py``; the exact WGS trajectory and the
+OSPR mean intensity are "parity unpinned" beyond the qualitative checks listed
+there.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "hologen_oracle.c")
+_LIB = os.path.join(_HERE, "liboracle.so")
+_lock = threading.Lock()
+_lib = None
+
+SLM_BINARY, SLM_LLEVEL, SLM_CONTINUOUS = 0, 1, 2
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle shared library with gcc (OpenMP over rows/columns)."""
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+        tmp = _LIB + ".tmp%d" % os.getpid()
+        subprocess.check_call(["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-fopenmp",
+                               _SRC, "-o", tmp, "-lm"])
+        os.replace(tmp, _LIB)
+    return _LIB
+
+
+def _load():
+    global _lib
+    with _lock:
+        if _lib is None:
+            build()
+            lib = ctypes.CDLL(_LIB)
+            P = ctypes.c_void_p
+            i = ctypes.c_int
+            u32 = ctypes.c_uint32
+            u64 = ctypes.c_uint64
+            lib.or_is_235.argtypes = [i]
+            lib.or_fft1d.argtypes = [i, P, P, i]
+            lib.or_fft2d.argtypes = [i, i, P, i]
+            lib.or_shift2d.argtypes = [i, i, P, P, i]
+            lib.or_shift2d.restype = None
+            lib.or_prepare_target.argtypes = [i, P, P]
+            lib.or_quantise.argtypes = [i, P, i, i, P]
+            lib.or_gs_step.argtypes = [i, i, P, P, P, i, i, i, P, P, P, P, P, P]
+            lib.or_gs_run.argtypes = [i, i, P, P, i, i, i, i, P, P, P, P, P, P]
+            lib.or_replay.argtypes = [i, i, i, P, i, i, P]
+            lib.or_philox4x32_10.argtypes = [P, P, P]
+            lib.or_philox4x32_10.restype = None
+            lib.or_random_phase.argtypes = [i, i, u64, u32, u32, u32, P]
+            lib.or_ospr_run.argtypes = [i, i, P, i, u64, u32, P, P, P]
+            _lib = lib
+    return _lib
+
+
+class OracleError(RuntimeError):
+    pass
+
+
+def _ck(st):
+    if st != 0:
+        raise OracleError("oracle call failed with status %d" % st)
+
+
+def _p(a):
+    return None if a is None else a.ctypes.data_as(ctypes.c_void_p)
+
+
+def _c128(a):
+    return np.ascontiguousarray(a, dtype=np.complex128)
+
+
+def is_235(n: int) -> bool:
+    return bool(_load().or_is_235(int(n)))
+
+
+def fft1d(x, sign: int = -1) -> np.ndarray:
+    """Unnormalised 1D DFT, X[k] = sum_j x[j] exp(sign 2 pi i jk/n)."""
+    x = _c128(x)
+    out = np.empty_like(x)
+    _ck(_load().or_fft1d(x.size, _p(x), _p(out), int(sign)))
+    return out
+
+
+def fft2(a, sign: int = -1) -> np.ndarray:
+    """Unitary 2D DFT (eqs. fouriertrans2d5c/d); sign=-1 forward, +1 inverse."""
+    a = _c128(a).copy()
+    ny, nx = a.shape
+    _ck(_load().or_fft2d(ny, nx, _p(a), int(sign)))
+    return a
+
+
+def shift2d(a, inverse: bool = False) -> np.ndarray:
+    a = np.ascontiguousarray(a, dtype=np.float64)
+    out = np.empty_like(a)
+    _load().or_shift2d(a.shape[0], a.shape[1], _p(a), _p(out), int(bool(inverse)))
+    return out
+
+
+def prepare_target(t_raw) -> np.ndarray:
+    t = np.ascontiguousarray(t_raw, dtype=np.float32)
+    out = np.empty(t.shape, np.float64)
+    _ck(_load().or_prepare_target(t.size, _p(t), _p(out)))
+    return out
+
+
+def quantise(h, kind: int, levels: int = 2) -> np.ndarray:
+    h = _c128(h)
+    q = np.empty(h.shape, np.uint8)
+    _ck(_load().or_quantise(h.size, _p(h), int(kind), int(levels), _p(q)))
+    return q
+
+
+def gs_step(T, phase, w=None, kind=SLM_BINARY, levels=2, wgs=False):
+    """One GS/WGS iteration from state (phase, w).  T normalised, replay order.
+
+    Returns dict(h, holo, R, mse, amp_mse, eff, sum_r2, phase, w)."""
+    T = np.ascontiguousarray(T, dtype=np.float64)
+    ny, nx = T.shape
+    ph = np.ascontiguousarray(phase, dtype=np.float64)
+    w_in = None if w is None else np.ascontiguousarray(w, dtype=np.float64)
+    h = np.empty((ny, nx), np.complex128)
+    holo = np.empty((ny, nx), np.uint8)
+    R = np.empty((ny, nx), np.complex128)
+    met = np.empty(4, np.float64)
+    ph_out = np.empty((ny, nx), np.float64)
+    w_out = np.empty((ny, nx), np.float64)
+    _ck(_load().or_gs_step(ny, nx, _p(T), _p(ph), _p(w_in), int(kind), int(levels), int(bool(wgs)),
+                           _p(h), _p(holo), _p(R), _p(met), _p(ph_out), _p(w_out)))
+    return dict(h=h, holo=holo, R=R, mse=met[0], amp_mse=met[1], eff=met[2], sum_r2=met[3],
+                phase=ph_out, w=w_out)
+
+
+def gs_run(t_raw, phase0, iters, kind=SLM_BINARY, levels=2, wgs=False):
+    """Whole GS/WGS run; returns dict(holo, mse[iters], amp_mse, eff, phase, w)."""
+    t = np.ascontiguousarray(t_raw, dtype=np.float32)
+    ny, nx = t.shape
+    ph = np.ascontiguousarray(phase0, dtype=np.float64)
+    holo = np.empty((ny, nx), np.uint8)
+    mse = np.empty(iters, np.float64)
+    amp = np.empty(iters, np.float64)
+    eff = np.empty(iters, np.float64)
+    ph_out = np.empty((ny, nx), np.float64)
+    w_out = np.empty((ny, nx), np.float64)
+    _ck(_load().or_gs_run(ny, nx, _p(t), _p(ph), int(iters), int(kind), int(levels), int(bool(wgs)),
+                          _p(holo), _p(mse), _p(amp), _p(eff), _p(ph_out), _p(w_out)))
+    return dict(holo=holo, mse=mse, amp_mse=amp, eff=eff, phase=ph_out, w=w_out)
+
+
+def replay(holo, kind=SLM_BINARY, levels=2) -> np.ndarray:
+    """Normalised replay intensity (sum 1, replay order); holo [count][ny][nx]
+    or [ny][nx]; several holograms are time-averaged."""
+    h = np.ascontiguousarray(holo, dtype=np.uint8)
+    if h.ndim == 2:
+        h = h[None]
+    c, ny, nx = h.shape
+    out = np.empty((ny, nx), np.float64)
+    _ck(_load().or_replay(ny, nx, c, _p(h), int(kind), int(levels), _p(out)))
+    return out
+
+
+def philox4x32_10(ctr, key) -> np.ndarray:
+    c = np.ascontiguousarray(ctr, dtype=np.uint32)
+    k = np.ascontiguousarray(key, dtype=np.uint32)
+    out = np.empty(4, np.uint32)
+    _load().or_philox4x32_10(_p(c), _p(k), _p(out))
+    return out
+
+
+def random_phase(ny, nx, seed, t, sub, stream) -> np.ndarray:
+    out = np.empty((ny, nx), np.float64)
+    _ck(_load().or_random_phase(int(ny), int(nx), int(seed), int(t), int(sub), int(stream), _p(out)))
+    return out
+
+
+def ospr_run(t_raw, nsub, seed, t_index=0):
+    """OSPR over nsub subframes; returns dict(holo[nsub], I (normalised time
+    average), mse, amp_mse, eff)."""
+    t = np.ascontiguousarray(t_raw, dtype=np.float32)
+    ny, nx = t.shape
+    holo = np.empty((nsub, ny, nx), np.uint8)
+    I_out = np.empty((ny, nx), np.float64)
+    met = np.empty(4, np.float64)
+    _ck(_load().or_ospr_run(ny, nx, _p(t), int(nsub), int(seed), int(t_index), _p(holo), _p(I_out),
+                            _p(met)))
+    return dict(holo=holo, I=I_out, mse=met[0], amp_mse=met[1], eff=met[2])
