@@ -1,0 +1,168 @@
+/*
+ * hologen.h -- C ABI of the GB300 iterative Fourier-transform hologram engine.
+ *
+ * The engine computes 2D Fourier holograms for phase-only spatial light
+ * modulators (SLMs) with the iterative Fourier-transform algorithms of
+ * HoloGen (Christopher, Kadis, Gordon, Wilkinson, arXiv:2008.12214):
+ * Gerchberg-Saxton (GS) and weighted GS (Section 3.2) and one-step phase
+ * retrieval (OSPR, Section 3.4).  The far field of the SLM is the unitary 2D
+ * DFT of Section 2, eqs. (fouriertrans2d5c) and (fouriertrans2d5d); the SLM
+ * keeps only phases on its levels (Section 3, Fig. 1); the error is the MSE of
+ * Section 3.1, eq. (mse), plus the intensity MSE described below.
+ *
+ * Conventions used by every call
+ *  - Images are row-major [ny][nx], x fastest, one image per target; a batch
+ *    is [batch][ny][nx].  ny and nx must be supported lengths (see
+ *    hg_supported_length); otherwise HG_ERR_UNSUPPORTED_SIZE.
+ *  - Targets and replay-plane quantities (target amplitude, phases, weights,
+ *    intensities) are in REPLAY order: the zero spatial frequency at pixel
+ *    (ny/2, nx/2) (integer division), i.e. replay = fftshift(FFT2(slm)).
+ *    Holograms are in natural SLM order.
+ *  - Pointers may be device pointers or ordinary host pointers.  With device
+ *    pointers the call only enqueues work on the plan's stream and returns
+ *    (errors detected on the device surface at hg_sync or at the next call
+ *    that synchronises); with any host pointer the call copies through
+ *    plan-owned device buffers and synchronises the stream before returning.
+ *  - The caller owns every buffer it passes; the plan owns its workspace.
+ *    No call keeps a caller pointer after it returns.
+ *  - No call throws, aborts, or falls back to a CPU path; failures come back
+ *    as a status code.  A plan must not be used from two threads at once.
+ */
+#ifndef HOLOGEN_H
+#define HOLOGEN_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct hg_plan_s *hg_plan;
+
+typedef enum {
+    HG_OK = 0,
+    HG_ERR_INVALID_ARG = 1,      /* bad pointer, size, enum, or target values */
+    HG_ERR_UNSUPPORTED_SIZE = 2, /* ny or nx has no compiled transform plan */
+    HG_ERR_OOM = 3,              /* device allocation failed */
+    HG_ERR_CUDA = 4,             /* a CUDA runtime call failed */
+    HG_ERR_TIMEOUT = 5,          /* a bounded device-side wait gave up */
+    HG_ERR_NUMERIC = 6           /* target with zero energy */
+} hg_status;
+
+/* SLM modulation (Section 3; Fig. 1).  BINARY: levels {0, pi}, level 0 iff
+ * Re h >= 0 for the back-propagated field h.  LLEVEL: `levels` phases
+ * 2 pi q / levels over the full circle, q = round-half-away(arg h /
+ * (2 pi / levels)) mod levels, 2 <= levels <= 256. */
+typedef enum { HG_SLM_BINARY = 0, HG_SLM_LLEVEL = 1 } hg_slm_kind;
+typedef struct {
+    int kind;   /* hg_slm_kind */
+    int levels; /* ignored for BINARY */
+} hg_slm;
+
+/* GS: Section 3.2.  WGS: GS whose target amplitude is multiplied by a weight
+ * updated every iteration as w <- w T / sqrt(I) on pixels with T > 0, where
+ * I is the energy-normalised replay intensity.  OSPR: Section 3.4, binary
+ * SLM only, `subframes` independent random-phase subframes per target whose
+ * replay intensities are averaged. */
+typedef enum { HG_GS = 0, HG_WGS = 1, HG_OSPR = 2 } hg_algo;
+
+typedef struct {
+    void *stream;      /* cudaStream_t to enqueue on; NULL = legacy default stream */
+    uint64_t seed;     /* Philox4x32-10 key for drawn phases */
+    int subframes;     /* OSPR subframes per target (>= 1); ignored otherwise */
+    int precision;     /* 0 = FP32 transforms (the only value accepted) */
+    int use_graph;     /* 1 = replay the iteration loop as a CUDA graph (default) */
+} hg_opts;
+
+/* Fills *opts with the defaults: stream NULL, seed 0, subframes 24,
+ * precision 0, use_graph 1. */
+void hg_opts_default(hg_opts *opts);
+
+/* 1 if a line of n samples (a row of nx or a column of ny) has a compiled
+ * transform plan, else 0. */
+int hg_supported_length(int n);
+
+/* Creates a plan for `batch` targets of ny x nx pixels on the current CUDA
+ * device.  Allocates the plan's device workspace (the field, the prepared
+ * targets, weights, twiddle tables and metric partials).  opts may be NULL
+ * (defaults).  Errors: HG_ERR_INVALID_ARG (out NULL, batch < 1, bad slm or
+ * algo, OSPR with a non-binary SLM, subframes < 1, precision != 0),
+ * HG_ERR_UNSUPPORTED_SIZE, HG_ERR_OOM, HG_ERR_CUDA. */
+hg_status hg_plan_create(hg_plan *out, int ny, int nx, int batch, hg_slm slm, hg_algo algo,
+                         const hg_opts *opts);
+
+/*
+ * Runs the algorithm on a batch (Section 3.2 / 3.4).
+ *  target      [batch][ny][nx] float, replay order, >= 0, finite, not all zero
+ *              per target.  Normalised inside to sum T^2 = 1.
+ *  init_phase  GS/WGS: [batch][ny][nx] float radians, replay order, the
+ *              starting replay phase; NULL draws U[0, 2 pi) from Philox with
+ *              counter {y*nx + x, 0, target index, 1}.  OSPR: must be NULL
+ *              (subframe n of target t uses counter {y*nx + x, n, t, 0}).
+ *  iters       GS/WGS iterations, >= 1.  OSPR: ignored.
+ *  holo_out    GS/WGS: [batch][ny][nx] uint8 level indices of the last
+ *              iteration's hologram; OSPR: [batch][subframes][ny][nx].  NULL
+ *              to skip.
+ *  mse_out     GS/WGS: [batch][iters] double, intensity MSE
+ *              mean((I - T^2)^2) of iteration k's replay (I = |R|^2 / sum|R|^2,
+ *              T normalised); OSPR: [batch] double, the MSE of the
+ *              time-averaged replay.  NULL to skip.
+ * WGS weights start at 1 unless hg_set_weights was called since the last
+ * run.  Errors: HG_ERR_INVALID_ARG (NULL target, iters < 1, OSPR with
+ * init_phase, negative / NaN / infinite target values), HG_ERR_NUMERIC
+ * (a target with zero energy), HG_ERR_OOM, HG_ERR_CUDA.  Value errors are
+ * found on the device: with device pointers they are returned by hg_sync.
+ */
+hg_status hg_run(hg_plan plan, const float *target, const float *init_phase, int iters,
+                 uint8_t *holo_out, double *mse_out);
+
+/* Per-iteration metrics of the last hg_run: [batch][iters][4] double with
+ * {intensity MSE, amplitude MSE of eq. (mse) on sqrt(I) vs T, diffraction
+ * efficiency sum_{T>0}|R|^2 / sum|R|^2, sum |R|^2}; OSPR: [batch][1][4].
+ * `count` is the number of doubles the buffer holds.  Errors:
+ * HG_ERR_INVALID_ARG (no run yet, NULL, count too small). */
+hg_status hg_get_metrics(hg_plan plan, double *out, size_t count);
+
+/* Normalised replay intensity (sums to 1, replay order) of holograms of level
+ * indices: holo [batch][ny][nx] (OSPR plans: [batch][subframes][ny][nx],
+ * time-averaged per target); intensity_out [batch][ny][nx] float. */
+hg_status hg_replay(hg_plan plan, const uint8_t *holo, float *intensity_out);
+
+/* Replay phase arg R after the last GS/WGS run (0 where R = 0), replay order,
+ * [batch][ny][nx] float radians: the state from which a run resumes. */
+hg_status hg_get_phase(hg_plan plan, float *phase_out);
+
+/* WGS weights, replay order, [batch][ny][nx] float.  hg_set_weights makes the
+ * next hg_run start from w instead of 1; hg_get_weights returns the weights
+ * after the last run's final update. */
+hg_status hg_set_weights(hg_plan plan, const float *w);
+hg_status hg_get_weights(hg_plan plan, float *w_out);
+
+/*
+ * One GS/WGS iteration with its intermediate fields, for checking:
+ *  h_out       [batch][ny][nx] complex64 (re, im) SLM-plane field
+ *              IFFT2(ifftshift(w T e^{i phase})) before quantisation
+ *  holo_out    [batch][ny][nx] uint8 level indices
+ *  replay_out  [batch][ny][nx] complex64 replay field fftshift(FFT2(e^{iH}))
+ *  metrics_out [batch][4] double as in hg_get_metrics
+ * phase_in is required; WGS uses the weights set by hg_set_weights (else 1).
+ * Any output may be NULL.
+ */
+hg_status hg_debug_step(hg_plan plan, const float *target, const float *phase_in, float *h_out,
+                        uint8_t *holo_out, float *replay_out, double *metrics_out);
+
+/* Waits for the plan's stream and reports errors found on the device since
+ * the last run started (invalid or zero-energy targets, CUDA faults). */
+hg_status hg_sync(hg_plan plan);
+
+/* Number of kernels the last hg_run / hg_replay / hg_debug_step enqueued. */
+int hg_last_launch_count(hg_plan plan);
+
+void hg_plan_destroy(hg_plan plan);
+const char *hg_status_string(hg_status st);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* HOLOGEN_H */

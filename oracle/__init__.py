@@ -64,6 +64,8 @@ def _load():
             lib.or_philox4x32_10.restype = None
             lib.or_random_phase.argtypes = [i, i, u64, u32, u32, u32, P]
             lib.or_ospr_run.argtypes = [i, i, P, i, u64, u32, P, P, P]
+            lib.or_replay_field.argtypes = [i, i, P, i, i, P]
+            lib.or_metrics.argtypes = [i, P, P, P]
             _lib = lib
     return _lib
 
@@ -199,3 +201,22 @@ def ospr_run(t_raw, nsub, seed, t_index=0):
     _ck(_load().or_ospr_run(ny, nx, _p(t), int(nsub), int(seed), int(t_index), _p(holo), _p(I_out),
                             _p(met)))
     return dict(holo=holo, I=I_out, mse=met[0], amp_mse=met[1], eff=met[2])
+
+
+def replay_field(holo, kind=SLM_BINARY, levels=2) -> np.ndarray:
+    """Replay field fftshift(FFT2(exp(iH))) (unitary, replay order) of one hologram."""
+    h = np.ascontiguousarray(holo, dtype=np.uint8)
+    ny, nx = h.shape
+    out = np.empty((ny, nx), np.complex128)
+    _ck(_load().or_replay_field(ny, nx, _p(h), int(kind), int(levels), _p(out)))
+    return out
+
+
+def metrics(R2, T):
+    """(intensity MSE, amplitude MSE, efficiency, sum |R|^2) of an unnormalised
+    replay intensity against a normalised target."""
+    r = np.ascontiguousarray(R2, dtype=np.float64)
+    t = np.ascontiguousarray(T, dtype=np.float64)
+    out = np.empty(4, np.float64)
+    _ck(_load().or_metrics(r.size, _p(r), _p(t), _p(out)))
+    return out

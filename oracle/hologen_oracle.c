@@ -533,3 +533,32 @@ int or_ospr_run(int ny, int nx, const float *t_raw, int nsub, uint64_t seed, uin
     free(T); free(ph); free(Rri); free(acc);
     return st;
 }
+
+/* ------------------------------------------------------------------------- */
+/* Helpers for checking a given hologram.                                     */
+/* ------------------------------------------------------------------------- */
+
+/* Replay field R = fftshift(FFT2(e^{iH})) (unitary, replay order) of one
+ * hologram of level indices. */
+int or_replay_field(int ny, int nx, const uint8_t *holo, int kind, int levels, double *R_out) {
+    if (ny < 1 || nx < 1 || !holo || !R_out) return OR_ERR_ARG;
+    if (!slm_ok(kind, levels) || kind == OR_SLM_CONTINUOUS) return OR_ERR_ARG;
+    size_t n = (size_t)nx * ny;
+    cplx *e = (cplx *)malloc(sizeof(cplx) * n);
+    cplx *R = (cplx *)malloc(sizeof(cplx) * n);
+    if (!e || !R) { free(e); free(R); return OR_ERR_MEM; }
+    for (size_t i = 0; i < n; ++i) e[i] = level_phasor(holo[i], kind, levels);
+    int st = replay_of(ny, nx, e, R);
+    if (st == OR_OK)
+        for (size_t i = 0; i < n; ++i) { R_out[2 * i] = creal(R[i]); R_out[2 * i + 1] = cimag(R[i]); }
+    free(e); free(R);
+    return st;
+}
+
+/* metrics[4] (as in or_gs_step) of an unnormalised replay intensity R2 against
+ * a normalised target T. */
+int or_metrics(int n, const double *R2, const double *T, double *metrics_out) {
+    if (n < 1 || !R2 || !T || !metrics_out) return OR_ERR_ARG;
+    metrics_of((size_t)n, R2, T, metrics_out);
+    return OR_OK;
+}

@@ -1,0 +1,767 @@
+// hg_api.cu -- the C ABI of include/hologen.h: plans, workspace, the launch
+// sequence of a run, and the small non-transform kernels (target preparation,
+// metric reduction, weight fill).
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <mutex>
+#include <new>
+
+#include "hg_kernels.cuh"
+#include "hologen.h"
+
+using namespace hg;
+
+// ------------------------------------------------------------------ kernels
+
+namespace {
+
+enum ErrBits : unsigned { ERR_BAD_VALUE = 1u, ERR_ZERO_ENERGY = 2u };
+
+constexpr int PREP_THREADS = 256;
+constexpr int PREP_BLOCKS = 64;  // per target
+
+// Partial sums of T^2 per (target, block) in double, fixed order; flags
+// negative, NaN and infinite values.
+__global__ void __launch_bounds__(PREP_THREADS)
+k_prep_sum(const float *__restrict__ t_raw, int npx, double *part, unsigned *err) {
+    __shared__ double red[PREP_THREADS / 32];
+    const int b = blockIdx.y;
+    const float *tb = t_raw + (size_t)b * npx;
+    double s = 0;
+    bool bad = false;
+    for (int i = blockIdx.x * PREP_THREADS + threadIdx.x; i < npx; i += PREP_BLOCKS * PREP_THREADS) {
+        const float v = tb[i];
+        if (!(v >= 0.f) || isinf(v)) bad = true;
+        s += (double)v * (double)v;
+    }
+    if (bad) atomicOr(err, ERR_BAD_VALUE);
+    for (int off = 16; off; off >>= 1) s += __shfl_down_sync(0xffffffffu, s, off);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double tot = 0;
+        for (int w = 0; w < PREP_THREADS / 32; ++w) tot += red[w];
+        part[(size_t)b * PREP_BLOCKS + blockIdx.x] = tot;
+    }
+}
+
+// scale[b] = 1 / sqrt(sum T^2) (0 and a flag for an all-zero target).
+__global__ void k_prep_scale(const double *part, int batch, double *scale, unsigned *err) {
+    const int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= batch) return;
+    double s = 0;
+    for (int i = 0; i < PREP_BLOCKS; ++i) s += part[(size_t)b * PREP_BLOCKS + i];
+    if (s > 0) {
+        scale[b] = 1.0 / sqrt(s);
+    } else {
+        scale[b] = 0;
+        atomicOr(err, ERR_ZERO_ENERGY);
+    }
+}
+
+// Prepared target in DFT order: Tf[b][y][x] = T[b][(y+ny/2)%ny][(x+nx/2)%nx] * scale[b],
+// rounded to float with the support T > 0 preserved.
+__global__ void k_prep_apply(const float *__restrict__ t_raw, int ny, int nx, int batch,
+                             const double *scale, float *__restrict__ tf) {
+    const size_t npx = (size_t)ny * nx, total = npx * batch;
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < total;
+         i += (size_t)gridDim.x * blockDim.x) {
+        const int b = (int)(i / npx);
+        const int rem = (int)(i - (size_t)b * npx);
+        const int y = rem / nx, x = rem - y * nx;
+        const int iy = (y + ny / 2) % ny, ix = (x + nx / 2) % nx;
+        const float v = t_raw[(size_t)b * npx + (size_t)iy * nx + ix];
+        float tv = (float)((double)v * scale[b]);
+        // keep the support {T > 0} of the input exactly: a positive value whose
+        // scaled float underflows becomes the smallest positive float
+        if (v > 0.f && !(tv > 0.f)) tv = __int_as_float(1);
+        tf[i] = tv;
+    }
+}
+
+// DFT-order <-> replay-order copies of a real [batch][ny][nx] array.
+// to_dft: dst[y][x] = src[(y+ny/2)%ny][(x+nx/2)%nx]; else the inverse map.
+__global__ void k_reorder(const float *__restrict__ src, float *__restrict__ dst, int ny, int nx,
+                          int batch, int to_dft) {
+    const size_t npx = (size_t)ny * nx, total = npx * batch;
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < total;
+         i += (size_t)gridDim.x * blockDim.x) {
+        const int b = (int)(i / npx);
+        const int rem = (int)(i - (size_t)b * npx);
+        const int y = rem / nx, x = rem - y * nx;
+        const size_t r = (size_t)b * npx + (size_t)((y + ny / 2) % ny) * nx + (x + nx / 2) % nx;
+        if (to_dft) dst[i] = src[r];
+        else dst[r] = src[i];
+    }
+}
+
+__global__ void k_fill(float *p, size_t n, float v) {
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n;
+         i += (size_t)gridDim.x * blockDim.x)
+        p[i] = v;
+}
+
+// metrics[b][k][4] from the per-panel partials part[k][b][panel][4]:
+// {sum d^2 / N, sum a^2 / N, in / total, total}; also mse_out[b][k].
+__global__ void k_reduce(const double *part, int iters, int batch, int panels, double invN,
+                         double *metrics, double *mse_out) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= iters * batch) return;
+    const int k = i / batch, b = i - k * batch;
+    const double *p = part + ((size_t)k * batch + b) * panels * NMET;
+    double s[NMET] = {0, 0, 0, 0};
+    for (int q = 0; q < panels; ++q)
+        for (int m = 0; m < NMET; ++m) s[m] += p[(size_t)q * NMET + m];
+    double *o = metrics + ((size_t)b * iters + k) * NMET;
+    o[0] = s[0] * invN;
+    o[1] = s[1] * invN;
+    o[2] = s[3] > 0 ? s[2] / s[3] : 0.0;
+    o[3] = s[3];
+    if (mse_out) mse_out[(size_t)b * iters + k] = o[0];
+}
+
+// ------------------------------------------------------------ registry
+
+const LineOps *find_ops(int n) {
+    const LineOps *o = ops_small(n);
+    if (!o) o = ops_mid(n);
+    if (!o) o = ops_1024(n);
+    if (!o) o = ops_2048(n);
+    if (!o) o = ops_hd(n);
+    return o;
+}
+
+std::mutex g_init_mu;
+constexpr int kMaxDev = 64;
+constexpr int kMaxOps = 64;
+const LineOps *g_inited[kMaxDev][kMaxOps];
+
+// Per-device one-time kernel attributes for a line length.
+cudaError_t ensure_init(int dev, const LineOps *o) {
+    std::lock_guard<std::mutex> lk(g_init_mu);
+    if (dev < 0 || dev >= kMaxDev) return cudaErrorInvalidDevice;
+    for (int i = 0; i < kMaxOps; ++i) {
+        if (g_inited[dev][i] == o) return cudaSuccess;
+        if (!g_inited[dev][i]) {
+            cudaError_t e = o->init(const_cast<LineOps *>(o));
+            if (e == cudaSuccess) g_inited[dev][i] = o;
+            return e;
+        }
+    }
+    return cudaErrorUnknown;
+}
+
+}  // namespace
+
+// ------------------------------------------------------------------ plan
+
+struct hg_plan_s {
+    int dev = 0, ny = 0, nx = 0, batch = 0, algo = 0, kind = 0, levels = 2, nsub = 1;
+    uint64_t seed = 0;
+    cudaStream_t stream = nullptr;     // user stream (may be the legacy default)
+    cudaStream_t cap_stream = nullptr; // private stream used only for graph capture
+    int use_graph = 1;
+    const LineOps *rops = nullptr, *cops = nullptr;
+    int nsm = 0, row_grid = 0, col_grid = 0, head_grid = 0, ppt = 0;
+    size_t npx = 0;
+    int nchains = 0;
+    float2 *field = nullptr;
+    float *tf = nullptr, *w = nullptr;
+    double *part = nullptr;
+    int part_iters = 0;
+    double *metrics = nullptr;
+    int metrics_iters = 0;
+    double *sum_part = nullptr, *scale = nullptr;
+    unsigned *err = nullptr;
+    float2 *twx = nullptr, *twy = nullptr, *lvl = nullptr;
+    void *stage = nullptr;
+    size_t stage_bytes = 0;
+    bool weights_preset = false, have_run = false;
+    bool field_from_run = false;  // field holds the last GS/WGS run's final column pass
+    int last_iters = 0, launches = 0;
+    cudaGraphExec_t gexec = nullptr;
+    int g_iters = -1;
+    double *g_part = nullptr;
+};
+
+namespace {
+
+#define HG_CK(x)                                   \
+    do {                                           \
+        cudaError_t e_ = (x);                      \
+        if (e_ != cudaSuccess) return map_err(e_); \
+    } while (0)
+
+hg_status map_err(cudaError_t e) {
+    if (e == cudaSuccess) return HG_OK;
+    if (e == cudaErrorMemoryAllocation) return HG_ERR_OOM;
+    return HG_ERR_CUDA;
+}
+
+// Forward roots W_n^e = exp(-2 pi i e / n), e < n: angle reduced as an exact
+// integer ratio, evaluated in long double, rounded to float.
+hg_status make_twiddles(int n, float2 **out) {
+    float2 *h = (float2 *)malloc(sizeof(float2) * n);
+    if (!h) return HG_ERR_OOM;
+    const long double two_pi = 6.283185307179586476925286766559005768L;
+    for (int e = 0; e < n; ++e) {
+        long double a = two_pi * (long double)e / (long double)n;
+        h[e] = make_float2((float)cosl(a), (float)-sinl(a));
+    }
+    cudaError_t ce = cudaMalloc(out, sizeof(float2) * n);
+    if (ce == cudaSuccess) ce = cudaMemcpy(*out, h, sizeof(float2) * n, cudaMemcpyHostToDevice);
+    free(h);
+    return map_err(ce);
+}
+
+bool is_device_ptr(const void *p) {
+    cudaPointerAttributes at;
+    if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+}
+
+hg_status ensure_stage(hg_plan p, size_t bytes) {
+    if (p->stage_bytes >= bytes) return HG_OK;
+    if (p->stage) cudaFree(p->stage);
+    p->stage = nullptr;
+    p->stage_bytes = 0;
+    HG_CK(cudaMalloc(&p->stage, bytes));
+    p->stage_bytes = bytes;
+    return HG_OK;
+}
+
+hg_status ensure_part(hg_plan p, int iters) {
+    if (p->part_iters >= iters) return HG_OK;
+    if (p->part) cudaFree(p->part);
+    p->part = nullptr;
+    p->part_iters = 0;
+    HG_CK(cudaMalloc(&p->part, sizeof(double) * NMET * (size_t)iters * p->batch * p->ppt));
+    p->part_iters = iters;
+    return HG_OK;
+}
+
+hg_status ensure_metrics(hg_plan p, int iters) {
+    if (p->metrics_iters >= iters) return HG_OK;
+    if (p->metrics) cudaFree(p->metrics);
+    p->metrics = nullptr;
+    p->metrics_iters = 0;
+    HG_CK(cudaMalloc(&p->metrics, sizeof(double) * NMET * (size_t)iters * p->batch));
+    p->metrics_iters = iters;
+    return HG_OK;
+}
+
+RowArgs row_args(hg_plan p) {
+    RowArgs a{};
+    a.ny = p->ny;
+    a.nx = p->nx;
+    a.items = p->batch;
+    a.nsub = 1;
+    a.field = p->field;
+    a.T = p->tf;
+    a.w = p->w;
+    a.seed_lo = (uint32_t)p->seed;
+    a.seed_hi = (uint32_t)(p->seed >> 32);
+    a.stream_id = 1;
+    a.tw = p->twx;
+    const double N = (double)p->npx;
+    a.invN = (float)(1.0 / N);
+    a.invN2 = (float)(1.0 / (N * N));
+    a.NN = (float)N;
+    a.invSqrtN = (float)(1.0 / std::sqrt(N));
+    return a;
+}
+
+ColArgs col_args(hg_plan p) {
+    ColArgs a{};
+    a.ny = p->ny;
+    a.nx = p->nx;
+    a.items = p->batch;
+    a.field = p->field;
+    a.lvl = p->lvl;
+    a.levels = p->levels;
+    a.qscale = (float)((double)p->levels / 6.283185307179586476925286766559005768);
+    a.tw = p->twy;
+    a.invSqrtN = (float)(1.0 / std::sqrt((double)p->npx));
+    return a;
+}
+
+int grid_for(int blocks_per_sm, int nsm, long work) {
+    long g = (long)blocks_per_sm * nsm;
+    if (g > work) g = work;
+    return g < 1 ? 1 : (int)g;
+}
+
+void launch_row(hg_plan p, int role, const RowArgs &a, cudaStream_t s) {
+    const long work = (long)a.items * p->ppt;
+    p->rops->row(role, a, grid_for(p->rops->row_blocks_per_sm, p->nsm, work), s);
+    p->launches++;
+}
+
+void launch_col(hg_plan p, int role, const ColArgs &a, cudaStream_t s) {
+    const long work = (long)a.items * ((p->nx + p->cops->col_c - 1) / p->cops->col_c);
+    p->cops->col(role, a, grid_for(p->cops->col_blocks_per_sm, p->nsm, work), s);
+    p->launches++;
+}
+
+int ew_grid(hg_plan p, size_t n) {
+    size_t g = (n + 255) / 256;
+    size_t cap = (size_t)p->nsm * 8;
+    return (int)(g < cap ? (g < 1 ? 1 : g) : cap);
+}
+
+// Target preparation (normalise to sum T^2 = 1, move to DFT order).
+void enqueue_prep(hg_plan p, const float *target) {
+    dim3 g(PREP_BLOCKS, p->batch);
+    k_prep_sum<<<g, PREP_THREADS, 0, p->stream>>>(target, (int)p->npx, p->sum_part, p->err);
+    k_prep_scale<<<(p->batch + 127) / 128, 128, 0, p->stream>>>(p->sum_part, p->batch, p->scale,
+                                                                 p->err);
+    k_prep_apply<<<ew_grid(p, p->npx * p->batch), 256, 0, p->stream>>>(
+        target, p->ny, p->nx, p->batch, p->scale, p->tf);
+    p->launches += 3;
+}
+
+int col_role_gs(hg_plan p) { return p->kind == HG_SLM_BINARY ? COL_GS_BIN : COL_GS_LVL; }
+int col_role_holo(hg_plan p) { return p->kind == HG_SLM_BINARY ? COL_HOLO_BIN : COL_HOLO_LVL; }
+
+// The middle of a GS run: for k = 0 .. iters-2, column pass k then row pass
+// k (metrics of iteration k, constraint for iteration k+1).
+void enqueue_loop(hg_plan p, int iters, cudaStream_t s) {
+    ColArgs ca = col_args(p);
+    RowArgs ra = row_args(p);
+    for (int k = 0; k + 1 < iters; ++k) {
+        launch_col(p, col_role_gs(p), ca, s);
+        ra.part = p->part + (size_t)k * p->batch * p->ppt * NMET;
+        launch_row(p, ROW_ITER, ra, s);
+    }
+}
+
+hg_status run_loop(hg_plan p, int iters) {
+    if (iters <= 1) return HG_OK;
+    if (!p->use_graph) {
+        enqueue_loop(p, iters, p->stream);
+        return map_err(cudaGetLastError());
+    }
+    if (!p->gexec || p->g_iters != iters || p->g_part != p->part) {
+        if (p->gexec) cudaGraphExecDestroy(p->gexec);
+        p->gexec = nullptr;
+        cudaGraph_t g = nullptr;
+        HG_CK(cudaStreamBeginCapture(p->cap_stream, cudaStreamCaptureModeThreadLocal));
+        const int before = p->launches;
+        enqueue_loop(p, iters, p->cap_stream);
+        p->launches = before;
+        cudaError_t e = cudaStreamEndCapture(p->cap_stream, &g);
+        if (e != cudaSuccess) return map_err(e);
+        e = cudaGraphInstantiate(&p->gexec, g, 0);
+        cudaGraphDestroy(g);
+        if (e != cudaSuccess) {
+            p->gexec = nullptr;
+            return map_err(e);
+        }
+        p->g_iters = iters;
+        p->g_part = p->part;
+    }
+    HG_CK(cudaGraphLaunch(p->gexec, p->stream));
+    p->launches += 2 * (iters - 1);
+    return HG_OK;
+}
+
+hg_status check_err_flag(hg_plan p) {
+    unsigned e = 0;
+    HG_CK(cudaMemcpyAsync(&e, p->err, sizeof(unsigned), cudaMemcpyDeviceToHost, p->stream));
+    HG_CK(cudaStreamSynchronize(p->stream));
+    if (e & ERR_BAD_VALUE) return HG_ERR_INVALID_ARG;
+    if (e & ERR_ZERO_ENERGY) return HG_ERR_NUMERIC;
+    return HG_OK;
+}
+
+struct DevGuard {
+    int prev = -1;
+    explicit DevGuard(int dev) {
+        if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+        if (prev != dev) cudaSetDevice(dev);
+    }
+    ~DevGuard() {
+        int cur = -1;
+        if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
+    }
+};
+
+}  // namespace
+
+// ------------------------------------------------------------------- ABI
+
+extern "C" {
+
+void hg_opts_default(hg_opts *o) {
+    if (!o) return;
+    memset(o, 0, sizeof *o);
+    o->subframes = 24;
+    o->use_graph = 1;
+}
+
+int hg_supported_length(int n) { return find_ops(n) != nullptr; }
+
+const char *hg_status_string(hg_status st) {
+    switch (st) {
+        case HG_OK: return "ok";
+        case HG_ERR_INVALID_ARG: return "invalid argument";
+        case HG_ERR_UNSUPPORTED_SIZE: return "unsupported size";
+        case HG_ERR_OOM: return "out of device memory";
+        case HG_ERR_CUDA: return "CUDA error";
+        case HG_ERR_TIMEOUT: return "device wait timed out";
+        case HG_ERR_NUMERIC: return "target has zero energy";
+        default: return "unknown status";
+    }
+}
+
+void hg_plan_destroy(hg_plan p) {
+    if (!p) return;
+    DevGuard g(p->dev);
+    if (p->stream || p->cap_stream) cudaStreamSynchronize(p->stream);
+    if (p->gexec) cudaGraphExecDestroy(p->gexec);
+    if (p->cap_stream) cudaStreamDestroy(p->cap_stream);
+    void *bufs[] = {p->field, p->tf, p->w, p->part, p->metrics, p->sum_part, p->scale,
+                    p->err, p->twx, p->twy, p->lvl, p->stage};
+    for (void *b : bufs)
+        if (b) cudaFree(b);
+    delete p;
+}
+
+hg_status hg_plan_create(hg_plan *out, int ny, int nx, int batch, hg_slm slm, hg_algo algo,
+                         const hg_opts *opts) {
+    if (!out) return HG_ERR_INVALID_ARG;
+    *out = nullptr;
+    hg_opts o;
+    hg_opts_default(&o);
+    if (opts) o = *opts;
+    if (batch < 1 || ny < 1 || nx < 1) return HG_ERR_INVALID_ARG;
+    if (algo != HG_GS && algo != HG_WGS && algo != HG_OSPR) return HG_ERR_INVALID_ARG;
+    if (slm.kind != HG_SLM_BINARY && slm.kind != HG_SLM_LLEVEL) return HG_ERR_INVALID_ARG;
+    if (slm.kind == HG_SLM_LLEVEL && (slm.levels < 2 || slm.levels > 256)) return HG_ERR_INVALID_ARG;
+    if (algo == HG_OSPR && (slm.kind != HG_SLM_BINARY || o.subframes < 1)) return HG_ERR_INVALID_ARG;
+    if (o.precision != 0) return HG_ERR_INVALID_ARG;
+    const LineOps *rops = find_ops(nx), *cops = find_ops(ny);
+    if (!rops || !cops) return HG_ERR_UNSUPPORTED_SIZE;
+    const size_t npx = (size_t)ny * nx;
+    const int nsub = algo == HG_OSPR ? o.subframes : 1;
+    if ((double)npx * batch * nsub > 2.0e9 || (double)batch * nsub > 1e6)
+        return HG_ERR_INVALID_ARG;
+
+    hg_plan p = new (std::nothrow) hg_plan_s();
+    if (!p) return HG_ERR_OOM;
+    if (cudaGetDevice(&p->dev) != cudaSuccess) {
+        delete p;
+        return HG_ERR_CUDA;
+    }
+    p->ny = ny;
+    p->nx = nx;
+    p->batch = batch;
+    p->algo = algo;
+    p->kind = slm.kind;
+    p->levels = slm.kind == HG_SLM_BINARY ? 2 : slm.levels;
+    p->nsub = nsub;
+    p->nchains = batch * nsub;
+    p->seed = o.seed;
+    p->stream = (cudaStream_t)o.stream;
+    p->use_graph = o.use_graph ? 1 : 0;
+    p->rops = rops;
+    p->cops = cops;
+    p->npx = npx;
+    p->ppt = (ny + rops->row_lines - 1) / rops->row_lines;
+
+    hg_status st = HG_OK;
+    auto fail = [&](hg_status s) {
+        hg_plan_destroy(p);
+        return s;
+    };
+    cudaError_t ce = ensure_init(p->dev, rops);
+    if (ce == cudaSuccess) ce = ensure_init(p->dev, cops);
+    if (ce == cudaSuccess) ce = cudaDeviceGetAttribute(&p->nsm, cudaDevAttrMultiProcessorCount, p->dev);
+    if (ce == cudaSuccess) ce = cudaStreamCreateWithFlags(&p->cap_stream, cudaStreamNonBlocking);
+    if (ce != cudaSuccess) return fail(map_err(ce));
+    ce = cudaMalloc(&p->field, sizeof(float2) * npx * p->nchains);
+    if (ce == cudaSuccess) ce = cudaMalloc(&p->tf, sizeof(float) * npx * batch);
+    if (ce == cudaSuccess && algo == HG_WGS) ce = cudaMalloc(&p->w, sizeof(float) * npx * batch);
+    if (ce == cudaSuccess) ce = cudaMalloc(&p->sum_part, sizeof(double) * PREP_BLOCKS * batch);
+    if (ce == cudaSuccess) ce = cudaMalloc(&p->scale, sizeof(double) * batch);
+    if (ce == cudaSuccess) ce = cudaMalloc(&p->err, sizeof(unsigned));
+    if (ce == cudaSuccess) ce = cudaMemset(p->err, 0, sizeof(unsigned));
+    if (ce != cudaSuccess) return fail(map_err(ce));
+    if ((st = make_twiddles(nx, &p->twx)) != HG_OK) return fail(st);
+    if ((st = make_twiddles(ny, &p->twy)) != HG_OK) return fail(st);
+    {
+        // SLM level phasors exp(2 pi i q / L), q < L
+        const int L = p->levels;
+        float2 h[256];
+        const long double two_pi = 6.283185307179586476925286766559005768L;
+        for (int q = 0; q < L; ++q) {
+            long double a = two_pi * (long double)q / (long double)L;
+            h[q] = make_float2((float)cosl(a), (float)sinl(a));
+        }
+        ce = cudaMalloc(&p->lvl, sizeof(float2) * L);
+        if (ce == cudaSuccess) ce = cudaMemcpy(p->lvl, h, sizeof(float2) * L, cudaMemcpyHostToDevice);
+        if (ce != cudaSuccess) return fail(map_err(ce));
+    }
+    if ((st = ensure_part(p, algo == HG_OSPR ? 1 : 8)) != HG_OK) return fail(st);
+    if ((st = ensure_metrics(p, 1)) != HG_OK) return fail(st);
+    *out = p;
+    return HG_OK;
+}
+
+hg_status hg_sync(hg_plan p) {
+    if (!p) return HG_ERR_INVALID_ARG;
+    DevGuard g(p->dev);
+    HG_CK(cudaStreamSynchronize(p->stream));
+    HG_CK(cudaGetLastError());
+    return check_err_flag(p);
+}
+
+int hg_last_launch_count(hg_plan p) { return p ? p->launches : 0; }
+
+hg_status hg_run(hg_plan p, const float *target, const float *init_phase, int iters,
+                 uint8_t *holo_out, double *mse_out) {
+    if (!p || !target) return HG_ERR_INVALID_ARG;
+    if (p->algo == HG_OSPR) {
+        if (init_phase) return HG_ERR_INVALID_ARG;
+        iters = 1;
+    } else if (iters < 1) {
+        return HG_ERR_INVALID_ARG;
+    }
+    DevGuard g(p->dev);
+    p->launches = 0;
+    const size_t fbytes = sizeof(float) * p->npx * p->batch;
+    const size_t hbytes = p->npx * p->nchains;
+    const size_t mbytes = sizeof(double) * p->batch * (p->algo == HG_OSPR ? 1 : iters);
+    const bool t_host = !is_device_ptr(target);
+    const bool ph_host = init_phase && !is_device_ptr(init_phase);
+    const bool ho_host = holo_out && !is_device_ptr(holo_out);
+    const bool mo_host = mse_out && !is_device_ptr(mse_out);
+    const bool any_host = t_host || ph_host || ho_host || mo_host;
+    hg_status st;
+    if (any_host) {
+        // layout: [target][phase][holo][mse], 256-byte aligned pieces
+        auto al = [](size_t n) { return (n + 255) & ~(size_t)255; };
+        if ((st = ensure_stage(p, al(fbytes) * 2 + al(hbytes) + al(mbytes))) != HG_OK) return st;
+    }
+    char *sb = (char *)p->stage;
+    auto al = [](size_t n) { return (n + 255) & ~(size_t)255; };
+    const float *d_t = target, *d_ph = init_phase;
+    uint8_t *d_ho = holo_out;
+    double *d_mo = mse_out;
+    if (t_host) {
+        HG_CK(cudaMemcpyAsync(sb, target, fbytes, cudaMemcpyHostToDevice, p->stream));
+        d_t = (const float *)sb;
+    }
+    if (ph_host) {
+        HG_CK(cudaMemcpyAsync(sb + al(fbytes), init_phase, fbytes, cudaMemcpyHostToDevice, p->stream));
+        d_ph = (const float *)(sb + al(fbytes));
+    }
+    if (ho_host) d_ho = (uint8_t *)(sb + 2 * al(fbytes));
+    if (mo_host) d_mo = (double *)(sb + 2 * al(fbytes) + al(hbytes));
+
+    if ((st = ensure_part(p, iters)) != HG_OK) return st;
+    if ((st = ensure_metrics(p, iters)) != HG_OK) return st;
+    HG_CK(cudaMemsetAsync(p->err, 0, sizeof(unsigned), p->stream));
+    enqueue_prep(p, d_t);
+
+    RowArgs ra = row_args(p);
+    ColArgs ca = col_args(p);
+    if (p->algo == HG_OSPR) {
+        ra.items = p->nchains;
+        ra.nsub = p->nsub;
+        ra.phase = nullptr;
+        ra.stream_id = 0;
+        launch_row(p, ROW_HEAD, ra, p->stream);
+        ca.items = p->nchains;
+        ca.holo = d_ho;
+        launch_col(p, COL_GS_BIN, ca, p->stream);
+        RowArgs rt = row_args(p);
+        rt.nsub = p->nsub;
+        rt.part = p->part;
+        launch_row(p, ROW_AVG, rt, p->stream);
+    } else {
+        if (p->algo == HG_WGS && !p->weights_preset) {
+            k_fill<<<ew_grid(p, p->npx * p->batch), 256, 0, p->stream>>>(p->w, p->npx * p->batch, 1.f);
+            p->launches++;
+        }
+        ra.phase = d_ph;
+        launch_row(p, ROW_HEAD, ra, p->stream);
+        if ((st = run_loop(p, iters)) != HG_OK) return st;
+        ca.holo = d_ho;
+        launch_col(p, col_role_gs(p), ca, p->stream);
+        RowArgs rt = row_args(p);
+        rt.part = p->part + (size_t)(iters - 1) * p->batch * p->ppt * NMET;
+        launch_row(p, ROW_TAIL, rt, p->stream);
+    }
+    k_reduce<<<(iters * p->batch + 127) / 128, 128, 0, p->stream>>>(
+        p->part, iters, p->batch, p->ppt, 1.0 / (double)p->npx, p->metrics, d_mo);
+    p->launches++;
+    HG_CK(cudaGetLastError());
+    p->weights_preset = false;
+    p->have_run = true;
+    p->field_from_run = p->algo != HG_OSPR;
+    p->last_iters = iters;
+    if (ho_host)
+        HG_CK(cudaMemcpyAsync(holo_out, d_ho, hbytes, cudaMemcpyDeviceToHost, p->stream));
+    if (mo_host) HG_CK(cudaMemcpyAsync(mse_out, d_mo, mbytes, cudaMemcpyDeviceToHost, p->stream));
+    if (any_host) return hg_sync(p);
+    return HG_OK;
+}
+
+hg_status hg_get_metrics(hg_plan p, double *out, size_t count) {
+    if (!p || !out || !p->have_run) return HG_ERR_INVALID_ARG;
+    const size_t n = (size_t)p->batch * p->last_iters * NMET;
+    if (count < n) return HG_ERR_INVALID_ARG;
+    DevGuard g(p->dev);
+    HG_CK(cudaMemcpyAsync(out, p->metrics, n * sizeof(double), cudaMemcpyDefault, p->stream));
+    if (!is_device_ptr(out)) HG_CK(cudaStreamSynchronize(p->stream));
+    return HG_OK;
+}
+
+hg_status hg_replay(hg_plan p, const uint8_t *holo, float *intensity_out) {
+    if (!p || !holo || !intensity_out) return HG_ERR_INVALID_ARG;
+    DevGuard g(p->dev);
+    p->launches = 0;
+    const size_t hbytes = p->npx * p->nchains, ibytes = sizeof(float) * p->npx * p->batch;
+    const bool h_host = !is_device_ptr(holo), i_host = !is_device_ptr(intensity_out);
+    hg_status st;
+    if (h_host || i_host)
+        if ((st = ensure_stage(p, hbytes + 256 + ibytes)) != HG_OK) return st;
+    const uint8_t *d_h = holo;
+    float *d_i = intensity_out;
+    if (h_host) {
+        HG_CK(cudaMemcpyAsync(p->stage, holo, hbytes, cudaMemcpyHostToDevice, p->stream));
+        d_h = (const uint8_t *)p->stage;
+    }
+    if (i_host) d_i = (float *)((char *)p->stage + ((hbytes + 255) & ~(size_t)255));
+    p->field_from_run = false;
+    ColArgs ca = col_args(p);
+    ca.items = p->nchains;
+    ca.holo = const_cast<uint8_t *>(d_h);
+    launch_col(p, col_role_holo(p), ca, p->stream);
+    RowArgs ra = row_args(p);
+    ra.nsub = p->nsub;
+    ra.T = nullptr;
+    ra.w = nullptr;
+    ra.I_out = d_i;
+    launch_row(p, ROW_AVG, ra, p->stream);
+    HG_CK(cudaGetLastError());
+    if (i_host) {
+        HG_CK(cudaMemcpyAsync(intensity_out, d_i, ibytes, cudaMemcpyDeviceToHost, p->stream));
+        HG_CK(cudaStreamSynchronize(p->stream));
+    }
+    return HG_OK;
+}
+
+hg_status hg_get_phase(hg_plan p, float *phase_out) {
+    if (!p || !phase_out || !p->field_from_run || p->algo == HG_OSPR) return HG_ERR_INVALID_ARG;
+    DevGuard g(p->dev);
+    p->launches = 0;
+    // Recompute arg R of the last replay field (still in the field buffer
+    // after the tail, which does not modify it) without touching metrics.
+    const size_t bytes = sizeof(float) * p->npx * p->batch;
+    const bool host = !is_device_ptr(phase_out);
+    hg_status st;
+    if (host && (st = ensure_stage(p, bytes)) != HG_OK) return st;
+    float *d = host ? (float *)p->stage : phase_out;
+    RowArgs ra = row_args(p);
+    ra.w = nullptr;  // no weight update
+    ra.phase_out = d;
+    launch_row(p, ROW_TAIL, ra, p->stream);
+    HG_CK(cudaGetLastError());
+    if (host) {
+        HG_CK(cudaMemcpyAsync(phase_out, d, bytes, cudaMemcpyDeviceToHost, p->stream));
+        HG_CK(cudaStreamSynchronize(p->stream));
+    }
+    return HG_OK;
+}
+
+hg_status hg_set_weights(hg_plan p, const float *w) {
+    if (!p || !w || p->algo != HG_WGS) return HG_ERR_INVALID_ARG;
+    DevGuard g(p->dev);
+    const size_t bytes = sizeof(float) * p->npx * p->batch;
+    const float *src = w;
+    hg_status st;
+    if (!is_device_ptr(w)) {
+        if ((st = ensure_stage(p, bytes)) != HG_OK) return st;
+        HG_CK(cudaMemcpyAsync(p->stage, w, bytes, cudaMemcpyHostToDevice, p->stream));
+        src = (const float *)p->stage;
+    }
+    k_reorder<<<ew_grid(p, p->npx * p->batch), 256, 0, p->stream>>>(src, p->w, p->ny, p->nx,
+                                                                     p->batch, 1);
+    HG_CK(cudaGetLastError());
+    p->weights_preset = true;
+    if (src != w) HG_CK(cudaStreamSynchronize(p->stream));
+    return HG_OK;
+}
+
+hg_status hg_get_weights(hg_plan p, float *w_out) {
+    if (!p || !w_out || p->algo != HG_WGS) return HG_ERR_INVALID_ARG;
+    DevGuard g(p->dev);
+    const size_t bytes = sizeof(float) * p->npx * p->batch;
+    const bool host = !is_device_ptr(w_out);
+    hg_status st;
+    if (host && (st = ensure_stage(p, bytes)) != HG_OK) return st;
+    float *d = host ? (float *)p->stage : w_out;
+    k_reorder<<<ew_grid(p, p->npx * p->batch), 256, 0, p->stream>>>(p->w, d, p->ny, p->nx,
+                                                                     p->batch, 0);
+    HG_CK(cudaGetLastError());
+    if (host) {
+        HG_CK(cudaMemcpyAsync(w_out, d, bytes, cudaMemcpyDeviceToHost, p->stream));
+        HG_CK(cudaStreamSynchronize(p->stream));
+    }
+    return HG_OK;
+}
+
+hg_status hg_debug_step(hg_plan p, const float *target, const float *phase_in, float *h_out,
+                        uint8_t *holo_out, float *replay_out, double *metrics_out) {
+    if (!p || !target || !phase_in || p->algo == HG_OSPR) return HG_ERR_INVALID_ARG;
+    for (const void *q : {(const void *)target, (const void *)phase_in, (const void *)h_out,
+                          (const void *)holo_out, (const void *)replay_out,
+                          (const void *)metrics_out})
+        if (q && !is_device_ptr(q)) return HG_ERR_INVALID_ARG;  // device buffers only
+    DevGuard g(p->dev);
+    p->launches = 0;
+    hg_status st;
+    if ((st = ensure_part(p, 1)) != HG_OK) return st;
+    if ((st = ensure_metrics(p, 1)) != HG_OK) return st;
+    HG_CK(cudaMemsetAsync(p->err, 0, sizeof(unsigned), p->stream));
+    enqueue_prep(p, target);
+    if (p->algo == HG_WGS && !p->weights_preset) {
+        k_fill<<<ew_grid(p, p->npx * p->batch), 256, 0, p->stream>>>(p->w, p->npx * p->batch, 1.f);
+        p->launches++;
+    }
+    RowArgs ra = row_args(p);
+    ra.phase = phase_in;
+    launch_row(p, ROW_HEAD, ra, p->stream);
+    ColArgs ca = col_args(p);
+    ca.holo = holo_out;
+    ca.h_out = (float2 *)h_out;
+    launch_col(p, col_role_gs(p), ca, p->stream);
+    RowArgs rt = row_args(p);
+    rt.part = p->part;
+    rt.R_out = (float2 *)replay_out;
+    launch_row(p, ROW_TAIL, rt, p->stream);
+    k_reduce<<<(p->batch + 127) / 128, 128, 0, p->stream>>>(p->part, 1, p->batch, p->ppt,
+                                                             1.0 / (double)p->npx, p->metrics,
+                                                             nullptr);
+    p->launches++;
+    if (metrics_out)
+        HG_CK(cudaMemcpyAsync(metrics_out, p->metrics, sizeof(double) * NMET * p->batch,
+                              cudaMemcpyDeviceToDevice, p->stream));
+    HG_CK(cudaGetLastError());
+    p->weights_preset = false;
+    p->have_run = true;
+    p->field_from_run = true;
+    p->last_iters = 1;
+    return HG_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,208 @@
+"""ctypes binding of libhologen.so (include/hologen.h), argument marshalling only.
+
+The functions carry the C names and take torch tensors (CUDA or CPU; CPU
+tensors are host buffers the library copies through its own device
+workspace) or None for optional outputs.  Every step of the computation runs
+in the library's CUDA kernels; there is no other code path: if the library
+is missing this module raises instead of computing anything.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import torch
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libhologen.so")
+
+HG_SLM_BINARY, HG_SLM_LLEVEL = 0, 1
+HG_GS, HG_WGS, HG_OSPR = 0, 1, 2
+NMET = 4
+
+STATUS = {0: "HG_OK", 1: "HG_ERR_INVALID_ARG", 2: "HG_ERR_UNSUPPORTED_SIZE", 3: "HG_ERR_OOM",
+          4: "HG_ERR_CUDA", 5: "HG_ERR_TIMEOUT", 6: "HG_ERR_NUMERIC"}
+
+
+class HgError(RuntimeError):
+    def __init__(self, status: int, where: str):
+        self.status = status
+        super().__init__("%s failed: %s (%d)" % (where, STATUS.get(status, "?"), status))
+
+
+class hg_opts(ctypes.Structure):
+    _fields_ = [("stream", ctypes.c_void_p), ("seed", ctypes.c_uint64), ("subframes", ctypes.c_int),
+                ("precision", ctypes.c_int), ("use_graph", ctypes.c_int)]
+
+
+class hg_slm(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int), ("levels", ctypes.c_int)]
+
+
+_lib = None
+
+
+def lib():
+    """Load libhologen.so; raises if it has not been built."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError("libhologen.so is not built (run paper_2008_12214_gb300.build.build())")
+        L = ctypes.CDLL(LIB_PATH)
+        P, I, Z = ctypes.c_void_p, ctypes.c_int, ctypes.c_size_t
+        L.hg_opts_default.argtypes = [ctypes.POINTER(hg_opts)]
+        L.hg_opts_default.restype = None
+        L.hg_supported_length.argtypes = [I]
+        L.hg_supported_length.restype = I
+        L.hg_plan_create.argtypes = [ctypes.POINTER(P), I, I, I, hg_slm, I, ctypes.POINTER(hg_opts)]
+        L.hg_run.argtypes = [P, P, P, I, P, P]
+        L.hg_get_metrics.argtypes = [P, P, Z]
+        L.hg_replay.argtypes = [P, P, P]
+        L.hg_get_phase.argtypes = [P, P]
+        L.hg_set_weights.argtypes = [P, P]
+        L.hg_get_weights.argtypes = [P, P]
+        L.hg_debug_step.argtypes = [P, P, P, P, P, P, P]
+        L.hg_sync.argtypes = [P]
+        L.hg_last_launch_count.argtypes = [P]
+        L.hg_last_launch_count.restype = I
+        L.hg_plan_destroy.argtypes = [P]
+        L.hg_plan_destroy.restype = None
+        L.hg_status_string.argtypes = [I]
+        L.hg_status_string.restype = ctypes.c_char_p
+        for name in ("hg_plan_create", "hg_run", "hg_get_metrics", "hg_replay", "hg_get_phase",
+                     "hg_set_weights", "hg_get_weights", "hg_debug_step", "hg_sync"):
+            getattr(L, name).restype = I
+        _lib = L
+    return _lib
+
+
+def _ck(st: int, where: str):
+    if st != 0:
+        raise HgError(st, where)
+
+
+def _ptr(t, dtype=None, numel=None, name="tensor"):
+    if t is None:
+        return None
+    if not isinstance(t, torch.Tensor):
+        raise TypeError("%s must be a torch.Tensor" % name)
+    if not t.is_contiguous():
+        raise ValueError("%s must be contiguous" % name)
+    if dtype is not None and t.dtype != dtype:
+        raise TypeError("%s must be %s, got %s" % (name, dtype, t.dtype))
+    if numel is not None and t.numel() < numel:
+        raise ValueError("%s holds %d elements, needs %d" % (name, t.numel(), numel))
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def hg_supported_length(n: int) -> bool:
+    return bool(lib().hg_supported_length(int(n)))
+
+
+def hg_status_string(st: int) -> str:
+    return lib().hg_status_string(int(st)).decode()
+
+
+def hg_plan_create(ny, nx, batch, slm_kind=HG_SLM_BINARY, levels=2, algo=HG_GS, stream=None,
+                   seed=0, subframes=24, precision=0, use_graph=True):
+    o = hg_opts()
+    lib().hg_opts_default(ctypes.byref(o))
+    if stream is None and torch.cuda.is_available():
+        stream = torch.cuda.current_stream().cuda_stream
+    o.stream = ctypes.c_void_p(int(stream or 0))
+    o.seed = int(seed)
+    o.subframes = int(subframes)
+    o.precision = int(precision)
+    o.use_graph = 1 if use_graph else 0
+    h = ctypes.c_void_p()
+    _ck(lib().hg_plan_create(ctypes.byref(h), int(ny), int(nx), int(batch),
+                             hg_slm(int(slm_kind), int(levels)), int(algo), ctypes.byref(o)),
+        "hg_plan_create")
+    return h
+
+
+def hg_run(plan, target, init_phase, iters, holo_out=None, mse_out=None):
+    _ck(lib().hg_run(plan, _ptr(target, torch.float32, name="target"),
+                     _ptr(init_phase, torch.float32, name="init_phase"), int(iters),
+                     _ptr(holo_out, torch.uint8, name="holo_out"),
+                     _ptr(mse_out, torch.float64, name="mse_out")), "hg_run")
+
+
+def hg_get_metrics(plan, out):
+    _ck(lib().hg_get_metrics(plan, _ptr(out, torch.float64, name="out"), out.numel()),
+        "hg_get_metrics")
+
+
+def hg_replay(plan, holo, intensity_out):
+    _ck(lib().hg_replay(plan, _ptr(holo, torch.uint8, name="holo"),
+                        _ptr(intensity_out, torch.float32, name="intensity_out")), "hg_replay")
+
+
+def hg_get_phase(plan, phase_out):
+    _ck(lib().hg_get_phase(plan, _ptr(phase_out, torch.float32, name="phase_out")), "hg_get_phase")
+
+
+def hg_set_weights(plan, w):
+    _ck(lib().hg_set_weights(plan, _ptr(w, torch.float32, name="w")), "hg_set_weights")
+
+
+def hg_get_weights(plan, w_out):
+    _ck(lib().hg_get_weights(plan, _ptr(w_out, torch.float32, name="w_out")), "hg_get_weights")
+
+
+def hg_debug_step(plan, target, phase_in, h_out=None, holo_out=None, replay_out=None,
+                  metrics_out=None):
+    _ck(lib().hg_debug_step(plan, _ptr(target, torch.float32, name="target"),
+                            _ptr(phase_in, torch.float32, name="phase_in"),
+                            _ptr(h_out, torch.complex64, name="h_out"),
+                            _ptr(holo_out, torch.uint8, name="holo_out"),
+                            _ptr(replay_out, torch.complex64, name="replay_out"),
+                            _ptr(metrics_out, torch.float64, name="metrics_out")), "hg_debug_step")
+
+
+def hg_sync(plan):
+    _ck(lib().hg_sync(plan), "hg_sync")
+
+
+def hg_last_launch_count(plan) -> int:
+    return lib().hg_last_launch_count(plan)
+
+
+def hg_plan_destroy(plan):
+    if plan:
+        lib().hg_plan_destroy(plan)
+
+
+class Plan:
+    """Owning wrapper of an hg_plan with shapes attached (same calls, same
+    semantics as the C functions)."""
+
+    def __init__(self, ny, nx, batch=1, slm_kind=HG_SLM_BINARY, levels=2, algo=HG_GS, **kw):
+        self.ny, self.nx, self.batch = int(ny), int(nx), int(batch)
+        self.algo = algo
+        self.subframes = int(kw.get("subframes", 24)) if algo == HG_OSPR else 1
+        self.h = hg_plan_create(ny, nx, batch, slm_kind, levels, algo, **kw)
+        self.iters = 0
+
+    def close(self):
+        if self.h:
+            hg_plan_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def run(self, target, init_phase=None, iters=1, holo_out=None, mse_out=None):
+        hg_run(self.h, target, init_phase, iters, holo_out, mse_out)
+        self.iters = 1 if self.algo == HG_OSPR else int(iters)
+
+    def metrics(self, device="cuda"):
+        out = torch.empty((self.batch, self.iters, NMET), dtype=torch.float64, device=device)
+        hg_get_metrics(self.h, out)
+        return out
+
+    def sync(self):
+        hg_sync(self.h)

@@ -325,3 +325,14 @@ def test_ospr_time_average_and_reciprocal_law():
     fit = A @ np.array([a, c])
     assert c > 0 and a > 0
     assert np.abs(fit - mses).max() < 0.1 * (mses[0] - mses[-1])
+
+
+def test_replay_field_and_metrics_helpers_agree_with_step():
+    ny, nx = 12, 20
+    T = oracle.prepare_target(synth.target(ny, nx, 8))
+    for kind, L in ((oracle.SLM_BINARY, 2), (oracle.SLM_LLEVEL, 8)):
+        o = oracle.gs_step(T, synth.init_phase(ny, nx, 8), kind=kind, levels=L)
+        R = oracle.replay_field(o["holo"], kind, L)
+        assert np.abs(R - o["R"]).max() < 1e-13
+        m = oracle.metrics(np.abs(R) ** 2, T)
+        assert np.allclose(m, [o["mse"], o["amp_mse"], o["eff"], o["sum_r2"]], rtol=1e-12, atol=0)
