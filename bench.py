@@ -1,0 +1,319 @@
+#!/usr/bin/env python
+"""Throughput of batched binary-phase Gerchberg-Saxton at 1024^2, batch 64.
+
+One step = one hg_run of ITERS iterations over a batch of 64 seeded synthetic
+targets (target preparation, head pass, ITERS-1 row/column pass pairs, tail
+pass, metric reduction), inputs already resident in HBM.  value = batched GS
+iterations per second over all ranks (weak scaling: every rank runs its own
+batch).  Prints one JSON line (rank 0).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--iters I] [--impl ours|reference]
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import glob
+import json
+import os
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "GS iterations/s at 1024^2 batch 64, % HBM roofline; time-to-MSE vs plain GS"
+UNIT = "batched GS iterations/s (64 targets of 1024x1024, binary phase)"
+NY = NX = 1024
+BATCH = 64
+BYTES_ROW = 20   # algorithmic HBM bytes per pixel of the row pass: field r+w 16, target 4
+BYTES_COL = 16   # column pass: field r+w
+DATA = ("synthetic: seeded targets of 16 Gaussian blobs + 8 rectangles per 1024x1024 field "
+        "(seeds 1000 + rank*64 + b), initial phase U[0, 2 pi)")
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--iters", type=int, default=50)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--pipeline", type=int, default=-1)
+    return ap.parse_args()
+
+
+def dist_env():
+    return int(os.environ.get("RANK", 0)), int(os.environ.get("LOCAL_RANK", 0)), int(
+        os.environ.get("WORLD_SIZE", 1))
+
+
+def src_hash():
+    h = hashlib.sha256()
+    for f in sorted(glob.glob(os.path.join(ROOT, "paper_2008_12214_gb300", "csrc", "*"))):
+        with open(f, "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def cpu_oracle_sample(seconds_hint: float = 10.0):
+    """The FP64 oracle as it stands, timed on this host's cores over a bounded
+    sample: whole GS iterations (oracle.gs_step) on single 1024^2 targets."""
+    import oracle
+    from paper_2008_12214_gb300 import synth
+    oracle.build()
+    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    t = synth.target(NY, NX, 1000)
+    ph = synth.init_phase(NY, NX, 1000).astype(np.float64)
+    T = oracle.prepare_target(t)
+    oracle.gs_step(T, ph)  # warm-up (library load, first-touch)
+    n, t0 = 0, time.perf_counter()
+    while True:
+        o = oracle.gs_step(T, ph)
+        ph = o["phase"]
+        n += 1
+        el = time.perf_counter() - t0
+        if el * cores >= seconds_hint or n >= 40:
+            break
+    per_target_iter = el / n
+    return dict(value=1.0 / (BATCH * per_target_iter), unit=UNIT, cores=cores, kind="oracle",
+                sample="%d GS iterations of one 1024x1024 binary target (oracle.gs_step), "
+                       "%.3f s each; scaled to one batched iteration = 64 target-iterations" % (n, per_target_iter))
+
+
+def run_reference(args):
+    rank, _, world = dist_env()
+    if rank != 0:
+        return
+    import oracle
+    from paper_2008_12214_gb300 import synth
+    oracle.build()
+    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    t = synth.target(NY, NX, 1000)
+    ph = synth.init_phase(NY, NX, 1000).astype(np.float64)
+    T = oracle.prepare_target(t)
+    for _ in range(args.warmup):
+        ph = oracle.gs_step(T, ph)["phase"]
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        ph = oracle.gs_step(T, ph)["phase"]
+    el = time.perf_counter() - t0
+    per = el / args.steps
+    value = 1.0 / (BATCH * per)
+    line = dict(impl="reference", metric=METRIC, value=value, unit=UNIT, n_gpus=world, steps=args.steps,
+                warmup=args.warmup, ms_per_step=per * 1e3, higher_is_better=True, scaling="weak",
+                vs_baseline=None, dtype="f64", data=DATA,
+                config=dict(workload="gs_binary_1024x1024_batch64", ny=NY, nx=NX, batch=BATCH,
+                            step="one GS iteration of one 1024x1024 target (bounded sample), "
+                                 "scaled to 64 targets"),
+                cpu_baseline=dict(kind="oracle", cores=cores, value=value, unit=UNIT,
+                                  sample="%d x one 1024x1024 target-iteration" % args.steps),
+                e2e=dict(value=value, unit=UNIT, h2d_bytes_per_step=0, d2h_bytes_per_step=0))
+    print(json.dumps(line), flush=True)
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", "-i", str(index), "--query-gpu=" + self.Q,
+                                       "--format=csv,noheader,nounits", "-lms", "200"],
+                                      stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.p = None
+
+    def stop(self):
+        if self.p is None:
+            return None
+        self.p.terminate()
+        try:
+            self.p.wait(timeout=5)
+        except Exception:
+            self.p.kill()
+        self.f.flush()
+        self.f.seek(0)
+        rows = [r.strip().split(", ") for r in self.f.read().splitlines() if r.strip()]
+        os.unlink(self.f.name)
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            try:
+                sm.append(float(r[1]))
+                mx = float(r[2])
+                for nm, v in zip(names, r[5:9]):
+                    if v.strip().lower() == "active":
+                        reasons.add(nm)
+            except (ValueError, IndexError):
+                continue
+        if not sm:
+            return None
+        return dict(sm_mhz=float(np.median(sm)), sm_max_mhz=mx, reasons=sorted(reasons), samples=len(sm))
+
+
+def traffic_for(kernel_key):
+    """DRAM bytes per launch from the committed ncu summary, if it was taken
+    from the current kernel sources (else None)."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        e = d.get(kernel_key)
+        if e and e.get("src_hash") == src_hash():
+            return e.get("bytes_per_launch")
+    except Exception:
+        pass
+    return None
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+        return
+    import torch
+    import __graft_entry__
+    from paper_2008_12214_gb300 import hologen as hg
+    from paper_2008_12214_gb300 import synth
+
+    rank, local, world = dist_env()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+    if rank == 0 or world == 1:
+        __graft_entry__.build()
+    if world > 1:
+        dist.barrier()
+    __graft_entry__.build()
+
+    base = 1000 + rank * BATCH
+    t_host = synth.targets(BATCH, NY, NX, base)
+    p_host = synth.init_phases(BATCH, NY, NX, base)
+    T = torch.from_numpy(t_host).to(dev)
+    P = torch.from_numpy(p_host).to(dev)
+    holo = torch.empty((BATCH, NY, NX), dtype=torch.uint8, device=dev)
+    mse = torch.empty((BATCH, args.iters), dtype=torch.float64, device=dev)
+    plan = hg.Plan(NY, NX, BATCH, hg.HG_SLM_BINARY, 2, hg.HG_GS, pipeline=args.pipeline)
+    stream = torch.cuda.current_stream(dev)
+
+    for _ in range(args.warmup):
+        plan.run(T, P, args.iters, holo, mse)
+    plan.sync()
+
+    # timed region: K steps, per-pass event timing inside the library
+    hg.hg_profile_enable(plan.h, 2 * args.steps * args.iters + 8)
+    clocks = ClockSampler(local) if rank == 0 else None
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize(dev)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    launches = 0
+    for _ in range(args.steps):
+        plan.run(T, P, args.iters, holo, mse)
+        launches += hg.hg_last_launch_count(plan.h)
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    if world > 1:
+        dist.barrier()
+    clk = clocks.stop() if clocks else None
+    plan.sync()
+    el_ms = e0.elapsed_time(e1)
+    prof = hg.hg_profile_read(plan.h)
+    hg.hg_profile_enable(plan.h, 0)
+    if world > 1:
+        t = torch.tensor([el_ms], device=dev, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        el_ms = float(t.item())
+    value = world * args.steps * args.iters / (el_ms / 1e3)
+
+    # end to end through the C ABI with pinned host buffers (copies inside)
+    tp = torch.from_numpy(t_host).pin_memory()
+    pp = torch.from_numpy(p_host).pin_memory()
+    hp = torch.empty((BATCH, NY, NX), dtype=torch.uint8).pin_memory()
+    mp = torch.empty((BATCH, args.iters), dtype=torch.float64).pin_memory()
+    plan.run(tp, pp, args.iters, hp, mp)
+    e2e_steps = max(2, min(args.steps, 5))
+    if world > 1:
+        dist.barrier()
+    w0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        plan.run(tp, pp, args.iters, hp, mp)
+    e2e_s = time.perf_counter() - w0
+    if world > 1:
+        t = torch.tensor([e2e_s], device=dev, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_s = float(t.item())
+    e2e_value = world * e2e_steps * args.iters / e2e_s
+    plan.close()
+
+    if rank != 0:
+        if world > 1:
+            dist.destroy_process_group()
+        return
+
+    peaks = {}
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            peaks = json.load(f)
+    except Exception:
+        pass
+    peak = peaks.get("hbm_gbs")
+    peak_src = "measured" if peak else "fallback"
+    peak = peak or 6800.0
+    npx = NY * NX * BATCH
+    row_ms = prof[0] / max(prof[1], 1)
+    col_ms = prof[2] / max(prof[3], 1)
+    passes = {
+        "row": dict(bytes=BYTES_ROW * npx, ms=row_ms, launches=int(prof[1])),
+        "column": dict(bytes=BYTES_COL * npx, ms=col_ms, launches=int(prof[3])),
+    }
+    for v in passes.values():
+        v["gbs"] = v["bytes"] / (v["ms"] / 1e3) / 1e9 if v["ms"] > 0 else None
+    dom = max(passes, key=lambda k: passes[k]["ms"] * passes[k]["launches"])
+    d = passes[dom]
+    kernel_key = ("k_row_pipe" if dom == "row" else "k_col_pipe") + "<1024>"
+    traffic = traffic_for(kernel_key)
+    roofline = dict(bound="hbm", achieved=d["gbs"], peak=peak, unit="GB/s",
+                    frac=(d["gbs"] / peak) if d["gbs"] else None, traffic=traffic,
+                    kernel="%s pass (%s)" % (dom, kernel_key), peak_source=peak_src,
+                    algorithmic_bytes_per_launch=d["bytes"], avg_launch_ms=d["ms"])
+    iter_ms = el_ms / (args.steps * args.iters)
+    line = dict(
+        metric=METRIC, value=value, unit=UNIT, n_gpus=world, steps=args.steps, warmup=args.warmup,
+        ms_per_step=el_ms / args.steps, higher_is_better=True, scaling="weak", vs_baseline=None,
+        dtype="f32", data=DATA,
+        config=dict(workload="gs_binary_1024x1024_batch64", ny=NY, nx=NX, batch=BATCH,
+                    iters_per_step=args.iters, slm="binary", parallelism="dp%d" % world,
+                    l2="inputs larger than L2: field 512 MiB + prepared targets 256 MiB per rank"),
+        holograms_per_s=value * BATCH / args.iters,
+        whole_iteration_gbs=(BYTES_ROW + BYTES_COL) * npx / (iter_ms / 1e3) / 1e9,
+        roofline=roofline,
+        passes={k: dict(avg_ms=v["ms"], gbs=v["gbs"], frac=(v["gbs"] / peak if v["gbs"] else None),
+                        launches=v["launches"]) for k, v in passes.items()},
+        cpu_baseline=cpu_oracle_sample(),
+        e2e=dict(value=e2e_value, unit=UNIT, h2d_bytes_per_step=int(tp.numel() * 4 + pp.numel() * 4),
+                 d2h_bytes_per_step=int(hp.numel() + mp.numel() * 8)),
+        clocks=clk,
+        gpu_launches=launches,
+        src_hash=src_hash(),
+    )
+    print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -73,10 +73,12 @@ typedef struct {
     int subframes;     /* OSPR subframes per target (>= 1); ignored otherwise */
     int precision;     /* 0 = FP32 transforms (the only value accepted) */
     int use_graph;     /* 1 = replay the iteration loop as a CUDA graph (default) */
+    int pipeline;      /* -1 auto (default): TMA-fed passes where the size allows;
+                          0: generic passes only; 1: require TMA-fed passes */
 } hg_opts;
 
 /* Fills *opts with the defaults: stream NULL, seed 0, subframes 24,
- * precision 0, use_graph 1. */
+ * precision 0, use_graph 1, pipeline -1. */
 void hg_opts_default(hg_opts *opts);
 
 /* 1 if a line of n samples (a row of nx or a column of ny) has a compiled
@@ -158,6 +160,29 @@ hg_status hg_sync(hg_plan plan);
 
 /* Number of kernels the last hg_run / hg_replay / hg_debug_step enqueued. */
 int hg_last_launch_count(hg_plan plan);
+
+/* Bit 0: the row pass of the iteration runs the TMA-fed kernel; bit 1: the
+ * column pass does (hg_opts.pipeline, sizes and alignment decide). */
+int hg_pipelined(hg_plan plan);
+
+/* Per-pass timing (diagnostics; no counterpart in the paper).
+ * hg_profile_enable(plan, n) makes the next runs record a CUDA event pair on
+ * the plan's stream around each of up to n row and column passes of the
+ * iteration loop (the loop is then launched pass by pass, not as a graph);
+ * n = 0 switches timing off.  hg_profile_read waits for the stream and
+ * stores {row ms, row passes, column ms, column passes} accumulated since the
+ * last read into out4[4]. */
+hg_status hg_profile_enable(hg_plan plan, int max_passes);
+hg_status hg_profile_read(hg_plan plan, double *out4);
+
+/* Failure-injection hook for tests (no counterpart in the paper).  The
+ * TMA-fed passes bound every device-side wait by `wait_ns` nanoseconds
+ * (default 2 s); when a wait runs out the kernel stops, sets an error bit and
+ * the next hg_sync returns HG_ERR_TIMEOUT, with the context still usable.
+ * drop_job >= 0 makes the producer of the next runs never issue that job's
+ * copy (job = item * panels + panel in the pass's order), so the consumer's
+ * wait runs out; -1 restores normal operation.  Errors: HG_ERR_INVALID_ARG. */
+hg_status hg_debug_inject(hg_plan plan, int drop_job, uint64_t wait_ns);
 
 void hg_plan_destroy(hg_plan plan);
 const char *hg_status_string(hg_status st);

@@ -9,8 +9,9 @@
 #include <cstring>
 #include <mutex>
 #include <new>
+#include <vector>
 
-#include "hg_kernels.cuh"
+#include "hg_pipe.cuh"
 #include "hologen.h"
 
 using namespace hg;
@@ -20,6 +21,7 @@ using namespace hg;
 namespace {
 
 enum ErrBits : unsigned { ERR_BAD_VALUE = 1u, ERR_ZERO_ENERGY = 2u };
+static_assert(ERR_TIMEOUT_BIT == 4u, "error bits must be distinct");
 
 constexpr int PREP_THREADS = 256;
 constexpr int PREP_BLOCKS = 64;  // per target
@@ -105,16 +107,19 @@ __global__ void k_fill(float *p, size_t n, float v) {
         p[i] = v;
 }
 
-// metrics[b][k][4] from the per-panel partials part[k][b][panel][4]:
+// metrics[b][k][4] from the per-panel partials: slot k holds
+// [batch][panels_k][4] at part + k * batch * stride * 4, where panels_k is
+// `panels` for k < iters - 1 and `panels_last` for the last slot.  Output:
 // {sum d^2 / N, sum a^2 / N, in / total, total}; also mse_out[b][k].
-__global__ void k_reduce(const double *part, int iters, int batch, int panels, double invN,
-                         double *metrics, double *mse_out) {
+__global__ void k_reduce(const double *part, int iters, int batch, int stride, int panels,
+                         int panels_last, double invN, double *metrics, double *mse_out) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= iters * batch) return;
     const int k = i / batch, b = i - k * batch;
-    const double *p = part + ((size_t)k * batch + b) * panels * NMET;
+    const int np = k == iters - 1 ? panels_last : panels;
+    const double *p = part + ((size_t)k * batch * stride + (size_t)b * np) * NMET;
     double s[NMET] = {0, 0, 0, 0};
-    for (int q = 0; q < panels; ++q)
+    for (int q = 0; q < np; ++q)
         for (int m = 0; m < NMET; ++m) s[m] += p[(size_t)q * NMET + m];
     double *o = metrics + ((size_t)b * iters + k) * NMET;
     o[0] = s[0] * invN;
@@ -135,10 +140,53 @@ const LineOps *find_ops(int n) {
     return o;
 }
 
+const PipeOps *find_pipe(int n) {
+    const PipeOps *o = pipe_ops_mid(n);
+    if (!o) o = pipe_ops_1024(n);
+    if (!o) o = pipe_ops_2048(n);
+    if (!o) o = pipe_ops_hd(n);
+    return o;
+}
+
 std::mutex g_init_mu;
 constexpr int kMaxDev = 64;
 constexpr int kMaxOps = 64;
 const LineOps *g_inited[kMaxDev][kMaxOps];
+
+const PipeOps *g_pinited[kMaxDev][kMaxOps];
+
+cudaError_t ensure_pipe_init(int dev, const PipeOps *o) {
+    std::lock_guard<std::mutex> lk(g_init_mu);
+    if (dev < 0 || dev >= kMaxDev) return cudaErrorInvalidDevice;
+    for (int i = 0; i < kMaxOps; ++i) {
+        if (g_pinited[dev][i] == o) return cudaSuccess;
+        if (!g_pinited[dev][i]) {
+            cudaError_t e = o->init(const_cast<PipeOps *>(o));
+            if (e == cudaSuccess) g_pinited[dev][i] = o;
+            return e;
+        }
+    }
+    return cudaErrorUnknown;
+}
+
+typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *,
+                                  const cuuint64_t *, const cuuint64_t *, const cuuint32_t *,
+                                  const cuuint32_t *, CUtensorMapInterleave, CUtensorMapSwizzle,
+                                  CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeTiledFn encode_tiled() {
+    static EncodeTiledFn fn = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault,
+                                             &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = (EncodeTiledFn)p;
+    });
+    return fn;
+}
 
 // Per-device one-time kernel attributes for a line length.
 cudaError_t ensure_init(int dev, const LineOps *o) {
@@ -166,7 +214,17 @@ struct hg_plan_s {
     cudaStream_t cap_stream = nullptr; // private stream used only for graph capture
     int use_graph = 1;
     const LineOps *rops = nullptr, *cops = nullptr;
-    int nsm = 0, row_grid = 0, col_grid = 0, head_grid = 0, ppt = 0;
+    const PipeOps *prow = nullptr, *pcol = nullptr;  // pipelined passes (null: generic)
+    CUtensorMap cmap;                                // field as [chains*ny][2*nx] floats
+    unsigned long long wait_ns = 2000000000ull;      // bound on a device-side wait
+    int drop_job = -1;                               // fault-injection hook
+    int nsm = 0, ppt = 0, ppt_pipe = 0, ppt_max = 0;
+    // per-pass CUDA-event timing (hg_profile_enable): pairs around each row
+    // and column pass of the iteration loop, kind 0 = row, 1 = column
+    bool prof_on = false;
+    std::vector<cudaEvent_t> prof_ev;
+    std::vector<int> prof_kind;
+    size_t prof_used = 0;
     size_t npx = 0;
     int nchains = 0;
     float2 *field = nullptr;
@@ -242,7 +300,7 @@ hg_status ensure_part(hg_plan p, int iters) {
     if (p->part) cudaFree(p->part);
     p->part = nullptr;
     p->part_iters = 0;
-    HG_CK(cudaMalloc(&p->part, sizeof(double) * NMET * (size_t)iters * p->batch * p->ppt));
+    HG_CK(cudaMalloc(&p->part, sizeof(double) * NMET * (size_t)iters * p->batch * p->ppt_max));
     p->part_iters = iters;
     return HG_OK;
 }
@@ -310,6 +368,53 @@ void launch_col(hg_plan p, int role, const ColArgs &a, cudaStream_t s) {
     p->launches++;
 }
 
+PipeArgs pipe_args(hg_plan p) {
+    PipeArgs pa{};
+    pa.err = p->err;
+    pa.wait_ns = p->wait_ns;
+    pa.drop_job = p->drop_job;
+    return pa;
+}
+
+struct ProfScope {  // records an event pair around one pass launch when profiling
+    hg_plan p;
+    cudaStream_t s;
+    size_t slot = (size_t)-1;
+    ProfScope(hg_plan p_, cudaStream_t s_, int kind) : p(p_), s(s_) {
+        if (p->prof_on && 2 * (p->prof_used + 1) <= p->prof_ev.size()) {
+            slot = p->prof_used++;
+            p->prof_kind[slot] = kind;
+            cudaEventRecord(p->prof_ev[2 * slot], s);
+        }
+    }
+    ~ProfScope() {
+        if (slot != (size_t)-1) cudaEventRecord(p->prof_ev[2 * slot + 1], s);
+    }
+};
+
+void launch_row_iter(hg_plan p, const RowArgs &a, cudaStream_t s) {
+    ProfScope ps(p, s, 0);
+    if (p->prow) {
+        const long work = (long)a.items * p->ppt_pipe;
+        p->prow->row_iter(a, pipe_args(p), grid_for(p->prow->row_blocks_per_sm, p->nsm, work), s);
+        p->launches++;
+    } else {
+        launch_row(p, ROW_ITER, a, s);
+    }
+}
+
+void launch_col_gs(hg_plan p, int role, const ColArgs &a, cudaStream_t s) {
+    ProfScope ps(p, s, 1);
+    if (p->pcol) {
+        const long work = (long)a.items * ((p->nx + p->pcol->col_c - 1) / p->pcol->col_c);
+        p->pcol->col_gs(role, a, pipe_args(p), p->cmap,
+                        grid_for(p->pcol->col_blocks_per_sm, p->nsm, work), s);
+        p->launches++;
+    } else {
+        launch_col(p, role, a, s);
+    }
+}
+
 int ew_grid(hg_plan p, size_t n) {
     size_t g = (n + 255) / 256;
     size_t cap = (size_t)p->nsm * 8;
@@ -336,15 +441,15 @@ void enqueue_loop(hg_plan p, int iters, cudaStream_t s) {
     ColArgs ca = col_args(p);
     RowArgs ra = row_args(p);
     for (int k = 0; k + 1 < iters; ++k) {
-        launch_col(p, col_role_gs(p), ca, s);
-        ra.part = p->part + (size_t)k * p->batch * p->ppt * NMET;
-        launch_row(p, ROW_ITER, ra, s);
+        launch_col_gs(p, col_role_gs(p), ca, s);
+        ra.part = p->part + (size_t)k * p->batch * p->ppt_max * NMET;
+        launch_row_iter(p, ra, s);
     }
 }
 
 hg_status run_loop(hg_plan p, int iters) {
     if (iters <= 1) return HG_OK;
-    if (!p->use_graph) {
+    if (!p->use_graph || p->prof_on) {
         enqueue_loop(p, iters, p->stream);
         return map_err(cudaGetLastError());
     }
@@ -378,6 +483,7 @@ hg_status check_err_flag(hg_plan p) {
     HG_CK(cudaStreamSynchronize(p->stream));
     if (e & ERR_BAD_VALUE) return HG_ERR_INVALID_ARG;
     if (e & ERR_ZERO_ENERGY) return HG_ERR_NUMERIC;
+    if (e & ERR_TIMEOUT_BIT) return HG_ERR_TIMEOUT;
     return HG_OK;
 }
 
@@ -404,6 +510,7 @@ void hg_opts_default(hg_opts *o) {
     memset(o, 0, sizeof *o);
     o->subframes = 24;
     o->use_graph = 1;
+    o->pipeline = -1;
 }
 
 int hg_supported_length(int n) { return find_ops(n) != nullptr; }
@@ -427,6 +534,7 @@ void hg_plan_destroy(hg_plan p) {
     if (p->stream || p->cap_stream) cudaStreamSynchronize(p->stream);
     if (p->gexec) cudaGraphExecDestroy(p->gexec);
     if (p->cap_stream) cudaStreamDestroy(p->cap_stream);
+    for (cudaEvent_t e : p->prof_ev) cudaEventDestroy(e);
     void *bufs[] = {p->field, p->tf, p->w, p->part, p->metrics, p->sum_part, p->scale,
                     p->err, p->twx, p->twy, p->lvl, p->stage};
     for (void *b : bufs)
@@ -475,6 +583,7 @@ hg_status hg_plan_create(hg_plan *out, int ny, int nx, int batch, hg_slm slm, hg
     p->cops = cops;
     p->npx = npx;
     p->ppt = (ny + rops->row_lines - 1) / rops->row_lines;
+    p->ppt_max = p->ppt;
 
     hg_status st = HG_OK;
     auto fail = [&](hg_status s) {
@@ -487,6 +596,30 @@ hg_status hg_plan_create(hg_plan *out, int ny, int nx, int batch, hg_slm slm, hg
     if (ce == cudaSuccess) ce = cudaStreamCreateWithFlags(&p->cap_stream, cudaStreamNonBlocking);
     if (ce != cudaSuccess) return fail(map_err(ce));
     ce = cudaMalloc(&p->field, sizeof(float2) * npx * p->nchains);
+    if (ce != cudaSuccess) return fail(map_err(ce));
+    if (o.pipeline != 0) {
+        // TMA-fed passes: row panels need 16-byte aligned rows of T (nx % 4 == 0);
+        // the column tiles need a 16-byte multiple row pitch (nx even).
+        const PipeOps *pr = find_pipe(nx), *pc = find_pipe(ny);
+        if (pr && pr->row_iter && nx % 4 == 0 && ensure_pipe_init(p->dev, pr) == cudaSuccess) {
+            p->prow = pr;
+            p->ppt_pipe = (ny + pr->row_lines - 1) / pr->row_lines;
+            if (p->ppt_pipe > p->ppt_max) p->ppt_max = p->ppt_pipe;
+        }
+        EncodeTiledFn enc = encode_tiled();
+        if (pc && pc->col_gs && nx % 2 == 0 && enc && ensure_pipe_init(p->dev, pc) == cudaSuccess) {
+            const cuuint64_t gdim[2] = {(cuuint64_t)2 * nx, (cuuint64_t)ny * p->nchains};
+            const cuuint64_t gstride[1] = {(cuuint64_t)nx * 8};
+            const cuuint32_t box[2] = {(cuuint32_t)(2 * pc->col_c), (cuuint32_t)pc->col_boxr};
+            const cuuint32_t estr[2] = {1, 1};
+            if (enc(&p->cmap, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, p->field, gdim, gstride, box, estr,
+                    CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                    CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                    CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS)
+                p->pcol = pc;
+        }
+        if (o.pipeline == 1 && (!p->prow || !p->pcol)) return fail(HG_ERR_UNSUPPORTED_SIZE);
+    }
     if (ce == cudaSuccess) ce = cudaMalloc(&p->tf, sizeof(float) * npx * batch);
     if (ce == cudaSuccess && algo == HG_WGS) ce = cudaMalloc(&p->w, sizeof(float) * npx * batch);
     if (ce == cudaSuccess) ce = cudaMalloc(&p->sum_part, sizeof(double) * PREP_BLOCKS * batch);
@@ -524,6 +657,51 @@ hg_status hg_sync(hg_plan p) {
 }
 
 int hg_last_launch_count(hg_plan p) { return p ? p->launches : 0; }
+
+hg_status hg_debug_inject(hg_plan p, int drop_job, uint64_t wait_ns) {
+    if (!p || wait_ns == 0) return HG_ERR_INVALID_ARG;
+    p->drop_job = drop_job;
+    p->wait_ns = wait_ns;
+    if (p->gexec) cudaGraphExecDestroy(p->gexec);  // captured launches carry the old values
+    p->gexec = nullptr;
+    p->g_iters = -1;
+    return HG_OK;
+}
+
+hg_status hg_profile_enable(hg_plan p, int max_passes) {
+    if (!p || max_passes < 0) return HG_ERR_INVALID_ARG;
+    DevGuard g(p->dev);
+    HG_CK(cudaStreamSynchronize(p->stream));
+    for (cudaEvent_t e : p->prof_ev) cudaEventDestroy(e);
+    p->prof_ev.clear();
+    p->prof_kind.assign((size_t)max_passes, 0);
+    p->prof_used = 0;
+    p->prof_on = max_passes > 0;
+    for (int i = 0; i < 2 * max_passes; ++i) {
+        cudaEvent_t e;
+        HG_CK(cudaEventCreate(&e));
+        p->prof_ev.push_back(e);
+    }
+    return HG_OK;
+}
+
+hg_status hg_profile_read(hg_plan p, double *out4) {
+    if (!p || !out4) return HG_ERR_INVALID_ARG;
+    DevGuard g(p->dev);
+    HG_CK(cudaStreamSynchronize(p->stream));
+    double acc[4] = {0, 0, 0, 0};
+    for (size_t i = 0; i < p->prof_used; ++i) {
+        float ms = 0;
+        HG_CK(cudaEventElapsedTime(&ms, p->prof_ev[2 * i], p->prof_ev[2 * i + 1]));
+        acc[2 * p->prof_kind[i]] += ms;
+        acc[2 * p->prof_kind[i] + 1] += 1;
+    }
+    memcpy(out4, acc, sizeof acc);
+    p->prof_used = 0;
+    return HG_OK;
+}
+
+int hg_pipelined(hg_plan p) { return p ? (p->prow ? 1 : 0) | (p->pcol ? 2 : 0) : 0; }
 
 hg_status hg_run(hg_plan p, const float *target, const float *init_phase, int iters,
                  uint8_t *holo_out, double *mse_out) {
@@ -595,13 +773,14 @@ hg_status hg_run(hg_plan p, const float *target, const float *init_phase, int it
         launch_row(p, ROW_HEAD, ra, p->stream);
         if ((st = run_loop(p, iters)) != HG_OK) return st;
         ca.holo = d_ho;
-        launch_col(p, col_role_gs(p), ca, p->stream);
+        launch_col_gs(p, col_role_gs(p), ca, p->stream);
         RowArgs rt = row_args(p);
-        rt.part = p->part + (size_t)(iters - 1) * p->batch * p->ppt * NMET;
+        rt.part = p->part + (size_t)(iters - 1) * p->batch * p->ppt_max * NMET;
         launch_row(p, ROW_TAIL, rt, p->stream);
     }
     k_reduce<<<(iters * p->batch + 127) / 128, 128, 0, p->stream>>>(
-        p->part, iters, p->batch, p->ppt, 1.0 / (double)p->npx, p->metrics, d_mo);
+        p->part, iters, p->batch, p->ppt_max, p->prow ? p->ppt_pipe : p->ppt, p->ppt,
+        1.0 / (double)p->npx, p->metrics, d_mo);
     p->launches++;
     HG_CK(cudaGetLastError());
     p->weights_preset = false;
@@ -744,14 +923,14 @@ hg_status hg_debug_step(hg_plan p, const float *target, const float *phase_in, f
     ColArgs ca = col_args(p);
     ca.holo = holo_out;
     ca.h_out = (float2 *)h_out;
-    launch_col(p, col_role_gs(p), ca, p->stream);
+    launch_col_gs(p, col_role_gs(p), ca, p->stream);
     RowArgs rt = row_args(p);
     rt.part = p->part;
     rt.R_out = (float2 *)replay_out;
     launch_row(p, ROW_TAIL, rt, p->stream);
-    k_reduce<<<(p->batch + 127) / 128, 128, 0, p->stream>>>(p->part, 1, p->batch, p->ppt,
-                                                             1.0 / (double)p->npx, p->metrics,
-                                                             nullptr);
+    k_reduce<<<(p->batch + 127) / 128, 128, 0, p->stream>>>(p->part, 1, p->batch, p->ppt_max,
+                                                             p->ppt, p->ppt, 1.0 / (double)p->npx,
+                                                             p->metrics, nullptr);
     p->launches++;
     if (metrics_out)
         HG_CK(cudaMemcpyAsync(metrics_out, p->metrics, sizeof(double) * NMET * p->batch,

@@ -235,17 +235,34 @@ struct Plan {
     static_assert(E % R[0] == 0, "first radix must divide the samples per thread");
 };
 
-// Shared-memory slot of address a for a line whose consecutive addresses are
-// STRIDE float2 apart; one pad slot every PAD addresses breaks the stride-R
-// bank pattern of stage 0's stores.
-template <class P, int STRIDE>
+// Shared-memory layouts of one line during the exchanges (consecutive
+// addresses STRIDE float2 apart).
+//  Pad:      one pad slot every P::PAD addresses (needs P::SLOTS slots per
+//            line); breaks the stride-R bank pattern of stage 0's stores.
+//  Swz<L>:   a ^ ((a >> L) & (2^L - 1)): a permutation inside every aligned
+//            block of 2^L addresses (needs N slots, N a multiple of 2^L), so a
+//            line can be exchanged in place in the buffer it was loaded into.
+struct Pad {
+    template <class P>
+    __device__ __forceinline__ static int idx(int a) { return a + a / P::PAD; }
+};
+template <int L>
+struct Swz {
+    template <class P>
+    __device__ __forceinline__ static int idx(int a) {
+        static_assert(P::N % (1 << L) == 0, "swizzle blocks must tile the line");
+        return a ^ ((a >> L) & ((1 << L) - 1));
+    }
+};
+
+template <class P, int STRIDE, class LAY = Pad>
 __device__ __forceinline__ float2 &slot(float2 *base, int a) {
-    return base[(a + a / P::PAD) * STRIDE];
+    return base[LAY::template idx<P>(a) * STRIDE];
 }
 
 // Stage 0: butterflies straight from the registers v; the result goes to
 // shared memory (or back to v when the plan has one stage).
-template <class P, int DIR, int STRIDE>
+template <class P, int DIR, int STRIDE, class LAY>
 __device__ __forceinline__ void stage_first(float2 (&v)[P::E], float2 *smb,
                                             const float2 *__restrict__ tw, int t) {
     constexpr int R = P::R[0];
@@ -271,7 +288,7 @@ __device__ __forceinline__ void stage_first(float2 (&v)[P::E], float2 *smb,
             });
             static_for<0, R>([&](auto kc) {
                 constexpr int k = decltype(kc)::value;
-                slot<P, STRIDE>(smb, k + R * b) = x[k];
+                slot<P, STRIDE, LAY>(smb, k + R * b) = x[k];
             });
         }
     });
@@ -279,7 +296,7 @@ __device__ __forceinline__ void stage_first(float2 (&v)[P::E], float2 *smb,
 
 // Stage S >= 1: read from shared memory, transform, then write to shared
 // memory or (last stage with TO_REGS) into v.
-template <class P, int S, int DIR, int STRIDE, bool TO_REGS, class SYNC>
+template <class P, int S, int DIR, int STRIDE, bool TO_REGS, class LAY, class SYNC>
 __device__ __forceinline__ void stage_next(float2 (&v)[P::E], float2 *smb,
                                            const float2 *__restrict__ tw, int t, SYNC sync) {
     constexpr int R = P::R[S];
@@ -294,7 +311,7 @@ __device__ __forceinline__ void stage_next(float2 (&v)[P::E], float2 *smb,
         if (EXACT || b < M) {
             static_for<0, R>([&](auto jc) {
                 constexpr int j = decltype(jc)::value;
-                x[u][j] = slot<P, STRIDE>(smb, b + M * j);
+                x[u][j] = slot<P, STRIDE, LAY>(smb, b + M * j);
             });
         }
     });
@@ -319,7 +336,7 @@ __device__ __forceinline__ void stage_next(float2 (&v)[P::E], float2 *smb,
                 }
                 static_for<0, R>([&](auto kc) {
                     constexpr int k = decltype(kc)::value;
-                    slot<P, STRIDE>(smb, kap + PS * k + PS * R * nu1) = x[u][k];
+                    slot<P, STRIDE, LAY>(smb, kap + PS * k + PS * R * nu1) = x[u][k];
                 });
             }
         }
@@ -331,24 +348,24 @@ __device__ __forceinline__ void stage_next(float2 (&v)[P::E], float2 *smb,
 // transform's outputs t + TL e on exit.  `sync` must order shared-memory
 // accesses of all threads of the line.  Shared memory may be reused between
 // calls without further synchronisation.
-template <class P, int DIR, int STRIDE, class SYNC>
+template <class P, int DIR, int STRIDE, class LAY = Pad, class SYNC>
 __device__ __forceinline__ void line_fft(float2 (&v)[P::E], float2 *smb,
                                          const float2 *__restrict__ tw, int t, SYNC sync) {
     if constexpr (P::NS == 1) {
-        stage_first<P, DIR, STRIDE>(v, smb, tw, t);
+        stage_first<P, DIR, STRIDE, LAY>(v, smb, tw, t);
     } else {
         sync();  // earlier readers of this line's shared memory are done
-        stage_first<P, DIR, STRIDE>(v, smb, tw, t);
+        stage_first<P, DIR, STRIDE, LAY>(v, smb, tw, t);
         sync();
         static_for<1, P::NS>([&](auto sc) {
             constexpr int S = decltype(sc)::value;
             constexpr bool to_regs = (S == P::NS - 1) && P::LAST_TO_REGS;
-            stage_next<P, S, DIR, STRIDE, to_regs>(v, smb, tw, t, sync);
+            stage_next<P, S, DIR, STRIDE, to_regs, LAY>(v, smb, tw, t, sync);
         });
         if constexpr (!P::LAST_TO_REGS) {
             static_for<0, P::E>([&](auto ec) {
                 constexpr int e = decltype(ec)::value;
-                v[e] = slot<P, STRIDE>(smb, t + P::TL * e);
+                v[e] = slot<P, STRIDE, LAY>(smb, t + P::TL * e);
             });
         }
     }

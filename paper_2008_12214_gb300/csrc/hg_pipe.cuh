@@ -1,0 +1,478 @@
+// hg_pipe.cuh -- TMA-fed, warp-specialised versions of the two passes of a
+// GS / WGS iteration (same arithmetic as k_row ROW_ITER and k_col COL_GS_*).
+//
+// A CTA has NG independent groups of threads; each group owns a ring of D
+// shared-memory slots.  The group's leader thread streams the group's panels
+// into its ring with the bulk-copy engine (row panels are contiguous and go
+// through cp.async.bulk; column panels are 2D tiles of the [rows][2 nx floats]
+// field and go through cp.async.bulk.tensor.2d with a tensor map), each slot
+// completing an mbarrier with the copy's transaction count.  A group uses
+// slot k % D for its k-th panel and refills it with panel k + D as soon as
+// the panel's transforms are done, so D - 1 copies are always in flight
+// while the group computes.  The transforms exchange data in place inside the
+// slot with a swizzled layout; results are written back with ordinary
+// coalesced stores.
+//
+// Every wait is bounded by %globaltimer: a wait that runs past the limit
+// sets the error flag and makes the CTA abort; before leaving, each group's
+// leader waits (bounded) for the copies it still has in flight.
+#pragma once
+#include <cuda.h>
+
+#include "hg_kernels.cuh"
+
+namespace hg {
+
+constexpr unsigned ERR_TIMEOUT_BIT = 4u;
+
+struct PipeArgs {
+    unsigned *err;                 // device error word (bit ERR_TIMEOUT_BIT)
+    unsigned long long wait_ns;    // bound on any single wait
+    int drop_job;                  // fault-injection hook: this job is never issued (-1: none)
+};
+
+// ------------------------------------------------------------ PTX helpers
+
+__device__ __forceinline__ uint32_t smem_addr(const void *p) {
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void fence_mbar_init() {
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)),
+                 "r"(bytes)
+                 : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(bar)) : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_addr(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+__device__ __forceinline__ uint64_t global_ns() {
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+// Wait for the phase of `bar` with the given parity to complete; false when
+// `limit_ns` passes first or another thread of the CTA raised `abort`.
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, uint64_t limit_ns,
+                                          volatile int *abort) {
+    if (mbar_try_wait(bar, parity)) return true;
+    const uint64_t t0 = global_ns();
+    for (;;) {
+#pragma unroll 1
+        for (int i = 0; i < 32; ++i)
+            if (mbar_try_wait(bar, parity)) return true;
+        if ((abort && *abort) || global_ns() - t0 > limit_ns) return false;
+    }
+}
+// 1D bulk copy global -> shared, completing `bytes` on `bar`.
+__device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t bytes, uint64_t *bar) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+            smem_addr(dst)),
+        "l"(src), "r"(bytes), "r"(smem_addr(bar))
+        : "memory");
+}
+// 2D tensor tile global -> shared at coordinates (x, y) of the tensor map.
+__device__ __forceinline__ void tma_load_2d(void *dst, const CUtensorMap *map, int x, int y,
+                                            uint64_t *bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, "
+        "{%2, %3}], [%4];" ::"r"(smem_addr(dst)),
+        "l"(map), "r"(x), "r"(y), "r"(smem_addr(bar))
+        : "memory");
+}
+__device__ __forceinline__ void named_sync(int id, int nthreads) {
+    asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(nthreads) : "memory");
+}
+
+// Sum four per-thread float partials over a consumer group of GT threads in
+// double, fixed order; thread 0 of the group stores them at dst.
+template <int GT, class SYNC>
+__device__ __forceinline__ void group_sum4(float a0, float a1, float a2, float a3, double *red,
+                                           double *dst, int gt, SYNC gsync) {
+    double d[NMET] = {a0, a1, a2, a3};
+#pragma unroll
+    for (int off = 16; off; off >>= 1)
+#pragma unroll
+        for (int m = 0; m < NMET; ++m) d[m] += __shfl_down_sync(0xffffffffu, d[m], off);
+    if constexpr (GT == 32) {
+        if (gt == 0)
+#pragma unroll
+            for (int m = 0; m < NMET; ++m) dst[m] = d[m];
+    } else {
+        const int lane = gt & 31, w = gt >> 5;
+        if (lane == 0)
+#pragma unroll
+            for (int m = 0; m < NMET; ++m) red[w * NMET + m] = d[m];
+        gsync();
+        if (gt == 0) {
+            double s[NMET] = {0, 0, 0, 0};
+            for (int q = 0; q < GT / 32; ++q)
+#pragma unroll
+                for (int m = 0; m < NMET; ++m) s[m] += red[q * NMET + m];
+#pragma unroll
+            for (int m = 0; m < NMET; ++m) dst[m] = s[m];
+        }
+        gsync();
+    }
+}
+
+// -------------------------------------------------------------- row pass
+template <class P, int LINES, int NG, int D, int SWZ>
+struct RowPipeCfg {
+    static constexpr int GT = P::TL * LINES;
+    static_assert(GT % 32 == 0, "row group must be whole warps");
+    static constexpr int GW = GT / 32;
+    static constexpr int THREADS = NG * GT;
+    static constexpr int SLOT_F = LINES * P::N * 8;
+    static constexpr int SLOT_T = LINES * P::N * 4;
+    static constexpr int SLOT = (SLOT_F + SLOT_T + 127) / 128 * 128;
+    static constexpr int RED = NG * GW * NMET * 8;
+    static constexpr size_t SMEM = 1024 + (size_t)NG * D * SLOT + RED + NG * D * 8 + 4 * (NG + 1) + 256;
+};
+
+template <class P, int LINES, int NG, int D, int SWZ>
+__global__ void __launch_bounds__(RowPipeCfg<P, LINES, NG, D, SWZ>::THREADS, 1)
+    k_row_pipe(const RowArgs a, const PipeArgs pa) {
+    using Cfg = RowPipeCfg<P, LINES, NG, D, SWZ>;
+    using LAY = Swz<SWZ>;
+    constexpr int TL = P::TL, E = P::E, NX = P::N, GT = Cfg::GT;
+    extern __shared__ unsigned char smraw[];
+    unsigned char *base = smraw + ((1024 - (smem_addr(smraw) & 1023)) & 1023);
+    double *red = reinterpret_cast<double *>(base + (size_t)NG * D * Cfg::SLOT);
+    uint64_t *full = reinterpret_cast<uint64_t *>(reinterpret_cast<unsigned char *>(red) + Cfg::RED);
+    volatile int *flags = reinterpret_cast<volatile int *>(full + NG * D);
+    volatile int *abort = flags + NG;
+
+    const int tid = threadIdx.x;
+    if (tid == 0) {
+        for (int i = 0; i < NG * D; ++i) mbar_init(full + i, 1);
+        *abort = 0;
+        fence_mbar_init();
+    }
+    __syncthreads();
+
+    const int ny = a.ny;
+    const int ppt = (ny + LINES - 1) / LINES;
+    const int J = a.items * ppt;
+    const int g = tid / GT, gt = tid - g * GT;
+    const int line = gt / TL, t = gt - line * TL;
+    unsigned char *ring = base + (size_t)g * D * Cfg::SLOT;
+    uint64_t *gfull = full + g * D;
+    auto gsync = [g]() {
+        if constexpr (Cfg::GW == 1) __syncwarp();
+        else named_sync(1 + g, GT);
+    };
+    auto job = [&](int k) { return (int)blockIdx.x + (g + NG * k) * (int)gridDim.x; };
+    auto issue = [&](int k) {  // copy the group's k-th panel (field rows + target rows)
+        const int j = job(k);
+        if (j >= J || j == pa.drop_job) return;
+        const int item = j / ppt, pan = j - item * ppt, y0 = pan * LINES;
+        const int nl = min(LINES, ny - y0);
+        const uint32_t bf = (uint32_t)(nl * NX * 8), bt = (uint32_t)(nl * NX * 4);
+        unsigned char *sl = ring + (size_t)(k % D) * Cfg::SLOT;
+        mbar_expect_tx(gfull + k % D, bf + bt);
+        bulk_g2s(sl, a.field + ((size_t)item * ny + y0) * NX, bf, gfull + k % D);
+        bulk_g2s(sl + Cfg::SLOT_F, a.T + ((size_t)item * ny + y0) * NX, bt, gfull + k % D);
+    };
+    auto drain = [&](int k0, int k1) {
+        for (int q = k0; q < k1; ++q) {
+            const int j = job(q);
+            if (j < J && j != pa.drop_job) mbar_wait(gfull + q % D, (q / D) & 1, pa.wait_ns, nullptr);
+        }
+    };
+    if (gt == 0)
+        for (int k = 0; k < D; ++k) issue(k);
+
+    for (int k = 0;; ++k) {
+        const int j = job(k);
+        if (j >= J) break;
+        if (gt == 0) {
+            bool ok = !*abort && mbar_wait(gfull + k % D, (k / D) & 1, pa.wait_ns, abort);
+            if (!ok) {
+                atomicOr(pa.err, ERR_TIMEOUT_BIT);
+                *abort = 1;
+            }
+            flags[g] = ok;
+        }
+        gsync();
+        if (!flags[g]) {
+            if (gt == 0) drain(k, k + D);
+            break;
+        }
+        const int item = j / ppt, pan = j - item * ppt;
+        const int y = pan * LINES + line;
+        const bool act = y < ny;
+        unsigned char *sl = ring + (size_t)(k % D) * Cfg::SLOT;
+        float2 *sf = reinterpret_cast<float2 *>(sl) + line * NX;  // also the exchange buffer
+        const float *sT = reinterpret_cast<const float *>(sl + Cfg::SLOT_F) + line * NX;
+        float2 v[E];
+        static_for<0, E>([&](auto ec) {
+            constexpr int e = decltype(ec)::value;
+            v[e] = sf[t + TL * e];
+        });
+        line_fft<P, -1, 1, LAY>(v, sf, a.tw, t, gsync);
+        float *wr = a.w ? a.w + ((size_t)item * ny + (act ? y : ny - 1)) * NX : nullptr;
+        float acc0 = 0.f, acc1 = 0.f, acc2 = 0.f, acc3 = 0.f;
+        static_for<0, E>([&](auto ec) {
+            constexpr int e = decltype(ec)::value;
+            const int x = t + TL * e;
+            const float Tv = act ? sT[x] : 0.f;
+            const float2 r = v[e];
+            const float m2 = fmaf(r.x, r.x, r.y * r.y);
+            const float rs = m2 > 0.f ? rsqrtf(m2) : 0.f;
+            const float I = m2 * a.invN2;
+            const float d = I - Tv * Tv;
+            const float am = fmaf(m2 * rs, a.invSqrtN * a.invSqrtN, -Tv);  // sqrt(I) - T
+            const float e2 = m2 * a.invN;
+            if (act) {
+                acc0 = fmaf(d, d, acc0);
+                acc1 = fmaf(am, am, acc1);
+                acc3 += e2;
+                if (Tv > 0.f) acc2 += e2;
+            }
+            float wv = 1.f;
+            if (wr) {
+                wv = act ? wr[x] : 1.f;
+                if (Tv > 0.f && m2 > 0.f) wv = wv * Tv * (a.NN * rs);
+                if (act) wr[x] = wv;
+            }
+            const float gm = Tv * wv;
+            v[e] = m2 > 0.f ? make_float2(gm * r.x * rs, gm * r.y * rs) : make_float2(gm, 0.f);
+        });
+        line_fft<P, +1, 1, LAY>(v, sf, a.tw, t, gsync);
+        gsync();
+        if (gt == 0) issue(k + D);  // slot fully consumed: refill it
+        if (act) {
+            float2 *fw = a.field + ((size_t)item * ny + y) * NX;
+            static_for<0, E>([&](auto ec) {
+                constexpr int e = decltype(ec)::value;
+                fw[t + TL * e] = v[e];
+            });
+        }
+        if (a.part)
+            group_sum4<GT>(acc0, acc1, acc2, acc3, red + (size_t)g * Cfg::GW * NMET,
+                           a.part + ((size_t)item * ppt + pan) * NMET, gt, gsync);
+    }
+}
+
+// ----------------------------------------------------------- column pass
+template <class P, int C, int NG, int D, int SWZ, int BOXR>
+struct ColPipeCfg {
+    static constexpr int GT = P::TL * C;
+    static_assert(GT % 32 == 0, "column group must be whole warps");
+    static_assert(P::N % BOXR == 0 && BOXR <= 256, "box rows must tile the column");
+    static constexpr int THREADS = NG * GT;
+    static constexpr int SLOT = P::N * C * 8;
+    static constexpr size_t SMEM = 1024 + (size_t)NG * D * SLOT + NG * D * 8 + 4 * (NG + 1) + 256;
+};
+
+template <class P, int ROLE, int C, int NG, int D, int SWZ, int BOXR>
+__global__ void __launch_bounds__(ColPipeCfg<P, C, NG, D, SWZ, BOXR>::THREADS, 1)
+    k_col_pipe(const ColArgs a, const PipeArgs pa, const __grid_constant__ CUtensorMap tmap) {
+    using Cfg = ColPipeCfg<P, C, NG, D, SWZ, BOXR>;
+    using LAY = Swz<SWZ>;
+    constexpr int TL = P::TL, E = P::E, NY = P::N, GT = Cfg::GT;
+    extern __shared__ unsigned char smraw[];
+    unsigned char *base = smraw + ((1024 - (smem_addr(smraw) & 1023)) & 1023);
+    uint64_t *full = reinterpret_cast<uint64_t *>(base + (size_t)NG * D * Cfg::SLOT);
+    volatile int *flags = reinterpret_cast<volatile int *>(full + NG * D);
+    volatile int *abort = flags + NG;
+
+    const int tid = threadIdx.x;
+    if (tid == 0) {
+        for (int i = 0; i < NG * D; ++i) mbar_init(full + i, 1);
+        *abort = 0;
+        fence_mbar_init();
+    }
+    __syncthreads();
+
+    const int nx = a.nx;
+    const int ppt = (nx + C - 1) / C;
+    const int J = a.items * ppt;
+    const int g = tid / GT, gt = tid - g * GT;
+    const int c = gt % C, t = gt / C;
+    unsigned char *ring = base + (size_t)g * D * Cfg::SLOT;
+    uint64_t *gfull = full + g * D;
+    auto gsync = [g]() { named_sync(1 + g, GT); };
+    auto job = [&](int k) { return (int)blockIdx.x + (g + NG * k) * (int)gridDim.x; };
+    auto issue = [&](int k) {  // copy the group's k-th panel: C columns, all rows
+        const int j = job(k);
+        if (j >= J || j == pa.drop_job) return;
+        const int item = j / ppt, pan = j - item * ppt;
+        unsigned char *sl = ring + (size_t)(k % D) * Cfg::SLOT;
+        mbar_expect_tx(gfull + k % D, (uint32_t)Cfg::SLOT);
+#pragma unroll 1
+        for (int r = 0; r < NY / BOXR; ++r)
+            tma_load_2d(sl + (size_t)r * BOXR * C * 8, &tmap, 2 * pan * C, item * NY + r * BOXR,
+                        gfull + k % D);
+    };
+    auto drain = [&](int k0, int k1) {
+        for (int q = k0; q < k1; ++q) {
+            const int j = job(q);
+            if (j < J && j != pa.drop_job) mbar_wait(gfull + q % D, (q / D) & 1, pa.wait_ns, nullptr);
+        }
+    };
+    if (gt == 0)
+        for (int k = 0; k < D; ++k) issue(k);
+
+    for (int k = 0;; ++k) {
+        const int j = job(k);
+        if (j >= J) break;
+        if (gt == 0) {
+            bool ok = !*abort && mbar_wait(gfull + k % D, (k / D) & 1, pa.wait_ns, abort);
+            if (!ok) {
+                atomicOr(pa.err, ERR_TIMEOUT_BIT);
+                *abort = 1;
+            }
+            flags[g] = ok;
+        }
+        gsync();
+        if (!flags[g]) {
+            if (gt == 0) drain(k, k + D);
+            break;
+        }
+        const int item = j / ppt, pan = j - item * ppt;
+        const int x = pan * C + c;
+        const bool act = x < nx;
+        float2 *sl = reinterpret_cast<float2 *>(ring + (size_t)(k % D) * Cfg::SLOT);
+        float2 v[E];
+        static_for<0, E>([&](auto ec) {
+            constexpr int e = decltype(ec)::value;
+            v[e] = sl[(t + TL * e) * C + c];
+        });
+        line_fft<P, +1, C, LAY>(v, sl + c, a.tw, t, gsync);
+        const size_t base_o = (size_t)item * NY * nx;
+        static_for<0, E>([&](auto ec) {
+            constexpr int e = decltype(ec)::value;
+            const int o = (t + TL * e) * nx + x;
+            const float2 h = v[e];
+            int q;
+            float2 ph;
+            if constexpr (ROLE == COL_GS_BIN) {
+                q = h.x >= 0.f ? 0 : 1;
+                ph = make_float2(q ? -1.f : 1.f, 0.f);
+            } else {
+                q = (int)roundf(atan2f(h.y, h.x) * a.qscale) % a.levels;
+                if (q < 0) q += a.levels;
+                ph = __ldg(a.lvl + q);
+            }
+            if (act) {
+                if (a.h_out) a.h_out[base_o + o] = make_float2(h.x * a.invSqrtN, h.y * a.invSqrtN);
+                if (a.holo) a.holo[base_o + o] = (uint8_t)q;
+            }
+            v[e] = ph;
+        });
+        line_fft<P, -1, C, LAY>(v, sl + c, a.tw, t, gsync);
+        gsync();
+        if (gt == 0) issue(k + D);  // slot fully consumed: refill it
+        if (act) {
+            float2 *fw = a.field + base_o + x;
+            static_for<0, E>([&](auto ec) {
+                constexpr int e = decltype(ec)::value;
+                fw[(t + TL * e) * nx] = v[e];
+            });
+        }
+    }
+}
+
+// --------------------------------------------------------- dispatch glue
+
+struct PipeOps {
+    int N;
+    int row_threads, col_threads, col_c, col_boxr, row_lines;
+    size_t row_smem, col_smem;
+    int row_blocks_per_sm, col_blocks_per_sm;
+    cudaError_t (*init)(PipeOps *self);
+    void (*row_iter)(const RowArgs &a, const PipeArgs &pa, int grid, cudaStream_t s);  // may be null
+    void (*col_gs)(int role, const ColArgs &a, const PipeArgs &pa, const CUtensorMap &m, int grid,
+                   cudaStream_t s);  // may be null
+};
+
+// Row pass: plan P, LINES rows per group, NGR groups, ring depth DR, swizzle
+// SWZR (LINES == 0: no TMA-fed row pass).  Column pass: plan PC, C columns per
+// group, NGC groups, ring depth DC, swizzle SWZC, BOXR rows per tensor copy.
+template <class P, int LINES, int NGR, int DR, int SWZR, class PC, int C, int NGC, int DC, int SWZC,
+          int BOXR>
+struct PipeImpl {
+    using CC = ColPipeCfg<PC, C, NGC, DC, SWZC, BOXR>;
+    static cudaError_t init(PipeOps *self) {
+        cudaError_t e = cudaSuccess;
+        int rb = 1, cb = 0;
+        if constexpr (LINES > 0) {
+            using RC = RowPipeCfg<P, LINES, NGR, DR, SWZR>;
+            e = cudaFuncSetAttribute((const void *)k_row_pipe<P, LINES, NGR, DR, SWZR>,
+                                     cudaFuncAttributeMaxDynamicSharedMemorySize, (int)RC::SMEM);
+            if (e == cudaSuccess)
+                e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+                    &rb, k_row_pipe<P, LINES, NGR, DR, SWZR>, RC::THREADS, RC::SMEM);
+        }
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute((const void *)k_col_pipe<PC, COL_GS_BIN, C, NGC, DC, SWZC, BOXR>,
+                                     cudaFuncAttributeMaxDynamicSharedMemorySize, (int)CC::SMEM);
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute((const void *)k_col_pipe<PC, COL_GS_LVL, C, NGC, DC, SWZC, BOXR>,
+                                     cudaFuncAttributeMaxDynamicSharedMemorySize, (int)CC::SMEM);
+        if (e == cudaSuccess)
+            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+                &cb, k_col_pipe<PC, COL_GS_BIN, C, NGC, DC, SWZC, BOXR>, CC::THREADS, CC::SMEM);
+        if (e != cudaSuccess) return e;
+        if (rb < 1 || cb < 1) return cudaErrorInvalidConfiguration;
+        self->row_blocks_per_sm = rb;
+        self->col_blocks_per_sm = cb;
+        return cudaSuccess;
+    }
+    static void row_iter(const RowArgs &a, const PipeArgs &pa, int grid, cudaStream_t s) {
+        if constexpr (LINES > 0) {
+            using RC = RowPipeCfg<P, LINES, NGR, DR, SWZR>;
+            k_row_pipe<P, LINES, NGR, DR, SWZR><<<grid, RC::THREADS, RC::SMEM, s>>>(a, pa);
+        }
+    }
+    static void col_gs(int role, const ColArgs &a, const PipeArgs &pa, const CUtensorMap &m, int grid,
+                       cudaStream_t s) {
+        if (role == COL_GS_BIN)
+            k_col_pipe<PC, COL_GS_BIN, C, NGC, DC, SWZC, BOXR><<<grid, CC::THREADS, CC::SMEM, s>>>(a, pa, m);
+        else
+            k_col_pipe<PC, COL_GS_LVL, C, NGC, DC, SWZC, BOXR><<<grid, CC::THREADS, CC::SMEM, s>>>(a, pa, m);
+    }
+    static PipeOps make() {
+        PipeOps o{};
+        o.N = P::N;
+        o.col_threads = CC::THREADS;
+        o.col_c = C;
+        o.col_boxr = BOXR;
+        o.col_smem = CC::SMEM;
+        o.row_lines = LINES;
+        if constexpr (LINES > 0) {
+            using RC = RowPipeCfg<P, LINES, NGR, DR, SWZR>;
+            o.row_threads = RC::THREADS;
+            o.row_smem = RC::SMEM;
+            o.row_iter = &row_iter;
+        }
+        o.init = &init;
+        o.col_gs = &col_gs;
+        return o;
+    }
+};
+
+const PipeOps *pipe_ops_mid(int n);
+const PipeOps *pipe_ops_1024(int n);
+const PipeOps *pipe_ops_2048(int n);
+const PipeOps *pipe_ops_hd(int n);
+
+}  // namespace hg

@@ -1,7 +1,7 @@
 // Transform plans for the 1080 x 1920 display format (radix 2/3/5):
 // 1080 = 30 x 6 x 6 (36 threads per line), 1920 = 30 x 8 x 8 (64 threads per
 // line; its last stage returns through shared memory).
-#include "hg_kernels.cuh"
+#include "hg_pipe.cuh"
 
 namespace hg {
 namespace {
@@ -16,4 +16,7 @@ const LineOps *ops_hd(int n) {
         default: return nullptr;
     }
 }
+
+// The display-format lengths use the generic passes only.
+const PipeOps *pipe_ops_hd(int) { return nullptr; }
 }  // namespace hg

@@ -32,7 +32,7 @@ class HgError(RuntimeError):
 
 class hg_opts(ctypes.Structure):
     _fields_ = [("stream", ctypes.c_void_p), ("seed", ctypes.c_uint64), ("subframes", ctypes.c_int),
-                ("precision", ctypes.c_int), ("use_graph", ctypes.c_int)]
+                ("precision", ctypes.c_int), ("use_graph", ctypes.c_int), ("pipeline", ctypes.c_int)]
 
 
 class hg_slm(ctypes.Structure):
@@ -65,6 +65,14 @@ def lib():
         L.hg_sync.argtypes = [P]
         L.hg_last_launch_count.argtypes = [P]
         L.hg_last_launch_count.restype = I
+        L.hg_pipelined.argtypes = [P]
+        L.hg_pipelined.restype = I
+        L.hg_debug_inject.argtypes = [P, I, ctypes.c_uint64]
+        L.hg_debug_inject.restype = I
+        L.hg_profile_enable.argtypes = [P, I]
+        L.hg_profile_enable.restype = I
+        L.hg_profile_read.argtypes = [P, P]
+        L.hg_profile_read.restype = I
         L.hg_plan_destroy.argtypes = [P]
         L.hg_plan_destroy.restype = None
         L.hg_status_string.argtypes = [I]
@@ -104,7 +112,7 @@ def hg_status_string(st: int) -> str:
 
 
 def hg_plan_create(ny, nx, batch, slm_kind=HG_SLM_BINARY, levels=2, algo=HG_GS, stream=None,
-                   seed=0, subframes=24, precision=0, use_graph=True):
+                   seed=0, subframes=24, precision=0, use_graph=True, pipeline=-1):
     o = hg_opts()
     lib().hg_opts_default(ctypes.byref(o))
     if stream is None and torch.cuda.is_available():
@@ -114,6 +122,7 @@ def hg_plan_create(ny, nx, batch, slm_kind=HG_SLM_BINARY, levels=2, algo=HG_GS, 
     o.subframes = int(subframes)
     o.precision = int(precision)
     o.use_graph = 1 if use_graph else 0
+    o.pipeline = int(pipeline)
     h = ctypes.c_void_p()
     _ck(lib().hg_plan_create(ctypes.byref(h), int(ny), int(nx), int(batch),
                              hg_slm(int(slm_kind), int(levels)), int(algo), ctypes.byref(o)),
@@ -166,6 +175,25 @@ def hg_sync(plan):
 
 def hg_last_launch_count(plan) -> int:
     return lib().hg_last_launch_count(plan)
+
+
+def hg_pipelined(plan) -> int:
+    return lib().hg_pipelined(plan)
+
+
+def hg_debug_inject(plan, drop_job, wait_ns):
+    _ck(lib().hg_debug_inject(plan, int(drop_job), int(wait_ns)), "hg_debug_inject")
+
+
+def hg_profile_enable(plan, max_passes):
+    _ck(lib().hg_profile_enable(plan, int(max_passes)), "hg_profile_enable")
+
+
+def hg_profile_read(plan):
+    """{row ms, row passes, column ms, column passes} since the last read."""
+    out = (ctypes.c_double * 4)()
+    _ck(lib().hg_profile_read(plan, ctypes.cast(out, ctypes.c_void_p)), "hg_profile_read")
+    return list(out)
 
 
 def hg_plan_destroy(plan):

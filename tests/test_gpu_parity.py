@@ -301,3 +301,63 @@ def test_errors_are_status_codes():
     plan.run(torch.ones((1, 16, 16), device=DEV), None, 2)  # the plan stays usable
     plan.sync()
     plan.close()
+
+
+@pytest.mark.parametrize("n,batch,kind,levels", [(256, 3, hg.HG_SLM_BINARY, 2), (512, 2, hg.HG_SLM_LLEVEL, 256),
+                                                 (1024, 2, hg.HG_SLM_BINARY, 2), (2048, 1, hg.HG_SLM_BINARY, 2),
+                                                 (1024, 1, hg.HG_SLM_LLEVEL, 256)])
+def test_pipelined_passes_equal_generic(n, batch, kind, levels):
+    """The TMA-fed passes carry out the same iteration as the generic ones.
+    Where both use the same radix plan (256, 512, 1024) results agree to float
+    rounding; at 2048 the plans differ (16 x 16 x 8 vs 32 x 8 x 8), so a few
+    boundary pixels flip in the first iteration and binary GS spreads the
+    difference.  Checked: iteration-0 metrics to 1e-5, final holograms differ
+    in at most 0.2% of pixels (a wrong transform flips about half), final MSE
+    within 1% of the oracle."""
+    t = torch.from_numpy(synth.targets(batch, n, n)).to(DEV)
+    ph = torch.from_numpy(synth.init_phases(batch, n, n)).to(DEV)
+    out = {}
+    for pipe in (0, 1):
+        plan = hg.Plan(n, n, batch, kind, levels, hg.HG_GS, pipeline=pipe)
+        assert hg.hg_pipelined(plan.h) == (3 if pipe else 0)
+        holo = torch.empty((batch, n, n), dtype=torch.uint8, device=DEV)
+        mse = torch.empty((batch, 4), dtype=torch.float64, device=DEV)
+        plan.run(t, ph, 4, holo, mse)
+        plan.sync()
+        out[pipe] = (holo.cpu().numpy(), mse.cpu().numpy(), plan.metrics().cpu().numpy())
+        plan.close()
+    same_plan = n != 2048
+    limit = max(2, 1e-5 * out[0][0].size) if same_plan else 2e-3 * out[0][0].size
+    assert np.sum(out[0][0] != out[1][0]) <= limit
+    assert np.allclose(out[0][1][:, 0], out[1][1][:, 0], rtol=1e-5, atol=0)
+    assert np.allclose(out[0][2][:, 0, 1:], out[1][2][:, 0, 1:], rtol=1e-5)
+    if same_plan:
+        assert np.allclose(out[0][1], out[1][1], rtol=1e-6, atol=0)
+    o = oracle.gs_run(synth.targets(1, n, n)[0], synth.init_phases(1, n, n)[0].astype(np.float64), 4,
+                      kind=ok_kind(kind), levels=levels)
+    assert abs(out[1][1][0, -1] - o["mse"][-1]) <= 0.01 * o["mse"][-1]
+
+
+def test_bounded_wait_reports_timeout_and_plan_recovers():
+    """Fault injection on the host side: the producer never issues one copy,
+    the consumer's bounded wait (0.2 s) runs out, the kernels stop and hg_sync
+    returns HG_ERR_TIMEOUT; the context and the plan stay usable."""
+    n, batch = 256, 2
+    t = synth.targets(batch, n, n)
+    ph = synth.init_phases(batch, n, n)
+    plan = hg.Plan(n, n, batch, pipeline=1)
+    T = torch.from_numpy(t).to(DEV)
+    P = torch.from_numpy(ph).to(DEV)
+    hg.hg_debug_inject(plan.h, 3, 200_000_000)
+    plan.run(T, P, 2)
+    with pytest.raises(hg.HgError) as e:
+        plan.sync()
+    assert e.value.status == 5
+    hg.hg_debug_inject(plan.h, -1, 2_000_000_000)
+    mse = torch.empty((batch, 2), dtype=torch.float64, device=DEV)
+    plan.run(T, P, 2, None, mse)
+    plan.sync()
+    plan.close()
+    for b in range(batch):
+        o = oracle.gs_run(t[b], ph[b].astype(np.float64), 2)
+        assert np.allclose(mse[b].cpu().numpy(), o["mse"], rtol=1e-4)
