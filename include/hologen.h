@@ -75,10 +75,14 @@ typedef struct {
     int use_graph;     /* 1 = replay the iteration loop as a CUDA graph (default) */
     int pipeline;      /* -1 auto (default): TMA-fed passes where the size allows;
                           0: generic passes only; 1: require TMA-fed passes */
+    int autotune;      /* 1 (default): time the candidate pass variants on the plan's
+                          own buffers at creation and keep the fastest (cached per
+                          device and shape); 0: first candidate; 2 + k: candidate k
+                          for both passes (HG_ERR_UNSUPPORTED_SIZE if absent) */
 } hg_opts;
 
 /* Fills *opts with the defaults: stream NULL, seed 0, subframes 24,
- * precision 0, use_graph 1, pipeline -1. */
+ * precision 0, use_graph 1, pipeline -1, autotune 1. */
 void hg_opts_default(hg_opts *opts);
 
 /* 1 if a line of n samples (a row of nx or a column of ny) has a compiled
@@ -164,6 +168,11 @@ int hg_last_launch_count(hg_plan plan);
 /* Bit 0: the row pass of the iteration runs the TMA-fed kernel; bit 1: the
  * column pass does (hg_opts.pipeline, sizes and alignment decide). */
 int hg_pipelined(hg_plan plan);
+
+/* Name of the variant running the row (pass 0) or column (pass 1) pass of
+ * the iteration loop ("generic" or the TMA-fed plan's radix/threads tag).
+ * The string is static; NULL plan gives "". */
+const char *hg_plan_variant(hg_plan plan, int pass);
 
 /* Per-pass timing (diagnostics; no counterpart in the paper).
  * hg_profile_enable(plan, n) makes the next runs record a CUDA event pair on

@@ -26,20 +26,22 @@ static_assert(ERR_TIMEOUT_BIT == 4u, "error bits must be distinct");
 constexpr int PREP_THREADS = 256;
 constexpr int PREP_BLOCKS = 64;  // per target
 
-// Partial sums of T^2 per (target, block) in double, fixed order; flags
+// Partial sums of T^2 per (target, block), fixed order: each thread sums its
+// strided elements in float, threads and warps combine in double.  Flags
 // negative, NaN and infinite values.
 __global__ void __launch_bounds__(PREP_THREADS)
 k_prep_sum(const float *__restrict__ t_raw, int npx, double *part, unsigned *err) {
     __shared__ double red[PREP_THREADS / 32];
     const int b = blockIdx.y;
     const float *tb = t_raw + (size_t)b * npx;
-    double s = 0;
+    float sf = 0.f;
     bool bad = false;
     for (int i = blockIdx.x * PREP_THREADS + threadIdx.x; i < npx; i += PREP_BLOCKS * PREP_THREADS) {
         const float v = tb[i];
         if (!(v >= 0.f) || isinf(v)) bad = true;
-        s += (double)v * (double)v;
+        sf = fmaf(v, v, sf);
     }
+    double s = sf;
     if (bad) atomicOr(err, ERR_BAD_VALUE);
     for (int off = 16; off; off >>= 1) s += __shfl_down_sync(0xffffffffu, s, off);
     if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
@@ -77,7 +79,7 @@ __global__ void k_prep_apply(const float *__restrict__ t_raw, int ny, int nx, in
         const int y = rem / nx, x = rem - y * nx;
         const int iy = (y + ny / 2) % ny, ix = (x + nx / 2) % nx;
         const float v = t_raw[(size_t)b * npx + (size_t)iy * nx + ix];
-        float tv = (float)((double)v * scale[b]);
+        float tv = v * (float)scale[b];
         // keep the support {T > 0} of the input exactly: a positive value whose
         // scaled float underflows becomes the smallest positive float
         if (v > 0.f && !(tv > 0.f)) tv = __int_as_float(1);
@@ -113,14 +115,19 @@ __global__ void k_fill(float *p, size_t n, float v) {
 // {sum d^2 / N, sum a^2 / N, in / total, total}; also mse_out[b][k].
 __global__ void k_reduce(const double *part, int iters, int batch, int stride, int panels,
                          int panels_last, double invN, double *metrics, double *mse_out) {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= iters * batch) return;
-    const int k = i / batch, b = i - k * batch;
+    // one warp per (iteration, target): lane l sums panels l, l+32, ...; the
+    // 32 lane sums are combined by a fixed shuffle tree
+    const int w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+    if (w >= iters * batch) return;
+    const int k = w / batch, b = w - k * batch;
     const int np = k == iters - 1 ? panels_last : panels;
     const double *p = part + ((size_t)k * batch * stride + (size_t)b * np) * NMET;
     double s[NMET] = {0, 0, 0, 0};
-    for (int q = 0; q < np; ++q)
+    for (int q = lane; q < np; q += 32)
         for (int m = 0; m < NMET; ++m) s[m] += p[(size_t)q * NMET + m];
+    for (int off = 16; off; off >>= 1)
+        for (int m = 0; m < NMET; ++m) s[m] += __shfl_down_sync(0xffffffffu, s[m], off);
+    if (lane) return;
     double *o = metrics + ((size_t)b * iters + k) * NMET;
     o[0] = s[0] * invN;
     o[1] = s[1] * invN;
@@ -140,13 +147,21 @@ const LineOps *find_ops(int n) {
     return o;
 }
 
-const PipeOps *find_pipe(int n) {
-    const PipeOps *o = pipe_ops_mid(n);
-    if (!o) o = pipe_ops_1024(n);
-    if (!o) o = pipe_ops_2048(n);
-    if (!o) o = pipe_ops_hd(n);
-    return o;
+int pipe_candidates(int n, const PipeOps **out, int max) {
+    int k = pipe_ops_mid(n, out, max);
+    if (!k) k = pipe_ops_1024(n, out, max);
+    if (!k) k = pipe_ops_2048(n, out, max);
+    if (!k) k = pipe_ops_hd(n, out, max);
+    return k;
 }
+
+// Autotuner cache: (device, ny, nx, items, slm kind) -> chosen candidates.
+struct TuneEntry {
+    int dev, ny, nx, items, kind;
+    const PipeOps *row, *col;
+};
+std::mutex g_tune_mu;
+std::vector<TuneEntry> g_tune;
 
 std::mutex g_init_mu;
 constexpr int kMaxDev = 64;
@@ -215,6 +230,7 @@ struct hg_plan_s {
     int use_graph = 1;
     const LineOps *rops = nullptr, *cops = nullptr;
     const PipeOps *prow = nullptr, *pcol = nullptr;  // pipelined passes (null: generic)
+    float tune_ms[8] = {0};                          // autotuner timings: row cands, col cands
     CUtensorMap cmap;                                // field as [chains*ny][2*nx] floats
     unsigned long long wait_ns = 2000000000ull;      // bound on a device-side wait
     int drop_job = -1;                               // fault-injection hook
@@ -487,6 +503,56 @@ hg_status check_err_flag(hg_plan p) {
     return HG_OK;
 }
 
+bool make_cmap(hg_plan p, const PipeOps *pc, CUtensorMap *m) {
+    EncodeTiledFn enc = encode_tiled();
+    if (!enc) return false;
+    const cuuint64_t gdim[2] = {(cuuint64_t)2 * p->nx, (cuuint64_t)p->ny * p->nchains};
+    const cuuint64_t gstride[1] = {(cuuint64_t)p->nx * 8};
+    const cuuint32_t box[2] = {(cuuint32_t)(2 * pc->col_c), (cuuint32_t)pc->col_boxr};
+    const cuuint32_t estr[2] = {1, 1};
+    return enc(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, p->field, gdim, gstride, box, estr,
+               CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+               CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+// Best-of-3 launch time (ms, after one warm-up launch) of one pass variant on
+// the plan's own zeroed buffers, on the private capture stream.
+float time_variant(hg_plan p, const PipeOps *o, bool row) {
+    if (!p->field || !p->tf || !p->twx || !p->twy || !p->lvl || !p->err) return 1e30f;
+    cudaStream_t s = p->cap_stream;
+    RowArgs ra = row_args(p);
+    ra.w = nullptr;
+    ra.part = nullptr;
+    ColArgs ca = col_args(p);
+    CUtensorMap m;
+    if (!row && !make_cmap(p, o, &m)) return 1e30f;
+    const int ppt = row ? (p->ny + o->row_lines - 1) / o->row_lines : (p->nx + o->col_c - 1) / o->col_c;
+    const int grid = grid_for(row ? o->row_blocks_per_sm : o->col_blocks_per_sm, p->nsm,
+                              (long)p->batch * ppt);
+    PipeArgs pa = pipe_args(p);
+    cudaEvent_t e0, e1;
+    if (cudaEventCreate(&e0) != cudaSuccess) return 1e30f;
+    if (cudaEventCreate(&e1) != cudaSuccess) {
+        cudaEventDestroy(e0);
+        return 1e30f;
+    }
+    float best = 1e30f;
+    for (int it = 0; it < 4; ++it) {
+        cudaEventRecord(e0, s);
+        if (row) o->row_iter(ra, pa, grid, s);
+        else o->col_gs(p->kind == HG_SLM_BINARY ? COL_GS_BIN : COL_GS_LVL, ca, pa, m, grid, s);
+        cudaEventRecord(e1, s);
+        if (cudaEventSynchronize(e1) != cudaSuccess) break;
+        float ms = 0;
+        cudaEventElapsedTime(&ms, e0, e1);
+        if (it > 0 && ms < best) best = ms;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (cudaGetLastError() != cudaSuccess) return 1e30f;
+    return best;
+}
+
 struct DevGuard {
     int prev = -1;
     explicit DevGuard(int dev) {
@@ -511,6 +577,7 @@ void hg_opts_default(hg_opts *o) {
     o->subframes = 24;
     o->use_graph = 1;
     o->pipeline = -1;
+    o->autotune = 1;
 }
 
 int hg_supported_length(int n) { return find_ops(n) != nullptr; }
@@ -596,31 +663,9 @@ hg_status hg_plan_create(hg_plan *out, int ny, int nx, int batch, hg_slm slm, hg
     if (ce == cudaSuccess) ce = cudaStreamCreateWithFlags(&p->cap_stream, cudaStreamNonBlocking);
     if (ce != cudaSuccess) return fail(map_err(ce));
     ce = cudaMalloc(&p->field, sizeof(float2) * npx * p->nchains);
-    if (ce != cudaSuccess) return fail(map_err(ce));
-    if (o.pipeline != 0) {
-        // TMA-fed passes: row panels need 16-byte aligned rows of T (nx % 4 == 0);
-        // the column tiles need a 16-byte multiple row pitch (nx even).
-        const PipeOps *pr = find_pipe(nx), *pc = find_pipe(ny);
-        if (pr && pr->row_iter && nx % 4 == 0 && ensure_pipe_init(p->dev, pr) == cudaSuccess) {
-            p->prow = pr;
-            p->ppt_pipe = (ny + pr->row_lines - 1) / pr->row_lines;
-            if (p->ppt_pipe > p->ppt_max) p->ppt_max = p->ppt_pipe;
-        }
-        EncodeTiledFn enc = encode_tiled();
-        if (pc && pc->col_gs && nx % 2 == 0 && enc && ensure_pipe_init(p->dev, pc) == cudaSuccess) {
-            const cuuint64_t gdim[2] = {(cuuint64_t)2 * nx, (cuuint64_t)ny * p->nchains};
-            const cuuint64_t gstride[1] = {(cuuint64_t)nx * 8};
-            const cuuint32_t box[2] = {(cuuint32_t)(2 * pc->col_c), (cuuint32_t)pc->col_boxr};
-            const cuuint32_t estr[2] = {1, 1};
-            if (enc(&p->cmap, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, p->field, gdim, gstride, box, estr,
-                    CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
-                    CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
-                    CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS)
-                p->pcol = pc;
-        }
-        if (o.pipeline == 1 && (!p->prow || !p->pcol)) return fail(HG_ERR_UNSUPPORTED_SIZE);
-    }
     if (ce == cudaSuccess) ce = cudaMalloc(&p->tf, sizeof(float) * npx * batch);
+    if (ce != cudaSuccess) return fail(map_err(ce));
+
     if (ce == cudaSuccess && algo == HG_WGS) ce = cudaMalloc(&p->w, sizeof(float) * npx * batch);
     if (ce == cudaSuccess) ce = cudaMalloc(&p->sum_part, sizeof(double) * PREP_BLOCKS * batch);
     if (ce == cudaSuccess) ce = cudaMalloc(&p->scale, sizeof(double) * batch);
@@ -641,6 +686,74 @@ hg_status hg_plan_create(hg_plan *out, int ny, int nx, int batch, hg_slm slm, hg
         ce = cudaMalloc(&p->lvl, sizeof(float2) * L);
         if (ce == cudaSuccess) ce = cudaMemcpy(p->lvl, h, sizeof(float2) * L, cudaMemcpyHostToDevice);
         if (ce != cudaSuccess) return fail(map_err(ce));
+    }
+    // Pass variants are chosen (and timed) only once every buffer they touch exists.
+    if (o.pipeline != 0) {
+        // TMA-fed passes: row panels need 16-byte aligned rows of T (nx % 4 == 0);
+        // the column tiles need a 16-byte multiple row pitch (nx even).
+        const PipeOps *rc[4], *cc[4];
+        int nr = 0, nc = 0;
+        {
+            const PipeOps *all[4];
+            const int k = pipe_candidates(nx, all, 4);
+            for (int i = 0; i < k; ++i)
+                if (all[i]->row_iter && nx % 4 == 0 && ensure_pipe_init(p->dev, all[i]) == cudaSuccess)
+                    rc[nr++] = all[i];
+        }
+        {
+            const PipeOps *all[4];
+            const int k = pipe_candidates(ny, all, 4);
+            CUtensorMap m;
+            for (int i = 0; i < k; ++i)
+                if (all[i]->col_gs && nx % 2 == 0 && ensure_pipe_init(p->dev, all[i]) == cudaSuccess &&
+                    make_cmap(p, all[i], &m))
+                    cc[nc++] = all[i];
+        }
+        const PipeOps *row = nr ? rc[0] : nullptr, *col = nc ? cc[0] : nullptr;
+        if (o.autotune >= 2) {  // forced candidate (tests, benchmarks of one variant)
+            const int k = o.autotune - 2;
+            if (k >= nr || k >= nc) return fail(HG_ERR_UNSUPPORTED_SIZE);
+            row = rc[k];
+            col = cc[k];
+        } else if (o.autotune == 1 && (nr > 1 || nc > 1)) {
+            bool cached = false;
+            {
+                std::lock_guard<std::mutex> lk(g_tune_mu);
+                for (const TuneEntry &t : g_tune)
+                    if (t.dev == p->dev && t.ny == ny && t.nx == nx && t.items == p->nchains &&
+                        t.kind == slm.kind) {
+                        row = t.row;
+                        col = t.col;
+                        cached = true;
+                    }
+            }
+            if (!cached) {
+                ce = cudaMemset(p->field, 0, sizeof(float2) * npx * p->nchains);
+                if (ce == cudaSuccess) ce = cudaMemset(p->tf, 0, sizeof(float) * npx * batch);
+                if (ce != cudaSuccess) return fail(map_err(ce));
+                float best = 1e30f;
+                for (int i = 0; i < nr && nr > 1; ++i) {
+                    const float ms = time_variant(p, rc[i], true);
+                    p->tune_ms[i] = ms;
+                    if (ms < best) best = ms, row = rc[i];
+                }
+                best = 1e30f;
+                for (int i = 0; i < nc && nc > 1; ++i) {
+                    const float ms = time_variant(p, cc[i], false);
+                    p->tune_ms[4 + i] = ms;
+                    if (ms < best) best = ms, col = cc[i];
+                }
+                std::lock_guard<std::mutex> lk(g_tune_mu);
+                g_tune.push_back({p->dev, ny, nx, p->nchains, slm.kind, row, col});
+            }
+        }
+        if (row) {
+            p->prow = row;
+            p->ppt_pipe = (ny + row->row_lines - 1) / row->row_lines;
+            if (p->ppt_pipe > p->ppt_max) p->ppt_max = p->ppt_pipe;
+        }
+        if (col && make_cmap(p, col, &p->cmap)) p->pcol = col;
+        if (o.pipeline == 1 && (!p->prow || !p->pcol)) return fail(HG_ERR_UNSUPPORTED_SIZE);
     }
     if ((st = ensure_part(p, algo == HG_OSPR ? 1 : 8)) != HG_OK) return fail(st);
     if ((st = ensure_metrics(p, 1)) != HG_OK) return fail(st);
@@ -699,6 +812,12 @@ hg_status hg_profile_read(hg_plan p, double *out4) {
     memcpy(out4, acc, sizeof acc);
     p->prof_used = 0;
     return HG_OK;
+}
+
+const char *hg_plan_variant(hg_plan p, int pass) {
+    if (!p) return "";
+    const PipeOps *o = pass == 0 ? p->prow : p->pcol;
+    return o ? o->name : "generic";
 }
 
 int hg_pipelined(hg_plan p) { return p ? (p->prow ? 1 : 0) | (p->pcol ? 2 : 0) : 0; }
@@ -778,7 +897,7 @@ hg_status hg_run(hg_plan p, const float *target, const float *init_phase, int it
         rt.part = p->part + (size_t)(iters - 1) * p->batch * p->ppt_max * NMET;
         launch_row(p, ROW_TAIL, rt, p->stream);
     }
-    k_reduce<<<(iters * p->batch + 127) / 128, 128, 0, p->stream>>>(
+    k_reduce<<<(iters * p->batch * 32 + 127) / 128, 128, 0, p->stream>>>(
         p->part, iters, p->batch, p->ppt_max, p->prow ? p->ppt_pipe : p->ppt, p->ppt,
         1.0 / (double)p->npx, p->metrics, d_mo);
     p->launches++;
@@ -928,7 +1047,7 @@ hg_status hg_debug_step(hg_plan p, const float *target, const float *phase_in, f
     rt.part = p->part;
     rt.R_out = (float2 *)replay_out;
     launch_row(p, ROW_TAIL, rt, p->stream);
-    k_reduce<<<(p->batch + 127) / 128, 128, 0, p->stream>>>(p->part, 1, p->batch, p->ppt_max,
+    k_reduce<<<(p->batch * 32 + 127) / 128, 128, 0, p->stream>>>(p->part, 1, p->batch, p->ppt_max,
                                                              p->ppt, p->ppt, 1.0 / (double)p->npx,
                                                              p->metrics, nullptr);
     p->launches++;

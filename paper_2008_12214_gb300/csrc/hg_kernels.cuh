@@ -133,7 +133,9 @@ __global__ void __launch_bounds__(P::TL *LINES) k_row(const RowArgs a) {
                 if (wr) amp *= wr[x];
                 float s, c;
                 if (a.phase) {
-                    sincosf(__ldg(a.phase + ((size_t)b * ny + iy) * NX + ix), &s, &c);
+                    // phase in half-turns: the reduction is exact, no large-argument path
+                    sincospif(__ldg(a.phase + ((size_t)b * ny + iy) * NX + ix) * 0.318309886183790672f,
+                              &s, &c);
                 } else {
                     const uint32_t r = philox_word0((uint32_t)(iy * NX + ix), (uint32_t)sub,
                                                     (uint32_t)b, a.stream_id, a.seed_lo, a.seed_hi);

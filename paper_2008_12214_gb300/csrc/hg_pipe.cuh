@@ -395,6 +395,7 @@ __global__ void __launch_bounds__(ColPipeCfg<P, C, NG, D, SWZ, BOXR>::THREADS, 1
 
 struct PipeOps {
     int N;
+    const char *name;
     int row_threads, col_threads, col_c, col_boxr, row_lines;
     size_t row_smem, col_smem;
     int row_blocks_per_sm, col_blocks_per_sm;
@@ -450,9 +451,10 @@ struct PipeImpl {
         else
             k_col_pipe<PC, COL_GS_LVL, C, NGC, DC, SWZC, BOXR><<<grid, CC::THREADS, CC::SMEM, s>>>(a, pa, m);
     }
-    static PipeOps make() {
+    static PipeOps make(const char *name) {
         PipeOps o{};
         o.N = P::N;
+        o.name = name;
         o.col_threads = CC::THREADS;
         o.col_c = C;
         o.col_boxr = BOXR;
@@ -470,9 +472,11 @@ struct PipeImpl {
     }
 };
 
-const PipeOps *pipe_ops_mid(int n);
-const PipeOps *pipe_ops_1024(int n);
-const PipeOps *pipe_ops_2048(int n);
-const PipeOps *pipe_ops_hd(int n);
+// Candidate pipelined variants for a line length (count returned, up to max
+// written); the first is the default when autotuning is off.
+int pipe_ops_mid(int n, const PipeOps **out, int max);
+int pipe_ops_1024(int n, const PipeOps **out, int max);
+int pipe_ops_2048(int n, const PipeOps **out, int max);
+int pipe_ops_hd(int n, const PipeOps **out, int max);
 
 }  // namespace hg

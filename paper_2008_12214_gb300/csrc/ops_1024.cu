@@ -1,14 +1,26 @@
-// Transform plan for 1024-sample lines: 32 x 32, one warp per row, 32
-// samples per thread; the column pass takes 16 columns per CTA.
+// Transform plans for 1024-sample lines.  Generic passes: 32 x 32, one warp
+// per row, 32 samples per thread, 16 columns per CTA.  TMA-fed candidates:
+// 32 x 32 with 32 samples per thread (8 warps per SM), and 16 x 16 x 4 with 16
+// samples per thread (16 warps per SM); the autotuner picks per pass.
 #include "hg_pipe.cuh"
 
 namespace hg {
 namespace {
 LineOps o1024 = OpsImpl<Plan<1024, 32, 32, 32, 32>, 8, 16>::make();
-PipeOps p1024 = PipeImpl<Plan<1024, 32, 32, 32, 32>, 1, 8, 2, 5, Plan<1024, 32, 32, 32, 32>, 8, 1, 3, 5, 256>::make();
+PipeOps p1024a = PipeImpl<Plan<1024, 32, 32, 32, 32>, 1, 8, 2, 5, Plan<1024, 32, 32, 32, 32>, 8, 1, 3, 5,
+                          256>::make("1024:r32x32e32");
+PipeOps p1024b = PipeImpl<Plan<1024, 64, 16, 16, 16, 4>, 1, 8, 2, 4, Plan<1024, 64, 16, 16, 16, 4>, 8, 1, 3,
+                          4, 256>::make("1024:r16x16x4e16");
 }  // namespace
 
 const LineOps *ops_1024(int n) { return n == 1024 ? &o1024 : nullptr; }
 
-const PipeOps *pipe_ops_1024(int n) { return n == 1024 ? &p1024 : nullptr; }
+int pipe_ops_1024(int n, const PipeOps **out, int max) {
+    if (n != 1024) return 0;
+    const PipeOps *c[] = {&p1024a, &p1024b};
+    int k = 0;
+    for (const PipeOps *o : c)
+        if (k < max) out[k++] = o;
+    return k;
+}
 }  // namespace hg

@@ -1,13 +1,25 @@
-// Transform plan for 2048-sample lines: 32 x 8 x 8, 64 threads per line.
+// Transform plans for 2048-sample lines.  Generic passes: 32 x 8 x 8, 64
+// threads per line.  TMA-fed candidates: 16 x 16 x 8 with 16 samples per
+// thread, and 32 x 8 x 8 with 32 samples per thread.
 #include "hg_pipe.cuh"
 
 namespace hg {
 namespace {
 LineOps o2048 = OpsImpl<Plan<2048, 64, 32, 32, 8, 8>, 4, 8>::make();
-PipeOps p2048 = PipeImpl<Plan<2048, 128, 16, 16, 16, 8>, 1, 4, 2, 4, Plan<2048, 128, 16, 16, 16, 8>, 4, 1, 3, 4, 256>::make();
+PipeOps p2048a = PipeImpl<Plan<2048, 128, 16, 16, 16, 8>, 1, 4, 2, 4, Plan<2048, 128, 16, 16, 16, 8>, 4, 1,
+                          3, 4, 256>::make("2048:r16x16x8e16");
+PipeOps p2048b = PipeImpl<Plan<2048, 64, 32, 32, 8, 8>, 1, 4, 2, 5, Plan<2048, 64, 32, 32, 8, 8>, 4, 1, 3,
+                          5, 256>::make("2048:r32x8x8e32");
 }  // namespace
 
 const LineOps *ops_2048(int n) { return n == 2048 ? &o2048 : nullptr; }
 
-const PipeOps *pipe_ops_2048(int n) { return n == 2048 ? &p2048 : nullptr; }
+int pipe_ops_2048(int n, const PipeOps **out, int max) {
+    if (n != 2048) return 0;
+    const PipeOps *c[] = {&p2048a, &p2048b};
+    int k = 0;
+    for (const PipeOps *o : c)
+        if (k < max) out[k++] = o;
+    return k;
+}
 }  // namespace hg

@@ -18,5 +18,5 @@ const LineOps *ops_hd(int n) {
 }
 
 // The display-format lengths use the generic passes only.
-const PipeOps *pipe_ops_hd(int) { return nullptr; }
+int pipe_ops_hd(int, const PipeOps **, int) { return 0; }
 }  // namespace hg

@@ -5,8 +5,12 @@ namespace hg {
 namespace {
 LineOps o256 = OpsImpl<Plan<256, 16, 16, 16, 16>, 16, 16>::make();
 LineOps o512 = OpsImpl<Plan<512, 16, 32, 32, 16>, 16, 16>::make();
-PipeOps p256 = PipeImpl<Plan<256, 16, 16, 16, 16>, 2, 12, 3, 4, Plan<256, 16, 16, 16, 16>, 8, 3, 4, 4, 256>::make();
-PipeOps p512 = PipeImpl<Plan<512, 16, 32, 32, 16>, 2, 8, 2, 5, Plan<512, 16, 32, 32, 16>, 8, 2, 3, 5, 256>::make();
+PipeOps p256 = PipeImpl<Plan<256, 16, 16, 16, 16>, 2, 12, 3, 4, Plan<256, 16, 16, 16, 16>, 8, 3, 4, 4,
+                         256>::make("256:r16x16e16");
+PipeOps p512a = PipeImpl<Plan<512, 16, 32, 32, 16>, 2, 8, 2, 5, Plan<512, 16, 32, 32, 16>, 8, 2, 3, 5,
+                          256>::make("512:r32x16e32");
+PipeOps p512b = PipeImpl<Plan<512, 32, 16, 16, 16, 2>, 1, 16, 2, 4, Plan<512, 32, 16, 16, 16, 2>, 8, 2, 3,
+                          4, 256>::make("512:r16x16x2e16");
 }  // namespace
 
 const LineOps *ops_mid(int n) {
@@ -17,11 +21,13 @@ const LineOps *ops_mid(int n) {
     }
 }
 
-const PipeOps *pipe_ops_mid(int n) {
-    switch (n) {
-        case 256: return &p256;
-        case 512: return &p512;
-        default: return nullptr;
+int pipe_ops_mid(int n, const PipeOps **out, int max) {
+    int k = 0;
+    if (n == 256 && k < max) out[k++] = &p256;
+    if (n == 512) {
+        if (k < max) out[k++] = &p512a;
+        if (k < max) out[k++] = &p512b;
     }
+    return k;
 }
 }  // namespace hg

@@ -32,7 +32,8 @@ class HgError(RuntimeError):
 
 class hg_opts(ctypes.Structure):
     _fields_ = [("stream", ctypes.c_void_p), ("seed", ctypes.c_uint64), ("subframes", ctypes.c_int),
-                ("precision", ctypes.c_int), ("use_graph", ctypes.c_int), ("pipeline", ctypes.c_int)]
+                ("precision", ctypes.c_int), ("use_graph", ctypes.c_int), ("pipeline", ctypes.c_int),
+                ("autotune", ctypes.c_int)]
 
 
 class hg_slm(ctypes.Structure):
@@ -67,6 +68,8 @@ def lib():
         L.hg_last_launch_count.restype = I
         L.hg_pipelined.argtypes = [P]
         L.hg_pipelined.restype = I
+        L.hg_plan_variant.argtypes = [P, I]
+        L.hg_plan_variant.restype = ctypes.c_char_p
         L.hg_debug_inject.argtypes = [P, I, ctypes.c_uint64]
         L.hg_debug_inject.restype = I
         L.hg_profile_enable.argtypes = [P, I]
@@ -112,7 +115,7 @@ def hg_status_string(st: int) -> str:
 
 
 def hg_plan_create(ny, nx, batch, slm_kind=HG_SLM_BINARY, levels=2, algo=HG_GS, stream=None,
-                   seed=0, subframes=24, precision=0, use_graph=True, pipeline=-1):
+                   seed=0, subframes=24, precision=0, use_graph=True, pipeline=-1, autotune=True):
     o = hg_opts()
     lib().hg_opts_default(ctypes.byref(o))
     if stream is None and torch.cuda.is_available():
@@ -123,6 +126,7 @@ def hg_plan_create(ny, nx, batch, slm_kind=HG_SLM_BINARY, levels=2, algo=HG_GS, 
     o.precision = int(precision)
     o.use_graph = 1 if use_graph else 0
     o.pipeline = int(pipeline)
+    o.autotune = int(autotune)
     h = ctypes.c_void_p()
     _ck(lib().hg_plan_create(ctypes.byref(h), int(ny), int(nx), int(batch),
                              hg_slm(int(slm_kind), int(levels)), int(algo), ctypes.byref(o)),
@@ -179,6 +183,10 @@ def hg_last_launch_count(plan) -> int:
 
 def hg_pipelined(plan) -> int:
     return lib().hg_pipelined(plan)
+
+
+def hg_plan_variant(plan, which) -> str:
+    return lib().hg_plan_variant(plan, int(which)).decode()
 
 
 def hg_debug_inject(plan, drop_job, wait_ns):

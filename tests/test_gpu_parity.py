@@ -318,7 +318,7 @@ def test_pipelined_passes_equal_generic(n, batch, kind, levels):
     ph = torch.from_numpy(synth.init_phases(batch, n, n)).to(DEV)
     out = {}
     for pipe in (0, 1):
-        plan = hg.Plan(n, n, batch, kind, levels, hg.HG_GS, pipeline=pipe)
+        plan = hg.Plan(n, n, batch, kind, levels, hg.HG_GS, pipeline=pipe, autotune=0)
         assert hg.hg_pipelined(plan.h) == (3 if pipe else 0)
         holo = torch.empty((batch, n, n), dtype=torch.uint8, device=DEV)
         mse = torch.empty((batch, 4), dtype=torch.float64, device=DEV)
@@ -361,3 +361,34 @@ def test_bounded_wait_reports_timeout_and_plan_recovers():
     for b in range(batch):
         o = oracle.gs_run(t[b], ph[b].astype(np.float64), 2)
         assert np.allclose(mse[b].cpu().numpy(), o["mse"], rtol=1e-4)
+
+
+@pytest.mark.parametrize("n,cand", [(256, 0), (512, 0), (512, 1), (1024, 0), (1024, 1), (2048, 0), (2048, 1)])
+def test_every_pipelined_variant_against_oracle(n, cand):
+    """Each TMA-fed candidate the autotuner may pick, forced in turn: the
+    column pass through a single step, the row pass through the metrics it
+    produces for iterations 0 and 1, and a 4-iteration run's final MSE."""
+    batch = 2
+    t = synth.targets(batch, n, n)
+    ph = synth.init_phases(batch, n, n)
+    plan = hg.Plan(n, n, batch, pipeline=1, autotune=2 + cand)
+    assert hg.hg_pipelined(plan.h) == 3
+    T = torch.from_numpy(t).to(DEV)
+    P = torch.from_numpy(ph).to(DEV)
+    mse = torch.empty((batch, 4), dtype=torch.float64, device=DEV)
+    plan.run(T, P, 4, None, mse)
+    plan.sync()
+    h_out = torch.empty((batch, n, n), dtype=torch.complex64, device=DEV)
+    hg.hg_debug_step(plan.h, T, P, h_out, None, None, None)
+    plan.sync()
+    name = hg.hg_plan_variant(plan.h, 0), hg.hg_plan_variant(plan.h, 1)
+    plan.close()
+    mse, h_out = mse.cpu().numpy(), h_out.cpu().numpy()
+    for b in range(batch):
+        Tn = oracle.prepare_target(t[b])
+        o = oracle.gs_step(Tn, ph[b].astype(np.float64))
+        assert rel_l2(h_out[b], o["h"]) <= 1e-5, (name, rel_l2(h_out[b], o["h"]))
+        run = oracle.gs_run(t[b], ph[b].astype(np.float64), 4)
+        assert abs(mse[b, 0] - run["mse"][0]) <= 1e-4 * run["mse"][0], name
+        assert abs(mse[b, 1] - run["mse"][1]) <= 1e-3 * run["mse"][1], name
+        assert abs(mse[b, 3] - run["mse"][3]) <= 1e-2 * run["mse"][3], name
