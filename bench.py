@@ -44,6 +44,9 @@ def parse():
     ap.add_argument("--iters", type=int, default=50)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--pipeline", type=int, default=-1)
+    ap.add_argument("--autotune", type=int, default=1, help="1 tune, 0 first variant, 2+k variant k")
+    ap.add_argument("--batch", type=int, default=BATCH, help="targets per rank (profiling runs)")
+    ap.add_argument("--quick", action="store_true", help="skip the e2e and CPU-baseline legs")
     return ap.parse_args()
 
 
@@ -107,7 +110,7 @@ def run_reference(args):
     line = dict(impl="reference", metric=METRIC, value=value, unit=UNIT, n_gpus=world, steps=args.steps,
                 warmup=args.warmup, ms_per_step=per * 1e3, higher_is_better=True, scaling="weak",
                 vs_baseline=None, dtype="f64", data=DATA,
-                config=dict(workload="gs_binary_1024x1024_batch64", ny=NY, nx=NX, batch=BATCH,
+                config=dict(workload="gs_binary_1024x1024_batch%d" % B, ny=NY, nx=NX, batch=B,
                             step="one GS iteration of one 1024x1024 target (bounded sample), "
                                  "scaled to 64 targets"),
                 cpu_baseline=dict(kind="oracle", cores=cores, value=value, unit=UNIT,
@@ -198,14 +201,16 @@ def main():
         dist.barrier()
     __graft_entry__.build()
 
-    base = 1000 + rank * BATCH
-    t_host = synth.targets(BATCH, NY, NX, base)
-    p_host = synth.init_phases(BATCH, NY, NX, base)
+    B = args.batch
+    base = 1000 + rank * B
+    t_host = synth.targets(B, NY, NX, base)
+    p_host = synth.init_phases(B, NY, NX, base)
     T = torch.from_numpy(t_host).to(dev)
     P = torch.from_numpy(p_host).to(dev)
-    holo = torch.empty((BATCH, NY, NX), dtype=torch.uint8, device=dev)
-    mse = torch.empty((BATCH, args.iters), dtype=torch.float64, device=dev)
-    plan = hg.Plan(NY, NX, BATCH, hg.HG_SLM_BINARY, 2, hg.HG_GS, pipeline=args.pipeline)
+    holo = torch.empty((B, NY, NX), dtype=torch.uint8, device=dev)
+    mse = torch.empty((B, args.iters), dtype=torch.float64, device=dev)
+    plan = hg.Plan(NY, NX, B, hg.HG_SLM_BINARY, 2, hg.HG_GS, pipeline=args.pipeline,
+                   autotune=args.autotune)
     stream = torch.cuda.current_stream(dev)
 
     for _ in range(args.warmup):
@@ -240,23 +245,27 @@ def main():
     value = world * args.steps * args.iters / (el_ms / 1e3)
 
     # end to end through the C ABI with pinned host buffers (copies inside)
-    tp = torch.from_numpy(t_host).pin_memory()
-    pp = torch.from_numpy(p_host).pin_memory()
-    hp = torch.empty((BATCH, NY, NX), dtype=torch.uint8).pin_memory()
-    mp = torch.empty((BATCH, args.iters), dtype=torch.float64).pin_memory()
-    plan.run(tp, pp, args.iters, hp, mp)
-    e2e_steps = max(2, min(args.steps, 5))
-    if world > 1:
-        dist.barrier()
-    w0 = time.perf_counter()
-    for _ in range(e2e_steps):
+    e2e = None
+    if not args.quick:
+        tp = torch.from_numpy(t_host).pin_memory()
+        pp = torch.from_numpy(p_host).pin_memory()
+        hp = torch.empty((B, NY, NX), dtype=torch.uint8).pin_memory()
+        mp = torch.empty((B, args.iters), dtype=torch.float64).pin_memory()
         plan.run(tp, pp, args.iters, hp, mp)
-    e2e_s = time.perf_counter() - w0
-    if world > 1:
-        t = torch.tensor([e2e_s], device=dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_s = float(t.item())
-    e2e_value = world * e2e_steps * args.iters / e2e_s
+        e2e_steps = max(2, min(args.steps, 5))
+        if world > 1:
+            dist.barrier()
+        w0 = time.perf_counter()
+        for _ in range(e2e_steps):
+            plan.run(tp, pp, args.iters, hp, mp)
+        e2e_s = time.perf_counter() - w0
+        if world > 1:
+            t = torch.tensor([e2e_s], device=dev, dtype=torch.float64)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            e2e_s = float(t.item())
+        e2e = dict(value=world * e2e_steps * args.iters / e2e_s, unit=UNIT,
+                   h2d_bytes_per_step=int(tp.numel() * 4 + pp.numel() * 4),
+                   d2h_bytes_per_step=int(hp.numel() + mp.numel() * 8))
     variants = (hg.hg_plan_variant(plan.h, 0), hg.hg_plan_variant(plan.h, 1))
     plan.close()
 
@@ -274,7 +283,7 @@ def main():
     peak = peaks.get("hbm_gbs")
     peak_src = "measured" if peak else "fallback"
     peak = peak or 6800.0
-    npx = NY * NX * BATCH
+    npx = NY * NX * B
     row_ms = prof[0] / max(prof[1], 1)
     col_ms = prof[2] / max(prof[3], 1)
     passes = {
@@ -296,18 +305,17 @@ def main():
         metric=METRIC, value=value, unit=UNIT, n_gpus=world, steps=args.steps, warmup=args.warmup,
         ms_per_step=el_ms / args.steps, higher_is_better=True, scaling="weak", vs_baseline=None,
         dtype="f32", data=DATA,
-        config=dict(workload="gs_binary_1024x1024_batch64", ny=NY, nx=NX, batch=BATCH,
+        config=dict(workload="gs_binary_1024x1024_batch%d" % B, ny=NY, nx=NX, batch=B,
                     iters_per_step=args.iters, slm="binary", parallelism="dp%d" % world,
                     row_variant=variants[0], column_variant=variants[1],
                     l2="inputs larger than L2: field 512 MiB + prepared targets 256 MiB per rank"),
-        holograms_per_s=value * BATCH / args.iters,
+        holograms_per_s=value * B / args.iters,
         whole_iteration_gbs=(BYTES_ROW + BYTES_COL) * npx / (iter_ms / 1e3) / 1e9,
         roofline=roofline,
         passes={k: dict(avg_ms=v["ms"], gbs=v["gbs"], frac=(v["gbs"] / peak if v["gbs"] else None),
                         launches=v["launches"]) for k, v in passes.items()},
-        cpu_baseline=cpu_oracle_sample(),
-        e2e=dict(value=e2e_value, unit=UNIT, h2d_bytes_per_step=int(tp.numel() * 4 + pp.numel() * 4),
-                 d2h_bytes_per_step=int(hp.numel() + mp.numel() * 8)),
+        cpu_baseline=None if args.quick else cpu_oracle_sample(),
+        e2e=e2e,
         clocks=clk,
         gpu_launches=launches,
         src_hash=src_hash(),

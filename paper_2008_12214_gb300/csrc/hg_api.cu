@@ -155,6 +155,11 @@ int pipe_candidates(int n, const PipeOps **out, int max) {
     return k;
 }
 
+// Row panels per item of a TMA-fed row pass.
+int row_panels(const PipeOps *o, int ny) {
+    return o->paired ? ny / 2 + 1 : (ny + o->row_lines - 1) / o->row_lines;
+}
+
 // Autotuner cache: (device, ny, nx, items, slm kind) -> chosen candidates.
 struct TuneEntry {
     int dev, ny, nx, items, kind;
@@ -456,6 +461,7 @@ int col_role_holo(hg_plan p) { return p->kind == HG_SLM_BINARY ? COL_HOLO_BIN : 
 void enqueue_loop(hg_plan p, int iters, cudaStream_t s) {
     ColArgs ca = col_args(p);
     RowArgs ra = row_args(p);
+    ca.half = p->prow && p->prow->paired;  // the paired row pass rebuilds rows ny - ky
     for (int k = 0; k + 1 < iters; ++k) {
         launch_col_gs(p, col_role_gs(p), ca, s);
         ra.part = p->part + (size_t)k * p->batch * p->ppt_max * NMET;
@@ -526,7 +532,7 @@ float time_variant(hg_plan p, const PipeOps *o, bool row) {
     ColArgs ca = col_args(p);
     CUtensorMap m;
     if (!row && !make_cmap(p, o, &m)) return 1e30f;
-    const int ppt = row ? (p->ny + o->row_lines - 1) / o->row_lines : (p->nx + o->col_c - 1) / o->col_c;
+    const int ppt = row ? row_panels(o, p->ny) : (p->nx + o->col_c - 1) / o->col_c;
     const int grid = grid_for(row ? o->row_blocks_per_sm : o->col_blocks_per_sm, p->nsm,
                               (long)p->batch * ppt);
     PipeArgs pa = pipe_args(p);
@@ -696,25 +702,29 @@ hg_status hg_plan_create(hg_plan *out, int ny, int nx, int batch, hg_slm slm, hg
         {
             const PipeOps *all[4];
             const int k = pipe_candidates(nx, all, 4);
-            for (int i = 0; i < k; ++i)
+            for (int i = 0; i < k; ++i) {
+                // paired rows need a binary SLM (real e^{iH}), an even column length and the
+                // GS/WGS loop
+                if (all[i]->paired && (slm.kind != HG_SLM_BINARY || ny % 2 || algo == HG_OSPR)) continue;
                 if (all[i]->row_iter && nx % 4 == 0 && ensure_pipe_init(p->dev, all[i]) == cudaSuccess)
                     rc[nr++] = all[i];
+            }
         }
         {
             const PipeOps *all[4];
             const int k = pipe_candidates(ny, all, 4);
             CUtensorMap m;
             for (int i = 0; i < k; ++i)
-                if (all[i]->col_gs && nx % 2 == 0 && ensure_pipe_init(p->dev, all[i]) == cudaSuccess &&
-                    make_cmap(p, all[i], &m))
+                if (!all[i]->paired && all[i]->col_gs && nx % 2 == 0 &&
+                    ensure_pipe_init(p->dev, all[i]) == cudaSuccess && make_cmap(p, all[i], &m))
                     cc[nc++] = all[i];
         }
         const PipeOps *row = nr ? rc[0] : nullptr, *col = nc ? cc[0] : nullptr;
         if (o.autotune >= 2) {  // forced candidate (tests, benchmarks of one variant)
             const int k = o.autotune - 2;
-            if (k >= nr || k >= nc) return fail(HG_ERR_UNSUPPORTED_SIZE);
+            if (k >= nr) return fail(HG_ERR_UNSUPPORTED_SIZE);
             row = rc[k];
-            col = cc[k];
+            col = k < nc ? cc[k] : (nc ? cc[0] : nullptr);
         } else if (o.autotune == 1 && (nr > 1 || nc > 1)) {
             bool cached = false;
             {
@@ -749,7 +759,7 @@ hg_status hg_plan_create(hg_plan *out, int ny, int nx, int batch, hg_slm slm, hg
         }
         if (row) {
             p->prow = row;
-            p->ppt_pipe = (ny + row->row_lines - 1) / row->row_lines;
+            p->ppt_pipe = row_panels(row, ny);
             if (p->ppt_pipe > p->ppt_max) p->ppt_max = p->ppt_pipe;
         }
         if (col && make_cmap(p, col, &p->cmap)) p->pcol = col;

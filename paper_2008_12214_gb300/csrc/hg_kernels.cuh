@@ -53,6 +53,8 @@ struct ColArgs {
     float qscale;          // L / (2 pi)
     const float2 *tw;      // W_ny^e, e < ny
     float invSqrtN;
+    int half;              // store only rows y <= ny/2 of the result (binary GS whose next
+                           // row pass rebuilds rows ny - y from the Hermitian symmetry)
 };
 
 // Sum four per-thread float partials over the block in double, in a fixed

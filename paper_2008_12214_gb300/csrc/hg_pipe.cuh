@@ -271,6 +271,204 @@ __global__ void __launch_bounds__(RowPipeCfg<P, LINES, NG, D, SWZ>::THREADS, 1)
     }
 }
 
+// --------------------------------------------------- paired row pass (binary)
+// For a binary SLM e^{iH} is real, so after the column FFTs every column is
+// Hermitian in ky: C[ny - ky][x] = conj(C[ky][x]), hence for the full 2D
+// transform R[ny - ky][kx] = conj(R[ky][(nx - kx) % nx]).  The column pass then
+// stores rows ky <= ny/2 only, and this pass handles the rows (ky, ny - ky) of
+// one panel with a single forward row FFT: row ny - ky's spectrum is the
+// conjugated reversal of row ky's, fetched through shared memory.  The
+// self-conjugate rows 0 and ny/2 are panels of their own.  Each panel then
+// applies the constraint to its rows and runs their inverse FFTs, as the
+// plain row pass does.
+// Constraint of one replay row held as E samples per thread (binary pairs):
+// metric partials, optional weight update, F = w T R / |R| in place.
+template <class P>
+__device__ __forceinline__ void pair_constrain(float2 (&w)[P::E], const float *sT, float *wr,
+                                               const RowArgs &a, int t, float &acc0, float &acc1,
+                                               float &acc2, float &acc3) {
+    static_for<0, P::E>([&](auto ec) {
+        constexpr int e = decltype(ec)::value;
+        const int x = t + P::TL * e;
+        const float Tv = sT[x];
+        const float2 r = w[e];
+        const float m2 = fmaf(r.x, r.x, r.y * r.y);
+        const float rs = m2 > 0.f ? rsqrtf(m2) : 0.f;
+        const float I = m2 * a.invN2;
+        const float d = I - Tv * Tv;
+        const float am = fmaf(m2 * rs, a.invSqrtN * a.invSqrtN, -Tv);
+        const float e2 = m2 * a.invN;
+        acc0 = fmaf(d, d, acc0);
+        acc1 = fmaf(am, am, acc1);
+        acc3 += e2;
+        if (Tv > 0.f) acc2 += e2;
+        float wv = 1.f;
+        if (wr) {
+            wv = wr[x];
+            if (Tv > 0.f && m2 > 0.f) wv = wv * Tv * (a.NN * rs);
+            wr[x] = wv;
+        }
+        const float gm = Tv * wv;
+        w[e] = m2 > 0.f ? make_float2(gm * r.x * rs, gm * r.y * rs) : make_float2(gm, 0.f);
+    });
+}
+
+// Inverse row FFT of one row (exchange in `xbuf`) and its store.
+template <class P, class LAY, class SYNC>
+__device__ __forceinline__ void pair_finish(float2 (&w)[P::E], float2 *xbuf, const float2 *tw, int t,
+                                            SYNC gsync, float2 *fw) {
+    line_fft<P, +1, 1, LAY>(w, xbuf, tw, t, gsync);
+    static_for<0, P::E>([&](auto ec) {
+        constexpr int e = decltype(ec)::value;
+        fw[t + P::TL * e] = w[e];
+    });
+}
+
+template <class P, int NG, int D, int SWZ>
+struct PairPipeCfg {
+    static constexpr int GT = P::TL;
+    static_assert(GT % 32 == 0, "paired row group must be whole warps");
+    static constexpr int GW = GT / 32;
+    static constexpr int THREADS = NG * GT;
+    static constexpr int SLOT_F = P::N * 8;
+    static constexpr int SLOT = SLOT_F + 2 * P::N * 4;  // field row ky, targets of both rows
+    static constexpr int RED = NG * GW * NMET * 8;
+    static constexpr size_t SMEM = 1024 + (size_t)NG * D * SLOT + RED + NG * D * 8 + 4 * (NG + 1) + 256;
+};
+
+template <class P, int NG, int D, int SWZ>
+__global__ void __launch_bounds__(PairPipeCfg<P, NG, D, SWZ>::THREADS, 1)
+    k_row_pipe_pair(const RowArgs a, const PipeArgs pa) {
+    using Cfg = PairPipeCfg<P, NG, D, SWZ>;
+    using LAY = Swz<SWZ>;
+    constexpr int TL = P::TL, E = P::E, NX = P::N, GT = Cfg::GT;
+    static_assert((NX & (NX - 1)) == 0, "paired rows use a power-of-two row length");
+    extern __shared__ unsigned char smraw[];
+    unsigned char *base = smraw + ((1024 - (smem_addr(smraw) & 1023)) & 1023);
+    double *red = reinterpret_cast<double *>(base + (size_t)NG * D * Cfg::SLOT);
+    uint64_t *full = reinterpret_cast<uint64_t *>(reinterpret_cast<unsigned char *>(red) + Cfg::RED);
+    volatile int *flags = reinterpret_cast<volatile int *>(full + NG * D);
+    volatile int *abort = flags + NG;
+
+    const int tid = threadIdx.x;
+    if (tid == 0) {
+        for (int i = 0; i < NG * D; ++i) mbar_init(full + i, 1);
+        *abort = 0;
+        fence_mbar_init();
+    }
+    __syncthreads();
+
+    // panels per item: p = 0 (row 0 alone), 1 .. ny/2 - 1 (rows p and ny - p),
+    // ny/2 (row ny/2 alone)
+    const int ny = a.ny, hy = ny / 2;
+    const int ppt = hy + 1;
+    const int J = a.items * ppt;
+    const int g = tid / GT, t = tid - g * GT;
+    unsigned char *ring = base + (size_t)g * D * Cfg::SLOT;
+    uint64_t *gfull = full + g * D;
+    auto gsync = [g]() {
+        if constexpr (Cfg::GW == 1) __syncwarp();
+        else named_sync(1 + g, GT);
+    };
+    auto job = [&](int k) { return (int)blockIdx.x + (g + NG * k) * (int)gridDim.x; };
+    auto issue = [&](int k) {
+        const int j = job(k);
+        if (j >= J || j == pa.drop_job) return;
+        const int item = j / ppt, pan = j - item * ppt;
+        const bool partner = pan != 0 && pan != hy;
+        unsigned char *sl = ring + (size_t)(k % D) * Cfg::SLOT;
+        mbar_expect_tx(gfull + k % D, (uint32_t)(NX * (partner ? 16 : 12)));
+        bulk_g2s(sl, a.field + ((size_t)item * ny + pan) * NX, NX * 8, gfull + k % D);
+        bulk_g2s(sl + Cfg::SLOT_F, a.T + ((size_t)item * ny + pan) * NX, NX * 4, gfull + k % D);
+        if (partner)
+            bulk_g2s(sl + Cfg::SLOT_F + NX * 4, a.T + ((size_t)item * ny + ny - pan) * NX, NX * 4,
+                     gfull + k % D);
+    };
+    auto drain = [&](int k0, int k1) {
+        for (int q = k0; q < k1; ++q) {
+            const int j = job(q);
+            if (j < J && j != pa.drop_job) mbar_wait(gfull + q % D, (q / D) & 1, pa.wait_ns, nullptr);
+        }
+    };
+    if (t == 0)
+        for (int k = 0; k < D; ++k) issue(k);
+
+    for (int k = 0;; ++k) {
+        const int j = job(k);
+        if (j >= J) break;
+        if (t == 0) {
+            bool ok = !*abort && mbar_wait(gfull + k % D, (k / D) & 1, pa.wait_ns, abort);
+            if (!ok) {
+                atomicOr(pa.err, ERR_TIMEOUT_BIT);
+                *abort = 1;
+            }
+            flags[g] = ok;
+        }
+        gsync();
+        if (!flags[g]) {
+            if (t == 0) drain(k, k + D);
+            break;
+        }
+        const int item = j / ppt, pan = j - item * ppt;
+        const bool partner = pan != 0 && pan != hy;
+        unsigned char *sl = ring + (size_t)(k % D) * Cfg::SLOT;
+        float2 *sf = reinterpret_cast<float2 *>(sl);  // field row, then exchange buffer
+        const float *sTa = reinterpret_cast<const float *>(sl + Cfg::SLOT_F);
+        float2 *park = reinterpret_cast<float2 *>(sl + Cfg::SLOT_F);  // row ny - p after use of T
+        float2 v[E];
+        static_for<0, E>([&](auto ec) {
+            constexpr int e = decltype(ec)::value;
+            v[e] = sf[t + TL * e];
+        });
+        line_fft<P, -1, 1, LAY>(v, sf, a.tw, t, gsync);
+        float acc0 = 0.f, acc1 = 0.f, acc2 = 0.f, acc3 = 0.f;
+        if (partner) {
+            // spectrum of row ny - p: conj(X[(nx - kx) % nx]), through shared memory;
+            // its constraint is applied now and the result parked where the
+            // (consumed) targets were
+            gsync();
+            static_for<0, E>([&](auto ec) {
+                constexpr int e = decltype(ec)::value;
+                sf[t + TL * e] = v[e];
+            });
+            gsync();
+            float2 vb[E];
+            static_for<0, E>([&](auto ec) {
+                constexpr int e = decltype(ec)::value;
+                const float2 q = sf[(NX - (t + TL * e)) & (NX - 1)];
+                vb[e] = make_float2(q.x, -q.y);
+            });
+            pair_constrain<P>(vb, sTa + NX, a.w ? a.w + ((size_t)item * ny + ny - pan) * NX : nullptr, a,
+                              t, acc0, acc1, acc2, acc3);
+            pair_constrain<P>(v, sTa, a.w ? a.w + ((size_t)item * ny + pan) * NX : nullptr, a, t, acc0,
+                              acc1, acc2, acc3);
+            gsync();
+            static_for<0, E>([&](auto ec) {
+                constexpr int e = decltype(ec)::value;
+                park[t + TL * e] = vb[e];
+            });
+        } else {
+            pair_constrain<P>(v, sTa, a.w ? a.w + ((size_t)item * ny + pan) * NX : nullptr, a, t, acc0,
+                              acc1, acc2, acc3);
+        }
+#pragma unroll 1
+        for (int r = 0; r < (partner ? 2 : 1); ++r) {
+            if (r == 1)
+                static_for<0, E>([&](auto ec) {
+                    constexpr int e = decltype(ec)::value;
+                    v[e] = park[t + TL * e];
+                });
+            pair_finish<P, LAY>(v, sf, a.tw, t, gsync,
+                                a.field + ((size_t)item * ny + (r ? ny - pan : pan)) * NX);
+        }
+        gsync();
+        if (t == 0) issue(k + D);  // slot fully consumed: refill it
+        if (a.part)
+            group_sum4<GT>(acc0, acc1, acc2, acc3, red + (size_t)g * Cfg::GW * NMET,
+                           a.part + ((size_t)item * ppt + pan) * NMET, t, gsync);
+    }
+}
+
 // ----------------------------------------------------------- column pass
 template <class P, int C, int NG, int D, int SWZ, int BOXR>
 struct ColPipeCfg {
@@ -385,7 +583,7 @@ __global__ void __launch_bounds__(ColPipeCfg<P, C, NG, D, SWZ, BOXR>::THREADS, 1
             float2 *fw = a.field + base_o + x;
             static_for<0, E>([&](auto ec) {
                 constexpr int e = decltype(ec)::value;
-                fw[(t + TL * e) * nx] = v[e];
+                if (!a.half || t + TL * e <= NY / 2) fw[(t + TL * e) * nx] = v[e];
             });
         }
     }
@@ -399,6 +597,7 @@ struct PipeOps {
     int row_threads, col_threads, col_c, col_boxr, row_lines;
     size_t row_smem, col_smem;
     int row_blocks_per_sm, col_blocks_per_sm;
+    int paired;  // row pass is k_row_pipe_pair (binary SLM, even ny, half-row column stores)
     cudaError_t (*init)(PipeOps *self);
     void (*row_iter)(const RowArgs &a, const PipeArgs &pa, int grid, cudaStream_t s);  // may be null
     void (*col_gs)(int role, const ColArgs &a, const PipeArgs &pa, const CUtensorMap &m, int grid,
@@ -468,6 +667,52 @@ struct PipeImpl {
         }
         o.init = &init;
         o.col_gs = &col_gs;
+        return o;
+    }
+};
+
+
+// A paired-row variant: plan P (TL a multiple of 32), NG groups, ring depth D,
+// swizzle SWZ, and the column pass of another variant `col`.
+template <class P, int NG, int D, int SWZ>
+struct PairImpl {
+    using RC = PairPipeCfg<P, NG, D, SWZ>;
+    static cudaError_t init_row(int *blocks) {
+        cudaError_t e = cudaFuncSetAttribute((const void *)k_row_pipe_pair<P, NG, D, SWZ>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)RC::SMEM);
+        if (e == cudaSuccess)
+            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, k_row_pipe_pair<P, NG, D, SWZ>,
+                                                              RC::THREADS, RC::SMEM);
+        return e;
+    }
+    static void row_iter(const RowArgs &a, const PipeArgs &pa, int grid, cudaStream_t s) {
+        k_row_pipe_pair<P, NG, D, SWZ><<<grid, RC::THREADS, RC::SMEM, s>>>(a, pa);
+    }
+};
+
+// Combines a paired row pass with the column pass of an existing variant.
+template <class PAIR, const PipeOps *COL>
+struct PairedOps {
+    static cudaError_t init(PipeOps *self) {
+        cudaError_t e = COL->init(const_cast<PipeOps *>(COL));
+        if (e != cudaSuccess) return e;
+        int rb = 0;
+        e = PAIR::init_row(&rb);
+        if (e != cudaSuccess) return e;
+        if (rb < 1) return cudaErrorInvalidConfiguration;
+        self->row_blocks_per_sm = rb;
+        self->col_blocks_per_sm = COL->col_blocks_per_sm;
+        return cudaSuccess;
+    }
+    static PipeOps make(const char *name) {
+        PipeOps o = *COL;
+        o.name = name;
+        o.paired = 1;
+        o.row_lines = 2;  // two rows per panel except the self-conjugate rows 0 and ny/2
+        o.row_threads = PAIR::RC::THREADS;
+        o.row_smem = PAIR::RC::SMEM;
+        o.row_iter = &PAIR::row_iter;
+        o.init = &init;
         return o;
     }
 };

@@ -11,6 +11,8 @@ PipeOps p512a = PipeImpl<Plan<512, 16, 32, 32, 16>, 2, 8, 2, 5, Plan<512, 16, 32
                           256>::make("512:r32x16e32");
 PipeOps p512b = PipeImpl<Plan<512, 32, 16, 16, 16, 2>, 1, 16, 2, 4, Plan<512, 32, 16, 16, 16, 2>, 8, 2, 3,
                           4, 256>::make("512:r16x16x2e16");
+PipeOps p512c = PairedOps<PairImpl<Plan<512, 32, 16, 16, 16, 2>, 12, 2, 4>, &p512a>::make(
+    "512:pair16x16x2e16+c32x16e32");
 }  // namespace
 
 const LineOps *ops_mid(int n) {
@@ -27,6 +29,7 @@ int pipe_ops_mid(int n, const PipeOps **out, int max) {
     if (n == 512) {
         if (k < max) out[k++] = &p512a;
         if (k < max) out[k++] = &p512b;
+        if (k < max) out[k++] = &p512c;
     }
     return k;
 }

@@ -363,7 +363,8 @@ def test_bounded_wait_reports_timeout_and_plan_recovers():
         assert np.allclose(mse[b].cpu().numpy(), o["mse"], rtol=1e-4)
 
 
-@pytest.mark.parametrize("n,cand", [(256, 0), (512, 0), (512, 1), (1024, 0), (1024, 1), (2048, 0), (2048, 1)])
+@pytest.mark.parametrize("n,cand", [(256, 0), (512, 0), (512, 1), (512, 2), (1024, 0), (1024, 1), (1024, 2),
+                                    (1024, 3), (2048, 0), (2048, 1), (2048, 2)])
 def test_every_pipelined_variant_against_oracle(n, cand):
     """Each TMA-fed candidate the autotuner may pick, forced in turn: the
     column pass through a single step, the row pass through the metrics it
@@ -392,3 +393,31 @@ def test_every_pipelined_variant_against_oracle(n, cand):
         assert abs(mse[b, 0] - run["mse"][0]) <= 1e-4 * run["mse"][0], name
         assert abs(mse[b, 1] - run["mse"][1]) <= 1e-3 * run["mse"][1], name
         assert abs(mse[b, 3] - run["mse"][3]) <= 1e-2 * run["mse"][3], name
+
+
+@pytest.mark.parametrize("cand", [2, 3])
+def test_paired_rows_weighted_gs_binary(cand):
+    """The paired-row pass (binary SLM) also carries the weighted-GS update:
+    same metrics and weights as the generic passes on the first iterations."""
+    n, batch, iters = 1024, 1, 3
+    t = torch.from_numpy(synth.targets(batch, n, n)).to(DEV)
+    ph = torch.from_numpy(synth.init_phases(batch, n, n)).to(DEV)
+    res = {}
+    for pipe, tune in ((0, 0), (1, 2 + cand)):
+        plan = hg.Plan(n, n, batch, hg.HG_SLM_BINARY, 2, hg.HG_WGS, pipeline=pipe, autotune=tune)
+        mse = torch.empty((batch, iters), dtype=torch.float64, device=DEV)
+        plan.run(t, ph, iters, None, mse)
+        plan.sync()
+        w = torch.empty((batch, n, n), dtype=torch.float32, device=DEV)
+        hg.hg_get_weights(plan.h, w)
+        res[pipe] = (mse.cpu().numpy(), w.cpu().numpy(), hg.hg_plan_variant(plan.h, 0))
+        plan.close()
+    assert "pair" in res[1][2]
+    assert np.allclose(res[0][0][:, 0], res[1][0][:, 0], rtol=1e-5)
+    assert np.allclose(res[0][0][:, 1], res[1][0][:, 1], rtol=1e-3)
+    w0, w1 = res[0][1], res[1][1]
+    # weights divide by |R|: compare where the target is significant (Gaussian
+    # tails carry denormal, ill-conditioned weights in both runs)
+    tt = synth.targets(batch, n, n)
+    sig = tt > 1e-2 * tt.max()
+    assert np.median(np.abs(w0[sig] - w1[sig]) / w0[sig]) < 1e-4
