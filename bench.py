@@ -30,8 +30,14 @@ METRIC = "GS iterations/s at 1024^2 batch 64, % HBM roofline; time-to-MSE vs pla
 UNIT = "batched GS iterations/s (64 targets of 1024x1024, binary phase)"
 NY = NX = 1024
 BATCH = 64
-BYTES_ROW = 20   # algorithmic HBM bytes per pixel of the row pass: field r+w 16, target 4
-BYTES_COL = 16   # column pass: field r+w
+# Algorithmic HBM bytes per pixel and iteration.  Plain passes: row 20 (field
+# read + write 16, target 4), column 16 (field read + write): 36 B/px.  With the
+# paired-row pass (binary SLM: column spectra are Hermitian, so only rows
+# ky <= ny/2 are stored and read back): row 16 (half field 4, target 4, field
+# written 8), column 12 (field read 8, half written 4): 28 B/px.
+BYTES_ROW, BYTES_COL = 20, 16
+BYTES_ROW_PAIRED, BYTES_COL_PAIRED = 16, 12
+BYTES_SURVEY = 36
 DATA = ("synthetic: seeded targets of 16 Gaussian blobs + 8 rectangles per 1024x1024 field "
         "(seeds 1000 + rank*64 + b), initial phase U[0, 2 pi)")
 
@@ -286,15 +292,18 @@ def main():
     npx = NY * NX * B
     row_ms = prof[0] / max(prof[1], 1)
     col_ms = prof[2] / max(prof[3], 1)
+    paired = "pair" in variants[0]
+    b_row = BYTES_ROW_PAIRED if paired else BYTES_ROW
+    b_col = BYTES_COL_PAIRED if paired else BYTES_COL
     passes = {
-        "row": dict(bytes=BYTES_ROW * npx, ms=row_ms, launches=int(prof[1])),
-        "column": dict(bytes=BYTES_COL * npx, ms=col_ms, launches=int(prof[3])),
+        "row": dict(bytes=b_row * npx, ms=row_ms, launches=int(prof[1]), variant=variants[0]),
+        "column": dict(bytes=b_col * npx, ms=col_ms, launches=int(prof[3]), variant=variants[1]),
     }
     for v in passes.values():
         v["gbs"] = v["bytes"] / (v["ms"] / 1e3) / 1e9 if v["ms"] > 0 else None
     dom = max(passes, key=lambda k: passes[k]["ms"] * passes[k]["launches"])
     d = passes[dom]
-    kernel_key = ("k_row_pipe" if dom == "row" else "k_col_pipe") + "<1024>"
+    kernel_key = d["variant"] + (" row" if dom == "row" else " column")
     traffic = traffic_for(kernel_key)
     roofline = dict(bound="hbm", achieved=d["gbs"], peak=peak, unit="GB/s",
                     frac=(d["gbs"] / peak) if d["gbs"] else None, traffic=traffic,
@@ -310,10 +319,16 @@ def main():
                     row_variant=variants[0], column_variant=variants[1],
                     l2="inputs larger than L2: field 512 MiB + prepared targets 256 MiB per rank"),
         holograms_per_s=value * B / args.iters,
-        whole_iteration_gbs=(BYTES_ROW + BYTES_COL) * npx / (iter_ms / 1e3) / 1e9,
+        whole_iteration=dict(
+            ms=iter_ms, bytes_per_px_moved=b_row + b_col,
+            gbs_moved=(b_row + b_col) * npx / (iter_ms / 1e3) / 1e9,
+            bytes_per_px_36=BYTES_SURVEY,
+            gbs_at_36=BYTES_SURVEY * npx / (iter_ms / 1e3) / 1e9,
+            frac_at_36=BYTES_SURVEY * npx / (iter_ms / 1e3) / 1e9 / peak),
         roofline=roofline,
         passes={k: dict(avg_ms=v["ms"], gbs=v["gbs"], frac=(v["gbs"] / peak if v["gbs"] else None),
-                        launches=v["launches"]) for k, v in passes.items()},
+                        launches=v["launches"], bytes_per_px=v["bytes"] // npx, variant=v["variant"])
+                for k, v in passes.items()},
         cpu_baseline=None if args.quick else cpu_oracle_sample(),
         e2e=e2e,
         clocks=clk,
