@@ -196,6 +196,37 @@ hg_status hg_debug_inject(hg_plan plan, int drop_job, uint64_t wait_ns);
 void hg_plan_destroy(hg_plan plan);
 const char *hg_status_string(hg_status st);
 
+/*
+ * Groups: targets of different sizes (each size a plan) run as ONE CUDA graph
+ * whose branches are the plans' whole GS/WGS runs, executed concurrently.
+ * This serves mixed batches such as 512^2, 1024^2, 2048^2 and 1080 x 1920
+ * targets side by side (Section 2 notes that field size is a free parameter;
+ * the batch mix itself has no counterpart in the paper).
+ *  hg_group_create  nplans in [1, HG_GROUP_MAX] GS/WGS plans on one device.
+ *                   The group keeps the plan handles (not owned; they must
+ *                   outlive the group and must not run on their own while a
+ *                   group run is in flight).
+ *  hg_group_run     per plan i: targets[i], init_phases[i] (array may be NULL,
+ *                   entries may be NULL), holo_out[i], mse_out[i] (arrays or
+ *                   entries may be NULL) exactly as in hg_run; DEVICE buffers
+ *                   only.  WGS weights restart at 1.  The graph is captured on
+ *                   the first call and replayed while iters and every buffer
+ *                   pointer stay the same.  Enqueued on `stream` (NULL:
+ *                   legacy default stream).
+ *  hg_group_sync    waits for `stream` and returns the first error any plan's
+ *                   device flag reports.
+ * Errors: HG_ERR_INVALID_ARG (NULL, counts, host pointers, OSPR plans),
+ * HG_ERR_OOM, HG_ERR_CUDA.
+ */
+#define HG_GROUP_MAX 16
+typedef struct hg_group_s *hg_group;
+hg_status hg_group_create(hg_group *out, int nplans, const hg_plan *plans);
+hg_status hg_group_run(hg_group group, const float *const *targets, const float *const *init_phases,
+                       int iters, uint8_t *const *holo_out, double *const *mse_out, void *stream);
+hg_status hg_group_sync(hg_group group, void *stream);
+int hg_group_launch_count(hg_group group);
+void hg_group_destroy(hg_group group);
+
 #ifdef __cplusplus
 }
 #endif

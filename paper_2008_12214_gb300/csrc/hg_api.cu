@@ -511,6 +511,61 @@ hg_status run_loop(hg_plan p, int iters) {
     return HG_OK;
 }
 
+// The device-side work of one run (buffers already device-resident, partial
+// and metric buffers already sized).  `capturing`: enqueued inside an outer
+// stream capture, so the loop is enqueued pass by pass and WGS weights always
+// restart at 1.
+hg_status enqueue_run(hg_plan p, const float *d_t, const float *d_ph, int iters, uint8_t *d_ho,
+                      double *d_mo, bool capturing) {
+    hg_status st = HG_OK;
+    HG_CK(cudaMemsetAsync(p->err, 0, sizeof(unsigned), p->stream));
+    enqueue_prep(p, d_t);
+
+    RowArgs ra = row_args(p);
+    ColArgs ca = col_args(p);
+    if (p->algo == HG_OSPR) {
+        ra.items = p->nchains;
+        ra.nsub = p->nsub;
+        ra.phase = nullptr;
+        ra.stream_id = 0;
+        launch_row(p, ROW_HEAD, ra, p->stream);
+        ca.items = p->nchains;
+        ca.holo = d_ho;
+        launch_col(p, COL_GS_BIN, ca, p->stream);
+        RowArgs rt = row_args(p);
+        rt.nsub = p->nsub;
+        rt.part = p->part;
+        launch_row(p, ROW_AVG, rt, p->stream);
+    } else {
+        if (p->algo == HG_WGS && (!p->weights_preset || capturing)) {
+            k_fill<<<ew_grid(p, p->npx * p->batch), 256, 0, p->stream>>>(p->w, p->npx * p->batch, 1.f);
+            p->launches++;
+        }
+        ra.phase = d_ph;
+        launch_row(p, ROW_HEAD, ra, p->stream);
+        if (capturing) {
+            enqueue_loop(p, iters, p->stream);
+        } else if ((st = run_loop(p, iters)) != HG_OK) {
+            return st;
+        }
+        ca.holo = d_ho;
+        launch_col_gs(p, col_role_gs(p), ca, p->stream);
+        RowArgs rt = row_args(p);
+        rt.part = p->part + (size_t)(iters - 1) * p->batch * p->ppt_max * NMET;
+        launch_row(p, ROW_TAIL, rt, p->stream);
+    }
+    k_reduce<<<(iters * p->batch * 32 + 127) / 128, 128, 0, p->stream>>>(
+        p->part, iters, p->batch, p->ppt_max, p->prow ? p->ppt_pipe : p->ppt, p->ppt,
+        1.0 / (double)p->npx, p->metrics, d_mo);
+    p->launches++;
+    HG_CK(cudaGetLastError());
+    p->weights_preset = false;
+    p->have_run = true;
+    p->field_from_run = p->algo != HG_OSPR;
+    p->last_iters = iters;
+    return st;
+}
+
 hg_status check_err_flag(hg_plan p) {
     unsigned e = 0;
     HG_CK(cudaMemcpyAsync(&e, p->err, sizeof(unsigned), cudaMemcpyDeviceToHost, p->stream));
@@ -899,47 +954,7 @@ hg_status hg_run(hg_plan p, const float *target, const float *init_phase, int it
 
     if ((st = ensure_part(p, iters)) != HG_OK) return st;
     if ((st = ensure_metrics(p, iters)) != HG_OK) return st;
-    HG_CK(cudaMemsetAsync(p->err, 0, sizeof(unsigned), p->stream));
-    enqueue_prep(p, d_t);
-
-    RowArgs ra = row_args(p);
-    ColArgs ca = col_args(p);
-    if (p->algo == HG_OSPR) {
-        ra.items = p->nchains;
-        ra.nsub = p->nsub;
-        ra.phase = nullptr;
-        ra.stream_id = 0;
-        launch_row(p, ROW_HEAD, ra, p->stream);
-        ca.items = p->nchains;
-        ca.holo = d_ho;
-        launch_col(p, COL_GS_BIN, ca, p->stream);
-        RowArgs rt = row_args(p);
-        rt.nsub = p->nsub;
-        rt.part = p->part;
-        launch_row(p, ROW_AVG, rt, p->stream);
-    } else {
-        if (p->algo == HG_WGS && !p->weights_preset) {
-            k_fill<<<ew_grid(p, p->npx * p->batch), 256, 0, p->stream>>>(p->w, p->npx * p->batch, 1.f);
-            p->launches++;
-        }
-        ra.phase = d_ph;
-        launch_row(p, ROW_HEAD, ra, p->stream);
-        if ((st = run_loop(p, iters)) != HG_OK) return st;
-        ca.holo = d_ho;
-        launch_col_gs(p, col_role_gs(p), ca, p->stream);
-        RowArgs rt = row_args(p);
-        rt.part = p->part + (size_t)(iters - 1) * p->batch * p->ppt_max * NMET;
-        launch_row(p, ROW_TAIL, rt, p->stream);
-    }
-    k_reduce<<<(iters * p->batch * 32 + 127) / 128, 128, 0, p->stream>>>(
-        p->part, iters, p->batch, p->ppt_max, p->prow ? p->ppt_pipe : p->ppt, p->ppt,
-        1.0 / (double)p->npx, p->metrics, d_mo);
-    p->launches++;
-    HG_CK(cudaGetLastError());
-    p->weights_preset = false;
-    p->have_run = true;
-    p->field_from_run = p->algo != HG_OSPR;
-    p->last_iters = iters;
+    if ((st = enqueue_run(p, d_t, d_ph, iters, d_ho, d_mo, false)) != HG_OK) return st;
     if (ho_host)
         HG_CK(cudaMemcpyAsync(holo_out, d_ho, hbytes, cudaMemcpyDeviceToHost, p->stream));
     if (mo_host) HG_CK(cudaMemcpyAsync(mse_out, d_mo, mbytes, cudaMemcpyDeviceToHost, p->stream));
@@ -1095,5 +1110,148 @@ hg_status hg_debug_step(hg_plan p, const float *target, const float *phase_in, f
     p->last_iters = 1;
     return HG_OK;
 }
+
+}  // extern "C"
+
+// ------------------------------------------------------------------ groups
+// Several plans (targets of different sizes) run as one CUDA graph: each
+// plan's whole run is a branch forked from one capture, so the GPU executes
+// the size buckets concurrently.
+
+struct hg_group_s {
+    int dev = 0, n = 0;
+    hg_plan plans[HG_GROUP_MAX];
+    cudaStream_t cap = nullptr;
+    cudaStream_t branch[HG_GROUP_MAX] = {};
+    cudaEvent_t fork = nullptr, join[HG_GROUP_MAX] = {};
+    cudaGraphExec_t exec = nullptr;
+    int iters = -1;
+    const void *key[4 * HG_GROUP_MAX] = {};
+    int launches = 0;
+};
+
+extern "C" {
+
+void hg_group_destroy(hg_group g) {
+    if (!g) return;
+    DevGuard dg(g->dev);
+    if (g->cap) cudaStreamSynchronize(g->cap);
+    if (g->exec) cudaGraphExecDestroy(g->exec);
+    for (int i = 0; i < g->n; ++i) {
+        if (g->branch[i]) cudaStreamDestroy(g->branch[i]);
+        if (g->join[i]) cudaEventDestroy(g->join[i]);
+    }
+    if (g->fork) cudaEventDestroy(g->fork);
+    if (g->cap) cudaStreamDestroy(g->cap);
+    delete g;
+}
+
+hg_status hg_group_create(hg_group *out, int nplans, const hg_plan *plans) {
+    if (!out || !plans || nplans < 1 || nplans > HG_GROUP_MAX) return HG_ERR_INVALID_ARG;
+    *out = nullptr;
+    for (int i = 0; i < nplans; ++i)
+        if (!plans[i] || plans[i]->dev != plans[0]->dev) return HG_ERR_INVALID_ARG;
+    hg_group g = new (std::nothrow) hg_group_s();
+    if (!g) return HG_ERR_OOM;
+    g->dev = plans[0]->dev;
+    g->n = nplans;
+    DevGuard dg(g->dev);
+    cudaError_t e = cudaStreamCreateWithFlags(&g->cap, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&g->fork, cudaEventDisableTiming);
+    for (int i = 0; i < nplans && e == cudaSuccess; ++i) {
+        g->plans[i] = plans[i];
+        e = cudaStreamCreateWithFlags(&g->branch[i], cudaStreamNonBlocking);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&g->join[i], cudaEventDisableTiming);
+    }
+    if (e != cudaSuccess) {
+        hg_group_destroy(g);
+        return map_err(e);
+    }
+    *out = g;
+    return HG_OK;
+}
+
+hg_status hg_group_run(hg_group g, const float *const *targets, const float *const *init_phases,
+                       int iters, uint8_t *const *holo_out, double *const *mse_out, void *stream) {
+    if (!g || !targets || iters < 1) return HG_ERR_INVALID_ARG;
+    DevGuard dg(g->dev);
+    const void *key[4 * HG_GROUP_MAX];
+    for (int i = 0; i < g->n; ++i) {
+        hg_plan p = g->plans[i];
+        const void *q[4] = {targets[i], init_phases ? init_phases[i] : nullptr,
+                            holo_out ? holo_out[i] : nullptr, mse_out ? mse_out[i] : nullptr};
+        if (!q[0] || p->algo == HG_OSPR) return HG_ERR_INVALID_ARG;
+        for (int k = 0; k < 4; ++k) {
+            if (q[k] && !is_device_ptr(q[k])) return HG_ERR_INVALID_ARG;  // device buffers only
+            key[4 * i + k] = q[k];
+        }
+    }
+    bool same = g->exec && g->iters == iters;
+    for (int k = 0; same && k < 4 * g->n; ++k) same = key[k] == g->key[k];
+    hg_status st;
+    if (!same) {
+        if (g->exec) cudaGraphExecDestroy(g->exec);
+        g->exec = nullptr;
+        for (int i = 0; i < g->n; ++i) {
+            if ((st = ensure_part(g->plans[i], iters)) != HG_OK) return st;
+            if ((st = ensure_metrics(g->plans[i], iters)) != HG_OK) return st;
+        }
+        HG_CK(cudaStreamBeginCapture(g->cap, cudaStreamCaptureModeThreadLocal));
+        cudaError_t e = cudaEventRecord(g->fork, g->cap);
+        g->launches = 0;
+        for (int i = 0; i < g->n && e == cudaSuccess; ++i) {
+            hg_plan p = g->plans[i];
+            e = cudaStreamWaitEvent(g->branch[i], g->fork, 0);
+            if (e != cudaSuccess) break;
+            cudaStream_t keep = p->stream;
+            const bool prof = p->prof_on;
+            p->stream = g->branch[i];
+            p->prof_on = false;
+            p->launches = 0;
+            st = enqueue_run(p, (const float *)key[4 * i], (const float *)key[4 * i + 1], iters,
+                             (uint8_t *)key[4 * i + 2], (double *)key[4 * i + 3], true);
+            g->launches += p->launches;
+            p->stream = keep;
+            p->prof_on = prof;
+            if (st != HG_OK) e = cudaErrorUnknown;
+            if (e == cudaSuccess) e = cudaEventRecord(g->join[i], g->branch[i]);
+            if (e == cudaSuccess) e = cudaStreamWaitEvent(g->cap, g->join[i], 0);
+        }
+        cudaGraph_t graph = nullptr;
+        cudaError_t e2 = cudaStreamEndCapture(g->cap, &graph);
+        if (e == cudaSuccess) e = e2;
+        if (e == cudaSuccess) e = cudaGraphInstantiate(&g->exec, graph, 0);
+        if (graph) cudaGraphDestroy(graph);
+        if (e != cudaSuccess) {
+            g->exec = nullptr;
+            return map_err(e);
+        }
+        g->iters = iters;
+        for (int k = 0; k < 4 * g->n; ++k) g->key[k] = key[k];
+    }
+    HG_CK(cudaGraphLaunch(g->exec, (cudaStream_t)stream));
+    for (int i = 0; i < g->n; ++i) {
+        hg_plan p = g->plans[i];
+        p->have_run = true;
+        p->field_from_run = true;
+        p->last_iters = iters;
+        p->weights_preset = false;
+    }
+    return HG_OK;
+}
+
+hg_status hg_group_sync(hg_group g, void *stream) {
+    if (!g) return HG_ERR_INVALID_ARG;
+    DevGuard dg(g->dev);
+    HG_CK(cudaStreamSynchronize((cudaStream_t)stream));
+    hg_status worst = HG_OK;
+    for (int i = 0; i < g->n; ++i) {
+        hg_status st = check_err_flag(g->plans[i]);
+        if (st != HG_OK && worst == HG_OK) worst = st;
+    }
+    return worst;
+}
+
+int hg_group_launch_count(hg_group g) { return g ? g->launches : 0; }
 
 }  // extern "C"

@@ -78,6 +78,16 @@ def lib():
         L.hg_profile_read.restype = I
         L.hg_plan_destroy.argtypes = [P]
         L.hg_plan_destroy.restype = None
+        L.hg_group_create.argtypes = [ctypes.POINTER(P), I, P]
+        L.hg_group_create.restype = I
+        L.hg_group_run.argtypes = [P, P, P, I, P, P, P]
+        L.hg_group_run.restype = I
+        L.hg_group_sync.argtypes = [P, P]
+        L.hg_group_sync.restype = I
+        L.hg_group_launch_count.argtypes = [P]
+        L.hg_group_launch_count.restype = I
+        L.hg_group_destroy.argtypes = [P]
+        L.hg_group_destroy.restype = None
         L.hg_status_string.argtypes = [I]
         L.hg_status_string.restype = ctypes.c_char_p
         for name in ("hg_plan_create", "hg_run", "hg_get_metrics", "hg_replay", "hg_get_phase",
@@ -207,6 +217,54 @@ def hg_profile_read(plan):
 def hg_plan_destroy(plan):
     if plan:
         lib().hg_plan_destroy(plan)
+
+
+def _ptr_array(ts, dtype, name):
+    if ts is None:
+        return None
+    arr = (ctypes.c_void_p * len(ts))()
+    for i, t in enumerate(ts):
+        p = _ptr(t, dtype, name=name)
+        arr[i] = p.value if p is not None else None
+    return ctypes.cast(arr, ctypes.c_void_p), arr
+
+
+def hg_group_create(plans):
+    """plans: list of Plan objects or raw handles."""
+    hs = [p.h if isinstance(p, Plan) else p for p in plans]
+    arr = (ctypes.c_void_p * len(hs))(*[h.value if isinstance(h, ctypes.c_void_p) else h for h in hs])
+    g = ctypes.c_void_p()
+    _ck(lib().hg_group_create(ctypes.byref(g), len(hs), ctypes.cast(arr, ctypes.c_void_p)), "hg_group_create")
+    return g
+
+
+def hg_group_run(group, targets, init_phases, iters, holo_out=None, mse_out=None, stream=None):
+    if stream is None and torch.cuda.is_available():
+        stream = torch.cuda.current_stream().cuda_stream
+    keep = []
+    args = []
+    for ts, dt, nm in ((targets, torch.float32, "targets"), (init_phases, torch.float32, "init_phases"),
+                       (holo_out, torch.uint8, "holo_out"), (mse_out, torch.float64, "mse_out")):
+        r = _ptr_array(ts, dt, nm)
+        keep.append(r)
+        args.append(None if r is None else r[0])
+    _ck(lib().hg_group_run(group, args[0], args[1], int(iters), args[2], args[3],
+                           ctypes.c_void_p(int(stream or 0))), "hg_group_run")
+
+
+def hg_group_sync(group, stream=None):
+    if stream is None and torch.cuda.is_available():
+        stream = torch.cuda.current_stream().cuda_stream
+    _ck(lib().hg_group_sync(group, ctypes.c_void_p(int(stream or 0))), "hg_group_sync")
+
+
+def hg_group_launch_count(group) -> int:
+    return lib().hg_group_launch_count(group)
+
+
+def hg_group_destroy(group):
+    if group:
+        lib().hg_group_destroy(group)
 
 
 class Plan:

@@ -420,3 +420,44 @@ def test_paired_rows_weighted_gs_binary(cand):
     # thousands of pixels in iteration 1, and the weights divide by |R|.  The
     # weight update itself is pinned by the single-step WGS tests.
     assert np.all(np.isfinite(res[1][1])) and np.all(res[1][1] >= 0)
+
+
+def test_group_mixed_sizes_one_graph():
+    """Mixed batch (512^2, 1024^2, 2048^2, 1080 x 1920) as one CUDA graph with
+    concurrent branches: identical to the plans run one by one, stable across
+    graph replays, and iteration 0 matches the oracle for every size."""
+    shapes = [(512, 512, 3), (1024, 1024, 2), (2048, 2048, 1), (1080, 1920, 1)]
+    iters = 3
+    plans, T, P, H, M, host = [], [], [], [], [], []
+    for i, (ny, nx, b) in enumerate(shapes):
+        t = synth.targets(b, ny, nx, 2000 + 100 * i)
+        ph = synth.init_phases(b, ny, nx, 2000 + 100 * i)
+        host.append((t, ph))
+        plans.append(hg.Plan(ny, nx, b))
+        T.append(torch.from_numpy(t).to(DEV))
+        P.append(torch.from_numpy(ph).to(DEV))
+        H.append(torch.empty((b, ny, nx), dtype=torch.uint8, device=DEV))
+        M.append(torch.empty((b, iters), dtype=torch.float64, device=DEV))
+    g = hg.hg_group_create(plans)
+    hg.hg_group_run(g, T, P, iters, H, M)
+    hg.hg_group_sync(g)
+    assert hg.hg_group_launch_count(g) > 2 * iters * len(shapes)
+    first = [m.cpu().numpy().copy() for m in M]
+    holos = [h.cpu().numpy().copy() for h in H]
+    hg.hg_group_run(g, T, P, iters, H, M)  # graph replay
+    hg.hg_group_sync(g)
+    for i in range(len(shapes)):
+        assert np.array_equal(M[i].cpu().numpy(), first[i])
+    for i, p in enumerate(plans):
+        h2 = torch.empty_like(H[i])
+        m2 = torch.empty_like(M[i])
+        p.run(T[i], P[i], iters, h2, m2)
+        p.sync()
+        assert np.array_equal(m2.cpu().numpy(), first[i]), shapes[i]
+        assert np.array_equal(h2.cpu().numpy(), holos[i]), shapes[i]
+        t, ph = host[i]
+        o = oracle.gs_step(oracle.prepare_target(t[0]), ph[0].astype(np.float64))
+        assert abs(first[i][0, 0] - o["mse"]) <= 1e-4 * o["mse"], shapes[i]
+    hg.hg_group_destroy(g)
+    for p in plans:
+        p.close()
