@@ -51,8 +51,13 @@ def parse():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--pipeline", type=int, default=-1)
     ap.add_argument("--autotune", type=int, default=1, help="1 tune, 0 first variant, 2+k variant k")
+    ap.add_argument("--precision", type=int, default=0,
+                    help="0 FP32 engine; 1..4 tensor-core row pass (FP16 hi+lo, FP16, BF16 hi+lo, BF16)")
     ap.add_argument("--batch", type=int, default=BATCH, help="targets per rank (profiling runs)")
     ap.add_argument("--quick", action="store_true", help="skip the e2e and CPU-baseline legs")
+    ap.add_argument("--workload", choices=["headline", "ospr", "mixed"], default="headline",
+                    help="headline: binary GS 1024^2 x 64 (the benchmark line); ospr: 8 targets x 24 "
+                         "subframes of 1024^2; mixed: 16 targets each of 512^2, 1024^2, 2048^2, 1080x1920")
     return ap.parse_args()
 
 
@@ -184,10 +189,74 @@ def traffic_for(kernel_key):
     return None
 
 
+def run_side_workload(args):
+    """Throughput of the other configurations (reported in DESIGN, not the
+    benchmark line): OSPR subframes/s, and batched iterations/s of the mixed
+    batch run as one CUDA graph."""
+    import torch
+    import __graft_entry__
+    from paper_2008_12214_gb300 import hologen as hg
+    from paper_2008_12214_gb300 import synth
+    __graft_entry__.build()
+    dev = torch.device("cuda", 0)
+    s0 = torch.cuda.current_stream(dev)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    if args.workload == "ospr":
+        B, NS = 8, 24
+        T = torch.from_numpy(synth.targets(B, NY, NX)).to(dev)
+        holo = torch.empty((B, NS, NY, NX), dtype=torch.uint8, device=dev)
+        mse = torch.empty(B, dtype=torch.float64, device=dev)
+        plan = hg.Plan(NY, NX, B, hg.HG_SLM_BINARY, 2, hg.HG_OSPR, subframes=NS, seed=7)
+        for _ in range(args.warmup):
+            plan.run(T, None, 1, holo, mse)
+        plan.sync()
+        e0.record(s0)
+        for _ in range(args.steps):
+            plan.run(T, None, 1, holo, mse)
+        e1.record(s0)
+        plan.sync()
+        ms = e0.elapsed_time(e1) / args.steps
+        out = dict(workload="ospr_8x24_1024x1024", ms_per_step=ms, subframes_per_s=B * NS / (ms / 1e3),
+                   algorithmic_gbs=36.0 * B * NS * NY * NX / (ms / 1e3) / 1e9,
+                   mse=mse.cpu().numpy().tolist(), column_variant=hg.hg_plan_variant(plan.h, 1))
+        plan.close()
+    else:
+        shapes = [(512, 512), (1024, 1024), (2048, 2048), (1080, 1920)]
+        plans, Ts, Ps, Ms = [], [], [], []
+        for i, (ny, nx) in enumerate(shapes):
+            plans.append(hg.Plan(ny, nx, 16))
+            Ts.append(torch.from_numpy(synth.targets(16, ny, nx, 3000 + 16 * i)).to(dev))
+            Ps.append(torch.from_numpy(synth.init_phases(16, ny, nx, 3000 + 16 * i)).to(dev))
+            Ms.append(torch.empty((16, args.iters), dtype=torch.float64, device=dev))
+        g = hg.hg_group_create(plans)
+        for _ in range(args.warmup):
+            hg.hg_group_run(g, Ts, Ps, args.iters, None, Ms)
+        hg.hg_group_sync(g)
+        e0.record(s0)
+        for _ in range(args.steps):
+            hg.hg_group_run(g, Ts, Ps, args.iters, None, Ms)
+        e1.record(s0)
+        hg.hg_group_sync(g)
+        ms = e0.elapsed_time(e1) / args.steps
+        px = 16 * sum(a * b for a, b in shapes)
+        out = dict(workload="mixed_64_targets_one_graph", ms_per_step=ms, iters_per_step=args.iters,
+                   batched_iterations_per_s=args.iters / (ms / 1e3),
+                   algorithmic_gbs_at_36=36.0 * px * args.iters / (ms / 1e3) / 1e9,
+                   variants=[(hg.hg_plan_variant(p.h, 0), hg.hg_plan_variant(p.h, 1)) for p in plans],
+                   launches_per_step=hg.hg_group_launch_count(g))
+        hg.hg_group_destroy(g)
+        for p in plans:
+            p.close()
+    print(json.dumps(out), flush=True)
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
+        return
+    if args.workload != "headline":
+        run_side_workload(args)
         return
     import torch
     import __graft_entry__
@@ -216,7 +285,7 @@ def main():
     holo = torch.empty((B, NY, NX), dtype=torch.uint8, device=dev)
     mse = torch.empty((B, args.iters), dtype=torch.float64, device=dev)
     plan = hg.Plan(NY, NX, B, hg.HG_SLM_BINARY, 2, hg.HG_GS, pipeline=args.pipeline,
-                   autotune=args.autotune)
+                   autotune=args.autotune, precision=args.precision)
     stream = torch.cuda.current_stream(dev)
 
     for _ in range(args.warmup):
@@ -313,7 +382,8 @@ def main():
     line = dict(
         metric=METRIC, value=value, unit=UNIT, n_gpus=world, steps=args.steps, warmup=args.warmup,
         ms_per_step=el_ms / args.steps, higher_is_better=True, scaling="weak", vs_baseline=None,
-        dtype="f32", data=DATA,
+        dtype="f32" if args.precision == 0 else ["", "f16x2", "f16", "bf16x2", "bf16"][args.precision],
+        data=DATA,
         config=dict(workload="gs_binary_1024x1024_batch%d" % B, ny=NY, nx=NX, batch=B,
                     iters_per_step=args.iters, slm="binary", parallelism="dp%d" % world,
                     row_variant=variants[0], column_variant=variants[1],

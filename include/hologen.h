@@ -71,7 +71,12 @@ typedef struct {
     void *stream;      /* cudaStream_t to enqueue on; NULL = legacy default stream */
     uint64_t seed;     /* Philox4x32-10 key for drawn phases */
     int subframes;     /* OSPR subframes per target (>= 1); ignored otherwise */
-    int precision;     /* 0 = FP32 transforms (the only value accepted) */
+    int precision;     /* 0 (default): FP32 transforms.  1..4: the row pass runs its
+                          radix-32 DFT stages as tensor-core GEMMs (tcgen05, FP32
+                          accumulation) with 1 FP16 hi+lo split operands, 2 FP16,
+                          3 BF16 hi+lo, 4 BF16 (the 16-bit builds of Section 4.5);
+                          rows of 1024 samples only (else
+                          HG_ERR_UNSUPPORTED_SIZE), not OSPR */
     int use_graph;     /* 1 = replay the iteration loop as a CUDA graph (default) */
     int pipeline;      /* -1 auto (default): TMA-fed passes where the size allows;
                           0: generic passes only; 1: require TMA-fed passes */
@@ -93,7 +98,7 @@ int hg_supported_length(int n);
  * device.  Allocates the plan's device workspace (the field, the prepared
  * targets, weights, twiddle tables and metric partials).  opts may be NULL
  * (defaults).  Errors: HG_ERR_INVALID_ARG (out NULL, batch < 1, bad slm or
- * algo, OSPR with a non-binary SLM, subframes < 1, precision != 0),
+ * algo, OSPR with a non-binary SLM, subframes < 1, precision outside 0..4),
  * HG_ERR_UNSUPPORTED_SIZE, HG_ERR_OOM, HG_ERR_CUDA. */
 hg_status hg_plan_create(hg_plan *out, int ny, int nx, int batch, hg_slm slm, hg_algo algo,
                          const hg_opts *opts);

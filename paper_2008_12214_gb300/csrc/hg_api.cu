@@ -12,6 +12,7 @@
 #include <vector>
 
 #include "hg_pipe.cuh"
+#include "hg_tc.cuh"
 #include "hologen.h"
 
 using namespace hg;
@@ -201,6 +202,21 @@ cudaError_t ensure_pipe_init(int dev, const PipeOps *o) {
     return cudaErrorUnknown;
 }
 
+bool g_tc_inited[kMaxDev];
+int g_tc_blocks[kMaxDev];
+
+cudaError_t ensure_tc_init(int dev, int *blocks) {
+    std::lock_guard<std::mutex> lk(g_init_mu);
+    if (dev < 0 || dev >= kMaxDev) return cudaErrorInvalidDevice;
+    if (!g_tc_inited[dev]) {
+        cudaError_t e = tc_init(&g_tc_blocks[dev]);
+        if (e != cudaSuccess) return e;
+        g_tc_inited[dev] = true;
+    }
+    *blocks = g_tc_blocks[dev] > 0 ? g_tc_blocks[dev] : 1;
+    return cudaSuccess;
+}
+
 typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *,
                                   const cuuint64_t *, const cuuint64_t *, const cuuint32_t *,
                                   const cuuint32_t *, CUtensorMapInterleave, CUtensorMapSwizzle,
@@ -248,6 +264,9 @@ struct hg_plan_s {
     const LineOps *rops = nullptr, *cops = nullptr;
     const PipeOps *prow = nullptr, *pcol = nullptr;  // pipelined passes (null: generic)
     float tune_ms[8] = {0};                          // autotuner timings: row cands, col cands
+    int tc_prec = 0;                                 // tensor-core row pass precision (0: FP32 engine)
+    uint4 *tc_b = nullptr;                           // DFT-32 operand matrices
+    int tc_blocks = 1, ppt_tc = 0;
     CUtensorMap cmap;                                // field as [chains*ny][2*nx] floats
     unsigned long long wait_ns = 2000000000ull;      // bound on a device-side wait
     int drop_job = -1;                               // fault-injection hook
@@ -425,9 +444,24 @@ struct ProfScope {  // records an event pair around one pass launch when profili
     }
 };
 
+TcArgs tc_args(hg_plan p) {
+    TcArgs t{};
+    t.bmats = p->tc_b;
+    t.err = p->err;
+    t.wait_ns = p->wait_ns;
+    return t;
+}
+
+void launch_row_tc(hg_plan p, int role, const RowArgs &a, cudaStream_t s) {
+    tc_launch_row(p->tc_prec, role, a, tc_args(p), grid_for(p->tc_blocks, p->nsm, (long)a.items * p->ppt_tc), s);
+    p->launches++;
+}
+
 void launch_row_iter(hg_plan p, const RowArgs &a, cudaStream_t s) {
     ProfScope ps(p, s, 0);
-    if (p->prow) {
+    if (p->tc_prec) {
+        launch_row_tc(p, ROW_ITER, a, s);
+    } else if (p->prow) {
         const long work = (long)a.items * p->ppt_pipe;
         p->prow->row_iter(a, pipe_args(p), grid_for(p->prow->row_blocks_per_sm, p->nsm, work), s);
         p->launches++;
@@ -531,7 +565,7 @@ hg_status enqueue_run(hg_plan p, const float *d_t, const float *d_ph, int iters,
         launch_row(p, ROW_HEAD, ra, p->stream);
         ca.items = p->nchains;
         ca.holo = d_ho;
-        launch_col(p, COL_GS_BIN, ca, p->stream);
+        launch_col_gs(p, COL_GS_BIN, ca, p->stream);
         RowArgs rt = row_args(p);
         rt.nsub = p->nsub;
         rt.part = p->part;
@@ -552,11 +586,14 @@ hg_status enqueue_run(hg_plan p, const float *d_t, const float *d_ph, int iters,
         launch_col_gs(p, col_role_gs(p), ca, p->stream);
         RowArgs rt = row_args(p);
         rt.part = p->part + (size_t)(iters - 1) * p->batch * p->ppt_max * NMET;
-        launch_row(p, ROW_TAIL, rt, p->stream);
+        if (p->tc_prec) launch_row_tc(p, ROW_TAIL, rt, p->stream);
+        else launch_row(p, ROW_TAIL, rt, p->stream);
     }
+    const int panels_iter = p->tc_prec ? p->ppt_tc : p->prow ? p->ppt_pipe : p->ppt;
+    const int panels_last = (p->tc_prec && p->algo != HG_OSPR) ? p->ppt_tc : p->ppt;
     k_reduce<<<(iters * p->batch * 32 + 127) / 128, 128, 0, p->stream>>>(
-        p->part, iters, p->batch, p->ppt_max, p->prow ? p->ppt_pipe : p->ppt, p->ppt,
-        1.0 / (double)p->npx, p->metrics, d_mo);
+        p->part, iters, p->batch, p->ppt_max, panels_iter, panels_last, 1.0 / (double)p->npx, p->metrics,
+        d_mo);
     p->launches++;
     HG_CK(cudaGetLastError());
     p->weights_preset = false;
@@ -684,7 +721,7 @@ void hg_plan_destroy(hg_plan p) {
     if (p->cap_stream) cudaStreamDestroy(p->cap_stream);
     for (cudaEvent_t e : p->prof_ev) cudaEventDestroy(e);
     void *bufs[] = {p->field, p->tf, p->w, p->part, p->metrics, p->sum_part, p->scale,
-                    p->err, p->twx, p->twy, p->lvl, p->stage};
+                    p->err, p->twx, p->twy, p->lvl, p->stage, p->tc_b};
     for (void *b : bufs)
         if (b) cudaFree(b);
     delete p;
@@ -702,7 +739,8 @@ hg_status hg_plan_create(hg_plan *out, int ny, int nx, int batch, hg_slm slm, hg
     if (slm.kind != HG_SLM_BINARY && slm.kind != HG_SLM_LLEVEL) return HG_ERR_INVALID_ARG;
     if (slm.kind == HG_SLM_LLEVEL && (slm.levels < 2 || slm.levels > 256)) return HG_ERR_INVALID_ARG;
     if (algo == HG_OSPR && (slm.kind != HG_SLM_BINARY || o.subframes < 1)) return HG_ERR_INVALID_ARG;
-    if (o.precision != 0) return HG_ERR_INVALID_ARG;
+    if (o.precision < 0 || o.precision > 4) return HG_ERR_INVALID_ARG;
+    if (o.precision > 0 && (nx != TC_N || ny % 4 != 0 || algo == HG_OSPR)) return HG_ERR_UNSUPPORTED_SIZE;
     const LineOps *rops = find_ops(nx), *cops = find_ops(ny);
     if (!rops || !cops) return HG_ERR_UNSUPPORTED_SIZE;
     const size_t npx = (size_t)ny * nx;
@@ -766,6 +804,19 @@ hg_status hg_plan_create(hg_plan *out, int ny, int nx, int batch, hg_slm slm, hg
         }
         ce = cudaMalloc(&p->lvl, sizeof(float2) * L);
         if (ce == cudaSuccess) ce = cudaMemcpy(p->lvl, h, sizeof(float2) * L, cudaMemcpyHostToDevice);
+        if (ce != cudaSuccess) return fail(map_err(ce));
+    }
+    if (o.precision > 0) {  // tensor-core row pass: DFT-32 operands, per-device attributes
+        p->tc_prec = o.precision;
+        p->ppt_tc = ny / 4;
+        if (p->ppt_tc > p->ppt_max) p->ppt_max = p->ppt_tc;
+        ce = ensure_tc_init(p->dev, &p->tc_blocks);
+        uint16_t *hb = (uint16_t *)malloc(4 * TC_B);
+        if (!hb) return fail(HG_ERR_OOM);
+        tc_make_bmats(o.precision, hb);
+        if (ce == cudaSuccess) ce = cudaMalloc(&p->tc_b, 4 * TC_B);
+        if (ce == cudaSuccess) ce = cudaMemcpy(p->tc_b, hb, 4 * TC_B, cudaMemcpyHostToDevice);
+        free(hb);
         if (ce != cudaSuccess) return fail(map_err(ce));
     }
     // Pass variants are chosen (and timed) only once every buffer they touch exists.
@@ -836,7 +887,7 @@ hg_status hg_plan_create(hg_plan *out, int ny, int nx, int batch, hg_slm slm, hg
                 g_tune.push_back({p->dev, ny, nx, p->nchains, slm.kind, row, col});
             }
         }
-        if (row) {
+        if (row && !p->tc_prec) {
             p->prow = row;
             p->ppt_pipe = row_panels(row, ny);
             if (p->ppt_pipe > p->ppt_max) p->ppt_max = p->ppt_pipe;
@@ -905,6 +956,11 @@ hg_status hg_profile_read(hg_plan p, double *out4) {
 
 const char *hg_plan_variant(hg_plan p, int pass) {
     if (!p) return "";
+    if (pass == 0 && p->tc_prec) {
+        static const char *names[] = {"", "1024:tc32x32-fp16hilo", "1024:tc32x32-fp16", "1024:tc32x32-bf16hilo",
+                                      "1024:tc32x32-bf16"};
+        return names[p->tc_prec];
+    }
     const PipeOps *o = pass == 0 ? p->prow : p->pcol;
     return o ? o->name : "generic";
 }
@@ -1095,10 +1151,11 @@ hg_status hg_debug_step(hg_plan p, const float *target, const float *phase_in, f
     RowArgs rt = row_args(p);
     rt.part = p->part;
     rt.R_out = (float2 *)replay_out;
-    launch_row(p, ROW_TAIL, rt, p->stream);
-    k_reduce<<<(p->batch * 32 + 127) / 128, 128, 0, p->stream>>>(p->part, 1, p->batch, p->ppt_max,
-                                                             p->ppt, p->ppt, 1.0 / (double)p->npx,
-                                                             p->metrics, nullptr);
+    if (p->tc_prec) launch_row_tc(p, ROW_TAIL, rt, p->stream);
+    else launch_row(p, ROW_TAIL, rt, p->stream);
+    const int pl = p->tc_prec ? p->ppt_tc : p->ppt;
+    k_reduce<<<(p->batch * 32 + 127) / 128, 128, 0, p->stream>>>(p->part, 1, p->batch, p->ppt_max, pl, pl,
+                                                             1.0 / (double)p->npx, p->metrics, nullptr);
     p->launches++;
     if (metrics_out)
         HG_CK(cudaMemcpyAsync(metrics_out, p->metrics, sizeof(double) * NMET * p->batch,

@@ -1,0 +1,84 @@
+// Tensor-core row pass (1024-sample rows): instantiations, launchers and the
+// DFT-32 operand matrices.
+#include <cmath>
+
+#include "hg_pipe.cuh"
+#include "hg_tc.cuh"
+
+namespace hg {
+
+namespace {
+template <int PREC>
+cudaError_t set_attr() {
+    cudaError_t e = cudaFuncSetAttribute((const void *)k_row_tc<PREC, ROW_ITER>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, TC_SMEM);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute((const void *)k_row_tc<PREC, ROW_TAIL>,
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize, TC_SMEM);
+    return e;
+}
+
+template <int PREC>
+void launch(int role, const RowArgs &a, const TcArgs &ta, int grid, cudaStream_t s) {
+    if (role == ROW_ITER) k_row_tc<PREC, ROW_ITER><<<grid, 128, TC_SMEM, s>>>(a, ta);
+    else k_row_tc<PREC, ROW_TAIL><<<grid, 128, TC_SMEM, s>>>(a, ta);
+}
+
+uint16_t bits_of(float x, int prec, float *back) {
+    if (prec <= 2) {
+        __half h = __float2half_rn(x);
+        *back = __half2float(h);
+        return *reinterpret_cast<uint16_t *>(&h);
+    }
+    __nv_bfloat16 b = __float2bfloat16_rn(x);
+    *back = __bfloat162float(b);
+    return *reinterpret_cast<uint16_t *>(&b);
+}
+}  // namespace
+
+cudaError_t tc_init(int *blocks_per_sm) {
+    cudaError_t e = set_attr<1>();
+    if (e == cudaSuccess) e = set_attr<2>();
+    if (e == cudaSuccess) e = set_attr<3>();
+    if (e == cudaSuccess) e = set_attr<4>();
+    if (e == cudaSuccess)
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k_row_tc<1, ROW_ITER>, 128, TC_SMEM);
+    return e;
+}
+
+void tc_launch_row(int prec, int role, const RowArgs &a, const TcArgs &ta, int grid, cudaStream_t s) {
+    switch (prec) {
+        case 1: launch<1>(role, a, ta, grid, s); break;
+        case 2: launch<2>(role, a, ta, grid, s); break;
+        case 3: launch<3>(role, a, ta, grid, s); break;
+        default: launch<4>(role, a, ta, grid, s); break;
+    }
+}
+
+// B[2k + c_out][2n + c_in] for W = exp(DIR 2 pi i n k / 32): the real form of
+// y_k = sum_n W^{nk} x_n with interleaved (re, im).  Angles reduced as exact
+// integers and evaluated in long double; hi = round(B), lo = round(B - hi).
+void tc_make_bmats(int prec, uint16_t *out) {
+    const long double two_pi = 6.283185307179586476925286766559005768L;
+    for (int d = 0; d < 2; ++d) {
+        const int dir = d == 0 ? -1 : +1;
+        uint16_t *hi = out + (2 * d) * 4096, *lo = out + (2 * d + 1) * 4096;
+        for (int k = 0; k < 32; ++k)
+            for (int n = 0; n < 32; ++n) {
+                const long double ang = two_pi * (long double)((n * k) % 32) / 32.0L;
+                const float re = (float)cosl(ang), im = (float)(dir * sinl(ang));
+                const float vals[2][2] = {{re, -im}, {im, re}};  // [c_out][c_in]
+                for (int co = 0; co < 2; ++co)
+                    for (int ci = 0; ci < 2; ++ci) {
+                        const int r = 2 * k + co, c = 2 * n + ci;
+                        const int idx = ((r >> 3) * 1024 + (c >> 3) * 128 + (r & 7) * 16 + (c & 7) * 2) / 2;
+                        float back;
+                        hi[idx] = bits_of(vals[co][ci], prec, &back);
+                        float b2;
+                        lo[idx] = bits_of(vals[co][ci] - back, prec, &b2);
+                    }
+            }
+    }
+}
+
+}  // namespace hg

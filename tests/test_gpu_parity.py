@@ -461,3 +461,43 @@ def test_group_mixed_sizes_one_graph():
     hg.hg_group_destroy(g)
     for p in plans:
         p.close()
+
+
+@pytest.mark.parametrize("prec,tol", [(1, 1e-5), (2, 3e-3), (3, 1e-5), (4, 3e-3)])
+def test_tensor_core_row_pass_precision(prec, tol):
+    """Row-pass DFT stages as tcgen05 GEMMs (1 FP16 hi+lo, 2 FP16, 3 BF16
+    hi+lo, 4 BF16): the replay field the tensor-core pass computes from the
+    GPU's hologram, against the oracle's replay of that hologram (single-step
+    relative L2), and a 6-iteration run's final MSE against the FP32 engine."""
+    n, batch = 1024, 2
+    t = synth.targets(batch, n, n)
+    ph = synth.init_phases(batch, n, n)
+    T = torch.from_numpy(t).to(DEV)
+    P = torch.from_numpy(ph).to(DEV)
+    plan = hg.Plan(n, n, batch, precision=prec)
+    assert "tc32x32" in hg.hg_plan_variant(plan.h, 0)
+    holo = torch.empty((batch, n, n), dtype=torch.uint8, device=DEV)
+    R_out = torch.empty((batch, n, n), dtype=torch.complex64, device=DEV)
+    met = torch.empty((batch, 4), dtype=torch.float64, device=DEV)
+    hg.hg_debug_step(plan.h, T, P, None, holo, R_out, met)
+    plan.sync()
+    mse = torch.empty((batch, 6), dtype=torch.float64, device=DEV)
+    plan.run(T, P, 6, None, mse)
+    plan.sync()
+    plan.close()
+    ref_plan = hg.Plan(n, n, batch)
+    mse32 = torch.empty((batch, 6), dtype=torch.float64, device=DEV)
+    ref_plan.run(T, P, 6, None, mse32)
+    ref_plan.sync()
+    ref_plan.close()
+    holo, R_out, met = holo.cpu().numpy(), R_out.cpu().numpy(), met.cpu().numpy()
+    errs = []
+    for b in range(batch):
+        Rref = oracle.replay_field(holo[b])
+        errs.append(rel_l2(R_out[b], Rref))
+        mref = oracle.metrics(np.abs(Rref) ** 2, oracle.prepare_target(t[b]))
+        assert abs(met[b, 0] - mref[0]) <= max(10 * tol, 1e-4) * mref[0]
+    d = np.abs(mse.cpu().numpy()[:, -1] - mse32.cpu().numpy()[:, -1]) / mse32.cpu().numpy()[:, -1]
+    print("precision %d: single-step rel-L2 %s, final-MSE delta vs FP32 %s" % (prec, errs, d))
+    assert max(errs) <= tol
+    assert np.all(d < 0.05)
