@@ -263,11 +263,13 @@ struct hg_plan_s {
     int use_graph = 1;
     const LineOps *rops = nullptr, *cops = nullptr;
     const PipeOps *prow = nullptr, *pcol = nullptr;  // pipelined passes (null: generic)
-    float tune_ms[8] = {0};                          // autotuner timings: row cands, col cands
+    float tune_ms[8] = {0};                          // autotuner timings: row cands (+ implied column), col cands
     int tc_prec = 0;                                 // tensor-core row pass precision (0: FP32 engine)
     uint4 *tc_b = nullptr;                           // DFT-32 operand matrices
     int tc_blocks = 1, ppt_tc = 0;
     CUtensorMap cmap;                                // field as [chains*ny][2*nx] floats
+    CUtensorMap cmap_pack;                           // same field, tiles of the packed column pass
+    bool use_pack = false;                           // binary: packed column pass in the loop
     unsigned long long wait_ns = 2000000000ull;      // bound on a device-side wait
     int drop_job = -1;                               // fault-injection hook
     int nsm = 0, ppt = 0, ppt_pipe = 0, ppt_max = 0;
@@ -470,6 +472,13 @@ void launch_row_iter(hg_plan p, const RowArgs &a, cudaStream_t s) {
     }
 }
 
+void launch_col_pack(hg_plan p, const ColArgs &a, cudaStream_t s) {
+    ProfScope ps(p, s, 1);
+    const long work = (long)a.items * ((p->nx + p->prow->col_c - 1) / p->prow->col_c);
+    p->prow->col_pack(a, pipe_args(p), p->cmap_pack, grid_for(p->prow->pack_blocks_per_sm, p->nsm, work), s);
+    p->launches++;
+}
+
 void launch_col_gs(hg_plan p, int role, const ColArgs &a, cudaStream_t s) {
     ProfScope ps(p, s, 1);
     if (p->pcol) {
@@ -509,7 +518,8 @@ void enqueue_loop(hg_plan p, int iters, cudaStream_t s) {
     RowArgs ra = row_args(p);
     ca.half = p->prow && p->prow->paired;  // the paired row pass rebuilds rows ny - ky
     for (int k = 0; k + 1 < iters; ++k) {
-        launch_col_gs(p, col_role_gs(p), ca, s);
+        if (p->use_pack) launch_col_pack(p, ca, s);
+        else launch_col_gs(p, col_role_gs(p), ca, s);
         ra.part = p->part + (size_t)k * p->batch * p->ppt_max * NMET;
         launch_row_iter(p, ra, s);
     }
@@ -627,7 +637,7 @@ bool make_cmap(hg_plan p, const PipeOps *pc, CUtensorMap *m) {
 
 // Best-of-3 launch time (ms, after one warm-up launch) of one pass variant on
 // the plan's own zeroed buffers, on the private capture stream.
-float time_variant(hg_plan p, const PipeOps *o, bool row) {
+float time_variant(hg_plan p, const PipeOps *o, bool row, bool pack = false) {
     if (!p->field || !p->tf || !p->twx || !p->twy || !p->lvl || !p->err) return 1e30f;
     cudaStream_t s = p->cap_stream;
     RowArgs ra = row_args(p);
@@ -636,9 +646,10 @@ float time_variant(hg_plan p, const PipeOps *o, bool row) {
     ColArgs ca = col_args(p);
     CUtensorMap m;
     if (!row && !make_cmap(p, o, &m)) return 1e30f;
+    if (pack) ca.half = 1;
     const int ppt = row ? row_panels(o, p->ny) : (p->nx + o->col_c - 1) / o->col_c;
-    const int grid = grid_for(row ? o->row_blocks_per_sm : o->col_blocks_per_sm, p->nsm,
-                              (long)p->batch * ppt);
+    const int grid = grid_for(row ? o->row_blocks_per_sm : pack ? o->pack_blocks_per_sm : o->col_blocks_per_sm,
+                              p->nsm, (long)p->batch * ppt);
     PipeArgs pa = pipe_args(p);
     cudaEvent_t e0, e1;
     if (cudaEventCreate(&e0) != cudaSuccess) return 1e30f;
@@ -652,6 +663,7 @@ float time_variant(hg_plan p, const PipeOps *o, bool row) {
     for (int it = 0; it < 7; ++it) {
         cudaEventRecord(e0, s);
         if (row) o->row_iter(ra, pa, grid, s);
+        else if (pack) o->col_pack(ca, pa, m, grid, s);
         else o->col_gs(p->kind == HG_SLM_BINARY ? COL_GS_BIN : COL_GS_LVL, ca, pa, m, grid, s);
         cudaEventRecord(e1, s);
         if (cudaEventSynchronize(e1) != cudaSuccess) break;
@@ -823,11 +835,11 @@ hg_status hg_plan_create(hg_plan *out, int ny, int nx, int batch, hg_slm slm, hg
     if (o.pipeline != 0) {
         // TMA-fed passes: row panels need 16-byte aligned rows of T (nx % 4 == 0);
         // the column tiles need a 16-byte multiple row pitch (nx even).
-        const PipeOps *rc[4], *cc[4];
+        const PipeOps *rc[8], *cc[8];
         int nr = 0, nc = 0;
         {
-            const PipeOps *all[4];
-            const int k = pipe_candidates(nx, all, 4);
+            const PipeOps *all[8];
+            const int k = pipe_candidates(nx, all, 8);
             for (int i = 0; i < k; ++i) {
                 // paired rows need a binary SLM (real e^{iH}), an even column length and the
                 // GS/WGS loop
@@ -837,8 +849,8 @@ hg_status hg_plan_create(hg_plan *out, int ny, int nx, int batch, hg_slm slm, hg
             }
         }
         {
-            const PipeOps *all[4];
-            const int k = pipe_candidates(ny, all, 4);
+            const PipeOps *all[8];
+            const int k = pipe_candidates(ny, all, 8);
             CUtensorMap m;
             for (int i = 0; i < k; ++i)
                 if (!all[i]->paired && all[i]->col_gs && nx % 2 == 0 &&
@@ -871,17 +883,20 @@ hg_status hg_plan_create(hg_plan *out, int ny, int nx, int batch, hg_slm slm, hg
                 ce = cudaStreamSynchronize(p->cap_stream);
                 if (ce == cudaSuccess) ce = cudaGetLastError();
                 if (ce != cudaSuccess) return fail(map_err(ce));
-                float best = 1e30f;
-                for (int i = 0; i < nr && nr > 1; ++i) {
-                    const float ms = time_variant(p, rc[i], true);
-                    p->tune_ms[i] = ms;
-                    if (ms < best) best = ms, row = rc[i];
+                // columns first; a row candidate is scored by its own time plus
+                // the column pass it implies (its packed column pass, if any)
+                float best = 1e30f, best_col = 1e30f;
+                for (int i = 0; i < nc; ++i) {
+                    const float ms = nc > 1 || nr > 1 ? time_variant(p, cc[i], false) : 0.f;
+                    if (i < 4) p->tune_ms[4 + i] = ms;
+                    if (ms < best_col) best_col = ms, col = cc[i];
                 }
-                best = 1e30f;
-                for (int i = 0; i < nc && nc > 1; ++i) {
-                    const float ms = time_variant(p, cc[i], false);
-                    p->tune_ms[4 + i] = ms;
-                    if (ms < best) best = ms, col = cc[i];
+                for (int i = 0; i < nr; ++i) {
+                    float ms = time_variant(p, rc[i], true);
+                    if (i < 4) p->tune_ms[i] = ms;
+                    const bool pk = rc[i]->paired && rc[i]->col_pack && slm.kind == HG_SLM_BINARY;
+                    ms += pk ? time_variant(p, rc[i], false, true) : best_col;
+                    if (ms < best) best = ms, row = rc[i];
                 }
                 std::lock_guard<std::mutex> lk(g_tune_mu);
                 g_tune.push_back({p->dev, ny, nx, p->nchains, slm.kind, row, col});
@@ -889,6 +904,8 @@ hg_status hg_plan_create(hg_plan *out, int ny, int nx, int batch, hg_slm slm, hg
         }
         if (row && !p->tc_prec) {
             p->prow = row;
+            p->use_pack = row->paired && row->col_pack && slm.kind == HG_SLM_BINARY && nx % 2 == 0 &&
+                          ny == row->N && make_cmap(p, row, &p->cmap_pack);
             p->ppt_pipe = row_panels(row, ny);
             if (p->ppt_pipe > p->ppt_max) p->ppt_max = p->ppt_pipe;
         }
@@ -956,6 +973,7 @@ hg_status hg_profile_read(hg_plan p, double *out4) {
 
 const char *hg_plan_variant(hg_plan p, int pass) {
     if (!p) return "";
+    if (pass == 1 && p->use_pack) return "packed-binary-columns (with the row variant)";
     if (pass == 0 && p->tc_prec) {
         static const char *names[] = {"", "1024:tc32x32-fp16hilo", "1024:tc32x32-fp16", "1024:tc32x32-bf16hilo",
                                       "1024:tc32x32-bf16"};

@@ -57,11 +57,12 @@ struct ColArgs {
                            // row pass rebuilds rows ny - y from the Hermitian symmetry)
 };
 
-// Sum four per-thread float partials over the block in double, in a fixed
-// order, and store them at dst (thread 0).  All threads must call.
+// Sum four per-thread float partials over the block in a fixed order (lanes
+// in float, warps in double) and store them at dst (thread 0).  All threads
+// must call.
 __device__ __forceinline__ void block_sum4(float a0, float a1, float a2, float a3, double *red,
                                            double *dst, int nthreads) {
-    double d[NMET] = {a0, a1, a2, a3};
+    float d[NMET] = {a0, a1, a2, a3};
 #pragma unroll
     for (int off = 16; off; off >>= 1)
 #pragma unroll
@@ -69,7 +70,7 @@ __device__ __forceinline__ void block_sum4(float a0, float a1, float a2, float a
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     if (lane == 0)
 #pragma unroll
-        for (int m = 0; m < NMET; ++m) red[warp * NMET + m] = d[m];
+        for (int m = 0; m < NMET; ++m) red[warp * NMET + m] = (double)d[m];
     __syncthreads();
     if (threadIdx.x == 0) {
         double s[NMET] = {0, 0, 0, 0};

@@ -353,14 +353,14 @@ __global__ void __launch_bounds__(128, 1) k_row_tc(const RowArgs a, const TcArgs
             for (int e = 0; e < 32; ++e) fw[lane + 32 * e] = v[e];
         }
         if (a.part) {  // per-panel partial sums: warps in fixed order
-            double dm[NMET] = {acc0, acc1, acc2, acc3};
+            float dm[NMET] = {acc0, acc1, acc2, acc3};
 #pragma unroll
             for (int off = 16; off; off >>= 1)
 #pragma unroll
                 for (int q = 0; q < NMET; ++q) dm[q] += __shfl_down_sync(0xffffffffu, dm[q], off);
             if (lane == 0)
 #pragma unroll
-                for (int q = 0; q < NMET; ++q) red[warp * NMET + q] = dm[q];
+                for (int q = 0; q < NMET; ++q) red[warp * NMET + q] = (double)dm[q];
             __syncthreads();
             if (tid == 0)
                 for (int q = 0; q < NMET; ++q)

@@ -15,13 +15,17 @@ PipeOps p1024c = PairedOps<PairImpl<Plan<1024, 64, 16, 16, 16, 4>, 6, 2, 4>, &p1
     "1024:pair16x16x4e16+c32x32e32");
 PipeOps p1024d = PairedOps<PairImpl<Plan<1024, 32, 32, 32, 32>, 6, 2, 5>, &p1024a>::make(
     "1024:pair32x32e32+c32x32e32");
+PipeOps p1024e =
+    PairedOps<PairImpl<Plan<1024, 64, 16, 16, 16, 4>, 6, 2, 4>, &p1024a,
+              PackImpl<Plan<1024, 32, 32, 32, 32>, Plan<1024, 64, 16, 16, 16, 4>, 8, 1, 3, 5, 4, 256>>::
+        make("1024:pair16x16x4e16+pack32x32/16x16x4");
 }  // namespace
 
 const LineOps *ops_1024(int n) { return n == 1024 ? &o1024 : nullptr; }
 
 int pipe_ops_1024(int n, const PipeOps **out, int max) {
     if (n != 1024) return 0;
-    const PipeOps *c[] = {&p1024a, &p1024b, &p1024c, &p1024d};
+    const PipeOps *c[] = {&p1024a, &p1024b, &p1024c, &p1024d, &p1024e};
     int k = 0;
     for (const PipeOps *o : c)
         if (k < max) out[k++] = o;

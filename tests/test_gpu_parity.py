@@ -364,7 +364,7 @@ def test_bounded_wait_reports_timeout_and_plan_recovers():
 
 
 @pytest.mark.parametrize("n,cand", [(256, 0), (512, 0), (512, 1), (512, 2), (1024, 0), (1024, 1), (1024, 2),
-                                    (1024, 3), (2048, 0), (2048, 1), (2048, 2)])
+                                    (1024, 3), (1024, 4), (2048, 0), (2048, 1), (2048, 2)])
 def test_every_pipelined_variant_against_oracle(n, cand):
     """Each TMA-fed candidate the autotuner may pick, forced in turn: the
     column pass through a single step, the row pass through the metrics it
@@ -395,7 +395,7 @@ def test_every_pipelined_variant_against_oracle(n, cand):
         assert abs(mse[b, 3] - run["mse"][3]) <= 1e-2 * run["mse"][3], name
 
 
-@pytest.mark.parametrize("cand", [2, 3])
+@pytest.mark.parametrize("cand", [2, 3, 4])
 def test_paired_rows_weighted_gs_binary(cand):
     """The paired-row pass (binary SLM) also carries the weighted-GS update:
     same metrics and weights as the generic passes on the first iterations."""
