@@ -162,10 +162,7 @@ const LineOps *find_ops(int n) {
 
 int pipe_candidates(int n, const PipeOps **out, int max) {
     int k = pipe_ops_mid(n, out, max);
-    if (!k) {
-        k = pipe_ops_1024(n, out, max);
-        k += pipe_ops_1024x(n, out + k, max - k);
-    }
+    if (!k) k = pipe_ops_1024(n, out, max);
     if (!k) k = pipe_ops_2048(n, out, max);
     if (!k) k = pipe_ops_hd(n, out, max);
     return k;

@@ -908,7 +908,6 @@ struct PairedOps {
 // written); the first is the default when autotuning is off.
 int pipe_ops_mid(int n, const PipeOps **out, int max);
 int pipe_ops_1024(int n, const PipeOps **out, int max);
-int pipe_ops_1024x(int n, const PipeOps **out, int max);
 int pipe_ops_2048(int n, const PipeOps **out, int max);
 int pipe_ops_hd(int n, const PipeOps **out, int max);
 
