@@ -1,0 +1,91 @@
+"""The C ABI without a GPU: libhologen.so loads, exports every function that
+include/hologen.h declares, and its host-only logic (defaults, size support,
+status strings, argument checks made before any device work) behaves as the
+header documents."""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "hologen.h")
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2008_12214_gb300 import build, hologen
+    if not os.path.exists(build.LIB):
+        build.build()
+    return hologen.lib()
+
+
+def declared_functions():
+    src = open(HEADER).read()
+    src = re.sub(r"/\*.*?\*/", " ", src, flags=re.S)
+    src = re.sub(r"//[^\n]*", " ", src)
+    src = "\n".join(l for l in src.splitlines() if not l.lstrip().startswith("#"))
+    names = re.findall(r"\b(hg_\w+)\s*\(", src)
+    return sorted(set(names))
+
+
+def test_header_declares_the_documented_entry_points():
+    names = declared_functions()
+    for must in ("hg_plan_create", "hg_run", "hg_replay", "hg_debug_step", "hg_sync",
+                 "hg_plan_destroy", "hg_group_run"):
+        assert must in names
+    assert len(names) >= 24
+
+
+def test_library_exports_every_declared_function(lib):
+    missing = [n for n in declared_functions() if not hasattr(lib, n)]
+    assert not missing, missing
+
+
+def test_defaults_and_status_strings(lib):
+    from paper_2008_12214_gb300 import hologen as hg
+    o = hg.hg_opts()
+    lib.hg_opts_default(ctypes.byref(o))
+    assert (o.subframes, o.use_graph, o.pipeline, o.autotune, o.precision, o.seed) == (24, 1, -1, 1, 0, 0)
+    seen = set()
+    for st in range(7):
+        s = hg.hg_status_string(st)
+        assert s and s != "unknown status"
+        seen.add(s)
+    assert len(seen) == 7
+    assert hg.hg_status_string(99) == "unknown status"
+
+
+def test_supported_lengths_are_2_3_5_smooth_and_compiled(lib):
+    from paper_2008_12214_gb300 import hologen as hg
+    for n in (4, 8, 16, 32, 64, 128, 256, 512, 1024, 2048, 1080, 1920, 30, 60, 96):
+        assert hg.hg_supported_length(n), n
+    for n in (0, 1, 7, 14, 1000, 1023, 4096, -8):
+        assert not hg.hg_supported_length(n), n
+
+
+@pytest.mark.parametrize("ny,nx,batch,kind,levels,algo,want", [
+    (64, 64, 0, 0, 2, 0, 1),       # batch < 1
+    (0, 64, 1, 0, 2, 0, 1),        # ny < 1
+    (64, 64, 1, 5, 2, 0, 1),       # unknown SLM kind
+    (64, 64, 1, 1, 1, 0, 1),       # L-level with L < 2
+    (64, 64, 1, 1, 257, 0, 1),     # L-level with L > 256
+    (64, 64, 1, 1, 4, 2, 1),       # OSPR needs a binary SLM
+    (64, 64, 1, 0, 2, 7, 1),       # unknown algorithm
+    (64, 1000, 1, 0, 2, 0, 2),     # 1000 is not a compiled length
+    (14, 64, 1, 0, 2, 0, 2),       # nor 14
+])
+def test_plan_create_rejects_bad_arguments_before_device_work(lib, ny, nx, batch, kind, levels, algo, want):
+    from paper_2008_12214_gb300 import hologen as hg
+    h = ctypes.c_void_p(123)
+    st = lib.hg_plan_create(ctypes.byref(h), ny, nx, batch, hg.hg_slm(kind, levels), algo, None)
+    assert st == want
+    assert h.value is None
+
+
+def test_null_handles_are_rejected(lib):
+    assert lib.hg_run(None, None, None, 1, None, None) == 1
+    assert lib.hg_sync(None) == 1
+    assert lib.hg_replay(None, None, None) == 1
+    assert lib.hg_last_launch_count(None) == 0
+    lib.hg_plan_destroy(None)
