@@ -47,7 +47,8 @@ typedef enum {
     HG_ERR_OOM = 3,              /* device allocation failed */
     HG_ERR_CUDA = 4,             /* a CUDA runtime call failed */
     HG_ERR_TIMEOUT = 5,          /* a bounded device-side wait gave up */
-    HG_ERR_NUMERIC = 6           /* target with zero energy */
+    HG_ERR_NUMERIC = 6,          /* target with zero energy */
+    HG_ERR_TOO_LARGE = 7         /* hg_run_noalloc: a side above HG_NOALLOC_MAX_SIDE */
 } hg_status;
 
 /* SLM modulation (Section 3; Fig. 1).  BINARY: levels {0, pi}, level 0 iff
@@ -231,6 +232,65 @@ hg_status hg_group_run(hg_group group, const float *const *targets, const float 
 hg_status hg_group_sync(hg_group group, void *stream);
 int hg_group_launch_count(hg_group group);
 void hg_group_destroy(hg_group group);
+
+/*
+ * hg_run_noalloc -- one GS or WGS run (Section 3.2) of ONE target that
+ * allocates no device memory.  The paper has no counterpart: it is a
+ * deployment variant of hg_run, not part of the method.
+ *
+ * Who needs it: callers that must not allocate device memory at the moment
+ * they compute a hologram.  Examples: a display loop that refreshes an SLM
+ * within a fixed frame time (cudaMalloc and cudaFree may synchronise the
+ * whole device and take milliseconds, stalling every other stream); an
+ * application whose device memory is owned by another framework's pool or
+ * capped by a budget it may not exceed; code that must not meet an
+ * out-of-memory error once it is running.  hg_run cannot serve them because
+ * creating a plan allocates its workspace.
+ *
+ * What it computes: the same as hg_run with the same arguments on a plan of
+ * batch 1 created with opts.pipeline = 0 (the generic row and column
+ * passes) and opts.seed = 0.  Holograms and mse_out agree with that call.
+ *
+ * Where the work memory lives: one fixed region of HG_NOALLOC_SCRATCH_BYTES
+ * (about 4 MiB) of static device memory inside this library, reserved on
+ * each device where the library's kernels are loaded, and reused by every
+ * call on that device.  Its size is the limit: ny and nx must each be at
+ * most HG_NOALLOC_MAX_SIDE and supported lengths; a larger side returns
+ * HG_ERR_TOO_LARGE before any device work (use a plan for such sizes).  Each
+ * call clears the region's device error flag itself; nothing else in it has
+ * to start at zero.
+ *
+ *  ny, nx, slm, algo  as hg_plan_create (algo HG_GS or HG_WGS; WGS weights
+ *              start at 1 on every call).
+ *  target, init_phase, iters, holo_out, mse_out  as hg_run with batch 1, but
+ *              every pointer must be a DEVICE pointer (host pointers would
+ *              need staging buffers).  init_phase NULL draws the Philox
+ *              phases of seed 0.
+ *  stream      cudaStream_t to run on (NULL: the legacy default stream).
+ * The call waits for its work on `stream` to finish before it returns, so
+ * device-detected errors (bad target values, zero energy) are returned by
+ * the call itself.
+ *
+ * One-time setup: the first call on each device looks up the region's
+ * address and sets the kernel attributes of every supported length up to
+ * HG_NOALLOC_MAX_SIDE.  Make that first call before any stream capture
+ * begins on that device.
+ *
+ * Concurrency: all calls on one device share the one region.  Calls that
+ * overlap in time, for example from two host threads, overwrite each other's
+ * data and give wrong results: serialise them.  Calls on different devices
+ * are independent, and plans are unaffected (they own their memory).
+ *
+ * Errors: HG_ERR_INVALID_ARG (NULL target, iters < 1, OSPR, bad slm, a host
+ * pointer, negative / NaN / infinite target values), HG_ERR_TOO_LARGE,
+ * HG_ERR_UNSUPPORTED_SIZE (a length with no compiled plan),
+ * HG_ERR_NUMERIC (a target with zero energy), HG_ERR_CUDA.
+ */
+#define HG_NOALLOC_MAX_SIDE 512
+#define HG_NOALLOC_SCRATCH_BYTES 4222208u
+hg_status hg_run_noalloc(int ny, int nx, hg_slm slm, hg_algo algo, const float *target,
+                         const float *init_phase, int iters, uint8_t *holo_out, double *mse_out,
+                         void *stream);
 
 #ifdef __cplusplus
 }

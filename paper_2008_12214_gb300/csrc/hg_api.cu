@@ -721,6 +721,7 @@ const char *hg_status_string(hg_status st) {
         case HG_ERR_CUDA: return "CUDA error";
         case HG_ERR_TIMEOUT: return "device wait timed out";
         case HG_ERR_NUMERIC: return "target has zero energy";
+        case HG_ERR_TOO_LARGE: return "side exceeds the fixed work memory of hg_run_noalloc";
         default: return "unknown status";
     }
 }
@@ -1330,3 +1331,176 @@ hg_status hg_group_sync(hg_group g, void *stream) {
 int hg_group_launch_count(hg_group g) { return g ? g->launches : 0; }
 
 }  // extern "C"
+
+// ------------------------------------------------------- allocation-free run
+// hg_run_noalloc: a single-target GS/WGS run whose work memory is one static
+// device region instead of plan buffers.  It launches the same generic row
+// and column kernels as a plan made with pipeline = 0; the one difference in
+// the launch sequence is that each iteration's metric partials are reduced
+// right after its row pass, so the region holds one iteration's partials
+// rather than all of them and the iteration count is not bounded by it.
+
+namespace {
+
+constexpr int kNaSide = HG_NOALLOC_MAX_SIDE;
+constexpr size_t kNaPx = (size_t)kNaSide * kNaSide;
+constexpr size_t na_al(size_t n) { return (n + 255) & ~(size_t)255; }
+// region layout (byte offsets, each piece 256-byte aligned)
+constexpr size_t kNaField = 0;                                              // float2 [ny][nx]
+constexpr size_t kNaTf = kNaField + na_al(sizeof(float2) * kNaPx);          // float [ny][nx]
+constexpr size_t kNaW = kNaTf + na_al(sizeof(float) * kNaPx);               // float [ny][nx] (WGS)
+constexpr size_t kNaPart = kNaW + na_al(sizeof(float) * kNaPx);             // double [panels <= ny][NMET]
+constexpr size_t kNaMetrics = kNaPart + na_al(sizeof(double) * NMET * kNaSide);  // double [NMET]
+constexpr size_t kNaSumPart = kNaMetrics + na_al(sizeof(double) * NMET);   // double [PREP_BLOCKS]
+constexpr size_t kNaScale = kNaSumPart + na_al(sizeof(double) * PREP_BLOCKS);
+constexpr size_t kNaErr = kNaScale + na_al(sizeof(double));
+constexpr size_t kNaTwx = kNaErr + na_al(sizeof(unsigned));                 // float2 [nx]
+constexpr size_t kNaTwy = kNaTwx + na_al(sizeof(float2) * kNaSide);         // float2 [ny]
+constexpr size_t kNaLvl = kNaTwy + na_al(sizeof(float2) * kNaSide);         // float2 [256]
+constexpr size_t kNaBytes = kNaLvl + na_al(sizeof(float2) * 256);
+static_assert(kNaBytes == HG_NOALLOC_SCRATCH_BYTES, "header states the region's size");
+
+// The region itself: static device memory of this library, one per device.
+static __device__ __align__(256) unsigned char g_na_region[kNaBytes];
+
+struct NaDevice {
+    bool ready = false;
+    char *base = nullptr;
+    int nsm = 0;
+};
+std::mutex g_na_mu;
+NaDevice g_na[kMaxDev];
+
+// One-time per-device setup with `dev` current: the region's address, the SM
+// count, and the kernel attributes of every compiled length up to the limit.
+cudaError_t na_setup(int dev, NaDevice *out) {
+    std::lock_guard<std::mutex> lk(g_na_mu);
+    if (dev < 0 || dev >= kMaxDev) return cudaErrorInvalidDevice;
+    NaDevice &d = g_na[dev];
+    if (!d.ready) {
+        void *base = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&base, g_na_region);
+        if (e != cudaSuccess) return e;
+        e = cudaDeviceGetAttribute(&d.nsm, cudaDevAttrMultiProcessorCount, dev);
+        if (e != cudaSuccess) return e;
+        for (int n = 1; n <= kNaSide; ++n)
+            if (const LineOps *o = find_ops(n))
+                if ((e = ensure_init(dev, o)) != cudaSuccess) return e;
+        d.base = (char *)base;
+        d.ready = true;
+    }
+    *out = d;
+    return cudaSuccess;
+}
+
+// Forward roots exp(-2 pi i e / n), e < n, as make_twiddles computes them,
+// written into a caller array instead of a new device buffer.
+void na_twiddles(int n, float2 *h) {
+    const long double two_pi = 6.283185307179586476925286766559005768L;
+    for (int e = 0; e < n; ++e) {
+        long double a = two_pi * (long double)e / (long double)n;
+        h[e] = make_float2((float)cosl(a), (float)-sinl(a));
+    }
+}
+
+}  // namespace
+
+extern "C" hg_status hg_run_noalloc(int ny, int nx, hg_slm slm, hg_algo algo, const float *target,
+                                    const float *init_phase, int iters, uint8_t *holo_out,
+                                    double *mse_out, void *stream) {
+    if (ny < 1 || nx < 1 || !target || iters < 1) return HG_ERR_INVALID_ARG;
+    if (algo != HG_GS && algo != HG_WGS) return HG_ERR_INVALID_ARG;
+    if (slm.kind != HG_SLM_BINARY && slm.kind != HG_SLM_LLEVEL) return HG_ERR_INVALID_ARG;
+    if (slm.kind == HG_SLM_LLEVEL && (slm.levels < 2 || slm.levels > 256)) return HG_ERR_INVALID_ARG;
+    if (ny > kNaSide || nx > kNaSide) return HG_ERR_TOO_LARGE;
+    const LineOps *rops = find_ops(nx), *cops = find_ops(ny);
+    if (!rops || !cops) return HG_ERR_UNSUPPORTED_SIZE;
+    for (const void *ptr : {(const void *)target, (const void *)init_phase, (const void *)holo_out,
+                            (const void *)mse_out})
+        if (ptr && !is_device_ptr(ptr)) return HG_ERR_INVALID_ARG;
+
+    int dev = 0;
+    HG_CK(cudaGetDevice(&dev));
+    NaDevice d;
+    HG_CK(na_setup(dev, &d));
+    const cudaStream_t s = (cudaStream_t)stream;
+
+    // A plan record on the stack whose buffers all point into the region; it
+    // owns nothing and is never destroyed through hg_plan_destroy.
+    hg_plan_s q;
+    q.dev = dev;
+    q.ny = ny;
+    q.nx = nx;
+    q.batch = 1;
+    q.algo = algo;
+    q.kind = slm.kind;
+    q.levels = slm.kind == HG_SLM_BINARY ? 2 : slm.levels;
+    q.nchains = 1;
+    q.stream = s;
+    q.use_graph = 0;
+    q.rops = rops;
+    q.cops = cops;
+    q.nsm = d.nsm;
+    q.npx = (size_t)ny * nx;
+    q.ppt = (ny + rops->row_lines - 1) / rops->row_lines;
+    q.ppt_max = q.ppt;
+    q.field = (float2 *)(d.base + kNaField);
+    q.tf = (float *)(d.base + kNaTf);
+    q.w = algo == HG_WGS ? (float *)(d.base + kNaW) : nullptr;
+    q.part = (double *)(d.base + kNaPart);
+    q.metrics = (double *)(d.base + kNaMetrics);
+    q.sum_part = (double *)(d.base + kNaSumPart);
+    q.scale = (double *)(d.base + kNaScale);
+    q.err = (unsigned *)(d.base + kNaErr);
+    q.twx = (float2 *)(d.base + kNaTwx);
+    q.twy = (float2 *)(d.base + kNaTwy);
+    q.lvl = (float2 *)(d.base + kNaLvl);
+
+    // This call's tables, built on the host stack and copied into the region
+    // in stream order (the copy has read the stack array when it returns).
+    float2 hx[kNaSide], hy[kNaSide], hl[256];
+    na_twiddles(nx, hx);
+    na_twiddles(ny, hy);
+    {
+        const long double two_pi = 6.283185307179586476925286766559005768L;
+        for (int l = 0; l < q.levels; ++l) {
+            long double a = two_pi * (long double)l / (long double)q.levels;
+            hl[l] = make_float2((float)cosl(a), (float)sinl(a));
+        }
+    }
+    HG_CK(cudaMemcpyAsync(q.twx, hx, sizeof(float2) * nx, cudaMemcpyHostToDevice, s));
+    HG_CK(cudaMemcpyAsync(q.twy, hy, sizeof(float2) * ny, cudaMemcpyHostToDevice, s));
+    HG_CK(cudaMemcpyAsync(q.lvl, hl, sizeof(float2) * q.levels, cudaMemcpyHostToDevice, s));
+    HG_CK(cudaMemsetAsync(q.err, 0, sizeof(unsigned), s));  // the one piece that starts at zero
+
+    const double invN = 1.0 / (double)q.npx;
+    auto reduce = [&](int k) {  // metrics of iteration k -> mse_out[k]
+        k_reduce<<<1, 128, 0, s>>>(q.part, 1, 1, q.ppt_max, q.ppt, q.ppt, invN, q.metrics,
+                                   mse_out ? mse_out + k : nullptr);
+    };
+    enqueue_prep(&q, target);
+    if (q.w) k_fill<<<ew_grid(&q, q.npx), 256, 0, s>>>(q.w, q.npx, 1.f);
+    RowArgs ra = row_args(&q);
+    ra.phase = init_phase;
+    launch_row(&q, ROW_HEAD, ra, s);
+    ColArgs ca = col_args(&q);
+    RowArgs ri = row_args(&q);
+    ri.part = q.part;
+    for (int k = 0; k + 1 < iters; ++k) {
+        launch_col(&q, col_role_gs(&q), ca, s);
+        launch_row(&q, ROW_ITER, ri, s);
+        reduce(k);
+    }
+    ca.holo = holo_out;
+    launch_col(&q, col_role_gs(&q), ca, s);
+    launch_row(&q, ROW_TAIL, ri, s);
+    reduce(iters - 1);
+    HG_CK(cudaGetLastError());
+
+    unsigned e = 0;
+    HG_CK(cudaMemcpyAsync(&e, q.err, sizeof(unsigned), cudaMemcpyDeviceToHost, s));
+    HG_CK(cudaStreamSynchronize(s));
+    if (e & ERR_BAD_VALUE) return HG_ERR_INVALID_ARG;
+    if (e & ERR_ZERO_ENERGY) return HG_ERR_NUMERIC;
+    return HG_OK;
+}

@@ -21,7 +21,8 @@ HG_GS, HG_WGS, HG_OSPR = 0, 1, 2
 NMET = 4
 
 STATUS = {0: "HG_OK", 1: "HG_ERR_INVALID_ARG", 2: "HG_ERR_UNSUPPORTED_SIZE", 3: "HG_ERR_OOM",
-          4: "HG_ERR_CUDA", 5: "HG_ERR_TIMEOUT", 6: "HG_ERR_NUMERIC"}
+          4: "HG_ERR_CUDA", 5: "HG_ERR_TIMEOUT", 6: "HG_ERR_NUMERIC", 7: "HG_ERR_TOO_LARGE"}
+HG_NOALLOC_MAX_SIDE = 512
 
 
 class HgError(RuntimeError):
@@ -88,6 +89,8 @@ def lib():
         L.hg_group_launch_count.restype = I
         L.hg_group_destroy.argtypes = [P]
         L.hg_group_destroy.restype = None
+        L.hg_run_noalloc.argtypes = [I, I, hg_slm, I, P, P, I, P, P, P]
+        L.hg_run_noalloc.restype = I
         L.hg_status_string.argtypes = [I]
         L.hg_status_string.restype = ctypes.c_char_p
         for name in ("hg_plan_create", "hg_run", "hg_get_metrics", "hg_replay", "hg_get_phase",
@@ -149,6 +152,20 @@ def hg_run(plan, target, init_phase, iters, holo_out=None, mse_out=None):
                      _ptr(init_phase, torch.float32, name="init_phase"), int(iters),
                      _ptr(holo_out, torch.uint8, name="holo_out"),
                      _ptr(mse_out, torch.float64, name="mse_out")), "hg_run")
+
+
+def hg_run_noalloc(ny, nx, target, init_phase, iters, holo_out=None, mse_out=None,
+                   slm_kind=HG_SLM_BINARY, levels=2, algo=HG_GS, stream=None):
+    """One GS/WGS run of one target in the library's fixed device region (no
+    device allocation); CUDA tensors only.  Returns when the work is done."""
+    if stream is None and torch.cuda.is_available():
+        stream = torch.cuda.current_stream().cuda_stream
+    _ck(lib().hg_run_noalloc(int(ny), int(nx), hg_slm(int(slm_kind), int(levels)), int(algo),
+                             _ptr(target, torch.float32, ny * nx, name="target"),
+                             _ptr(init_phase, torch.float32, ny * nx, name="init_phase"), int(iters),
+                             _ptr(holo_out, torch.uint8, ny * nx, name="holo_out"),
+                             _ptr(mse_out, torch.float64, iters, name="mse_out"),
+                             ctypes.c_void_p(int(stream or 0))), "hg_run_noalloc")
 
 
 def hg_get_metrics(plan, out):

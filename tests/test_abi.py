@@ -48,11 +48,11 @@ def test_defaults_and_status_strings(lib):
     lib.hg_opts_default(ctypes.byref(o))
     assert (o.subframes, o.use_graph, o.pipeline, o.autotune, o.precision, o.seed) == (24, 1, -1, 1, 0, 0)
     seen = set()
-    for st in range(7):
+    for st in range(8):
         s = hg.hg_status_string(st)
         assert s and s != "unknown status"
         seen.add(s)
-    assert len(seen) == 7
+    assert len(seen) == 8
     assert hg.hg_status_string(99) == "unknown status"
 
 
