@@ -77,7 +77,7 @@ def test_phase_loss_special_values():
     rng = np.random.default_rng(5)
     T = rng.random((2, 4, 4))
     phi = rng.uniform(-np.pi, np.pi, (2, 4, 4))
-    k = 1e4  # |(c, s)| >> eps: the normalisation is exact to ~eps^2/k^2
+    k = 1e7  # |(c, s)| >> eps: the normalisation is exact to ~eps^2/k^2
     L, _, _ = cn.phase_loss(k * np.cos(phi), k * np.sin(phi), T, phi)
     assert L == pytest.approx(0.0, abs=1e-12)
     L, _, _ = cn.phase_loss(-k * np.cos(phi), -k * np.sin(phi), T, phi)
