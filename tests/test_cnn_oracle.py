@@ -77,13 +77,17 @@ def test_phase_loss_special_values():
     rng = np.random.default_rng(5)
     T = rng.random((2, 4, 4))
     phi = rng.uniform(-np.pi, np.pi, (2, 4, 4))
-    k = 1e7  # |(c, s)| >> eps: the normalisation is exact to ~eps^2/k^2
-    L, _, _ = cn.phase_loss(k * np.cos(phi), k * np.sin(phi), T, phi)
-    assert L == pytest.approx(0.0, abs=1e-12)
-    L, _, _ = cn.phase_loss(-k * np.cos(phi), -k * np.sin(phi), T, phi)
+    L, dc, ds = cn.phase_loss(np.cos(phi), np.sin(phi), T, phi)
+    assert L == pytest.approx(0.0, abs=1e-15) and np.abs(dc).max() < 1e-15 and np.abs(ds).max() < 1e-15
+    # on the unit circle the loss is the energy-weighted 1 - cos(phase error)
+    L, _, _ = cn.phase_loss(-np.cos(phi), -np.sin(phi), T, phi)
     assert L == pytest.approx(2.0, abs=1e-12)   # sum wT = 1 per image, mean over images
-    L, _, _ = cn.phase_loss(-k * np.sin(phi), k * np.cos(phi), T, phi)
+    L, _, _ = cn.phase_loss(-np.sin(phi), np.cos(phi), T, phi)
     assert L == pytest.approx(1.0, abs=1e-12)   # quarter-turn error
+    d = rng.uniform(-np.pi, np.pi, (2, 4, 4))
+    L, _, _ = cn.phase_loss(np.cos(phi + d), np.sin(phi + d), T, phi)
+    wT = T ** 2 / (T ** 2).sum(axis=(1, 2), keepdims=True)
+    assert L == pytest.approx((wT * (1 - np.cos(d))).sum() / 2, abs=1e-12)
     # pixels with T = 0 carry no weight
     T0 = T.copy()
     T0[:, :2] = 0
