@@ -91,6 +91,23 @@ def lib():
         L.hg_group_destroy.restype = None
         L.hg_run_noalloc.argtypes = [I, I, hg_slm, I, P, P, I, P, P, P]
         L.hg_run_noalloc.restype = I
+        L.hg_cnn_create.argtypes = [ctypes.POINTER(P), I, I, I, ctypes.c_uint64, P]
+        L.hg_cnn_destroy.argtypes = [P]
+        L.hg_cnn_destroy.restype = None
+        for name, args in (("hg_cnn_set_params", [P, P]), ("hg_cnn_get_params", [P, P]),
+                           ("hg_cnn_get_grads", [P, P]), ("hg_cnn_forward", [P, P, I, P, P]),
+                           ("hg_cnn_gradients", [P, P, P, I, P]),
+                           ("hg_cnn_train_step", [P, P, P, I, ctypes.c_float, P]), ("hg_cnn_sync", [P]),
+                           ("hg_cnn_launch_count", [P]),
+                           ("hg_conv3x3_forward", [P, I, I, I, I, P, I, P, I, P, P, P]),
+                           ("hg_conv3x3_dgrad", [P, I, I, I, I, P, I, P, P, P]),
+                           ("hg_conv3x3_wgrad", [P, P, I, I, I, I, I, P, P, P, Z, P]),
+                           ("hg_conv_status", [P])):
+            getattr(L, name).argtypes = args
+            getattr(L, name).restype = I
+        L.hg_cnn_create.restype = I
+        L.hg_conv3x3_wgrad_workspace.argtypes = [I, I, I, I, I]
+        L.hg_conv3x3_wgrad_workspace.restype = Z
         L.hg_status_string.argtypes = [I]
         L.hg_status_string.restype = ctypes.c_char_p
         for name in ("hg_plan_create", "hg_run", "hg_get_metrics", "hg_replay", "hg_get_phase",
@@ -317,3 +334,110 @@ class Plan:
 
     def sync(self):
         hg_sync(self.h)
+
+
+# ------------------------------------------------------------------ warm start
+
+HG_CNN_NPARAMS = 1946338
+
+
+def _stream(stream):
+    if stream is None and torch.cuda.is_available():
+        stream = torch.cuda.current_stream().cuda_stream
+    return ctypes.c_void_p(int(stream or 0))
+
+
+def hg_cnn_create(height, width, max_batch, seed=0, stream=None):
+    h = ctypes.c_void_p()
+    _ck(lib().hg_cnn_create(ctypes.byref(h), int(height), int(width), int(max_batch), int(seed), _stream(stream)),
+        "hg_cnn_create")
+    return h
+
+
+def hg_cnn_destroy(net):
+    lib().hg_cnn_destroy(net)
+
+
+def hg_cnn_set_params(net, params):
+    _ck(lib().hg_cnn_set_params(net, _ptr(params, torch.float32, HG_CNN_NPARAMS, "params")), "hg_cnn_set_params")
+
+
+def hg_cnn_get_params(net, params):
+    _ck(lib().hg_cnn_get_params(net, _ptr(params, torch.float32, HG_CNN_NPARAMS, "params")), "hg_cnn_get_params")
+
+
+def hg_cnn_get_grads(net, grads):
+    _ck(lib().hg_cnn_get_grads(net, _ptr(grads, torch.float32, HG_CNN_NPARAMS, "grads")), "hg_cnn_get_grads")
+
+
+def hg_cnn_forward(net, target, batch, cs_out=None, phase_out=None):
+    _ck(lib().hg_cnn_forward(net, _ptr(target, torch.float32, name="target"), int(batch),
+                             _ptr(cs_out, torch.float32, name="cs_out"),
+                             _ptr(phase_out, torch.float32, name="phase_out")), "hg_cnn_forward")
+
+
+def hg_cnn_gradients(net, target, phase_label, batch, loss_out=None):
+    _ck(lib().hg_cnn_gradients(net, _ptr(target, torch.float32, name="target"),
+                               _ptr(phase_label, torch.float32, name="phase_label"), int(batch),
+                               _ptr(loss_out, torch.float64, name="loss_out")), "hg_cnn_gradients")
+
+
+def hg_cnn_train_step(net, target, phase_label, batch, lr, loss_out=None):
+    _ck(lib().hg_cnn_train_step(net, _ptr(target, torch.float32, name="target"),
+                                _ptr(phase_label, torch.float32, name="phase_label"), int(batch), float(lr),
+                                _ptr(loss_out, torch.float64, name="loss_out")), "hg_cnn_train_step")
+
+
+def hg_cnn_sync(net):
+    _ck(lib().hg_cnn_sync(net), "hg_cnn_sync")
+
+
+def hg_cnn_launch_count(net) -> int:
+    return lib().hg_cnn_launch_count(net)
+
+
+def hg_conv3x3_forward(x, B, H, W, Cin, w, Cout, bias, relu, mask, y, stream=None):
+    _ck(lib().hg_conv3x3_forward(_ptr(x, torch.bfloat16, name="x"), B, H, W, Cin, _ptr(w, torch.bfloat16, name="w"),
+                                 Cout, _ptr(bias, torch.float32, name="bias"), int(relu),
+                                 _ptr(mask, torch.bfloat16, name="mask"), _ptr(y, torch.bfloat16, name="y"),
+                                 _stream(stream)), "hg_conv3x3_forward")
+
+
+def hg_conv3x3_dgrad(dy, B, H, W, Cout, w_rot, Cin, mask, dx, stream=None):
+    _ck(lib().hg_conv3x3_dgrad(_ptr(dy, torch.bfloat16, name="dy"), B, H, W, Cout,
+                               _ptr(w_rot, torch.bfloat16, name="w_rot"), Cin, _ptr(mask, torch.bfloat16, name="mask"),
+                               _ptr(dx, torch.bfloat16, name="dx"), _stream(stream)), "hg_conv3x3_dgrad")
+
+
+def hg_conv3x3_wgrad_workspace(B, H, W, Cin, Cout) -> int:
+    return int(lib().hg_conv3x3_wgrad_workspace(B, H, W, Cin, Cout))
+
+
+def hg_conv3x3_wgrad(x, dy, B, H, W, Cin, Cout, dw, db, workspace, stream=None):
+    _ck(lib().hg_conv3x3_wgrad(_ptr(x, torch.bfloat16, name="x"), _ptr(dy, torch.bfloat16, name="dy"), B, H, W, Cin,
+                               Cout, _ptr(dw, torch.float32, name="dw"), _ptr(db, torch.float32, name="db"),
+                               _ptr(workspace, torch.uint8, name="workspace"), workspace.numel(), _stream(stream)),
+        "hg_conv3x3_wgrad")
+
+
+def hg_conv_status(stream=None):
+    _ck(lib().hg_conv_status(_stream(stream)), "hg_conv_status")
+
+
+class CNN:
+    """Owning wrapper of an hg_cnn handle."""
+
+    def __init__(self, height, width, max_batch, seed=0, stream=None):
+        self.h = hg_cnn_create(height, width, max_batch, seed, stream)
+        self.height, self.width, self.max_batch = height, width, max_batch
+
+    def close(self):
+        if self.h is not None and self.h.value:
+            hg_cnn_destroy(self.h)
+        self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
