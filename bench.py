@@ -55,7 +55,9 @@ def parse():
                     help="0 FP32 engine; 1..4 tensor-core row pass (FP16 hi+lo, FP16, BF16 hi+lo, BF16)")
     ap.add_argument("--batch", type=int, default=BATCH, help="targets per rank (profiling runs)")
     ap.add_argument("--quick", action="store_true", help="skip the e2e and CPU-baseline legs")
-    ap.add_argument("--workload", choices=["headline", "ospr", "mixed"], default="headline",
+    ap.add_argument("--pairs", type=int, default=2048, help="warmstart: training pairs")
+    ap.add_argument("--heldout", type=int, default=64, help="warmstart: held-out targets")
+    ap.add_argument("--workload", choices=["headline", "ospr", "mixed", "warmstart"], default="headline",
                     help="headline: binary GS 1024^2 x 64 (the benchmark line); ospr: 8 targets x 24 "
                          "subframes of 1024^2; mixed: 16 targets each of 512^2, 1024^2, 2048^2, 1080x1920")
     return ap.parse_args()
@@ -189,6 +191,59 @@ def traffic_for(kernel_key):
     return None
 
 
+def run_warmstart(args, dev, s0):
+    """The learned warm start at 1024^2: training throughput of the tensor-core
+    network on the engine's own GS-200 phases, the tensor-core convolution
+    against the measured BF16 peak, and GS iterations / wall time from the
+    network's phase to the plain random-phase GS-100 MSE on held-out targets,
+    for the 256-level and the binary SLM."""
+    import torch
+    from paper_2008_12214_gb300 import hologen as hg
+    from paper_2008_12214_gb300 import warmstart as ws
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    peak = None
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            peak = json.load(f).get("bf16_tflops_sustained")
+    except Exception:
+        pass
+    # tensor-core convolutions of the 1024^2 net, batch 4: level-2 decoder input
+    # (384 -> 128 channels at 256^2) and the bottleneck (256 -> 256 at 128^2)
+    convs = []
+    for (Bc, Hc, cin, cout) in ((4, 256, 384, 128), (4, 128, 256, 256), (4, 1024, 96, 32)):
+        x = torch.randn(Bc, Hc, Hc, cin, device=dev).to(torch.bfloat16)
+        w = (torch.randn(9, cout, cin, device=dev) * 0.03).to(torch.bfloat16)
+        y = torch.empty(Bc, Hc, Hc, cout, device=dev, dtype=torch.bfloat16)
+        for _ in range(3):
+            hg.hg_conv3x3_forward(x, Bc, Hc, Hc, cin, w, cout, None, 1, None, y)
+        e0.record(s0)
+        for _ in range(20):
+            hg.hg_conv3x3_forward(x, Bc, Hc, Hc, cin, w, cout, None, 1, None, y)
+        e1.record(s0)
+        hg.hg_conv_status()
+        ms = e0.elapsed_time(e1) / 20
+        tf = 2.0 * 9 * cin * cout * Bc * Hc * Hc / (ms / 1e3) / 1e12
+        convs.append(dict(layer="%dx%d %d->%d batch %d" % (Hc, Hc, cin, cout, Bc), ms=ms, tflops=tf,
+                          frac_of_sustained_bf16=tf / peak if peak else None))
+        del x, w, y
+    res = dict(workload="warmstart_cnn_1024x1024", pairs=args.pairs, heldout=args.heldout, label_iters=200,
+               conv_kernel_k_conv_fwd=convs, peak_bf16_tflops_sustained=peak)
+    for name, kind, L in (("llevel256", hg.HG_SLM_LLEVEL, 256), ("binary", hg.HG_SLM_BINARY, 2)):
+        net, losses, secs = ws.train(NY, NX, args.pairs, batch=4, lr=1e-3, chunk=64, label_iters=200,
+                                     label_start="fixed", slm_kind=kind, levels=L)
+        ev = ws.evaluate(net, NY, NX, args.heldout, ref_iters=100, max_iters=100, chunk=4, slm_kind=kind, levels=L)
+        net.close()
+        pick = (0, 9, 49, 99)
+        res[name] = dict(train_seconds=secs, pairs_per_s=args.pairs / secs, loss_first=losses[0],
+                         loss_last20=float(sum(losses[-20:]) / 20), reached=ev["reached"],
+                         median_warm_iters=ev["median_warm_iters"], median_speedup=ev["median_speedup"],
+                         ms_cnn_per_batch=ev["ms_cnn_batch"], ms_gs_iter_per_batch=ev["ms_per_gs_iter_batch"],
+                         eval_batch=ev["batch"],
+                         rel_mse_random_at_1_10_50_100=[ev["rel_rand_curve"][i] for i in pick],
+                         rel_mse_warm_at_1_10_50_100=[ev["rel_warm_curve"][i] for i in pick])
+    return res
+
+
 def run_side_workload(args):
     """Throughput of the other configurations (reported in DESIGN, not the
     benchmark line): OSPR subframes/s, and batched iterations/s of the mixed
@@ -220,6 +275,8 @@ def run_side_workload(args):
                    algorithmic_gbs=36.0 * B * NS * NY * NX / (ms / 1e3) / 1e9,
                    mse=mse.cpu().numpy().tolist(), column_variant=hg.hg_plan_variant(plan.h, 1))
         plan.close()
+    elif args.workload == "warmstart":
+        out = run_warmstart(args, dev, s0)
     else:
         shapes = [(512, 512), (1024, 1024), (2048, 2048), (1080, 1920)]
         plans, Ts, Ps, Ms = [], [], [], []

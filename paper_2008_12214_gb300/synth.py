@@ -14,6 +14,11 @@ Target recipe (amplitude, replay order, zero background):
     preparation normalises to sum T^2 = 1).
 Target b of a batch uses seed base_seed + b (base 1000 by default).
 Initial phases are U[0, 2 pi) float32 from the stream (seed, 1).
+
+targets_device() draws the same per-seed parameters and renders them on a
+torch device (every component is an outer product of a y profile and an x
+profile), for the many targets a training set needs; it equals targets() up
+to float32 rounding.
 """
 from __future__ import annotations
 
@@ -21,6 +26,47 @@ import numpy as np
 
 BLOBS = 16
 RECTS = 8
+
+
+def _params(ny: int, nx: int, seed: int):
+    """Blob and rectangle parameters of target `seed`, in target()'s draw order."""
+    rng = np.random.default_rng(seed)
+    blobs, rects = [], []
+    for _ in range(BLOBS):
+        cy = rng.uniform(0, ny)
+        cx = rng.uniform(0, nx)
+        sigma = rng.uniform(2.0, 20.0)
+        peak = rng.uniform(0.2, 1.0)
+        blobs.append((cy, cx, sigma, peak))
+    for _ in range(RECTS):
+        h = max(1, int(round(rng.uniform(ny / 32, ny / 4))))
+        w = max(1, int(round(rng.uniform(nx / 32, nx / 4))))
+        y0 = int(rng.integers(0, ny))
+        x0 = int(rng.integers(0, nx))
+        amp = rng.uniform(0.3, 1.0)
+        rects.append((h, w, y0, x0, amp))
+    return blobs, rects
+
+
+def targets_device(batch: int, ny: int, nx: int, base_seed: int = 1000, device="cuda"):
+    """targets() rendered on `device` as a float32 torch tensor [batch][ny][nx]."""
+    import torch
+    K = BLOBS + RECTS
+    Y = np.zeros((batch, K, ny))
+    X = np.zeros((batch, K, nx))
+    y = np.arange(ny, dtype=np.float64)
+    x = np.arange(nx, dtype=np.float64)
+    for b in range(batch):
+        blobs, rects = _params(ny, nx, base_seed + b)
+        for k, (cy, cx, sigma, peak) in enumerate(blobs):
+            Y[b, k] = peak * np.exp(-((y - cy) ** 2) / (2 * sigma * sigma))
+            X[b, k] = np.exp(-((x - cx) ** 2) / (2 * sigma * sigma))
+        for k, (h, w, y0, x0, amp) in enumerate(rects):
+            Y[b, BLOBS + k, y0:y0 + h] = amp
+            X[b, BLOBS + k, x0:x0 + w] = 1.0
+    Yd = torch.from_numpy(Y.astype(np.float32)).to(device)
+    Xd = torch.from_numpy(X.astype(np.float32)).to(device)
+    return torch.bmm(Yd.transpose(1, 2), Xd).contiguous()
 
 
 def target(ny: int, nx: int, seed: int) -> np.ndarray:

@@ -336,3 +336,12 @@ def test_replay_field_and_metrics_helpers_agree_with_step():
         assert np.abs(R - o["R"]).max() < 1e-13
         m = oracle.metrics(np.abs(R) ** 2, T)
         assert np.allclose(m, [o["mse"], o["amp_mse"], o["eff"], o["sum_r2"]], rtol=1e-12, atol=0)
+
+
+def test_device_target_generator_matches_the_numpy_one():
+    torch = pytest.importorskip("torch")
+    from paper_2008_12214_gb300 import synth
+    a = synth.targets(3, 64, 96, 4242)
+    b = synth.targets_device(3, 64, 96, 4242, "cpu").numpy()
+    assert b.shape == a.shape and b.dtype == np.float32
+    assert np.abs(a - b).max() <= 1e-5 * np.abs(a).max()
