@@ -34,9 +34,15 @@ BATCH = 64
 # read + write 16, target 4), column 16 (field read + write): 36 B/px.  With the
 # paired-row pass (binary SLM: column spectra are Hermitian, so only rows
 # ky <= ny/2 are stored and read back): row 16 (half field 4, target 4, field
-# written 8), column 12 (field read 8, half written 4): 28 B/px.
+# written 8), column 12 (field read 8, half written 4): 28 B/px.  In Hermitian
+# form ("+herm": the row pass writes only rows ky <= ny/2 of the Hermitian part
+# of F): row 12 (half read 4, target 4, half written 4), column 8 (half read 4,
+# half written 4): 20 B/px.  The column pass after the head pass reads every
+# row and the last one writes every row; column bytes are averaged over the
+# passes of a run.
 BYTES_ROW, BYTES_COL = 20, 16
 BYTES_ROW_PAIRED, BYTES_COL_PAIRED = 16, 12
+BYTES_ROW_HERM, BYTES_COL_HERM = 12, 8
 BYTES_SURVEY = 36
 DATA = ("synthetic: seeded targets of 16 Gaussian blobs + 8 rectangles per 1024x1024 field "
         "(seeds 1000 + rank*64 + b), initial phase U[0, 2 pi)")
@@ -419,8 +425,16 @@ def main():
     row_ms = prof[0] / max(prof[1], 1)
     col_ms = prof[2] / max(prof[3], 1)
     paired = "pair" in variants[0]
-    b_row = BYTES_ROW_PAIRED if paired else BYTES_ROW
-    b_col = BYTES_COL_PAIRED if paired else BYTES_COL
+    herm = "+herm" in variants[0]
+    it = args.iters
+    if herm:
+        b_row = BYTES_ROW_HERM
+        b_col = (2 * 12 + max(it - 2, 0) * BYTES_COL_HERM) / it  # first: full read; last: full write
+    elif paired:
+        b_row = BYTES_ROW_PAIRED
+        b_col = ((it - 1) * BYTES_COL_PAIRED + 16) / it  # last column pass writes every row
+    else:
+        b_row, b_col = BYTES_ROW, BYTES_COL
     passes = {
         "row": dict(bytes=b_row * npx, ms=row_ms, launches=int(prof[1]), variant=variants[0]),
         "column": dict(bytes=b_col * npx, ms=col_ms, launches=int(prof[3]), variant=variants[1]),
@@ -454,7 +468,7 @@ def main():
             frac_at_36=BYTES_SURVEY * npx / (iter_ms / 1e3) / 1e9 / peak),
         roofline=roofline,
         passes={k: dict(avg_ms=v["ms"], gbs=v["gbs"], frac=(v["gbs"] / peak if v["gbs"] else None),
-                        launches=v["launches"], bytes_per_px=v["bytes"] // npx, variant=v["variant"])
+                        launches=v["launches"], bytes_per_px=v["bytes"] / npx, variant=v["variant"])
                 for k, v in passes.items()},
         cpu_baseline=None if args.quick else cpu_oracle_sample(),
         e2e=e2e,

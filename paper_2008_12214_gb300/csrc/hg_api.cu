@@ -298,6 +298,7 @@ struct hg_plan_s {
     cudaGraphExec_t gexec = nullptr;
     int g_iters = -1;
     double *g_part = nullptr;
+    char vname[2][128] = {};
 };
 
 namespace {
@@ -511,13 +512,22 @@ void enqueue_prep(hg_plan p, const float *target) {
 int col_role_gs(hg_plan p) { return p->kind == HG_SLM_BINARY ? COL_GS_BIN : COL_GS_LVL; }
 int col_role_holo(hg_plan p) { return p->kind == HG_SLM_BINARY ? COL_HOLO_BIN : COL_HOLO_LVL; }
 
+// Binary GS with the paired row pass and a TMA-fed column pass: the row pass
+// writes only the Hermitian part of F (rows ky <= ny/2) and the next column
+// pass reads those rows back (see herm_constrain).
+bool herm_loop(hg_plan p) {
+    return p->prow && p->prow->paired && p->pcol && !p->use_pack && p->kind == HG_SLM_BINARY;
+}
+
 // The middle of a GS run: for k = 0 .. iters-2, column pass k then row pass
 // k (metrics of iteration k, constraint for iteration k+1).
 void enqueue_loop(hg_plan p, int iters, cudaStream_t s) {
     ColArgs ca = col_args(p);
     RowArgs ra = row_args(p);
     ca.half = p->prow && p->prow->paired;  // the paired row pass rebuilds rows ny - ky
+    ra.herm = herm_loop(p);
     for (int k = 0; k + 1 < iters; ++k) {
+        ca.half_in = ra.herm && k > 0;  // column pass 0 follows the (full) head pass
         if (p->use_pack) launch_col_pack(p, ca, s);
         else launch_col_gs(p, col_role_gs(p), ca, s);
         ra.part = p->part + (size_t)k * p->batch * p->ppt_max * NMET;
@@ -593,6 +603,7 @@ hg_status enqueue_run(hg_plan p, const float *d_t, const float *d_ph, int iters,
             return st;
         }
         ca.holo = d_ho;
+        ca.half_in = herm_loop(p) && iters >= 2;
         launch_col_gs(p, col_role_gs(p), ca, p->stream);
         RowArgs rt = row_args(p);
         rt.part = p->part + (size_t)(iters - 1) * p->batch * p->ppt_max * NMET;
@@ -637,16 +648,18 @@ bool make_cmap(hg_plan p, const PipeOps *pc, CUtensorMap *m) {
 
 // Best-of-3 launch time (ms, after one warm-up launch) of one pass variant on
 // the plan's own zeroed buffers, on the private capture stream.
-float time_variant(hg_plan p, const PipeOps *o, bool row, bool pack = false) {
+float time_variant(hg_plan p, const PipeOps *o, bool row, bool pack = false, bool herm = false) {
     if (!p->field || !p->tf || !p->twx || !p->twy || !p->lvl || !p->err) return 1e30f;
     cudaStream_t s = p->cap_stream;
     RowArgs ra = row_args(p);
     ra.w = nullptr;
     ra.part = nullptr;
+    ra.herm = herm;
     ColArgs ca = col_args(p);
     CUtensorMap m;
     if (!row && !make_cmap(p, o, &m)) return 1e30f;
     if (pack) ca.half = 1;
+    if (!row && herm) ca.half = ca.half_in = 1;
     const int ppt = row ? row_panels(o, p->ny) : (p->nx + o->col_c - 1) / o->col_c;
     const int grid = grid_for(row ? o->row_blocks_per_sm : pack ? o->pack_blocks_per_sm : o->col_blocks_per_sm,
                               p->nsm, (long)p->batch * ppt);
@@ -893,10 +906,13 @@ hg_status hg_plan_create(hg_plan *out, int ny, int nx, int batch, hg_slm slm, hg
                     if (ms < best_col) best_col = ms, col = cc[i];
                 }
                 for (int i = 0; i < nr; ++i) {
-                    float ms = time_variant(p, rc[i], true);
-                    if (i < 4) p->tune_ms[i] = ms;
                     const bool pk = rc[i]->paired && rc[i]->col_pack && slm.kind == HG_SLM_BINARY;
-                    ms += pk ? time_variant(p, rc[i], false, true) : best_col;
+                    // a paired row pass with a TMA-fed column pass runs in Hermitian form
+                    const bool hm = rc[i]->paired && !pk && col && slm.kind == HG_SLM_BINARY;
+                    float ms = time_variant(p, rc[i], true, false, hm);
+                    if (i < 4) p->tune_ms[i] = ms;
+                    ms += pk ? time_variant(p, rc[i], false, true) : hm ? time_variant(p, col, false, false, true)
+                                                                          : best_col;
                     if (ms < best) best = ms, row = rc[i];
                 }
                 std::lock_guard<std::mutex> lk(g_tune_mu);
@@ -981,6 +997,10 @@ const char *hg_plan_variant(hg_plan p, int pass) {
         return names[p->tc_prec];
     }
     const PipeOps *o = pass == 0 ? p->prow : p->pcol;
+    if (o && herm_loop(p)) {  // Hermitian form of the binary loop
+        snprintf(p->vname[pass], sizeof p->vname[pass], "%s+herm", o->name);
+        return p->vname[pass];
+    }
     return o ? o->name : "generic";
 }
 

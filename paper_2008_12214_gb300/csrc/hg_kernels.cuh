@@ -40,6 +40,7 @@ struct RowArgs {
     float *I_out;          // AVG: normalised intensity, replay order, or null
     const float2 *tw;      // W_nx^e, e < nx (forward roots)
     float invN, invN2, NN, invSqrtN;
+    int herm;              // paired binary rows: write only the Hermitian part of F (rows y <= ny/2)
 };
 
 struct ColArgs {
@@ -55,6 +56,8 @@ struct ColArgs {
     float invSqrtN;
     int half;              // store only rows y <= ny/2 of the result (binary GS whose next
                            // row pass rebuilds rows ny - y from the Hermitian symmetry)
+    int half_in;           // the field holds rows y <= ny/2 of a field whose columns are
+                           // Hermitian: read those, take row ny - y as conj(row y)
 };
 
 // Sum four per-thread float partials over the block in a fixed order (lanes

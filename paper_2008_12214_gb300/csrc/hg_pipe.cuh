@@ -328,6 +328,61 @@ __device__ __forceinline__ void pair_finish(float2 (&w)[P::E], float2 *xbuf, con
     });
 }
 
+// Hermitian form of the binary constraint.  The binary quantiser reads only
+// Re h, and Re IFFT2(F) = IFFT2(F_H) with F_H(u) = (F(u) + conj F(-u)) / 2.
+// For a binary SLM the replay is Hermitian, R(-u) = conj R(u), so
+// F_H(u) = (wT(u) + wT(-u)) / 2 * R(u) / |R(u)|: the same constraint with a
+// symmetrised target, and F_H is Hermitian, so after the inverse row FFTs
+// row ny - y of the field is conj(row y).  Each thread takes its pixel u of
+// row p together with the mirror u' = (ny - p, nx - x): |R(u')| = |R(u)|, so
+// both pixels' metrics and weight updates come from the one spectrum, and
+// only row p of F_H is transformed and stored.  sTm: targets of row ny - p
+// (row p itself for the self-mirrored rows 0 and ny/2); wold_m: the mirror
+// row's weights before this pass (for self-mirrored rows a shared-memory
+// copy, since other threads update the row in place); store_m: write the
+// mirror's updated weight (partner rows only).
+template <class P>
+__device__ __forceinline__ void herm_constrain(float2 (&w)[P::E], const float *sT, const float *sTm, float *wr,
+                                               const float *wold_m, float *wrm, bool partner,
+                                               const RowArgs &a, int t, float &acc0, float &acc1,
+                                               float &acc2, float &acc3) {
+    static_for<0, P::E>([&](auto ec) {
+        constexpr int e = decltype(ec)::value;
+        const int x = t + P::TL * e;
+        const int xm = (P::N - x) & (P::N - 1);
+        const float Tv = sT[x], Tm = sTm[xm];
+        const float2 r = w[e];
+        const float m2 = fmaf(r.x, r.x, r.y * r.y);
+        const float rs = m2 > 0.f ? rsqrtf(m2) : 0.f;
+        const float I = m2 * a.invN2;
+        const float amp = m2 * rs * (a.invSqrtN * a.invSqrtN);
+        const float e2 = m2 * a.invN;
+        const float d = I - Tv * Tv, am = amp - Tv;
+        acc0 = fmaf(d, d, acc0);
+        acc1 = fmaf(am, am, acc1);
+        acc3 += e2;
+        if (Tv > 0.f) acc2 += e2;
+        if (partner) {
+            const float dm = I - Tm * Tm, amm = amp - Tm;
+            acc0 = fmaf(dm, dm, acc0);
+            acc1 = fmaf(amm, amm, acc1);
+            acc3 += e2;
+            if (Tm > 0.f) acc2 += e2;
+        }
+        float wv = 1.f, wm = 1.f;
+        if (wr) {
+            wv = wr[x];
+            if (Tv > 0.f && m2 > 0.f) wv = wv * Tv * (a.NN * rs);
+            wr[x] = wv;
+            wm = wold_m[xm];
+            if (Tm > 0.f && m2 > 0.f) wm = wm * Tm * (a.NN * rs);
+            if (partner) wrm[xm] = wm;
+        }
+        const float gm = 0.5f * fmaf(Tv, wv, Tm * wm);
+        w[e] = m2 > 0.f ? make_float2(gm * r.x * rs, gm * r.y * rs) : make_float2(gm, 0.f);
+    });
+}
+
 template <class P, int NG, int D, int SWZ>
 struct PairPipeCfg {
     static constexpr int GT = P::TL;
@@ -340,7 +395,7 @@ struct PairPipeCfg {
     static constexpr size_t SMEM = 1024 + (size_t)NG * D * SLOT + RED + NG * D * 8 + 4 * (NG + 1) + 256;
 };
 
-template <class P, int NG, int D, int SWZ>
+template <class P, int NG, int D, int SWZ, bool HERM>
 __global__ void __launch_bounds__(PairPipeCfg<P, NG, D, SWZ>::THREADS, 1)
     k_row_pipe_pair(const RowArgs a, const PipeArgs pa) {
     using Cfg = PairPipeCfg<P, NG, D, SWZ>;
@@ -426,6 +481,29 @@ __global__ void __launch_bounds__(PairPipeCfg<P, NG, D, SWZ>::THREADS, 1)
         });
         line_fft<P, -1, 1, LAY>(v, sf, a.tw, t, gsync);
         float acc0 = 0.f, acc1 = 0.f, acc2 = 0.f, acc3 = 0.f;
+        if constexpr (HERM) {
+            float *wrp = a.w ? a.w + ((size_t)item * ny + pan) * NX : nullptr;
+            float *wrm = a.w && partner ? a.w + ((size_t)item * ny + ny - pan) * NX : nullptr;
+            const float *wold = wrm;
+            if (a.w && !partner) {  // self-mirrored row: keep its old weights for the mirror reads
+                float *sW = const_cast<float *>(sTa) + NX;
+                static_for<0, E>([&](auto ec) {
+                    constexpr int e = decltype(ec)::value;
+                    sW[t + TL * e] = wrp[t + TL * e];
+                });
+                gsync();
+                wold = sW;
+            }
+            herm_constrain<P>(v, sTa, partner ? sTa + NX : sTa, wrp, wold, wrm, partner, a, t, acc0, acc1, acc2,
+                              acc3);
+            pair_finish<P, LAY>(v, sf, a.tw, t, gsync, a.field + ((size_t)item * ny + pan) * NX);
+            gsync();
+            if (t == 0) issue(k + D);
+            if (a.part)
+                group_sum4<GT>(acc0, acc1, acc2, acc3, red + (size_t)g * Cfg::GW * NMET,
+                               a.part + ((size_t)item * ppt + pan) * NMET, t, gsync);
+            continue;
+        } else {
         if (partner) {
             // spectrum of row ny - p: conj(X[(nx - kx) % nx]), through shared memory;
             // its constraint is applied now and the result parked where the
@@ -470,6 +548,7 @@ __global__ void __launch_bounds__(PairPipeCfg<P, NG, D, SWZ>::THREADS, 1)
         if (a.part)
             group_sum4<GT>(acc0, acc1, acc2, acc3, red + (size_t)g * Cfg::GW * NMET,
                            a.part + ((size_t)item * ppt + pan) * NMET, t, gsync);
+        }
     }
 }
 
@@ -513,16 +592,25 @@ __global__ void __launch_bounds__(ColPipeCfg<P, C, NG, D, SWZ, BOXR>::THREADS, 1
     uint64_t *gfull = full + g * D;
     auto gsync = [g]() { named_sync(1 + g, GT); };
     auto job = [&](int k) { return (int)blockIdx.x + (g + NG * k) * (int)gridDim.x; };
-    auto issue = [&](int k) {  // copy the group's k-th panel: C columns, all rows
+    // rows to bring in: all, or 0 .. ny/2 of a Hermitian-column field, as whole
+    // boxes plus (when one row is left over) a single-row bulk copy
+    const int rows_in = a.half_in ? NY / 2 + 1 : NY;
+    const int nbox = rows_in / BOXR, rem = rows_in - nbox * BOXR;
+    const int nbox_t = nbox + (rem > 1 ? 1 : 0);
+    const uint32_t slot_bytes = (uint32_t)(nbox_t * BOXR * C * 8 + (rem == 1 ? C * 8 : 0));
+    auto issue = [&](int k) {  // copy the group's k-th panel: C columns, the rows above
         const int j = job(k);
         if (j >= J || j == pa.drop_job) return;
         const int item = j / ppt, pan = j - item * ppt;
         unsigned char *sl = ring + (size_t)(k % D) * Cfg::SLOT;
-        mbar_expect_tx(gfull + k % D, (uint32_t)Cfg::SLOT);
+        mbar_expect_tx(gfull + k % D, slot_bytes);
 #pragma unroll 1
-        for (int r = 0; r < NY / BOXR; ++r)
+        for (int r = 0; r < nbox_t; ++r)
             tma_load_2d(sl + (size_t)r * BOXR * C * 8, &tmap, 2 * pan * C, item * NY + r * BOXR,
                         gfull + k % D);
+        if (rem == 1)
+            bulk_g2s(sl + (size_t)nbox * BOXR * C * 8, a.field + ((size_t)item * NY + nbox * BOXR) * nx + pan * C,
+                     C * 8, gfull + k % D);
     };
     auto drain = [&](int k0, int k1) {
         for (int q = k0; q < k1; ++q) {
@@ -556,7 +644,13 @@ __global__ void __launch_bounds__(ColPipeCfg<P, C, NG, D, SWZ, BOXR>::THREADS, 1
         float2 v[E];
         static_for<0, E>([&](auto ec) {
             constexpr int e = decltype(ec)::value;
-            v[e] = sl[(t + TL * e) * C + c];
+            const int n = t + TL * e;
+            if (a.half_in && n > NY / 2) {
+                const float2 q = sl[(NY - n) * C + c];
+                v[e] = make_float2(q.x, -q.y);
+            } else {
+                v[e] = sl[n * C + c];
+            }
         });
         line_fft<P, +1, C, LAY>(v, sl + c, a.tw, t, gsync);
         const size_t base_o = (size_t)item * NY * nx;
@@ -834,15 +928,19 @@ template <class P, int NG, int D, int SWZ>
 struct PairImpl {
     using RC = PairPipeCfg<P, NG, D, SWZ>;
     static cudaError_t init_row(int *blocks) {
-        cudaError_t e = cudaFuncSetAttribute((const void *)k_row_pipe_pair<P, NG, D, SWZ>,
+        cudaError_t e = cudaFuncSetAttribute((const void *)k_row_pipe_pair<P, NG, D, SWZ, false>,
                                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)RC::SMEM);
         if (e == cudaSuccess)
-            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, k_row_pipe_pair<P, NG, D, SWZ>,
+            e = cudaFuncSetAttribute((const void *)k_row_pipe_pair<P, NG, D, SWZ, true>,
+                                     cudaFuncAttributeMaxDynamicSharedMemorySize, (int)RC::SMEM);
+        if (e == cudaSuccess)
+            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, k_row_pipe_pair<P, NG, D, SWZ, false>,
                                                               RC::THREADS, RC::SMEM);
         return e;
     }
     static void row_iter(const RowArgs &a, const PipeArgs &pa, int grid, cudaStream_t s) {
-        k_row_pipe_pair<P, NG, D, SWZ><<<grid, RC::THREADS, RC::SMEM, s>>>(a, pa);
+        if (a.herm) k_row_pipe_pair<P, NG, D, SWZ, true><<<grid, RC::THREADS, RC::SMEM, s>>>(a, pa);
+        else k_row_pipe_pair<P, NG, D, SWZ, false><<<grid, RC::THREADS, RC::SMEM, s>>>(a, pa);
     }
 };
 
