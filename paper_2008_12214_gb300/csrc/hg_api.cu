@@ -270,6 +270,8 @@ struct hg_plan_s {
     CUtensorMap cmap;                                // field as [chains*ny][2*nx] floats
     CUtensorMap cmap_pack;                           // same field, tiles of the packed column pass
     bool use_pack = false;                           // binary: packed column pass in the loop
+    CUtensorMap cmap_herm;                           // same field, tiles of the column-pair Hermitian pass
+    bool use_herm_col = false;                       // Hermitian loop: column pairs share transforms
     unsigned long long wait_ns = 2000000000ull;      // bound on a device-side wait
     int drop_job = -1;                               // fault-injection hook
     int nsm = 0, ppt = 0, ppt_pipe = 0, ppt_max = 0;
@@ -480,6 +482,13 @@ void launch_col_pack(hg_plan p, const ColArgs &a, cudaStream_t s) {
     p->launches++;
 }
 
+void launch_col_herm(hg_plan p, const ColArgs &a, cudaStream_t s) {
+    ProfScope ps(p, s, 1);
+    const long work = (long)a.items * ((p->nx + p->prow->herm_c - 1) / p->prow->herm_c);
+    p->prow->col_herm(a, pipe_args(p), p->cmap_herm, grid_for(p->prow->herm_blocks_per_sm, p->nsm, work), s);
+    p->launches++;
+}
+
 void launch_col_gs(hg_plan p, int role, const ColArgs &a, cudaStream_t s) {
     ProfScope ps(p, s, 1);
     if (p->pcol) {
@@ -529,6 +538,7 @@ void enqueue_loop(hg_plan p, int iters, cudaStream_t s) {
     for (int k = 0; k + 1 < iters; ++k) {
         ca.half_in = ra.herm && k > 0;  // column pass 0 follows the (full) head pass
         if (p->use_pack) launch_col_pack(p, ca, s);
+        else if (ca.half_in && p->use_herm_col) launch_col_herm(p, ca, s);
         else launch_col_gs(p, col_role_gs(p), ca, s);
         ra.part = p->part + (size_t)k * p->batch * p->ppt_max * NMET;
         launch_row_iter(p, ra, s);
@@ -604,7 +614,8 @@ hg_status enqueue_run(hg_plan p, const float *d_t, const float *d_ph, int iters,
         }
         ca.holo = d_ho;
         ca.half_in = herm_loop(p) && iters >= 2;
-        launch_col_gs(p, col_role_gs(p), ca, p->stream);
+        if (ca.half_in && p->use_herm_col) launch_col_herm(p, ca, p->stream);
+        else launch_col_gs(p, col_role_gs(p), ca, p->stream);
         RowArgs rt = row_args(p);
         rt.part = p->part + (size_t)(iters - 1) * p->batch * p->ppt_max * NMET;
         if (p->tc_prec) launch_row_tc(p, ROW_TAIL, rt, p->stream);
@@ -634,6 +645,18 @@ hg_status check_err_flag(hg_plan p) {
     return HG_OK;
 }
 
+bool make_cmap_box(hg_plan p, int cols, int boxr, CUtensorMap *m) {
+    EncodeTiledFn enc = encode_tiled();
+    if (!enc || cols < 1 || boxr < 1) return false;
+    const cuuint64_t gdim[2] = {(cuuint64_t)2 * p->nx, (cuuint64_t)p->ny * p->nchains};
+    const cuuint64_t gstride[1] = {(cuuint64_t)p->nx * 8};
+    const cuuint32_t box[2] = {(cuuint32_t)(2 * cols), (cuuint32_t)boxr};
+    const cuuint32_t estr[2] = {1, 1};
+    return enc(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, p->field, gdim, gstride, box, estr,
+               CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+               CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
 bool make_cmap(hg_plan p, const PipeOps *pc, CUtensorMap *m) {
     EncodeTiledFn enc = encode_tiled();
     if (!enc) return false;
@@ -648,7 +671,8 @@ bool make_cmap(hg_plan p, const PipeOps *pc, CUtensorMap *m) {
 
 // Best-of-3 launch time (ms, after one warm-up launch) of one pass variant on
 // the plan's own zeroed buffers, on the private capture stream.
-float time_variant(hg_plan p, const PipeOps *o, bool row, bool pack = false, bool herm = false) {
+float time_variant(hg_plan p, const PipeOps *o, bool row, bool pack = false, bool herm = false,
+                   bool herm_pairs = false) {
     if (!p->field || !p->tf || !p->twx || !p->twy || !p->lvl || !p->err) return 1e30f;
     cudaStream_t s = p->cap_stream;
     RowArgs ra = row_args(p);
@@ -657,11 +681,18 @@ float time_variant(hg_plan p, const PipeOps *o, bool row, bool pack = false, boo
     ra.herm = herm;
     ColArgs ca = col_args(p);
     CUtensorMap m;
-    if (!row && !make_cmap(p, o, &m)) return 1e30f;
+    if (herm_pairs) {
+        if (!o->col_herm || !make_cmap_box(p, o->herm_c, o->herm_boxr, &m)) return 1e30f;
+    } else if (!row && !make_cmap(p, o, &m)) {
+        return 1e30f;
+    }
     if (pack) ca.half = 1;
     if (!row && herm) ca.half = ca.half_in = 1;
-    const int ppt = row ? row_panels(o, p->ny) : (p->nx + o->col_c - 1) / o->col_c;
-    const int grid = grid_for(row ? o->row_blocks_per_sm : pack ? o->pack_blocks_per_sm : o->col_blocks_per_sm,
+    const int ppt = row ? row_panels(o, p->ny) : (p->nx + (herm_pairs ? o->herm_c : o->col_c) - 1) /
+                                                     (herm_pairs ? o->herm_c : o->col_c);
+    const int grid = grid_for(row ? o->row_blocks_per_sm
+                                  : pack ? o->pack_blocks_per_sm
+                                         : herm_pairs ? o->herm_blocks_per_sm : o->col_blocks_per_sm,
                               p->nsm, (long)p->batch * ppt);
     PipeArgs pa = pipe_args(p);
     cudaEvent_t e0, e1;
@@ -676,6 +707,7 @@ float time_variant(hg_plan p, const PipeOps *o, bool row, bool pack = false, boo
     for (int it = 0; it < 7; ++it) {
         cudaEventRecord(e0, s);
         if (row) o->row_iter(ra, pa, grid, s);
+        else if (herm_pairs) o->col_herm(ca, pa, m, grid, s);
         else if (pack) o->col_pack(ca, pa, m, grid, s);
         else o->col_gs(p->kind == HG_SLM_BINARY ? COL_GS_BIN : COL_GS_LVL, ca, pa, m, grid, s);
         cudaEventRecord(e1, s);
@@ -911,8 +943,13 @@ hg_status hg_plan_create(hg_plan *out, int ny, int nx, int batch, hg_slm slm, hg
                     const bool hm = rc[i]->paired && !pk && col && slm.kind == HG_SLM_BINARY;
                     float ms = time_variant(p, rc[i], true, false, hm);
                     if (i < 4) p->tune_ms[i] = ms;
-                    ms += pk ? time_variant(p, rc[i], false, true) : hm ? time_variant(p, col, false, false, true)
-                                                                          : best_col;
+                    float cm = best_col;
+                    if (pk) cm = time_variant(p, rc[i], false, true);
+                    else if (hm) {
+                        cm = time_variant(p, col, false, false, true);
+                        if (rc[i]->col_herm) cm = fminf(cm, time_variant(p, rc[i], false, false, true, true));
+                    }
+                    ms += cm;
                     if (ms < best) best = ms, row = rc[i];
                 }
                 std::lock_guard<std::mutex> lk(g_tune_mu);
@@ -928,6 +965,17 @@ hg_status hg_plan_create(hg_plan *out, int ny, int nx, int batch, hg_slm slm, hg
         }
         if (col && make_cmap(p, col, &p->cmap)) p->pcol = col;
         if (o.pipeline == 1 && (!p->prow || !p->pcol)) return fail(HG_ERR_UNSUPPORTED_SIZE);
+        // Hermitian loop: the column-pair pass when it is at least as fast
+        if (herm_loop(p) && p->prow->col_herm && p->prow->herm_blocks_per_sm > 0 &&
+            make_cmap_box(p, p->prow->herm_c, p->prow->herm_boxr, &p->cmap_herm)) {
+            bool take = true;
+            if (o.autotune == 1) {
+                const float th = time_variant(p, p->prow, false, false, true, true);
+                const float tc = time_variant(p, p->pcol, false, false, true);
+                take = th <= tc;
+            }
+            p->use_herm_col = take;
+        }
     }
     if ((st = ensure_part(p, algo == HG_OSPR ? 1 : 8)) != HG_OK) return fail(st);
     if ((st = ensure_metrics(p, 1)) != HG_OK) return fail(st);
@@ -998,7 +1046,8 @@ const char *hg_plan_variant(hg_plan p, int pass) {
     }
     const PipeOps *o = pass == 0 ? p->prow : p->pcol;
     if (o && herm_loop(p)) {  // Hermitian form of the binary loop
-        snprintf(p->vname[pass], sizeof p->vname[pass], "%s+herm", o->name);
+        snprintf(p->vname[pass], sizeof p->vname[pass], "%s+herm%s", o->name,
+                 pass == 1 && p->use_herm_col ? "-colpairs" : "");
         return p->vname[pass];
     }
     return o ? o->name : "generic";

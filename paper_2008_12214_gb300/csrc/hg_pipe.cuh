@@ -687,6 +687,147 @@ __global__ void __launch_bounds__(ColPipeCfg<P, C, NG, D, SWZ, BOXR>::THREADS, 1
     }
 }
 
+
+// -------------------------- column pass of the Hermitian binary loop (pairs)
+// In the Hermitian loop (see herm_constrain) every column of the field is
+// Hermitian in ky, so its inverse FFT is real, and so is its binary
+// hologram; two columns a and b therefore share every transform.  The
+// inverse FFT of A + iB gives a + ib, whose signs are the two columns'
+// binary levels; the forward FFT of z = qa + i qb gives Z, and
+// QA[k] = (Z[k] + conj Z[N-k]) / 2, QB[k] = (Z[k] - conj Z[N-k]) / (2i).
+// Reads rows 0 .. ny/2 (the rest by conjugation), writes rows <= ny/2 (all
+// rows when a.half == 0).  C columns (C/2 pairs) per CTA, ring depth D.
+template <class P, int C, int D, int SWZ, int BOXR>
+struct ColHermCfg {
+    static constexpr int CP = C / 2;
+    static constexpr int GT = P::TL * CP;
+    static_assert(C % 2 == 0 && GT % 32 == 0, "column pairs must fill whole warps");
+    static_assert(BOXR <= 256, "box rows");
+    static constexpr int THREADS = GT;
+    static constexpr int ROWS_IN = P::N / 2 + 1;
+    static constexpr int NBOX = ROWS_IN / BOXR, REM = ROWS_IN - NBOX * BOXR;
+    static constexpr int NBOX_T = NBOX + (REM > 1 ? 1 : 0);
+    static constexpr int LOAD = NBOX_T * BOXR * C * 8 + (REM == 1 ? C * 8 : 0);
+    static constexpr int XCH = P::N * CP * 8;
+    static constexpr int SLOT = ((LOAD > XCH ? LOAD : XCH) + 1023) / 1024 * 1024;
+    static constexpr size_t SMEM = 1024 + (size_t)D * SLOT + D * 8 + 16 + 256;
+};
+
+template <class P, int C, int D, int SWZ, int BOXR>
+__global__ void __launch_bounds__(ColHermCfg<P, C, D, SWZ, BOXR>::THREADS, 1)
+    k_col_pipe_herm(const ColArgs a, const PipeArgs pa, const __grid_constant__ CUtensorMap tmap) {
+    using Cfg = ColHermCfg<P, C, D, SWZ, BOXR>;
+    using LAY = Swz<SWZ>;
+    constexpr int TL = P::TL, E = P::E, NY = P::N, CP = Cfg::CP, HY = NY / 2;
+    extern __shared__ unsigned char smraw[];
+    unsigned char *base = smraw + ((1024 - (smem_addr(smraw) & 1023)) & 1023);
+    uint64_t *full = reinterpret_cast<uint64_t *>(base + (size_t)D * Cfg::SLOT);
+    volatile int *flags = reinterpret_cast<volatile int *>(full + D);
+    volatile int *abort = flags + 1;
+
+    const int tid = threadIdx.x;
+    if (tid == 0) {
+        for (int i = 0; i < D; ++i) mbar_init(full + i, 1);
+        *abort = 0;
+        fence_mbar_init();
+    }
+    __syncthreads();
+
+    const int nx = a.nx;
+    const int ppt = (nx + C - 1) / C;
+    const int J = a.items * ppt;
+    const int cp = tid % CP, t = tid / CP;
+    auto sync = []() { __syncthreads(); };
+    auto job = [&](int k) { return (int)blockIdx.x + k * (int)gridDim.x; };
+    auto issue = [&](int k) {
+        const int j = job(k);
+        if (j >= J || j == pa.drop_job) return;
+        const int item = j / ppt, pan = j - item * ppt;
+        unsigned char *sl = base + (size_t)(k % D) * Cfg::SLOT;
+        mbar_expect_tx(full + k % D, (uint32_t)Cfg::LOAD);
+#pragma unroll 1
+        for (int r = 0; r < Cfg::NBOX_T; ++r)
+            tma_load_2d(sl + (size_t)r * BOXR * C * 8, &tmap, 2 * pan * C, item * NY + r * BOXR, full + k % D);
+        if constexpr (Cfg::REM == 1)
+            bulk_g2s(sl + (size_t)Cfg::NBOX * BOXR * C * 8,
+                     a.field + ((size_t)item * NY + Cfg::NBOX * BOXR) * nx + pan * C, C * 8, full + k % D);
+    };
+    auto drain = [&](int k0, int k1) {
+        for (int q = k0; q < k1; ++q) {
+            const int j = job(q);
+            if (j < J && j != pa.drop_job) mbar_wait(full + q % D, (q / D) & 1, pa.wait_ns, nullptr);
+        }
+    };
+    if (tid == 0)
+        for (int k = 0; k < D; ++k) issue(k);
+
+    for (int k = 0;; ++k) {
+        const int j = job(k);
+        if (j >= J) break;
+        if (tid == 0) {
+            bool ok = !*abort && mbar_wait(full + k % D, (k / D) & 1, pa.wait_ns, abort);
+            if (!ok) {
+                atomicOr(pa.err, ERR_TIMEOUT_BIT);
+                *abort = 1;
+            }
+            flags[0] = ok;
+        }
+        sync();
+        if (!flags[0]) {
+            if (tid == 0) drain(k, k + D);
+            break;
+        }
+        const int item = j / ppt, pan = j - item * ppt;
+        const int xa = pan * C + 2 * cp;
+        const bool act = xa + 1 < nx;
+        float2 *sl = reinterpret_cast<float2 *>(base + (size_t)(k % D) * Cfg::SLOT);
+        float2 v[E];
+        static_for<0, E>([&](auto ec) {
+            constexpr int e = decltype(ec)::value;
+            const int n = t + TL * e;
+            float2 A, B;
+            if (n <= HY) {
+                A = sl[n * C + 2 * cp];
+                B = sl[n * C + 2 * cp + 1];
+            } else {
+                const float2 qa = sl[(NY - n) * C + 2 * cp], qb = sl[(NY - n) * C + 2 * cp + 1];
+                A = make_float2(qa.x, -qa.y);
+                B = make_float2(qb.x, -qb.y);
+            }
+            v[e] = make_float2(A.x - B.y, A.y + B.x);  // A + iB
+        });
+        line_fft<P, +1, CP, LAY>(v, sl + cp, a.tw, t, sync);
+        const size_t base_o = (size_t)item * NY * nx;
+        static_for<0, E>([&](auto ec) {
+            constexpr int e = decltype(ec)::value;
+            const int n = t + TL * e;
+            const int qa = v[e].x >= 0.f ? 0 : 1, qb = v[e].y >= 0.f ? 0 : 1;
+            if (act && a.holo)
+                *reinterpret_cast<uint16_t *>(a.holo + base_o + (size_t)n * nx + xa) = (uint16_t)(qa | (qb << 8));
+            v[e] = make_float2(qa ? -1.f : 1.f, qb ? -1.f : 1.f);
+        });
+        line_fft<P, -1, CP, LAY>(v, sl + cp, a.tw, t, sync);
+        // separate the two spectra through Z[N - k]
+        sync();
+        static_for<0, E>([&](auto ec) {
+            constexpr int e = decltype(ec)::value;
+            sl[(t + TL * e) * CP + cp] = v[e];
+        });
+        sync();
+        float4 *fw = reinterpret_cast<float4 *>(a.field + base_o + xa);
+        static_for<0, E>([&](auto ec) {
+            constexpr int e = decltype(ec)::value;
+            const int kk = t + TL * e;
+            const float2 z = v[e], zm = sl[((NY - kk) & (NY - 1)) * CP + cp];
+            if (act && (!a.half || kk <= HY))
+                fw[(size_t)kk * nx / 2] = make_float4(0.5f * (z.x + zm.x), 0.5f * (z.y - zm.y),
+                                                     0.5f * (z.y + zm.y), 0.5f * (zm.x - z.x));
+        });
+        sync();
+        if (tid == 0) issue(k + D);  // slot fully consumed: refill it
+    }
+}
+
 // ------------------------------------- packed column pass (binary, half rows)
 // After binary quantisation every column of e^{iH} is real, so two columns a
 // and b are transformed by one complex FFT of z = a + i b: with Z = FFT(z),
@@ -852,6 +993,10 @@ struct PipeOps {
     // binary column pass with packed forward transforms, half rows (may be null)
     void (*col_pack)(const ColArgs &a, const PipeArgs &pa, const CUtensorMap &m, int grid, cudaStream_t s);
     int pack_blocks_per_sm;
+    // column pass of the Hermitian binary loop, two columns per transform (may be null);
+    // its tensor map has boxes of herm_c columns x herm_boxr rows
+    void (*col_herm)(const ColArgs &a, const PipeArgs &pa, const CUtensorMap &m, int grid, cudaStream_t s);
+    int herm_c, herm_boxr, herm_blocks_per_sm;
 };
 
 // Row pass: plan P, LINES rows per group, NGR groups, ring depth DR, swizzle
@@ -961,6 +1106,34 @@ struct PackImpl {
     }
 };
 
+// Column-pair Hermitian column pass launcher (see k_col_pipe_herm).
+template <class P, int C, int D, int SWZ, int BOXR>
+struct HermImpl {
+    using CC = ColHermCfg<P, C, D, SWZ, BOXR>;
+    static constexpr int COLS = C, BOX_ROWS = BOXR;
+    static cudaError_t init(int *blocks) {
+        cudaError_t e = cudaFuncSetAttribute((const void *)k_col_pipe_herm<P, C, D, SWZ, BOXR>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)CC::SMEM);
+        if (e == cudaSuccess)
+            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, k_col_pipe_herm<P, C, D, SWZ, BOXR>,
+                                                              CC::THREADS, CC::SMEM);
+        return e;
+    }
+    static void launch(const ColArgs &a, const PipeArgs &pa, const CUtensorMap &m, int grid, cudaStream_t s) {
+        k_col_pipe_herm<P, C, D, SWZ, BOXR><<<grid, CC::THREADS, CC::SMEM, s>>>(a, pa, m);
+    }
+};
+
+struct NoHerm {
+    static constexpr int COLS = 0, BOX_ROWS = 0;
+    static cudaError_t init(int *blocks) {
+        *blocks = 0;
+        return cudaSuccess;
+    }
+    static constexpr void (*launch)(const ColArgs &, const PipeArgs &, const CUtensorMap &, int,
+                                    cudaStream_t) = nullptr;
+};
+
 struct NoPack {
     static cudaError_t init(int *blocks) {
         *blocks = 0;
@@ -972,20 +1145,23 @@ struct NoPack {
 
 // Combines a paired row pass with the column pass of an existing variant (and
 // optionally a packed binary column pass with the same tile shape).
-template <class PAIR, const PipeOps *COL, class PACK = NoPack>
+template <class PAIR, const PipeOps *COL, class PACK = NoPack, class HERM = NoHerm>
 struct PairedOps {
     static cudaError_t init(PipeOps *self) {
         cudaError_t e = COL->init(const_cast<PipeOps *>(COL));
         if (e != cudaSuccess) return e;
-        int rb = 0, pb = 0;
+        int rb = 0, pb = 0, hb = 0;
         e = PAIR::init_row(&rb);
         if (e == cudaSuccess) e = PACK::init(&pb);
+        if (e == cudaSuccess) e = HERM::init(&hb);
         if (e != cudaSuccess) return e;
         if (rb < 1) return cudaErrorInvalidConfiguration;
         self->row_blocks_per_sm = rb;
         self->col_blocks_per_sm = COL->col_blocks_per_sm;
         self->pack_blocks_per_sm = pb;
+        self->herm_blocks_per_sm = hb;
         if (pb < 1) self->col_pack = nullptr;
+        if (hb < 1) self->col_herm = nullptr;
         return cudaSuccess;
     }
     static PipeOps make(const char *name) {
@@ -997,6 +1173,9 @@ struct PairedOps {
         o.row_smem = PAIR::RC::SMEM;
         o.row_iter = &PAIR::row_iter;
         o.col_pack = PACK::launch;
+        o.col_herm = HERM::launch;
+        o.herm_c = HERM::COLS;
+        o.herm_boxr = HERM::BOX_ROWS;
         o.init = &init;
         return o;
     }

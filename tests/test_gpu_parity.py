@@ -364,7 +364,7 @@ def test_bounded_wait_reports_timeout_and_plan_recovers():
 
 
 @pytest.mark.parametrize("n,cand", [(256, 0), (512, 0), (512, 1), (512, 2), (1024, 0), (1024, 1), (1024, 2),
-                                    (1024, 3), (1024, 4), (2048, 0), (2048, 1), (2048, 2)])
+                                    (1024, 3), (1024, 4), (1024, 5), (2048, 0), (2048, 1), (2048, 2)])
 def test_every_pipelined_variant_against_oracle(n, cand):
     """Each TMA-fed candidate the autotuner may pick, forced in turn: the
     column pass through a single step, the row pass through the metrics it
@@ -395,7 +395,7 @@ def test_every_pipelined_variant_against_oracle(n, cand):
         assert abs(mse[b, 3] - run["mse"][3]) <= 1e-2 * run["mse"][3], name
 
 
-@pytest.mark.parametrize("cand", [2, 3, 4])
+@pytest.mark.parametrize("cand", [2, 3, 4, 5])
 def test_paired_rows_weighted_gs_binary(cand):
     """The paired-row pass (binary SLM) also carries the weighted-GS update:
     same metrics and weights as the generic passes on the first iterations."""
@@ -501,3 +501,36 @@ def test_tensor_core_row_pass_precision(prec, tol):
     print("precision %d: single-step rel-L2 %s, final-MSE delta vs FP32 %s" % (prec, errs, d))
     assert max(errs) <= tol
     assert np.all(d < 0.05)
+
+
+@pytest.mark.parametrize("cand,wgs", [(2, False), (3, False), (5, False), (2, True)])
+def test_hermitian_binary_loop_matches_generic(cand, wgs):
+    """Binary GS in Hermitian form (paired rows write only the Hermitian part
+    of F, rows ky <= ny/2; the column passes read those rows back, two columns
+    per transform) against the generic passes: the same holograms and
+    metrics, since the quantiser only sees Re IFFT2(F) = IFFT2(F_H).  The two
+    paths round differently, so a boundary pixel may flip and binary GS then
+    spreads the difference: iteration 0 to 1e-5, holograms after three
+    iterations in at most 0.2% of pixels, MSE to 1e-3.  Weighted GS runs two
+    iterations only: its literal weight rule makes whole trajectories part
+    ways after a few iterations even between FP32 and FP64."""
+    n, batch = 1024, 2
+    iters = 2 if wgs else 3
+    algo = hg.HG_WGS if wgs else hg.HG_GS
+    t = torch.from_numpy(synth.targets(batch, n, n, 4100)).to(DEV)
+    ph = torch.from_numpy(synth.init_phases(batch, n, n, 4100)).to(DEV)
+    out = {}
+    for pipe, tune in ((0, 0), (1, 2 + cand)):
+        plan = hg.Plan(n, n, batch, hg.HG_SLM_BINARY, 2, algo, pipeline=pipe, autotune=tune)
+        holo = torch.empty((batch, n, n), dtype=torch.uint8, device=DEV)
+        mse = torch.empty((batch, iters), dtype=torch.float64, device=DEV)
+        plan.run(t, ph, iters, holo, mse)
+        plan.sync()
+        out[pipe] = (holo.cpu().numpy(), mse.cpu().numpy(), hg.hg_plan_variant(plan.h, 0),
+                     hg.hg_plan_variant(plan.h, 1))
+        plan.close()
+    assert "+herm" in out[1][2] and "+herm-colpairs" in out[1][3], out[1][2:]
+    assert np.allclose(out[0][1][:, 0], out[1][1][:, 0], rtol=1e-5, atol=0)
+    assert np.allclose(out[0][1], out[1][1], rtol=1e-3, atol=0), (out[0][1], out[1][1])
+    assert np.mean(out[0][0] != out[1][0]) <= 2e-3, np.mean(out[0][0] != out[1][0])
+    assert out[1][0].max() <= 1
