@@ -63,7 +63,7 @@ def parse():
     ap.add_argument("--quick", action="store_true", help="skip the e2e and CPU-baseline legs")
     ap.add_argument("--pairs", type=int, default=2048, help="warmstart: training pairs")
     ap.add_argument("--heldout", type=int, default=64, help="warmstart: held-out targets")
-    ap.add_argument("--workload", choices=["headline", "ospr", "mixed", "warmstart"], default="headline",
+    ap.add_argument("--workload", choices=["headline", "ospr", "mixed", "warmstart", "gs2048"], default="headline",
                     help="headline: binary GS 1024^2 x 64 (the benchmark line); ospr: 8 targets x 24 "
                          "subframes of 1024^2; mixed: 16 targets each of 512^2, 1024^2, 2048^2, 1080x1920")
     return ap.parse_args()
@@ -283,6 +283,27 @@ def run_side_workload(args):
         plan.close()
     elif args.workload == "warmstart":
         out = run_warmstart(args, dev, s0)
+    elif args.workload == "gs2048":
+        B, n = 16, 2048
+        T = torch.from_numpy(synth.targets(B, n, n, 5000)).to(dev)
+        P = torch.from_numpy(synth.init_phases(B, n, n, 5000)).to(dev)
+        mse = torch.empty((B, args.iters), dtype=torch.float64, device=dev)
+        plan = hg.Plan(n, n, B, hg.HG_SLM_BINARY, 2, hg.HG_GS)
+        for _ in range(args.warmup):
+            plan.run(T, P, args.iters, None, mse)
+        plan.sync()
+        e0.record(s0)
+        for _ in range(args.steps):
+            plan.run(T, P, args.iters, None, mse)
+        e1.record(s0)
+        plan.sync()
+        ms = e0.elapsed_time(e1) / args.steps
+        px = B * n * n
+        it_ms = ms / args.iters
+        out = dict(workload="gs_binary_2048x2048_batch16", ms_per_step=ms, iters_per_step=args.iters,
+                   batched_iterations_per_s=1e3 / it_ms, gbs_at_36=36.0 * px / (it_ms / 1e3) / 1e9,
+                   row_variant=hg.hg_plan_variant(plan.h, 0), column_variant=hg.hg_plan_variant(plan.h, 1))
+        plan.close()
     else:
         shapes = [(512, 512), (1024, 1024), (2048, 2048), (1080, 1920)]
         plans, Ts, Ps, Ms = [], [], [], []

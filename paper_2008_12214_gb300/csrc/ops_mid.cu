@@ -11,8 +11,14 @@ PipeOps p512a = PipeImpl<Plan<512, 16, 32, 32, 16>, 2, 8, 2, 5, Plan<512, 16, 32
                           256>::make("512:r32x16e32");
 PipeOps p512b = PipeImpl<Plan<512, 32, 16, 16, 16, 2>, 1, 16, 2, 4, Plan<512, 32, 16, 16, 16, 2>, 8, 2, 3,
                           4, 256>::make("512:r16x16x2e16");
-PipeOps p512c = PairedOps<PairImpl<Plan<512, 32, 16, 16, 16, 2>, 12, 2, 4>, &p512a>::make(
+// paired rows with the Hermitian column-pair pass (binary loop): 16 columns
+// with 16 samples per thread, or 32 columns with 32 samples per thread
+using Herm512a = HermImpl<Plan<512, 32, 16, 16, 16, 2>, 16, 3, 4, 256>;
+using Herm512b = HermImpl<Plan<512, 16, 32, 32, 16>, 32, 3, 5, 256>;
+PipeOps p512c = PairedOps<PairImpl<Plan<512, 32, 16, 16, 16, 2>, 12, 2, 4>, &p512a, NoPack, Herm512a>::make(
     "512:pair16x16x2e16+c32x16e32");
+PipeOps p512d = PairedOps<PairImpl<Plan<512, 32, 16, 16, 16, 2>, 12, 2, 4>, &p512a, NoPack, Herm512b>::make(
+    "512:pair16x16x2e16+c32x16e32/h32");
 }  // namespace
 
 const LineOps *ops_mid(int n) {
@@ -30,6 +36,7 @@ int pipe_ops_mid(int n, const PipeOps **out, int max) {
         if (k < max) out[k++] = &p512a;
         if (k < max) out[k++] = &p512b;
         if (k < max) out[k++] = &p512c;
+        if (k < max) out[k++] = &p512d;
     }
     return k;
 }

@@ -364,7 +364,8 @@ def test_bounded_wait_reports_timeout_and_plan_recovers():
 
 
 @pytest.mark.parametrize("n,cand", [(256, 0), (512, 0), (512, 1), (512, 2), (1024, 0), (1024, 1), (1024, 2),
-                                    (1024, 3), (1024, 4), (1024, 5), (2048, 0), (2048, 1), (2048, 2)])
+                                    (1024, 3), (1024, 4), (1024, 5), (512, 3), (2048, 0), (2048, 1), (2048, 2),
+                                    (2048, 3)])
 def test_every_pipelined_variant_against_oracle(n, cand):
     """Each TMA-fed candidate the autotuner may pick, forced in turn: the
     column pass through a single step, the row pass through the metrics it
@@ -503,8 +504,9 @@ def test_tensor_core_row_pass_precision(prec, tol):
     assert np.all(d < 0.05)
 
 
-@pytest.mark.parametrize("cand,wgs", [(2, False), (3, False), (5, False), (2, True)])
-def test_hermitian_binary_loop_matches_generic(cand, wgs):
+@pytest.mark.parametrize("n,cand,wgs", [(1024, 2, False), (1024, 3, False), (1024, 5, False), (1024, 2, True),
+                                        (512, 2, False), (512, 3, False), (2048, 2, False), (2048, 3, False)])
+def test_hermitian_binary_loop_matches_generic(n, cand, wgs):
     """Binary GS in Hermitian form (paired rows write only the Hermitian part
     of F, rows ky <= ny/2; the column passes read those rows back, two columns
     per transform) against the generic passes: the same holograms and
@@ -514,7 +516,7 @@ def test_hermitian_binary_loop_matches_generic(cand, wgs):
     iterations in at most 0.2% of pixels, MSE to 1e-3.  Weighted GS runs two
     iterations only: its literal weight rule makes whole trajectories part
     ways after a few iterations even between FP32 and FP64."""
-    n, batch = 1024, 2
+    batch = 1 if n == 2048 else 2
     iters = 2 if wgs else 3
     algo = hg.HG_WGS if wgs else hg.HG_GS
     t = torch.from_numpy(synth.targets(batch, n, n, 4100)).to(DEV)
@@ -531,6 +533,10 @@ def test_hermitian_binary_loop_matches_generic(cand, wgs):
         plan.close()
     assert "+herm" in out[1][2] and "+herm-colpairs" in out[1][3], out[1][2:]
     assert np.allclose(out[0][1][:, 0], out[1][1][:, 0], rtol=1e-5, atol=0)
-    assert np.allclose(out[0][1], out[1][1], rtol=1e-3, atol=0), (out[0][1], out[1][1])
-    assert np.mean(out[0][0] != out[1][0]) <= 2e-3, np.mean(out[0][0] != out[1][0])
+    if n == 2048:  # different radix plans on the two paths (16x16x8 vs 32x8x8): a few boundary flips spread
+        assert np.allclose(out[0][1], out[1][1], rtol=2e-2, atol=0), (out[0][1], out[1][1])
+        assert np.mean(out[0][0] != out[1][0]) <= 2e-2, np.mean(out[0][0] != out[1][0])
+    else:
+        assert np.allclose(out[0][1], out[1][1], rtol=1e-3, atol=0), (out[0][1], out[1][1])
+        assert np.mean(out[0][0] != out[1][0]) <= 2e-3, np.mean(out[0][0] != out[1][0])
     assert out[1][0].max() <= 1
