@@ -272,6 +272,8 @@ struct hg_plan_s {
     bool use_pack = false;                           // binary: packed column pass in the loop
     CUtensorMap cmap_herm;                           // same field, tiles of the column-pair Hermitian pass
     bool use_herm_col = false;                       // Hermitian loop: column pairs share transforms
+    const PipeOps *hops = nullptr;                   // variant providing the column-pair pass
+    bool ospr_herm = false;                          // binary OSPR in Hermitian form
     unsigned long long wait_ns = 2000000000ull;      // bound on a device-side wait
     int drop_job = -1;                               // fault-injection hook
     int nsm = 0, ppt = 0, ppt_pipe = 0, ppt_max = 0;
@@ -484,8 +486,9 @@ void launch_col_pack(hg_plan p, const ColArgs &a, cudaStream_t s) {
 
 void launch_col_herm(hg_plan p, const ColArgs &a, cudaStream_t s) {
     ProfScope ps(p, s, 1);
-    const long work = (long)a.items * ((p->nx + p->prow->herm_c - 1) / p->prow->herm_c);
-    p->prow->col_herm(a, pipe_args(p), p->cmap_herm, grid_for(p->prow->herm_blocks_per_sm, p->nsm, work), s);
+    const PipeOps *h = p->hops;
+    const long work = (long)a.items * ((p->nx + h->herm_c - 1) / h->herm_c);
+    h->col_herm(a, pipe_args(p), p->cmap_herm, grid_for(h->herm_blocks_per_sm, p->nsm, work), s);
     p->launches++;
 }
 
@@ -592,13 +595,20 @@ hg_status enqueue_run(hg_plan p, const float *d_t, const float *d_ph, int iters,
         ra.nsub = p->nsub;
         ra.phase = nullptr;
         ra.stream_id = 0;
+        ra.herm = p->ospr_herm;
         launch_row(p, ROW_HEAD, ra, p->stream);
         ca.items = p->nchains;
         ca.holo = d_ho;
-        launch_col_gs(p, COL_GS_BIN, ca, p->stream);
+        if (p->ospr_herm) {
+            ca.half_in = ca.half = 1;
+            launch_col_herm(p, ca, p->stream);
+        } else {
+            launch_col_gs(p, COL_GS_BIN, ca, p->stream);
+        }
         RowArgs rt = row_args(p);
         rt.nsub = p->nsub;
         rt.part = p->part;
+        rt.herm = p->ospr_herm;
         launch_row(p, ROW_AVG, rt, p->stream);
     } else {
         if (p->algo == HG_WGS && (!p->weights_preset || capturing)) {
@@ -622,7 +632,8 @@ hg_status enqueue_run(hg_plan p, const float *d_t, const float *d_ph, int iters,
         else launch_row(p, ROW_TAIL, rt, p->stream);
     }
     const int panels_iter = p->tc_prec ? p->ppt_tc : p->prow ? p->ppt_pipe : p->ppt;
-    const int panels_last = (p->tc_prec && p->algo != HG_OSPR) ? p->ppt_tc : p->ppt;
+    int panels_last = (p->tc_prec && p->algo != HG_OSPR) ? p->ppt_tc : p->ppt;
+    if (p->ospr_herm) panels_last = (p->ny / 2 + p->rops->row_lines) / p->rops->row_lines;  // rows <= ny/2
     k_reduce<<<(iters * p->batch * 32 + 127) / 128, 128, 0, p->stream>>>(
         p->part, iters, p->batch, p->ppt_max, panels_iter, panels_last, 1.0 / (double)p->npx, p->metrics,
         d_mo);
@@ -975,6 +986,19 @@ hg_status hg_plan_create(hg_plan *out, int ny, int nx, int batch, hg_slm slm, hg
                 take = th <= tc;
             }
             p->use_herm_col = take;
+            if (take) p->hops = p->prow;
+        }
+        // Binary OSPR: one pass per subframe in Hermitian form with the column-pair
+        // pass of any paired variant of this column length (square power-of-two fields)
+        if (algo == HG_OSPR && ny == nx && ny % 2 == 0) {
+            const PipeOps *all[8];
+            const int k = pipe_candidates(ny, all, 8);
+            for (int i = 0; i < k && !p->hops; ++i)
+                if (all[i]->paired && all[i]->col_herm && ensure_pipe_init(p->dev, all[i]) == cudaSuccess &&
+                    all[i]->herm_blocks_per_sm > 0 &&
+                    make_cmap_box(p, all[i]->herm_c, all[i]->herm_boxr, &p->cmap_herm))
+                    p->hops = all[i];
+            p->ospr_herm = p->hops != nullptr;
         }
     }
     if ((st = ensure_part(p, algo == HG_OSPR ? 1 : 8)) != HG_OK) return fail(st);
@@ -1039,6 +1063,10 @@ hg_status hg_profile_read(hg_plan p, double *out4) {
 const char *hg_plan_variant(hg_plan p, int pass) {
     if (!p) return "";
     if (pass == 1 && p->use_pack) return "packed-binary-columns (with the row variant)";
+    if (pass == 1 && p->ospr_herm) {
+        snprintf(p->vname[1], sizeof p->vname[1], "%s+herm-colpairs (OSPR)", p->hops->name);
+        return p->vname[1];
+    }
     if (pass == 0 && p->tc_prec) {
         static const char *names[] = {"", "1024:tc32x32-fp16hilo", "1024:tc32x32-fp16", "1024:tc32x32-bf16hilo",
                                       "1024:tc32x32-bf16"};

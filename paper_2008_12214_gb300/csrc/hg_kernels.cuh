@@ -103,8 +103,11 @@ struct ColCfg {
 };
 
 // --------------------------------------------------------------- row pass
-template <class P, int ROLE, int LINES>
-__global__ void __launch_bounds__(P::TL *LINES) k_row(const RowArgs a) {
+// H: Hermitian form of HEAD / AVG (binary OSPR): rows y <= ny/2 only, each
+// with its mirror row ny - y (see herm_constrain).  Kernels: k_row (H false)
+// and k_row_h (H true), sharing this body.
+template <class P, int ROLE, int LINES, bool H>
+__device__ __forceinline__ void row_body(const RowArgs &a) {
     using Cfg = RowCfg<P, LINES>;
     constexpr int TL = P::TL, E = P::E, NX = P::N;
     extern __shared__ __align__(16) unsigned char smraw[];
@@ -118,13 +121,14 @@ __global__ void __launch_bounds__(P::TL *LINES) k_row(const RowArgs a) {
         else __syncthreads();
     };
     const int ny = a.ny;
-    const int ppt = (ny + LINES - 1) / LINES;
+    const int rows = H ? ny / 2 + 1 : ny;
+    const int ppt = (rows + LINES - 1) / LINES;
     const int total = a.items * ppt;
     for (int p = blockIdx.x; p < total; p += gridDim.x) {
         const int item = p / ppt, pan = p - item * ppt;
         const int y = pan * LINES + line;
-        const bool act = y < ny;
-        const int yc = act ? y : ny - 1;
+        const bool act = y < rows;
+        const int yc = act ? y : rows - 1;
         const int iy = (yc + ny / 2) % ny;  // replay row of DFT row yc
         float2 v[E];
         if constexpr (ROLE == ROW_HEAD) {
@@ -148,6 +152,22 @@ __global__ void __launch_bounds__(P::TL *LINES) k_row(const RowArgs a) {
                     sincospif((float)(r >> 8) * (1.0f / 8388608.0f), &s, &c);  // pi * 2u
                 }
                 v[e] = make_float2(amp * c, amp * s);
+                if constexpr (H) {  // F_H = (F(u) + conj F(-u)) / 2, u' = (ny - y, nx - x)
+                    const int ym = (ny - yc) % ny, iym = (ym + ny / 2) % ny;
+                    const int xm = (NX - x) % NX, ixm = (xm + NX / 2) % NX;
+                    float snm, csm;
+                    if (a.phase) {
+                        sincospif(__ldg(a.phase + ((size_t)b * ny + iym) * NX + ixm) * 0.318309886183790672f,
+                                  &snm, &csm);
+                    } else {
+                        const uint32_t r = philox_word0((uint32_t)(iym * NX + ixm), (uint32_t)sub,
+                                                        (uint32_t)b, a.stream_id, a.seed_lo, a.seed_hi);
+                        sincospif((float)(r >> 8) * (1.0f / 8388608.0f), &snm, &csm);
+                    }
+                    float am = a.T[((size_t)b * ny + ym) * NX + xm];
+                    if (a.w) am *= a.w[((size_t)b * ny + ym) * NX + xm];
+                    v[e] = make_float2(0.5f * fmaf(am, csm, v[e].x), 0.5f * fmaf(-am, snm, v[e].y));
+                }
             });
             line_fft<P, +1, 1>(v, smb, a.tw, t, sync);
             if (act) {
@@ -252,11 +272,44 @@ __global__ void __launch_bounds__(P::TL *LINES) k_row(const RowArgs a) {
                     if (Tv > 0.f) acc2 += e2;
                 }
             });
+            if constexpr (H) {
+                // the intensity of mirror pixel (ny - y, nx - x) equals that of (y, x)
+                const int ym = (ny - yc) % ny, iym = (ym + ny / 2) % ny;
+                if (act && ym != yc) {
+                    const float *Tm = a.T ? a.T + ((size_t)item * ny + ym) * NX : nullptr;
+                    float *Im = a.I_out ? a.I_out + ((size_t)item * ny + iym) * NX : nullptr;
+                    static_for<0, E>([&](auto ec) {
+                        constexpr int e = decltype(ec)::value;
+                        const int xm = (NX - (t + TL * e)) % NX;
+                        const float I = acc[e] * inv_sub * a.invN2;
+                        if (Im) Im[(xm + NX / 2) % NX] = I;
+                        if (Tm) {
+                            const float Tv = Tm[xm];
+                            const float d = I - Tv * Tv;
+                            const float am = sqrtf(I) - Tv;
+                            const float e2 = acc[e] * inv_sub * a.invN;
+                            acc0 = fmaf(d, d, acc0);
+                            acc1 = fmaf(am, am, acc1);
+                            acc3 += e2;
+                            if (Tv > 0.f) acc2 += e2;
+                        }
+                    });
+                }
+            }
             if (a.part)
                 block_sum4(acc0, acc1, acc2, acc3, red,
                            a.part + ((size_t)item * ppt + pan) * NMET, Cfg::THREADS);
         }
     }
+}
+
+template <class P, int ROLE, int LINES>
+__global__ void __launch_bounds__(P::TL *LINES) k_row(const RowArgs a) {
+    row_body<P, ROLE, LINES, false>(a);
+}
+template <class P, int ROLE, int LINES>
+__global__ void __launch_bounds__(P::TL *LINES, ROLE == ROW_HEAD ? 2 : 1) k_row_h(const RowArgs a) {
+    row_body<P, ROLE, LINES, true>(a);
 }
 
 // ------------------------------------------------------------ column pass
@@ -337,7 +390,9 @@ struct LineOps {
     void (*col)(int role, const ColArgs &a, int grid, cudaStream_t s);
 };
 
-template <class P, int LINES, int C>
+// HERM: also instantiate the Hermitian HEAD / AVG rows (power-of-two lengths
+// that have a column-pair pass).
+template <class P, int LINES, int C, bool HERM = false>
 struct OpsImpl {
     using RC = RowCfg<P, LINES>;
     using CC = ColCfg<P, C>;
@@ -351,6 +406,10 @@ struct OpsImpl {
         set((const void *)k_row<P, ROW_ITER, LINES>, RC::SMEM);
         set((const void *)k_row<P, ROW_TAIL, LINES>, RC::SMEM);
         set((const void *)k_row<P, ROW_AVG, LINES>, RC::SMEM);
+        if constexpr (HERM) {
+            set((const void *)k_row_h<P, ROW_HEAD, LINES>, RC::SMEM);
+            set((const void *)k_row_h<P, ROW_AVG, LINES>, RC::SMEM);
+        }
         set((const void *)k_col<P, COL_GS_BIN, C>, CC::SMEM);
         set((const void *)k_col<P, COL_GS_LVL, C>, CC::SMEM);
         set((const void *)k_col<P, COL_HOLO_BIN, C>, CC::SMEM);
@@ -368,6 +427,16 @@ struct OpsImpl {
         return cudaSuccess;
     }
     static void row(int role, const RowArgs &a, int grid, cudaStream_t s) {
+        if constexpr (HERM) {
+            if (a.herm && role == ROW_HEAD) {
+                k_row_h<P, ROW_HEAD, LINES><<<grid, RC::THREADS, RC::SMEM, s>>>(a);
+                return;
+            }
+            if (a.herm && role == ROW_AVG) {
+                k_row_h<P, ROW_AVG, LINES><<<grid, RC::THREADS, RC::SMEM, s>>>(a);
+                return;
+            }
+        }
         switch (role) {
             case ROW_HEAD: k_row<P, ROW_HEAD, LINES><<<grid, RC::THREADS, RC::SMEM, s>>>(a); break;
             case ROW_ITER: k_row<P, ROW_ITER, LINES><<<grid, RC::THREADS, RC::SMEM, s>>>(a); break;

@@ -6,7 +6,7 @@
 
 namespace hg {
 namespace {
-LineOps o1024 = OpsImpl<Plan<1024, 32, 32, 32, 32>, 8, 16>::make();
+LineOps o1024 = OpsImpl<Plan<1024, 32, 32, 32, 32>, 8, 16, true>::make();
 PipeOps p1024a = PipeImpl<Plan<1024, 32, 32, 32, 32>, 1, 8, 2, 5, Plan<1024, 32, 32, 32, 32>, 8, 1, 3, 5,
                           256>::make("1024:r32x32e32");
 PipeOps p1024b = PipeImpl<Plan<1024, 64, 16, 16, 16, 4>, 1, 8, 2, 4, Plan<1024, 64, 16, 16, 16, 4>, 8, 1, 3,

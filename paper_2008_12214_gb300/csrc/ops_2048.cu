@@ -5,7 +5,7 @@
 
 namespace hg {
 namespace {
-LineOps o2048 = OpsImpl<Plan<2048, 64, 32, 32, 8, 8>, 4, 8>::make();
+LineOps o2048 = OpsImpl<Plan<2048, 64, 32, 32, 8, 8>, 4, 8, true>::make();
 PipeOps p2048a = PipeImpl<Plan<2048, 128, 16, 16, 16, 8>, 1, 4, 2, 4, Plan<2048, 128, 16, 16, 16, 8>, 4, 1,
                           3, 4, 256>::make("2048:r16x16x8e16");
 PipeOps p2048b = PipeImpl<Plan<2048, 64, 32, 32, 8, 8>, 1, 4, 2, 5, Plan<2048, 64, 32, 32, 8, 8>, 4, 1, 3,

@@ -4,7 +4,7 @@
 namespace hg {
 namespace {
 LineOps o256 = OpsImpl<Plan<256, 16, 16, 16, 16>, 16, 16>::make();
-LineOps o512 = OpsImpl<Plan<512, 16, 32, 32, 16>, 16, 16>::make();
+LineOps o512 = OpsImpl<Plan<512, 16, 32, 32, 16>, 16, 16, true>::make();
 PipeOps p256 = PipeImpl<Plan<256, 16, 16, 16, 16>, 2, 12, 3, 4, Plan<256, 16, 16, 16, 16>, 8, 3, 4, 4,
                          256>::make("256:r16x16e16");
 PipeOps p512a = PipeImpl<Plan<512, 16, 32, 32, 16>, 2, 8, 2, 5, Plan<512, 16, 32, 32, 16>, 8, 2, 3, 5,

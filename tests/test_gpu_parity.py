@@ -227,10 +227,16 @@ def test_replay_matches_oracle():
             assert rel_l2(I[b].cpu().numpy(), ref) <= 1e-5
 
 
-def test_ospr_matches_oracle():
-    ny, nx, batch, nsub, seed = 64, 64, 2, 6, 1234
+@pytest.mark.parametrize("ny,nsub", [(64, 6), (512, 3)])
+def test_ospr_matches_oracle(ny, nsub):
+    """At 512^2 the plan runs OSPR in Hermitian form (head writes rows ky <=
+    ny/2 of F_H with the mirror pixels' Philox phases, the column-pair pass,
+    the time average over rows ky <= ny/2 and their mirrors); at 64^2 the
+    generic passes."""
+    nx, batch, seed = ny, 2, 1234
     t = synth.targets(batch, ny, nx)
     plan = hg.Plan(ny, nx, batch, hg.HG_SLM_BINARY, 2, hg.HG_OSPR, subframes=nsub, seed=seed)
+    assert ("OSPR" in hg.hg_plan_variant(plan.h, 1)) == (ny == 512), hg.hg_plan_variant(plan.h, 1)
     holo = torch.empty((batch, nsub, ny, nx), dtype=torch.uint8, device=DEV)
     mse = torch.empty(batch, dtype=torch.float64, device=DEV)
     plan.run(torch.from_numpy(t).to(DEV), None, 1, holo, mse)
