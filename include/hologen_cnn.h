@@ -65,6 +65,12 @@ void hg_cnn_destroy(hg_cnn net);
  * also refreshes the BF16 copies the convolutions read. */
 hg_status hg_cnn_set_params(hg_cnn net, const float *params);
 hg_status hg_cnn_get_params(hg_cnn net, float *params);
+/* Training state for checkpoint / resume: `state` holds 3 x HG_CNN_NPARAMS
+ * floats (device): the parameters, then Adam's first and second moments, in
+ * the parameter order above; `step` is Adam's step count.  A net given the
+ * state of another continues its training bit for bit. */
+hg_status hg_cnn_get_state(hg_cnn net, float *state, int64_t *step);
+hg_status hg_cnn_set_state(hg_cnn net, const float *state, int64_t step);
 /* Gradient of the loss of the last hg_cnn_train_step / hg_cnn_gradients. */
 hg_status hg_cnn_get_grads(hg_cnn net, float *grads);
 

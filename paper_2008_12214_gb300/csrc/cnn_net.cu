@@ -11,6 +11,8 @@
 #include <new>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "cnn_conv.cuh"
 #include "hologen_cnn.h"
 
@@ -775,6 +777,30 @@ hg_status hg_cnn_get_params(hg_cnn n, float *params) {
     return HG_OK;
 }
 
+hg_status hg_cnn_get_state(hg_cnn n, float *state, int64_t *step) {
+    if (!n || !state || !step) return HG_ERR_INVALID_ARG;
+    CnnGuard g(n->dev);
+    const size_t b = sizeof(float) * kTab.n;
+    CN_CK(cudaMemcpyAsync(state, n->theta, b, cudaMemcpyDeviceToDevice, n->s));
+    CN_CK(cudaMemcpyAsync(state + kTab.n, n->m, b, cudaMemcpyDeviceToDevice, n->s));
+    CN_CK(cudaMemcpyAsync(state + 2 * kTab.n, n->v, b, cudaMemcpyDeviceToDevice, n->s));
+    *step = n->step;
+    return HG_OK;
+}
+
+hg_status hg_cnn_set_state(hg_cnn n, const float *state, int64_t step) {
+    if (!n || !state || step < 0) return HG_ERR_INVALID_ARG;
+    CnnGuard g(n->dev);
+    n->launches = 0;
+    const size_t b = sizeof(float) * kTab.n;
+    CN_CK(cudaMemcpyAsync(n->theta, state, b, cudaMemcpyDeviceToDevice, n->s));
+    CN_CK(cudaMemcpyAsync(n->m, state + kTab.n, b, cudaMemcpyDeviceToDevice, n->s));
+    CN_CK(cudaMemcpyAsync(n->v, state + 2 * kTab.n, b, cudaMemcpyDeviceToDevice, n->s));
+    n->step = step;
+    CN_CK(refresh_bf16(n));
+    return HG_OK;
+}
+
 hg_status hg_cnn_get_grads(hg_cnn n, float *grads) {
     if (!n || !grads) return HG_ERR_INVALID_ARG;
     CnnGuard g(n->dev);
@@ -784,6 +810,10 @@ hg_status hg_cnn_get_grads(hg_cnn n, float *grads) {
 
 hg_status hg_cnn_forward(hg_cnn n, const float *T, int B, float *cs_out, float *phase_out) {
     if (!n || !T || B < 1 || B > n->maxB) return HG_ERR_INVALID_ARG;
+    nvtxRangePushA("hg_cnn_forward");
+    struct Pop {
+        ~Pop() { nvtxRangePop(); }
+    } pop;
     CnnGuard g(n->dev);
     n->launches = 0;
     CN_CK(enqueue_forward(n, T, B));
@@ -807,6 +837,10 @@ hg_status hg_cnn_gradients(hg_cnn n, const float *T, const float *phi, int B, do
 
 hg_status hg_cnn_train_step(hg_cnn n, const float *T, const float *phi, int B, float lr, double *loss_out) {
     if (!n || !T || !phi || B < 1 || B > n->maxB || !(lr > 0.f)) return HG_ERR_INVALID_ARG;
+    nvtxRangePushA("hg_cnn_train_step");
+    struct Pop {
+        ~Pop() { nvtxRangePop(); }
+    } pop;
     CnnGuard g(n->dev);
     n->launches = 0;
     CN_CK(enqueue_forward(n, T, B));

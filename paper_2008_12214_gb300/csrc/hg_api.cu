@@ -11,11 +11,19 @@
 #include <new>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "hg_pipe.cuh"
 #include "hg_tc.cuh"
 #include "hologen.h"
 
 using namespace hg;
+
+// NVTX range around a host call (visible to Nsight tools; free without one).
+struct NvtxRange {
+    explicit NvtxRange(const char *name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+};
 
 // ------------------------------------------------------------------ kernels
 
@@ -1085,6 +1093,7 @@ int hg_pipelined(hg_plan p) { return p ? (p->prow ? 1 : 0) | (p->pcol ? 2 : 0) :
 
 hg_status hg_run(hg_plan p, const float *target, const float *init_phase, int iters,
                  uint8_t *holo_out, double *mse_out) {
+    NvtxRange nv("hg_run");
     if (!p || !target) return HG_ERR_INVALID_ARG;
     if (p->algo == HG_OSPR) {
         if (init_phase) return HG_ERR_INVALID_ARG;
@@ -1145,6 +1154,7 @@ hg_status hg_get_metrics(hg_plan p, double *out, size_t count) {
 }
 
 hg_status hg_replay(hg_plan p, const uint8_t *holo, float *intensity_out) {
+    NvtxRange nv("hg_replay");
     if (!p || !holo || !intensity_out) return HG_ERR_INVALID_ARG;
     DevGuard g(p->dev);
     p->launches = 0;
@@ -1241,6 +1251,7 @@ hg_status hg_get_weights(hg_plan p, float *w_out) {
 
 hg_status hg_debug_step(hg_plan p, const float *target, const float *phase_in, float *h_out,
                         uint8_t *holo_out, float *replay_out, double *metrics_out) {
+    NvtxRange nv("hg_debug_step");
     if (!p || !target || !phase_in || p->algo == HG_OSPR) return HG_ERR_INVALID_ARG;
     for (const void *q : {(const void *)target, (const void *)phase_in, (const void *)h_out,
                           (const void *)holo_out, (const void *)replay_out,
@@ -1346,6 +1357,7 @@ hg_status hg_group_create(hg_group *out, int nplans, const hg_plan *plans) {
 
 hg_status hg_group_run(hg_group g, const float *const *targets, const float *const *init_phases,
                        int iters, uint8_t *const *holo_out, double *const *mse_out, void *stream) {
+    NvtxRange nv("hg_group_run");
     if (!g || !targets || iters < 1) return HG_ERR_INVALID_ARG;
     DevGuard dg(g->dev);
     const void *key[4 * HG_GROUP_MAX];

@@ -106,6 +106,10 @@ def lib():
             getattr(L, name).argtypes = args
             getattr(L, name).restype = I
         L.hg_cnn_create.restype = I
+        L.hg_cnn_get_state.argtypes = [P, P, ctypes.POINTER(ctypes.c_int64)]
+        L.hg_cnn_get_state.restype = I
+        L.hg_cnn_set_state.argtypes = [P, P, ctypes.c_int64]
+        L.hg_cnn_set_state.restype = I
         L.hg_conv3x3_wgrad_workspace.argtypes = [I, I, I, I, I]
         L.hg_conv3x3_wgrad_workspace.restype = Z
         L.hg_status_string.argtypes = [I]
@@ -364,6 +368,19 @@ def hg_cnn_set_params(net, params):
 
 def hg_cnn_get_params(net, params):
     _ck(lib().hg_cnn_get_params(net, _ptr(params, torch.float32, HG_CNN_NPARAMS, "params")), "hg_cnn_get_params")
+
+
+def hg_cnn_get_state(net, state) -> int:
+    """Fills state (3 x HG_CNN_NPARAMS floats) and returns Adam's step count."""
+    st = ctypes.c_int64()
+    _ck(lib().hg_cnn_get_state(net, _ptr(state, torch.float32, 3 * HG_CNN_NPARAMS, "state"), ctypes.byref(st)),
+        "hg_cnn_get_state")
+    return st.value
+
+
+def hg_cnn_set_state(net, state, step):
+    _ck(lib().hg_cnn_set_state(net, _ptr(state, torch.float32, 3 * HG_CNN_NPARAMS, "state"), int(step)),
+        "hg_cnn_set_state")
 
 
 def hg_cnn_get_grads(net, grads):

@@ -264,3 +264,30 @@ def test_training_lowers_the_loss_on_gs_phases():
     # Adam's first steps overshoot; after them the loss must keep falling
     assert np.mean(losses[-5:]) < 0.9 * losses[0], losses
     assert np.mean(losses[-5:]) < 0.97 * np.mean(losses[10:15]), losses
+
+
+def test_checkpoint_resume_continues_training_bit_for_bit():
+    B, H, W = 2, 128, 128
+    T, phi = net_inputs(B, H, W, 600)
+    Td, Pd = torch.from_numpy(T).to(DEV), torch.from_numpy(phi).to(DEV)
+    a, b = hg.CNN(H, W, B, seed=4), hg.CNN(H, W, B, seed=5)
+    try:
+        for _ in range(2):
+            hg.hg_cnn_train_step(a.h, Td, Pd, B, 1e-3)
+        state = torch.empty(3 * hg.HG_CNN_NPARAMS, dtype=torch.float32, device=DEV)
+        step = hg.hg_cnn_get_state(a.h, state)
+        hg.hg_cnn_sync(a.h)
+        assert step == 2
+        hg.hg_cnn_train_step(a.h, Td, Pd, B, 1e-3)
+        hg.hg_cnn_set_state(b.h, state, step)
+        hg.hg_cnn_train_step(b.h, Td, Pd, B, 1e-3)
+        pa = torch.empty(hg.HG_CNN_NPARAMS, dtype=torch.float32, device=DEV)
+        pb = torch.empty_like(pa)
+        hg.hg_cnn_get_params(a.h, pa)
+        hg.hg_cnn_get_params(b.h, pb)
+        hg.hg_cnn_sync(a.h)
+        hg.hg_cnn_sync(b.h)
+    finally:
+        a.close()
+        b.close()
+    assert torch.equal(pa, pb)

@@ -546,3 +546,32 @@ def test_hermitian_binary_loop_matches_generic(n, cand, wgs):
         assert np.allclose(out[0][1], out[1][1], rtol=1e-3, atol=0), (out[0][1], out[1][1])
         assert np.mean(out[0][0] != out[1][0]) <= 2e-3, np.mean(out[0][0] != out[1][0])
     assert out[1][0].max() <= 1
+
+
+@pytest.mark.parametrize("n,pipe", [(256, 0), (1024, -1)])
+def test_gs_resumes_from_its_returned_phase(n, pipe):
+    """GS state is the replay phase: a run of k iterations, then a run started
+    from hg_get_phase, follows the uninterrupted run (the resumed run's first
+    iteration is the continuous run's iteration k)."""
+    batch, k, m = 2, 3, 3
+    t = torch.from_numpy(synth.targets(batch, n, n, 4200)).to(DEV)
+    ph = torch.from_numpy(synth.init_phases(batch, n, n, 4200)).to(DEV)
+    plan = hg.Plan(n, n, batch, pipeline=pipe)
+    full = torch.empty((batch, k + m), dtype=torch.float64, device=DEV)
+    plan.run(t, ph, k + m, None, full)
+    first = torch.empty((batch, k), dtype=torch.float64, device=DEV)
+    plan.run(t, ph, k, None, first)
+    phase = torch.empty((batch, n, n), dtype=torch.float32, device=DEV)
+    hg.hg_get_phase(plan.h, phase)
+    rest = torch.empty((batch, m), dtype=torch.float64, device=DEV)
+    plan.run(t, phase, m, None, rest)
+    plan.sync()
+    plan.close()
+    full, first, rest = full.cpu().numpy(), first.cpu().numpy(), rest.cpu().numpy()
+    # a run's last iteration is scored by the tail pass, inside a longer run by
+    # the (Hermitian) row pass: the same metrics up to rounding
+    assert np.allclose(first, full[:, :k], rtol=1e-6, atol=0)
+    # the phase passes through float radians and back: rounding-level changes,
+    # which a binary boundary pixel may amplify in later iterations
+    assert np.allclose(rest[:, 0], full[:, k], rtol=1e-4, atol=0), (rest, full)
+    assert np.allclose(rest, full[:, k:], rtol=2e-2, atol=0), (rest, full)
