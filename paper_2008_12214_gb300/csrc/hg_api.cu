@@ -966,7 +966,8 @@ hg_status hg_plan_create(hg_plan *out, int ny, int nx, int batch, hg_slm slm, hg
                     if (pk) cm = time_variant(p, rc[i], false, true);
                     else if (hm) {
                         cm = time_variant(p, col, false, false, true);
-                        if (rc[i]->col_herm) cm = fminf(cm, time_variant(p, rc[i], false, false, true, true));
+                        if (rc[i]->col_herm && rc[i]->N == ny)
+                            cm = fminf(cm, time_variant(p, rc[i], false, false, true, true));
                     }
                     ms += cm;
                     if (ms < best) best = ms, row = rc[i];
@@ -984,17 +985,39 @@ hg_status hg_plan_create(hg_plan *out, int ny, int nx, int batch, hg_slm slm, hg
         }
         if (col && make_cmap(p, col, &p->cmap)) p->pcol = col;
         if (o.pipeline == 1 && (!p->prow || !p->pcol)) return fail(HG_ERR_UNSUPPORTED_SIZE);
-        // Hermitian loop: the column-pair pass when it is at least as fast
-        if (herm_loop(p) && p->prow->col_herm && p->prow->herm_blocks_per_sm > 0 &&
-            make_cmap_box(p, p->prow->herm_c, p->prow->herm_boxr, &p->cmap_herm)) {
-            bool take = true;
-            if (o.autotune == 1) {
-                const float th = time_variant(p, p->prow, false, false, true, true);
-                const float tc = time_variant(p, p->pcol, false, false, true);
-                take = th <= tc;
+        // Hermitian loop: a column-pair pass of the column length, when it is at
+        // least as fast as the per-column pass (a forced square candidate keeps
+        // its own)
+        if (herm_loop(p)) {
+            const PipeOps *hc[8];
+            int nh = 0;
+            if (o.autotune >= 2 && p->prow->col_herm && p->prow->N == ny) {
+                if (ensure_pipe_init(p->dev, p->prow) == cudaSuccess && p->prow->herm_blocks_per_sm > 0)
+                    hc[nh++] = p->prow;
+            } else {
+                const PipeOps *all[8];
+                const int k = pipe_candidates(ny, all, 8);
+                for (int i = 0; i < k; ++i)
+                    if (all[i]->col_herm && ensure_pipe_init(p->dev, all[i]) == cudaSuccess &&
+                        all[i]->herm_blocks_per_sm > 0)
+                        hc[nh++] = all[i];
             }
-            p->use_herm_col = take;
-            if (take) p->hops = p->prow;
+            const PipeOps *best = nullptr;
+            float best_ms = 1e30f;
+            for (int i = 0; i < nh; ++i) {
+                CUtensorMap m;
+                if (!make_cmap_box(p, hc[i]->herm_c, hc[i]->herm_boxr, &m)) continue;
+                const float ms = (o.autotune == 1 && nh > 0) ? time_variant(p, hc[i], false, false, true, true) : 0.f;
+                if (!best || ms < best_ms) best = hc[i], best_ms = ms;
+            }
+            if (best) {
+                bool take = true;
+                if (o.autotune == 1) take = best_ms <= time_variant(p, p->pcol, false, false, true);
+                if (take && make_cmap_box(p, best->herm_c, best->herm_boxr, &p->cmap_herm)) {
+                    p->use_herm_col = true;
+                    p->hops = best;
+                }
+            }
         }
         // Binary OSPR: one pass per subframe in Hermitian form with the column-pair
         // pass of any paired variant of this column length (square power-of-two fields)

@@ -31,6 +31,13 @@ struct PipeArgs {
     int drop_job;                  // fault-injection hook: this job is never issued (-1: none)
 };
 
+// Index of the mirror sample (N - x) mod N, for any line length N.
+template <int N>
+__device__ __forceinline__ int mirror_idx(int x) {
+    if constexpr ((N & (N - 1)) == 0) return (N - x) & (N - 1);
+    else return x ? N - x : 0;
+}
+
 // ------------------------------------------------------------ PTX helpers
 
 __device__ __forceinline__ uint32_t smem_addr(const void *p) {
@@ -349,7 +356,7 @@ __device__ __forceinline__ void herm_constrain(float2 (&w)[P::E], const float *s
     static_for<0, P::E>([&](auto ec) {
         constexpr int e = decltype(ec)::value;
         const int x = t + P::TL * e;
-        const int xm = (P::N - x) & (P::N - 1);
+        const int xm = mirror_idx<P::N>(x);
         const float Tv = sT[x], Tm = sTm[xm];
         const float2 r = w[e];
         const float m2 = fmaf(r.x, r.x, r.y * r.y);
@@ -401,7 +408,6 @@ __global__ void __launch_bounds__(PairPipeCfg<P, NG, D, SWZ>::THREADS, 1)
     using Cfg = PairPipeCfg<P, NG, D, SWZ>;
     using LAY = Swz<SWZ>;
     constexpr int TL = P::TL, E = P::E, NX = P::N, GT = Cfg::GT;
-    static_assert((NX & (NX - 1)) == 0, "paired rows use a power-of-two row length");
     extern __shared__ unsigned char smraw[];
     unsigned char *base = smraw + ((1024 - (smem_addr(smraw) & 1023)) & 1023);
     double *red = reinterpret_cast<double *>(base + (size_t)NG * D * Cfg::SLOT);
@@ -517,7 +523,7 @@ __global__ void __launch_bounds__(PairPipeCfg<P, NG, D, SWZ>::THREADS, 1)
             float2 vb[E];
             static_for<0, E>([&](auto ec) {
                 constexpr int e = decltype(ec)::value;
-                const float2 q = sf[(NX - (t + TL * e)) & (NX - 1)];
+                const float2 q = sf[mirror_idx<NX>(t + TL * e)];
                 vb[e] = make_float2(q.x, -q.y);
             });
             pair_constrain<P>(vb, sTa + NX, a.w ? a.w + ((size_t)item * ny + ny - pan) * NX : nullptr, a,
@@ -818,7 +824,7 @@ __global__ void __launch_bounds__(ColHermCfg<P, C, D, SWZ, BOXR>::THREADS, 1)
         static_for<0, E>([&](auto ec) {
             constexpr int e = decltype(ec)::value;
             const int kk = t + TL * e;
-            const float2 z = v[e], zm = sl[((NY - kk) & (NY - 1)) * CP + cp];
+            const float2 z = v[e], zm = sl[mirror_idx<NY>(kk) * CP + cp];
             if (act && (!a.half || kk <= HY))
                 fw[(size_t)kk * nx / 2] = make_float4(0.5f * (z.x + zm.x), 0.5f * (z.y - zm.y),
                                                      0.5f * (z.y + zm.y), 0.5f * (zm.x - z.x));
@@ -963,7 +969,7 @@ __global__ void __launch_bounds__(ColPackCfg<P, PB, C, NG, D, SWZ, SWZB, BOXR>::
             const int kk = tb + TLB * e;
             if (kk <= NY / 2) {
                 const float2 z = w[e];
-                const float2 zm = sl[((NY - kk) & (NY - 1)) * CP + cp];  // Z[N - k]
+                const float2 zm = sl[mirror_idx<NY>(kk) * CP + cp];  // Z[N - k]
                 // A = (Z + conj(Zm)) / 2, B = (Z - conj(Zm)) / (2i)
                 const float2 A = make_float2(0.5f * (z.x + zm.x), 0.5f * (z.y - zm.y));
                 const float2 B = make_float2(0.5f * (z.y + zm.y), -0.5f * (z.x - zm.x));
@@ -1173,6 +1179,33 @@ struct PairedOps {
         o.row_smem = PAIR::RC::SMEM;
         o.row_iter = &PAIR::row_iter;
         o.col_pack = PACK::launch;
+        o.col_herm = HERM::launch;
+        o.herm_c = HERM::COLS;
+        o.herm_boxr = HERM::BOX_ROWS;
+        o.init = &init;
+        return o;
+    }
+};
+
+// A column variant that also offers the column-pair pass of the Hermitian
+// binary loop for its column length (lengths without a paired row pass).
+template <const PipeOps *BASE, class HERM>
+struct WithHerm {
+    static cudaError_t init(PipeOps *self) {
+        cudaError_t e = BASE->init(const_cast<PipeOps *>(BASE));
+        if (e != cudaSuccess) return e;
+        int hb = 0;
+        e = HERM::init(&hb);
+        if (e != cudaSuccess) return e;
+        self->row_blocks_per_sm = BASE->row_blocks_per_sm;
+        self->col_blocks_per_sm = BASE->col_blocks_per_sm;
+        self->herm_blocks_per_sm = hb;
+        if (hb < 1) self->col_herm = nullptr;
+        return cudaSuccess;
+    }
+    static PipeOps make(const char *name) {
+        PipeOps o = *BASE;
+        o.name = name;
         o.col_herm = HERM::launch;
         o.herm_c = HERM::COLS;
         o.herm_boxr = HERM::BOX_ROWS;

@@ -1,12 +1,21 @@
 // Transform plans for the 1080 x 1920 display format (radix 2/3/5):
 // 1080 = 30 x 6 x 6 (36 threads per line), 1920 = 30 x 8 x 8 (64 threads per
-// line; its last stage returns through shared memory).
+// line; its last stage returns through shared memory).  TMA-fed variants:
+// 1080-sample columns (8 per CTA, 288 threads, boxes of 180 rows) with their
+// column-pair pass (16 columns), 1920-sample columns (4 per CTA, boxes of 240
+// rows), and the paired row pass on 1920-sample rows.
 #include "hg_pipe.cuh"
 
 namespace hg {
 namespace {
-LineOps o1080 = OpsImpl<Plan<1080, 36, 30, 30, 6, 6>, 8, 16>::make();
-LineOps o1920 = OpsImpl<Plan<1920, 64, 30, 30, 8, 8>, 4, 8>::make();
+using P1080 = Plan<1080, 36, 30, 30, 6, 6>;
+using P1920 = Plan<1920, 64, 30, 30, 8, 8>;
+LineOps o1080 = OpsImpl<P1080, 8, 16>::make();
+LineOps o1920 = OpsImpl<P1920, 4, 8>::make();
+PipeOps p1080c = PipeImpl<P1080, 0, 1, 1, 3, P1080, 8, 1, 3, 3, 180>::make("1080:c30x6x6");
+PipeOps p1080h = WithHerm<&p1080c, HermImpl<P1080, 16, 3, 3, 180>>::make("1080:c30x6x6");
+PipeOps p1920c = PipeImpl<P1920, 0, 1, 1, 4, P1920, 4, 1, 3, 4, 240>::make("1920:c30x8x8");
+PipeOps p1920p = PairedOps<PairImpl<P1920, 3, 2, 4>, &p1920c>::make("1920:pair30x8x8+c30x8x8");
 }  // namespace
 
 const LineOps *ops_hd(int n) {
@@ -17,6 +26,13 @@ const LineOps *ops_hd(int n) {
     }
 }
 
-// The display-format lengths use the generic passes only.
-int pipe_ops_hd(int, const PipeOps **, int) { return 0; }
+int pipe_ops_hd(int n, const PipeOps **out, int max) {
+    int k = 0;
+    if (n == 1080 && k < max) out[k++] = &p1080h;
+    if (n == 1920) {
+        if (k < max) out[k++] = &p1920c;
+        if (k < max) out[k++] = &p1920p;
+    }
+    return k;
+}
 }  // namespace hg

@@ -511,7 +511,8 @@ def test_tensor_core_row_pass_precision(prec, tol):
 
 
 @pytest.mark.parametrize("n,cand,wgs", [(1024, 2, False), (1024, 3, False), (1024, 5, False), (1024, 2, True),
-                                        (512, 2, False), (512, 3, False), (2048, 2, False), (2048, 3, False)])
+                                        (512, 2, False), (512, 3, False), (2048, 2, False), (2048, 3, False),
+                                        ((1080, 1920), 0, False)])
 def test_hermitian_binary_loop_matches_generic(n, cand, wgs):
     """Binary GS in Hermitian form (paired rows write only the Hermitian part
     of F, rows ky <= ny/2; the column passes read those rows back, two columns
@@ -522,15 +523,16 @@ def test_hermitian_binary_loop_matches_generic(n, cand, wgs):
     iterations in at most 0.2% of pixels, MSE to 1e-3.  Weighted GS runs two
     iterations only: its literal weight rule makes whole trajectories part
     ways after a few iterations even between FP32 and FP64."""
-    batch = 1 if n == 2048 else 2
+    ny, nx = n if isinstance(n, tuple) else (n, n)
+    batch = 1 if ny * nx >= 2048 * 1024 else 2
     iters = 2 if wgs else 3
     algo = hg.HG_WGS if wgs else hg.HG_GS
-    t = torch.from_numpy(synth.targets(batch, n, n, 4100)).to(DEV)
-    ph = torch.from_numpy(synth.init_phases(batch, n, n, 4100)).to(DEV)
+    t = torch.from_numpy(synth.targets(batch, ny, nx, 4100)).to(DEV)
+    ph = torch.from_numpy(synth.init_phases(batch, ny, nx, 4100)).to(DEV)
     out = {}
     for pipe, tune in ((0, 0), (1, 2 + cand)):
-        plan = hg.Plan(n, n, batch, hg.HG_SLM_BINARY, 2, algo, pipeline=pipe, autotune=tune)
-        holo = torch.empty((batch, n, n), dtype=torch.uint8, device=DEV)
+        plan = hg.Plan(ny, nx, batch, hg.HG_SLM_BINARY, 2, algo, pipeline=pipe, autotune=tune)
+        holo = torch.empty((batch, ny, nx), dtype=torch.uint8, device=DEV)
         mse = torch.empty((batch, iters), dtype=torch.float64, device=DEV)
         plan.run(t, ph, iters, holo, mse)
         plan.sync()
@@ -539,7 +541,7 @@ def test_hermitian_binary_loop_matches_generic(n, cand, wgs):
         plan.close()
     assert "+herm" in out[1][2] and "+herm-colpairs" in out[1][3], out[1][2:]
     assert np.allclose(out[0][1][:, 0], out[1][1][:, 0], rtol=1e-5, atol=0)
-    if n == 2048:  # different radix plans on the two paths (16x16x8 vs 32x8x8): a few boundary flips spread
+    if ny == 2048:  # different radix plans on the two paths (16x16x8 vs 32x8x8): a few boundary flips spread
         assert np.allclose(out[0][1], out[1][1], rtol=2e-2, atol=0), (out[0][1], out[1][1])
         assert np.mean(out[0][0] != out[1][0]) <= 2e-2, np.mean(out[0][0] != out[1][0])
     else:
