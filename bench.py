@@ -288,7 +288,7 @@ def run_side_workload(args):
         T = torch.from_numpy(synth.targets(B, n, n, 5000)).to(dev)
         P = torch.from_numpy(synth.init_phases(B, n, n, 5000)).to(dev)
         mse = torch.empty((B, args.iters), dtype=torch.float64, device=dev)
-        plan = hg.Plan(n, n, B, hg.HG_SLM_BINARY, 2, hg.HG_GS)
+        plan = hg.Plan(n, n, B, hg.HG_SLM_BINARY, 2, hg.HG_GS, precision=args.precision)
         for _ in range(args.warmup):
             plan.run(T, P, args.iters, None, mse)
         plan.sync()
@@ -300,7 +300,8 @@ def run_side_workload(args):
         ms = e0.elapsed_time(e1) / args.steps
         px = B * n * n
         it_ms = ms / args.iters
-        out = dict(workload="gs_binary_2048x2048_batch16", ms_per_step=ms, iters_per_step=args.iters,
+        out = dict(workload="gs_binary_2048x2048_batch16", precision=args.precision, ms_per_step=ms,
+                   iters_per_step=args.iters, final_mse_mean=float(mse[:, -1].mean().item()),
                    batched_iterations_per_s=1e3 / it_ms, gbs_at_36=36.0 * px / (it_ms / 1e3) / 1e9,
                    row_variant=hg.hg_plan_variant(plan.h, 0), column_variant=hg.hg_plan_variant(plan.h, 1))
         plan.close()

@@ -76,8 +76,10 @@ typedef struct {
                           radix-32 DFT stages as tensor-core GEMMs (tcgen05, FP32
                           accumulation) with 1 FP16 hi+lo split operands, 2 FP16,
                           3 BF16 hi+lo, 4 BF16 (the 16-bit builds of Section 4.5);
-                          rows of 1024 samples only (else
-                          HG_ERR_UNSUPPORTED_SIZE), not OSPR */
+                          rows of 1024 or 2048 samples (2048 = a radix-2 step
+                          over two 1024-point halves) and ny a multiple of 4
+                          (1024) or 2 (2048), else HG_ERR_UNSUPPORTED_SIZE;
+                          not OSPR */
     int use_graph;     /* 1 = replay the iteration loop as a CUDA graph (default) */
     int pipeline;      /* -1 auto (default): TMA-fed passes where the size allows;
                           0: generic passes only; 1: require TMA-fed passes */

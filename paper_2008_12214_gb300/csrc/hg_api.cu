@@ -817,7 +817,8 @@ hg_status hg_plan_create(hg_plan *out, int ny, int nx, int batch, hg_slm slm, hg
     if (slm.kind == HG_SLM_LLEVEL && (slm.levels < 2 || slm.levels > 256)) return HG_ERR_INVALID_ARG;
     if (algo == HG_OSPR && (slm.kind != HG_SLM_BINARY || o.subframes < 1)) return HG_ERR_INVALID_ARG;
     if (o.precision < 0 || o.precision > 4) return HG_ERR_INVALID_ARG;
-    if (o.precision > 0 && (nx != TC_N || ny % 4 != 0 || algo == HG_OSPR)) return HG_ERR_UNSUPPORTED_SIZE;
+    if (o.precision > 0 && ((nx != 1024 && nx != 2048) || ny % (nx == 1024 ? 4 : 2) != 0 || algo == HG_OSPR))
+        return HG_ERR_UNSUPPORTED_SIZE;
     const LineOps *rops = find_ops(nx), *cops = find_ops(ny);
     if (!rops || !cops) return HG_ERR_UNSUPPORTED_SIZE;
     const size_t npx = (size_t)ny * nx;
@@ -885,7 +886,7 @@ hg_status hg_plan_create(hg_plan *out, int ny, int nx, int batch, hg_slm slm, hg
     }
     if (o.precision > 0) {  // tensor-core row pass: DFT-32 operands, per-device attributes
         p->tc_prec = o.precision;
-        p->ppt_tc = ny / 4;
+        p->ppt_tc = ny / (nx == 1024 ? 4 : 2);  // CTA panels: 4 rows of 1024 or 2 rows of 2048
         if (p->ppt_tc > p->ppt_max) p->ppt_max = p->ppt_tc;
         ce = ensure_tc_init(p->dev, &p->tc_blocks);
         uint16_t *hb = (uint16_t *)malloc(4 * TC_B);
@@ -1099,9 +1100,11 @@ const char *hg_plan_variant(hg_plan p, int pass) {
         return p->vname[1];
     }
     if (pass == 0 && p->tc_prec) {
-        static const char *names[] = {"", "1024:tc32x32-fp16hilo", "1024:tc32x32-fp16", "1024:tc32x32-bf16hilo",
-                                      "1024:tc32x32-bf16"};
-        return names[p->tc_prec];
+        static const char *names[2][5] = {
+            {"", "1024:tc32x32-fp16hilo", "1024:tc32x32-fp16", "1024:tc32x32-bf16hilo", "1024:tc32x32-bf16"},
+            {"", "2048:2x(tc32x32)-fp16hilo", "2048:2x(tc32x32)-fp16", "2048:2x(tc32x32)-bf16hilo",
+             "2048:2x(tc32x32)-bf16"}};
+        return names[p->nx == 2048][p->tc_prec];
     }
     const PipeOps *o = pass == 0 ? p->prow : p->pcol;
     if (o && herm_loop(p)) {  // Hermitian form of the binary loop

@@ -182,10 +182,11 @@ __device__ __forceinline__ bool tc_wait(TcCtx &c, unsigned long long limit, unsi
     return *c.flag != 0;
 }
 
-// Forward (DIR = -1) or inverse (+1) 1024-point transform of the 4 rows held
-// by the CTA (warp r holds row r, thread `lane` samples lane + 32 e on entry
-// and on exit), unnormalised like the CUDA-core engine.
-template <int PREC, int DIR>
+// Forward (DIR = -1) or inverse (+1) 1024-point transform of the 4 lines held
+// by the CTA (warp r holds line r, thread `lane` samples lane + 32 e on entry
+// and on exit), unnormalised like the CUDA-core engine.  tw holds the roots of
+// order 1024 * TWS (W_1024^j = tw[TWS j]).
+template <int PREC, int DIR, int TWS = 1>
 __device__ __forceinline__ void tc_fft(float2 (&v)[32], TcCtx &c, const float2 *__restrict__ tw,
                                        const TcArgs &ta) {
     using PR = TcPrec<PREC>;
@@ -229,7 +230,7 @@ __device__ __forceinline__ void tc_fft(float2 (&v)[32], TcCtx &c, const float2 *
 #pragma unroll
     for (int k2 = 0; k2 < 32; ++k2) {
         float2 y = make_float2(d[2 * k2] * inv0, d[2 * k2 + 1] * inv0);
-        if (k2) y = cmul_root<DIR>(y, __ldg(tw + lane * k2));  // W_1024^{n1 k2}
+        if (k2) y = cmul_root<DIR>(y, __ldg(tw + TWS * lane * k2));  // W_1024^{n1 k2}
         v[k2] = y;
     }
     // ---- stage 1: vector (warp, k2), DFT over n1 = lane; operand written MN-major
@@ -270,11 +271,46 @@ __device__ __forceinline__ void tc_fft(float2 (&v)[32], TcCtx &c, const float2 *
     tc_fence_before();  // the next stage's MMA overwrites tensor memory after a barrier
 }
 
-// Row pass on tensor cores for 1024-sample rows: ROW_ITER (forward transform,
-// metrics, constraint and weight update, inverse transform) or ROW_TAIL
-// (forward transform, metrics, replay field / phase / weights).
-template <int PREC, int ROLE>
+// Radix-2 step between the two 1024-point halves of 2048-point rows: the CTA
+// holds rows as (even, odd) sample warps 2r, 2r+1, and xbuf (4 x 1024 float2,
+// reused operand memory) carries each warp's values to its partner.
+//   forward (after the halves' FFTs E, O): X[k] = E + W^k O, X[k+1024] = E - W^k O
+//     (the even warp keeps k < 1024, the odd warp k >= 1024);
+//   inverse (before the halves' IFFTs): E = X[k] + X[k+1024],
+//     O = (X[k] - X[k+1024]) W^{-k}, W = exp(-2 pi i / 2048).
+template <int DIR>
+__device__ __forceinline__ void tc_radix2(float2 (&v)[32], float2 *xbuf, const float2 *__restrict__ tw) {
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31, odd = warp & 1;
+    if (DIR < 0 && odd) {
+#pragma unroll
+        for (int e = 0; e < 32; ++e) v[e] = cmul_root<-1>(v[e], __ldg(tw + lane + 32 * e));
+    }
+    __syncthreads();
+#pragma unroll
+    for (int e = 0; e < 32; ++e) xbuf[warp * 1024 + lane + 32 * e] = v[e];
+    __syncthreads();
+#pragma unroll
+    for (int e = 0; e < 32; ++e) {
+        const int k = lane + 32 * e;
+        const float2 o = xbuf[(warp ^ 1) * 1024 + k];
+        if (DIR < 0) {
+            v[e] = odd ? make_float2(o.x - v[e].x, o.y - v[e].y) : make_float2(v[e].x + o.x, v[e].y + o.y);
+        } else {
+            v[e] = odd ? cmul_root<+1>(make_float2(o.x - v[e].x, o.y - v[e].y), __ldg(tw + k))
+                       : make_float2(v[e].x + o.x, v[e].y + o.y);
+        }
+    }
+    __syncthreads();
+}
+
+// Row pass on tensor cores for 1024- or 2048-sample rows: ROW_ITER (forward
+// transform, metrics, constraint and weight update, inverse transform) or
+// ROW_TAIL (forward transform, metrics, replay field / phase / weights).  A
+// CTA holds 4 rows of 1024 (warp = row), or 2 rows of 2048 as their even and
+// odd samples (warps 2r, 2r+1) joined by tc_radix2.
+template <int PREC, int ROLE, int NX>
 __global__ void __launch_bounds__(128, 1) k_row_tc(const RowArgs a, const TcArgs ta) {
+    static_assert(NX == 1024 || NX == 2048, "tensor-core rows are 1024 or 2048 samples");
     extern __shared__ unsigned char smraw[];
     unsigned char *sm = smraw + ((1024 - (smem_addr(smraw) & 1023)) & 1023);
     uint64_t *bar = reinterpret_cast<uint64_t *>(sm + 4 * TC_B + 2 * TC_A0 + 2 * TC_A1);
@@ -282,7 +318,10 @@ __global__ void __launch_bounds__(128, 1) k_row_tc(const RowArgs a, const TcArgs
     volatile int *flag = reinterpret_cast<volatile int *>(tslot + 1);
     double *red = reinterpret_cast<double *>(bar + 2);  // [4 warps][NMET]
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    constexpr int NX = TC_N;
+    constexpr int RPC = NX == 1024 ? 4 : 2;     // rows per CTA panel
+    constexpr int TWS = NX / 1024;              // twiddle stride
+    const int half = NX == 2048 ? (warp & 1) : 0;  // 2048: even / odd samples of a row
+    float2 *xbuf = reinterpret_cast<float2 *>(sm + 4 * TC_B);  // operand memory, free between transforms
 
     for (int i = tid; i < 4 * TC_B / 16; i += 128) reinterpret_cast<uint4 *>(sm)[i] = ta.bmats[i];
     if (tid == 0) {
@@ -299,24 +338,25 @@ __global__ void __launch_bounds__(128, 1) k_row_tc(const RowArgs a, const TcArgs
     TcCtx c{sm, bar, flag, *tslot, 0u, true};
 
     const int ny = a.ny;
-    const int ppt = ny / 4;  // 4-row panels
+    const int ppt = ny / RPC;
     const int J = a.items * ppt;
     for (int p = blockIdx.x; p < J && c.ok; p += gridDim.x) {
         const int item = p / ppt, pan = p - item * ppt;
-        const int y = pan * 4 + warp;
+        const int y = pan * RPC + (NX == 1024 ? warp : warp >> 1);
         const int iy = (y + ny / 2) % ny;
         const float2 *fr = a.field + ((size_t)item * ny + y) * NX;
         float2 v[32];
 #pragma unroll
-        for (int e = 0; e < 32; ++e) v[e] = fr[lane + 32 * e];
-        tc_fft<PREC, -1>(v, c, a.tw, ta);
+        for (int e = 0; e < 32; ++e) v[e] = fr[TWS * (lane + 32 * e) + half];
+        tc_fft<PREC, -1, TWS>(v, c, a.tw, ta);
         if (!c.ok) break;
+        if constexpr (NX == 2048) tc_radix2<-1>(v, xbuf, a.tw);
         const float *Tr = a.T + ((size_t)item * ny + y) * NX;
         float *wr = a.w ? a.w + ((size_t)item * ny + y) * NX : nullptr;
         float acc0 = 0.f, acc1 = 0.f, acc2 = 0.f, acc3 = 0.f;
 #pragma unroll
         for (int e = 0; e < 32; ++e) {
-            const int x = lane + 32 * e;
+            const int x = half * 1024 + lane + 32 * e;
             const float Tv = Tr[x];
             const float2 r = v[e];
             const float m2 = fmaf(r.x, r.x, r.y * r.y);
@@ -346,11 +386,12 @@ __global__ void __launch_bounds__(128, 1) k_row_tc(const RowArgs a, const TcArgs
             }
         }
         if constexpr (ROLE == ROW_ITER) {
-            tc_fft<PREC, +1>(v, c, a.tw, ta);
+            if constexpr (NX == 2048) tc_radix2<+1>(v, xbuf, a.tw);
+            tc_fft<PREC, +1, TWS>(v, c, a.tw, ta);
             if (!c.ok) break;
             float2 *fw = a.field + ((size_t)item * ny + y) * NX;
 #pragma unroll
-            for (int e = 0; e < 32; ++e) fw[lane + 32 * e] = v[e];
+            for (int e = 0; e < 32; ++e) fw[TWS * (lane + 32 * e) + half] = v[e];
         }
         if (a.part) {  // per-panel partial sums: warps in fixed order
             float dm[NMET] = {acc0, acc1, acc2, acc3};

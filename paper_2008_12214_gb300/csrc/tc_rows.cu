@@ -1,5 +1,5 @@
-// Tensor-core row pass (1024-sample rows): instantiations, launchers and the
-// DFT-32 operand matrices.
+// Tensor-core row pass (1024- and 2048-sample rows): instantiations,
+// launchers and the DFT-32 operand matrices.
 #include <cmath>
 
 #include "hg_pipe.cuh"
@@ -8,20 +8,31 @@
 namespace hg {
 
 namespace {
-template <int PREC>
-cudaError_t set_attr() {
-    cudaError_t e = cudaFuncSetAttribute((const void *)k_row_tc<PREC, ROW_ITER>,
+template <int PREC, int NX>
+cudaError_t set_attr_n() {
+    cudaError_t e = cudaFuncSetAttribute((const void *)k_row_tc<PREC, ROW_ITER, NX>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, TC_SMEM);
     if (e == cudaSuccess)
-        e = cudaFuncSetAttribute((const void *)k_row_tc<PREC, ROW_TAIL>,
+        e = cudaFuncSetAttribute((const void *)k_row_tc<PREC, ROW_TAIL, NX>,
                                  cudaFuncAttributeMaxDynamicSharedMemorySize, TC_SMEM);
+    return e;
+}
+template <int PREC>
+cudaError_t set_attr() {
+    cudaError_t e = set_attr_n<PREC, 1024>();
+    if (e == cudaSuccess) e = set_attr_n<PREC, 2048>();
     return e;
 }
 
 template <int PREC>
 void launch(int role, const RowArgs &a, const TcArgs &ta, int grid, cudaStream_t s) {
-    if (role == ROW_ITER) k_row_tc<PREC, ROW_ITER><<<grid, 128, TC_SMEM, s>>>(a, ta);
-    else k_row_tc<PREC, ROW_TAIL><<<grid, 128, TC_SMEM, s>>>(a, ta);
+    if (a.nx == 2048) {
+        if (role == ROW_ITER) k_row_tc<PREC, ROW_ITER, 2048><<<grid, 128, TC_SMEM, s>>>(a, ta);
+        else k_row_tc<PREC, ROW_TAIL, 2048><<<grid, 128, TC_SMEM, s>>>(a, ta);
+    } else {
+        if (role == ROW_ITER) k_row_tc<PREC, ROW_ITER, 1024><<<grid, 128, TC_SMEM, s>>>(a, ta);
+        else k_row_tc<PREC, ROW_TAIL, 1024><<<grid, 128, TC_SMEM, s>>>(a, ta);
+    }
 }
 
 uint16_t bits_of(float x, int prec, float *back) {
@@ -42,7 +53,7 @@ cudaError_t tc_init(int *blocks_per_sm) {
     if (e == cudaSuccess) e = set_attr<3>();
     if (e == cudaSuccess) e = set_attr<4>();
     if (e == cudaSuccess)
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k_row_tc<1, ROW_ITER>, 128, TC_SMEM);
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k_row_tc<1, ROW_ITER, 1024>, 128, TC_SMEM);
     return e;
 }
 

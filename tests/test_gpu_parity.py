@@ -470,19 +470,21 @@ def test_group_mixed_sizes_one_graph():
         p.close()
 
 
-@pytest.mark.parametrize("prec,tol", [(1, 1e-5), (2, 3e-3), (3, 1e-5), (4, 3e-3)])
-def test_tensor_core_row_pass_precision(prec, tol):
+@pytest.mark.parametrize("n,prec,tol", [(1024, 1, 1e-5), (1024, 2, 3e-3), (1024, 3, 1e-5), (1024, 4, 3e-3),
+                                        (2048, 1, 1e-5), (2048, 2, 3e-3), (2048, 3, 1e-5), (2048, 4, 3e-3)])
+def test_tensor_core_row_pass_precision(n, prec, tol):
     """Row-pass DFT stages as tcgen05 GEMMs (1 FP16 hi+lo, 2 FP16, 3 BF16
     hi+lo, 4 BF16): the replay field the tensor-core pass computes from the
     GPU's hologram, against the oracle's replay of that hologram (single-step
-    relative L2), and a 6-iteration run's final MSE against the FP32 engine."""
-    n, batch = 1024, 2
+    relative L2), and a 6-iteration run's final MSE against the FP32 engine.
+    2048-sample rows run as two 1024-point halves joined by a radix-2 step."""
+    batch = 2 if n == 1024 else 1
     t = synth.targets(batch, n, n)
     ph = synth.init_phases(batch, n, n)
     T = torch.from_numpy(t).to(DEV)
     P = torch.from_numpy(ph).to(DEV)
     plan = hg.Plan(n, n, batch, precision=prec)
-    assert "tc32x32" in hg.hg_plan_variant(plan.h, 0)
+    assert "tc32x32" in hg.hg_plan_variant(plan.h, 0) and hg.hg_plan_variant(plan.h, 0).startswith(str(n))
     holo = torch.empty((batch, n, n), dtype=torch.uint8, device=DEV)
     R_out = torch.empty((batch, n, n), dtype=torch.complex64, device=DEV)
     met = torch.empty((batch, 4), dtype=torch.float64, device=DEV)
@@ -505,7 +507,7 @@ def test_tensor_core_row_pass_precision(prec, tol):
         mref = oracle.metrics(np.abs(Rref) ** 2, oracle.prepare_target(t[b]))
         assert abs(met[b, 0] - mref[0]) <= max(10 * tol, 1e-4) * mref[0]
     d = np.abs(mse.cpu().numpy()[:, -1] - mse32.cpu().numpy()[:, -1]) / mse32.cpu().numpy()[:, -1]
-    print("precision %d: single-step rel-L2 %s, final-MSE delta vs FP32 %s" % (prec, errs, d))
+    print("n %d precision %d: single-step rel-L2 %s, final-MSE delta vs FP32 %s" % (n, prec, errs, d))
     assert max(errs) <= tol
     assert np.all(d < 0.05)
 
