@@ -63,7 +63,8 @@ def parse():
     ap.add_argument("--quick", action="store_true", help="skip the e2e and CPU-baseline legs")
     ap.add_argument("--pairs", type=int, default=2048, help="warmstart: training pairs")
     ap.add_argument("--heldout", type=int, default=64, help="warmstart: held-out targets")
-    ap.add_argument("--workload", choices=["headline", "ospr", "mixed", "warmstart", "gs2048"], default="headline",
+    ap.add_argument("--workload", choices=["headline", "ospr", "mixed", "warmstart", "gs2048", "wgs256"],
+                    default="headline",
                     help="headline: binary GS 1024^2 x 64 (the benchmark line); ospr: 8 targets x 24 "
                          "subframes of 1024^2; mixed: 16 targets each of 512^2, 1024^2, 2048^2, 1080x1920")
     return ap.parse_args()
@@ -283,6 +284,29 @@ def run_side_workload(args):
         plan.close()
     elif args.workload == "warmstart":
         out = run_warmstart(args, dev, s0)
+    elif args.workload == "wgs256":
+        # weighted GS, one 1024^2 target, 256-level SLM, 100 iterations
+        n, iters = 1024, 100
+        T = torch.from_numpy(synth.targets(1, n, n, 6000)).to(dev)
+        P = torch.from_numpy(synth.init_phases(1, n, n, 6000)).to(dev)
+        mse = torch.empty((1, iters), dtype=torch.float64, device=dev)
+        holo = torch.empty((1, n, n), dtype=torch.uint8, device=dev)
+        plan = hg.Plan(n, n, 1, hg.HG_SLM_LLEVEL, 256, hg.HG_WGS)
+        for _ in range(args.warmup):
+            plan.run(T, P, iters, holo, mse)
+        plan.sync()
+        e0.record(s0)
+        for _ in range(args.steps):
+            plan.run(T, P, iters, holo, mse)
+        e1.record(s0)
+        plan.sync()
+        ms = e0.elapsed_time(e1) / args.steps
+        met = plan.metrics().cpu().numpy()[0]
+        out = dict(workload="wgs_llevel256_1024x1024_batch1", ms_per_run=ms, iterations_per_s=iters / (ms / 1e3),
+                   final_mse=float(met[-1, 0]), final_amplitude_mse=float(met[-1, 1]),
+                   diffraction_efficiency=float(met[-1, 2]), mse_iter_1_10_100=[float(met[i, 0]) for i in (0, 9, 99)],
+                   row_variant=hg.hg_plan_variant(plan.h, 0), column_variant=hg.hg_plan_variant(plan.h, 1))
+        plan.close()
     elif args.workload == "gs2048":
         B, n = 16, 2048
         T = torch.from_numpy(synth.targets(B, n, n, 5000)).to(dev)

@@ -7,10 +7,12 @@ It shares no code with the CUDA path.  The arithmetic lives in
 with gcc on first use and wraps it with ctypes, returning numpy arrays.
 
 Every function cites the passage of arXiv:2008.12214 (HoloGen) it follows in
-the C source's header.  Parity status: the FFT, quantiser, GS step, replay and
-Philox are pinned by ``tests/test_oracle.py``; the exact WGS trajectory and the
-OSPR mean intensity are "parity unpinned" beyond the qualitative checks listed
-there.
+the C source's header (adaptive OSPR, whose feedback the paper does not spell
+out, is a reading written here from the C steps).  Parity status: the FFT,
+quantiser, GS step, replay and Philox are pinned by ``tests/test_oracle.py``;
+the exact WGS trajectory, the OSPR mean intensity and the adaptive-OSPR
+sequence beyond its first subframe are "parity unpinned" beyond the
+qualitative and structural checks listed there.
 """
 from __future__ import annotations
 
@@ -201,6 +203,37 @@ def ospr_run(t_raw, nsub, seed, t_index=0):
     _ck(_load().or_ospr_run(ny, nx, _p(t), int(nsub), int(seed), int(t_index), _p(holo), _p(I_out),
                             _p(met)))
     return dict(holo=holo, I=I_out, mse=met[0], amp_mse=met[1], eff=met[2])
+
+
+def adaptive_target(T, I_prev_sum, n):
+    """Target amplitude of adaptive-OSPR subframe n (1-based).  The paper
+    (Section 3.4) states only that adaptive OSPR feeds the cumulative error
+    back into later subframes; the reading here: after n - 1 subframes whose
+    energy-normalised intensities sum to I_prev_sum, subframe n aims at the
+    deficit n T^2 - I_prev_sum (T normalised to sum T^2 = 1), clipped at
+    zero, so T_n = sqrt(max(n T^2 - I_prev_sum, 0)), normalised to sum 1.
+    Subframe 1 is plain OSPR's first subframe."""
+    D = np.maximum(n * T * T - I_prev_sum, 0.0)
+    s = D.sum()
+    return np.sqrt(D / s) if s > 0 else T.copy()
+
+
+def adaptive_ospr_run(t_raw, nsub, seed, t_index=0):
+    """Adaptive OSPR over nsub subframes (random phases as OSPR's, Philox
+    counter {pixel, n, t_index, 0}); returns dict(holo[nsub], I (time-averaged
+    normalised intensity), mse, amp_mse, eff)."""
+    Tn = prepare_target(t_raw)
+    ny, nx = Tn.shape
+    acc = np.zeros((ny, nx))
+    holo = np.empty((nsub, ny, nx), np.uint8)
+    for n in range(1, nsub + 1):
+        Tt = adaptive_target(Tn, acc, n)
+        st = gs_step(Tt, random_phase(ny, nx, seed, t_index, n - 1, 0))
+        holo[n - 1] = st["holo"]
+        I = np.abs(st["R"]) ** 2
+        acc += I / I.sum()
+    m = metrics(acc / nsub, Tn)
+    return dict(holo=holo, I=acc / nsub, mse=m[0], amp_mse=m[1], eff=m[2])
 
 
 def replay_field(holo, kind=SLM_BINARY, levels=2) -> np.ndarray:

@@ -345,3 +345,41 @@ def test_device_target_generator_matches_the_numpy_one():
     b = synth.targets_device(3, 64, 96, 4242, "cpu").numpy()
     assert b.shape == a.shape and b.dtype == np.float32
     assert np.abs(a - b).max() <= 1e-5 * np.abs(a).max()
+
+
+def test_adaptive_target_rule():
+    """Adaptive OSPR's subframe target: an ideal history (each earlier
+    subframe delivered exactly T^2) leaves T unchanged; the deficit is
+    clipped at zero; the result is normalised."""
+    rng = np.random.default_rng(21)
+    T = oracle.prepare_target(rng.random((8, 8)))
+    for n in (1, 2, 5):
+        Tn = oracle.adaptive_target(T, (n - 1) * T * T, n)
+        assert np.allclose(Tn, T, atol=1e-15)
+    prev = 3 * T * T
+    prev[0, 0] = 10.0  # over-delivered pixel: nothing more asked there
+    Tn = oracle.adaptive_target(T, prev, 4)
+    assert Tn[0, 0] == 0.0
+    assert (Tn ** 2).sum() == pytest.approx(1.0, abs=1e-12)
+    d = np.maximum(4 * T * T - prev, 0)
+    assert np.allclose(Tn, np.sqrt(d / d.sum()), atol=1e-15)
+
+
+def test_adaptive_ospr_first_subframe_is_ospr():
+    t = synth.target(32, 32, 31)
+    a, o = oracle.adaptive_ospr_run(t, 1, 7, 2), oracle.ospr_run(t, 1, 7, 2)
+    assert np.array_equal(a["holo"], o["holo"])
+    assert a["mse"] == pytest.approx(o["mse"], rel=1e-12)
+    a3, o3 = oracle.adaptive_ospr_run(t, 3, 7, 2), oracle.ospr_run(t, 3, 7, 2)
+    assert np.array_equal(a3["holo"][0], o3["holo"][0])
+    assert not np.array_equal(a3["holo"][2], o3["holo"][2])  # the feedback changes later subframes
+    assert np.allclose(a3["I"], sum(oracle.replay(a3["holo"][n]) for n in range(3)) / 3, rtol=1e-12,
+                       atol=1e-18)
+
+
+def test_adaptive_ospr_feedback_lowers_the_time_averaged_error():
+    ratios = []
+    for b in range(4):
+        t = synth.target(32, 32, 2000 + b)
+        ratios.append(oracle.adaptive_ospr_run(t, 12, 7, b)["mse"] / oracle.ospr_run(t, 12, 7, b)["mse"])
+    assert np.mean(ratios) < 0.8, ratios
