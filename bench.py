@@ -63,7 +63,7 @@ def parse():
     ap.add_argument("--quick", action="store_true", help="skip the e2e and CPU-baseline legs")
     ap.add_argument("--pairs", type=int, default=2048, help="warmstart: training pairs")
     ap.add_argument("--heldout", type=int, default=64, help="warmstart: held-out targets")
-    ap.add_argument("--workload", choices=["headline", "ospr", "mixed", "warmstart", "gs2048", "wgs256"],
+    ap.add_argument("--workload", choices=["headline", "ospr", "adospr", "mixed", "warmstart", "gs2048", "wgs256"],
                     default="headline",
                     help="headline: binary GS 1024^2 x 64 (the benchmark line); ospr: 8 targets x 24 "
                          "subframes of 1024^2; mixed: 16 targets each of 512^2, 1024^2, 2048^2, 1080x1920")
@@ -263,12 +263,13 @@ def run_side_workload(args):
     dev = torch.device("cuda", 0)
     s0 = torch.cuda.current_stream(dev)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    if args.workload == "ospr":
+    if args.workload in ("ospr", "adospr"):
         B, NS = 8, 24
         T = torch.from_numpy(synth.targets(B, NY, NX)).to(dev)
         holo = torch.empty((B, NS, NY, NX), dtype=torch.uint8, device=dev)
         mse = torch.empty(B, dtype=torch.float64, device=dev)
-        plan = hg.Plan(NY, NX, B, hg.HG_SLM_BINARY, 2, hg.HG_OSPR, subframes=NS, seed=7)
+        algo = hg.HG_OSPR if args.workload == "ospr" else hg.HG_ADOSPR
+        plan = hg.Plan(NY, NX, B, hg.HG_SLM_BINARY, 2, algo, subframes=NS, seed=7)
         for _ in range(args.warmup):
             plan.run(T, None, 1, holo, mse)
         plan.sync()
@@ -278,7 +279,7 @@ def run_side_workload(args):
         e1.record(s0)
         plan.sync()
         ms = e0.elapsed_time(e1) / args.steps
-        out = dict(workload="ospr_8x24_1024x1024", ms_per_step=ms, subframes_per_s=B * NS / (ms / 1e3),
+        out = dict(workload="%s_8x24_1024x1024" % args.workload, ms_per_step=ms, subframes_per_s=B * NS / (ms / 1e3),
                    algorithmic_gbs=36.0 * B * NS * NY * NX / (ms / 1e3) / 1e9,
                    mse=mse.cpu().numpy().tolist(), column_variant=hg.hg_plan_variant(plan.h, 1))
         plan.close()

@@ -65,8 +65,12 @@ typedef struct {
  * updated every iteration as w <- w T / sqrt(I) on pixels with T > 0, where
  * I is the energy-normalised replay intensity.  OSPR: Section 3.4, binary
  * SLM only, `subframes` independent random-phase subframes per target whose
- * replay intensities are averaged. */
-typedef enum { HG_GS = 0, HG_WGS = 1, HG_OSPR = 2 } hg_algo;
+ * replay intensities are averaged.  ADOSPR: adaptive OSPR (Section 3.4's
+ * feedback variant), binary only: the subframes run in order and subframe n
+ * (1-based) aims at the intensity deficit sqrt(max(n T^2 - S, 0)), S the sum
+ * of the earlier subframes' energy-normalised intensities; same random
+ * phases and outputs as OSPR. */
+typedef enum { HG_GS = 0, HG_WGS = 1, HG_OSPR = 2, HG_ADOSPR = 3 } hg_algo;
 
 typedef struct {
     void *stream;      /* cudaStream_t to enqueue on; NULL = legacy default stream */
@@ -114,7 +118,7 @@ hg_status hg_plan_create(hg_plan *out, int ny, int nx, int batch, hg_slm slm, hg
  *              starting replay phase; NULL draws U[0, 2 pi) from Philox with
  *              counter {y*nx + x, 0, target index, 1}.  OSPR: must be NULL
  *              (subframe n of target t uses counter {y*nx + x, n, t, 0}).
- *  iters       GS/WGS iterations, >= 1.  OSPR: ignored.
+ *  iters       GS/WGS iterations, >= 1.  OSPR / ADOSPR: ignored.
  *  holo_out    GS/WGS: [batch][ny][nx] uint8 level indices of the last
  *              iteration's hologram; OSPR: [batch][subframes][ny][nx].  NULL
  *              to skip.

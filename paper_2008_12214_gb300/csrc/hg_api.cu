@@ -282,6 +282,8 @@ struct hg_plan_s {
     bool use_herm_col = false;                       // Hermitian loop: column pairs share transforms
     const PipeOps *hops = nullptr;                   // variant providing the column-pair pass
     bool ospr_herm = false;                          // binary OSPR in Hermitian form
+    float *acc = nullptr;                            // adaptive OSPR: summed subframe intensities
+    uint8_t *holo_tmp = nullptr;                     // adaptive OSPR: one subframe's holograms
     unsigned long long wait_ns = 2000000000ull;      // bound on a device-side wait
     int drop_job = -1;                               // fault-injection hook
     int nsm = 0, ppt = 0, ppt_pipe = 0, ppt_max = 0;
@@ -532,6 +534,8 @@ void enqueue_prep(hg_plan p, const float *target) {
 int col_role_gs(hg_plan p) { return p->kind == HG_SLM_BINARY ? COL_GS_BIN : COL_GS_LVL; }
 int col_role_holo(hg_plan p) { return p->kind == HG_SLM_BINARY ? COL_HOLO_BIN : COL_HOLO_LVL; }
 
+bool is_ospr(int algo) { return algo == HG_OSPR || algo == HG_ADOSPR; }
+
 // Binary GS with the paired row pass and a TMA-fed column pass: the row pass
 // writes only the Hermitian part of F (rows ky <= ny/2) and the next column
 // pass reads those rows back (see herm_constrain).
@@ -598,7 +602,33 @@ hg_status enqueue_run(hg_plan p, const float *d_t, const float *d_ph, int iters,
 
     RowArgs ra = row_args(p);
     ColArgs ca = col_args(p);
-    if (p->algo == HG_OSPR) {
+    if (p->algo == HG_ADOSPR) {
+        HG_CK(cudaMemsetAsync(p->acc, 0, sizeof(float) * p->npx * p->batch, p->stream));
+        ra.items = p->batch;
+        ra.nsub = 1;  // the head draws subframe 0 of target `item`
+        ra.phase = nullptr;
+        ra.stream_id = 0;
+        launch_row(p, ROW_HEAD, ra, p->stream);
+        ca.items = p->batch;
+        RowArgs rn = row_args(p);
+        rn.acc = p->acc;
+        rn.stream_id = 0;
+        rn.nsub = p->nsub;
+        for (int n = 0; n < p->nsub; ++n) {
+            ca.holo = d_ho ? p->holo_tmp : nullptr;
+            launch_col_gs(p, COL_GS_BIN, ca, p->stream);
+            if (d_ho)  // subframe n of each target: [batch][subframes][ny][nx]
+                HG_CK(cudaMemcpy2DAsync(d_ho + (size_t)n * p->npx, p->npx * p->nsub, p->holo_tmp, p->npx, p->npx,
+                                        p->batch, cudaMemcpyDeviceToDevice, p->stream));
+            rn.sub = n + 1;
+            if (n + 1 < p->nsub) {
+                launch_row(p, ROW_ADAPT, rn, p->stream);
+            } else {
+                rn.part = p->part;
+                launch_row(p, ROW_ADFIN, rn, p->stream);
+            }
+        }
+    } else if (p->algo == HG_OSPR) {
         ra.items = p->nchains;
         ra.nsub = p->nsub;
         ra.phase = nullptr;
@@ -640,7 +670,7 @@ hg_status enqueue_run(hg_plan p, const float *d_t, const float *d_ph, int iters,
         else launch_row(p, ROW_TAIL, rt, p->stream);
     }
     const int panels_iter = p->tc_prec ? p->ppt_tc : p->prow ? p->ppt_pipe : p->ppt;
-    int panels_last = (p->tc_prec && p->algo != HG_OSPR) ? p->ppt_tc : p->ppt;
+    int panels_last = (p->tc_prec && !is_ospr(p->algo)) ? p->ppt_tc : p->ppt;
     if (p->ospr_herm) panels_last = (p->ny / 2 + p->rops->row_lines) / p->rops->row_lines;  // rows <= ny/2
     k_reduce<<<(iters * p->batch * 32 + 127) / 128, 128, 0, p->stream>>>(
         p->part, iters, p->batch, p->ppt_max, panels_iter, panels_last, 1.0 / (double)p->npx, p->metrics,
@@ -649,7 +679,7 @@ hg_status enqueue_run(hg_plan p, const float *d_t, const float *d_ph, int iters,
     HG_CK(cudaGetLastError());
     p->weights_preset = false;
     p->have_run = true;
-    p->field_from_run = p->algo != HG_OSPR;
+    p->field_from_run = !is_ospr(p->algo);
     p->last_iters = iters;
     return st;
 }
@@ -798,7 +828,7 @@ void hg_plan_destroy(hg_plan p) {
     if (p->cap_stream) cudaStreamDestroy(p->cap_stream);
     for (cudaEvent_t e : p->prof_ev) cudaEventDestroy(e);
     void *bufs[] = {p->field, p->tf, p->w, p->part, p->metrics, p->sum_part, p->scale,
-                    p->err, p->twx, p->twy, p->lvl, p->stage, p->tc_b};
+                    p->err, p->twx, p->twy, p->lvl, p->stage, p->tc_b, p->acc, p->holo_tmp};
     for (void *b : bufs)
         if (b) cudaFree(b);
     delete p;
@@ -812,17 +842,17 @@ hg_status hg_plan_create(hg_plan *out, int ny, int nx, int batch, hg_slm slm, hg
     hg_opts_default(&o);
     if (opts) o = *opts;
     if (batch < 1 || ny < 1 || nx < 1) return HG_ERR_INVALID_ARG;
-    if (algo != HG_GS && algo != HG_WGS && algo != HG_OSPR) return HG_ERR_INVALID_ARG;
+    if (algo != HG_GS && algo != HG_WGS && algo != HG_OSPR && algo != HG_ADOSPR) return HG_ERR_INVALID_ARG;
     if (slm.kind != HG_SLM_BINARY && slm.kind != HG_SLM_LLEVEL) return HG_ERR_INVALID_ARG;
     if (slm.kind == HG_SLM_LLEVEL && (slm.levels < 2 || slm.levels > 256)) return HG_ERR_INVALID_ARG;
-    if (algo == HG_OSPR && (slm.kind != HG_SLM_BINARY || o.subframes < 1)) return HG_ERR_INVALID_ARG;
+    if (is_ospr(algo) && (slm.kind != HG_SLM_BINARY || o.subframes < 1)) return HG_ERR_INVALID_ARG;
     if (o.precision < 0 || o.precision > 4) return HG_ERR_INVALID_ARG;
-    if (o.precision > 0 && ((nx != 1024 && nx != 2048) || ny % (nx == 1024 ? 4 : 2) != 0 || algo == HG_OSPR))
+    if (o.precision > 0 && ((nx != 1024 && nx != 2048) || ny % (nx == 1024 ? 4 : 2) != 0 || is_ospr(algo)))
         return HG_ERR_UNSUPPORTED_SIZE;
     const LineOps *rops = find_ops(nx), *cops = find_ops(ny);
     if (!rops || !cops) return HG_ERR_UNSUPPORTED_SIZE;
     const size_t npx = (size_t)ny * nx;
-    const int nsub = algo == HG_OSPR ? o.subframes : 1;
+    const int nsub = is_ospr(algo) ? o.subframes : 1;
     if ((double)npx * batch * nsub > 2.0e9 || (double)batch * nsub > 1e6)
         return HG_ERR_INVALID_ARG;
 
@@ -909,7 +939,7 @@ hg_status hg_plan_create(hg_plan *out, int ny, int nx, int batch, hg_slm slm, hg
             for (int i = 0; i < k; ++i) {
                 // paired rows need a binary SLM (real e^{iH}), an even column length and the
                 // GS/WGS loop
-                if (all[i]->paired && (slm.kind != HG_SLM_BINARY || ny % 2 || algo == HG_OSPR)) continue;
+                if (all[i]->paired && (slm.kind != HG_SLM_BINARY || ny % 2 || is_ospr(algo))) continue;
                 if (all[i]->row_iter && nx % 4 == 0 && ensure_pipe_init(p->dev, all[i]) == cudaSuccess)
                     rc[nr++] = all[i];
             }
@@ -1033,7 +1063,12 @@ hg_status hg_plan_create(hg_plan *out, int ny, int nx, int batch, hg_slm slm, hg
             p->ospr_herm = p->hops != nullptr;
         }
     }
-    if ((st = ensure_part(p, algo == HG_OSPR ? 1 : 8)) != HG_OK) return fail(st);
+    if ((st = ensure_part(p, is_ospr(algo) ? 1 : 8)) != HG_OK) return fail(st);
+    if (algo == HG_ADOSPR) {
+        ce = cudaMalloc(&p->acc, sizeof(float) * npx * batch);
+        if (ce == cudaSuccess) ce = cudaMalloc(&p->holo_tmp, npx * batch);
+        if (ce != cudaSuccess) return fail(map_err(ce));
+    }
     if ((st = ensure_metrics(p, 1)) != HG_OK) return fail(st);
     *out = p;
     return HG_OK;
@@ -1121,7 +1156,7 @@ hg_status hg_run(hg_plan p, const float *target, const float *init_phase, int it
                  uint8_t *holo_out, double *mse_out) {
     NvtxRange nv("hg_run");
     if (!p || !target) return HG_ERR_INVALID_ARG;
-    if (p->algo == HG_OSPR) {
+    if (is_ospr(p->algo)) {
         if (init_phase) return HG_ERR_INVALID_ARG;
         iters = 1;
     } else if (iters < 1) {
@@ -1131,7 +1166,7 @@ hg_status hg_run(hg_plan p, const float *target, const float *init_phase, int it
     p->launches = 0;
     const size_t fbytes = sizeof(float) * p->npx * p->batch;
     const size_t hbytes = p->npx * p->nchains;
-    const size_t mbytes = sizeof(double) * p->batch * (p->algo == HG_OSPR ? 1 : iters);
+    const size_t mbytes = sizeof(double) * p->batch * (is_ospr(p->algo) ? 1 : iters);
     const bool t_host = !is_device_ptr(target);
     const bool ph_host = init_phase && !is_device_ptr(init_phase);
     const bool ho_host = holo_out && !is_device_ptr(holo_out);
@@ -1216,7 +1251,7 @@ hg_status hg_replay(hg_plan p, const uint8_t *holo, float *intensity_out) {
 }
 
 hg_status hg_get_phase(hg_plan p, float *phase_out) {
-    if (!p || !phase_out || !p->field_from_run || p->algo == HG_OSPR) return HG_ERR_INVALID_ARG;
+    if (!p || !phase_out || !p->field_from_run || is_ospr(p->algo)) return HG_ERR_INVALID_ARG;
     DevGuard g(p->dev);
     p->launches = 0;
     // Recompute arg R of the last replay field (still in the field buffer
@@ -1278,7 +1313,7 @@ hg_status hg_get_weights(hg_plan p, float *w_out) {
 hg_status hg_debug_step(hg_plan p, const float *target, const float *phase_in, float *h_out,
                         uint8_t *holo_out, float *replay_out, double *metrics_out) {
     NvtxRange nv("hg_debug_step");
-    if (!p || !target || !phase_in || p->algo == HG_OSPR) return HG_ERR_INVALID_ARG;
+    if (!p || !target || !phase_in || is_ospr(p->algo)) return HG_ERR_INVALID_ARG;
     for (const void *q : {(const void *)target, (const void *)phase_in, (const void *)h_out,
                           (const void *)holo_out, (const void *)replay_out,
                           (const void *)metrics_out})
@@ -1391,7 +1426,7 @@ hg_status hg_group_run(hg_group g, const float *const *targets, const float *con
         hg_plan p = g->plans[i];
         const void *q[4] = {targets[i], init_phases ? init_phases[i] : nullptr,
                             holo_out ? holo_out[i] : nullptr, mse_out ? mse_out[i] : nullptr};
-        if (!q[0] || p->algo == HG_OSPR) return HG_ERR_INVALID_ARG;
+        if (!q[0] || is_ospr(p->algo)) return HG_ERR_INVALID_ARG;
         for (int k = 0; k < 4; ++k) {
             if (q[k] && !is_device_ptr(q[k])) return HG_ERR_INVALID_ARG;  // device buffers only
             key[4 * i + k] = q[k];

@@ -20,7 +20,7 @@
 
 namespace hg {
 
-enum RowRole { ROW_HEAD = 0, ROW_ITER = 1, ROW_TAIL = 2, ROW_AVG = 3 };
+enum RowRole { ROW_HEAD = 0, ROW_ITER = 1, ROW_TAIL = 2, ROW_AVG = 3, ROW_ADAPT = 4, ROW_ADFIN = 5 };
 enum ColRole { COL_GS_BIN = 0, COL_GS_LVL = 1, COL_HOLO_BIN = 2, COL_HOLO_LVL = 3 };
 
 constexpr int NMET = 4;  // per-panel partial sums: (I-T^2)^2, (sqrt I - T)^2, |R|^2 in T>0, |R|^2
@@ -41,6 +41,8 @@ struct RowArgs {
     const float2 *tw;      // W_nx^e, e < nx (forward roots)
     float invN, invN2, NN, invSqrtN;
     int herm;              // paired binary rows: write only the Hermitian part of F (rows y <= ny/2)
+    float *acc;            // ADAPT / ADFIN: summed normalised intensities [targets][ny][nx], DFT order
+    int sub;               // ADAPT: subframes delivered so far (index of the next one)
 };
 
 struct ColArgs {
@@ -235,6 +237,63 @@ __device__ __forceinline__ void row_body(const RowArgs &a) {
             if (a.part)
                 block_sum4(acc0, acc1, acc2, acc3, red,
                            a.part + ((size_t)item * ppt + pan) * NMET, Cfg::THREADS);
+        } else if constexpr (ROLE == ROW_ADAPT || ROLE == ROW_ADFIN) {
+            // adaptive OSPR: replay of the subframe just quantised, its normalised
+            // intensity added to the running sum; ADAPT then forms the next
+            // subframe's target from the deficit sqrt(max((sub + 1) T^2 - sum, 0))
+            // with its random phase and starts its inverse FFT; ADFIN scores the
+            // time average sum / nsub
+            const float2 *fr = a.field + ((size_t)item * ny + yc) * NX;
+            static_for<0, E>([&](auto ec) {
+                constexpr int e = decltype(ec)::value;
+                v[e] = fr[t + TL * e];
+            });
+            line_fft<P, -1, 1>(v, smb, a.tw, t, sync);
+            const float *Tr = a.T + ((size_t)item * ny + yc) * NX;
+            float *ar = a.acc + ((size_t)item * ny + yc) * NX;
+            float acc0 = 0.f, acc1 = 0.f, acc2 = 0.f, acc3 = 0.f;
+            const float inv_sub = 1.0f / (float)a.nsub;
+            static_for<0, E>([&](auto ec) {
+                constexpr int e = decltype(ec)::value;
+                const int x = t + TL * e;
+                const float m2 = fmaf(v[e].x, v[e].x, v[e].y * v[e].y);
+                const float sum = (act ? ar[x] : 0.f) + m2 * a.invN2;
+                const float Tv = act ? Tr[x] : 0.f;
+                if constexpr (ROLE == ROW_ADAPT) {
+                    if (act) ar[x] = sum;
+                    const float amp = sqrtf(fmaxf(fmaf((float)(a.sub + 1), Tv * Tv, -sum), 0.f));
+                    const int ix = (x + NX / 2) % NX;
+                    const uint32_t r = philox_word0((uint32_t)(iy * NX + ix), (uint32_t)a.sub, (uint32_t)item,
+                                                    a.stream_id, a.seed_lo, a.seed_hi);
+                    float s, c;
+                    sincospif((float)(r >> 8) * (1.0f / 8388608.0f), &s, &c);  // pi * 2u
+                    v[e] = make_float2(amp * c, amp * s);
+                } else {
+                    const float I = sum * inv_sub;
+                    if (act && a.I_out) a.I_out[((size_t)item * ny + iy) * NX + (x + NX / 2) % NX] = I;
+                    if (act) {
+                        const float d = I - Tv * Tv;
+                        const float am = sqrtf(I) - Tv;
+                        const float e2 = I * a.NN;  // unitary |R|^2 of the average
+                        acc0 = fmaf(d, d, acc0);
+                        acc1 = fmaf(am, am, acc1);
+                        acc3 += e2;
+                        if (Tv > 0.f) acc2 += e2;
+                    }
+                }
+            });
+            if constexpr (ROLE == ROW_ADAPT) {
+                line_fft<P, +1, 1>(v, smb, a.tw, t, sync);
+                if (act) {
+                    float2 *fw = a.field + ((size_t)item * ny + y) * NX;
+                    static_for<0, E>([&](auto ec) {
+                        constexpr int e = decltype(ec)::value;
+                        fw[t + TL * e] = v[e];
+                    });
+                }
+            } else if (a.part) {
+                block_sum4(acc0, acc1, acc2, acc3, red, a.part + ((size_t)item * ppt + pan) * NMET, Cfg::THREADS);
+            }
         } else {  // ROW_AVG
             float acc[E];
             static_for<0, E>([&](auto ec) { acc[decltype(ec)::value] = 0.f; });
@@ -406,6 +465,8 @@ struct OpsImpl {
         set((const void *)k_row<P, ROW_ITER, LINES>, RC::SMEM);
         set((const void *)k_row<P, ROW_TAIL, LINES>, RC::SMEM);
         set((const void *)k_row<P, ROW_AVG, LINES>, RC::SMEM);
+        set((const void *)k_row<P, ROW_ADAPT, LINES>, RC::SMEM);
+        set((const void *)k_row<P, ROW_ADFIN, LINES>, RC::SMEM);
         if constexpr (HERM) {
             set((const void *)k_row_h<P, ROW_HEAD, LINES>, RC::SMEM);
             set((const void *)k_row_h<P, ROW_AVG, LINES>, RC::SMEM);
@@ -441,6 +502,8 @@ struct OpsImpl {
             case ROW_HEAD: k_row<P, ROW_HEAD, LINES><<<grid, RC::THREADS, RC::SMEM, s>>>(a); break;
             case ROW_ITER: k_row<P, ROW_ITER, LINES><<<grid, RC::THREADS, RC::SMEM, s>>>(a); break;
             case ROW_TAIL: k_row<P, ROW_TAIL, LINES><<<grid, RC::THREADS, RC::SMEM, s>>>(a); break;
+            case ROW_ADAPT: k_row<P, ROW_ADAPT, LINES><<<grid, RC::THREADS, RC::SMEM, s>>>(a); break;
+            case ROW_ADFIN: k_row<P, ROW_ADFIN, LINES><<<grid, RC::THREADS, RC::SMEM, s>>>(a); break;
             default: k_row<P, ROW_AVG, LINES><<<grid, RC::THREADS, RC::SMEM, s>>>(a); break;
         }
     }

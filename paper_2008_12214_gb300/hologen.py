@@ -17,7 +17,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libhologen.so")
 
 HG_SLM_BINARY, HG_SLM_LLEVEL = 0, 1
-HG_GS, HG_WGS, HG_OSPR = 0, 1, 2
+HG_GS, HG_WGS, HG_OSPR, HG_ADOSPR = 0, 1, 2, 3
 NMET = 4
 
 STATUS = {0: "HG_OK", 1: "HG_ERR_INVALID_ARG", 2: "HG_ERR_UNSUPPORTED_SIZE", 3: "HG_ERR_OOM",
