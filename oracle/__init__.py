@@ -236,6 +236,47 @@ def adaptive_ospr_run(t_raw, nsub, seed, t_index=0):
     return dict(holo=holo, I=acc / nsub, mse=m[0], amp_mse=m[1], eff=m[2])
 
 
+def lt_fraction(j, f0, grow):
+    """Side fraction of the Liu-Taghizadeh window for constraint j (0 = the
+    initial field): f0 growing linearly to 1 over `grow` constraints."""
+    return 1.0 if grow <= 0 else min(1.0, f0 + (1.0 - f0) * j / grow)
+
+
+def lt_window(ny, nx, f):
+    """Centred window of replay pixels (iy, ix): |iy - ny/2| <= floor(f ny/2)
+    and |ix - nx/2| <= floor(f nx/2)."""
+    hy, hx = int(np.floor(f * ny / 2)), int(np.floor(f * nx / 2))
+    iy = np.arange(ny)[:, None]
+    ix = np.arange(nx)[None, :]
+    return (np.abs(iy - ny // 2) <= hy) & (np.abs(ix - nx // 2) <= hx)
+
+
+def lt_run(t_raw, phase0, iters, f0, grow, kind=SLM_BINARY, levels=2):
+    """Liu-Taghizadeh GS (Section 3.2: only part of the replay field is
+    targeted at first, the targeted region then grows).  Reading: a centred
+    window (lt_window) of side fraction lt_fraction(k); inside it the GS
+    constraint with the target carrying the replay's total energy
+    (sqrt(N) T with sum T^2 = 1, unitary transforms), outside it the replay
+    field is left as it is.  The initial field is the windowed target with
+    phase0.  Returns dict(holo (last), mse[iters], phase (arg R, last))."""
+    Tn = prepare_target(t_raw)
+    ny, nx = Tn.shape
+    N = ny * nx
+    A = np.sqrt(N) * Tn
+    F = np.where(lt_window(ny, nx, lt_fraction(0, f0, grow)), A, 0.0) * np.exp(1j * np.asarray(phase0))
+    mse = np.empty(iters)
+    for k in range(iters):
+        h = fft2(np.fft.ifftshift(F), +1)
+        H = quantise(h, kind, levels)
+        step = np.pi if kind == SLM_BINARY else 2 * np.pi / levels
+        R = np.fft.fftshift(fft2(np.exp(1j * step * H), -1))
+        mse[k] = metrics(np.abs(R) ** 2, Tn)[0]
+        mag = np.abs(R)
+        ph = np.where(mag > 0, R / np.where(mag > 0, mag, 1.0), 1.0)
+        F = np.where(lt_window(ny, nx, lt_fraction(k + 1, f0, grow)), A * ph, R)
+    return dict(holo=H, mse=mse, phase=np.angle(R))
+
+
 def replay_field(holo, kind=SLM_BINARY, levels=2) -> np.ndarray:
     """Replay field fftshift(FFT2(exp(iH))) (unitary, replay order) of one hologram."""
     h = np.ascontiguousarray(holo, dtype=np.uint8)

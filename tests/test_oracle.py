@@ -383,3 +383,44 @@ def test_adaptive_ospr_feedback_lowers_the_time_averaged_error():
         t = synth.target(32, 32, 2000 + b)
         ratios.append(oracle.adaptive_ospr_run(t, 12, 7, b)["mse"] / oracle.ospr_run(t, 12, 7, b)["mse"])
     assert np.mean(ratios) < 0.8, ratios
+
+
+def test_lt_window_and_growth():
+    W = oracle.lt_window(8, 12, 0.5)
+    assert W.sum() == 5 * 7 and W[4, 6] and W[2, 3] and not W[1, 6] and not W[4, 2]
+    assert oracle.lt_window(8, 12, 1.0).all()
+    assert [oracle.lt_fraction(j, 0.25, 3) for j in range(5)] == [0.25, 0.5, 0.75, 1.0, 1.0]
+    W = oracle.lt_window(16, 16, 0.5)
+    assert np.array_equal(W, W[::-1, ::-1][np.r_[-1, 0:15]][:, np.r_[-1, 0:15]])  # symmetric under u -> -u
+
+
+def test_lt_with_a_full_window_is_gs():
+    """A window covering the field from the start makes LT plain GS (the
+    target's scale does not change a binary or L-level hologram)."""
+    t = synth.target(32, 32, 61)
+    ph = synth.init_phase(32, 32, 61).astype(np.float64)
+    for kind, levels in ((oracle.SLM_BINARY, 2), (oracle.SLM_LLEVEL, 8)):
+        lt = oracle.lt_run(t, ph, 4, 1.0, 0, kind, levels)
+        gs = oracle.gs_run(t, ph, 4, kind=kind, levels=levels)
+        assert np.allclose(lt["mse"], gs["mse"], rtol=1e-9)
+        assert np.array_equal(lt["holo"], gs["holo"])
+
+
+def test_lt_leaves_the_field_outside_the_window_free():
+    """With the window frozen at its initial size, iterations only constrain
+    the window: the replay outside it is whatever the hologram gives, so the
+    error inside the window falls below plain GS's there."""
+    t = synth.target(32, 32, 62)
+    ph = synth.init_phase(32, 32, 62).astype(np.float64)
+    Tn = oracle.prepare_target(t)
+    W = oracle.lt_window(32, 32, 0.5)
+    lt = oracle.lt_run(t, ph, 12, 0.5, 10 ** 9, oracle.SLM_LLEVEL, 64)
+    gs = oracle.gs_run(t, ph, 12, kind=oracle.SLM_LLEVEL, levels=64)
+
+    def win_err(holo):
+        I = oracle.replay(holo, oracle.SLM_LLEVEL, 64)
+        I_w = I[W] / I[W].sum()
+        T_w = Tn[W] ** 2 / (Tn[W] ** 2).sum()
+        return np.mean((I_w - T_w) ** 2)
+
+    assert win_err(lt["holo"]) < win_err(gs["holo"])
