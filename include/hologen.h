@@ -69,8 +69,12 @@ typedef struct {
  * feedback variant), binary only: the subframes run in order and subframe n
  * (1-based) aims at the intensity deficit sqrt(max(n T^2 - S, 0)), S the sum
  * of the earlier subframes' energy-normalised intensities; same random
- * phases and outputs as OSPR. */
-typedef enum { HG_GS = 0, HG_WGS = 1, HG_OSPR = 2, HG_ADOSPR = 3 } hg_algo;
+ * phases and outputs as OSPR.  LT: Liu-Taghizadeh GS (Section 3.2): only a
+ * centred window of the replay field is constrained at first, and the window
+ * grows each iteration (hg_opts lt_start, lt_grow): inside it the GS
+ * constraint with the target carrying the replay's total energy, outside it
+ * the replay field is left free; the first field is the windowed target. */
+typedef enum { HG_GS = 0, HG_WGS = 1, HG_OSPR = 2, HG_ADOSPR = 3, HG_LT = 4 } hg_algo;
 
 typedef struct {
     void *stream;      /* cudaStream_t to enqueue on; NULL = legacy default stream */
@@ -91,9 +95,15 @@ typedef struct {
                           own buffers at creation and keep the fastest (cached per
                           device and shape); 0: first candidate; 2 + k: candidate k
                           for both passes (HG_ERR_UNSUPPORTED_SIZE if absent) */
+    float lt_start;    /* LT: window side fraction of the first field, in (0, 1]
+                          (default 0.25); constraint k uses min(1, lt_start +
+                          (1 - lt_start) k / lt_grow) */
+    int lt_grow;       /* LT: constraints over which the window grows to the full
+                          field (>= 1, default 10) */
 } hg_opts;
 
-/* Fills *opts with the defaults: stream NULL, seed 0, subframes 24,
+/* Fills *opts with the defaults: stream NULL, seed 0, subframes 24, lt_start
+ * 0.25, lt_grow 10,
  * precision 0, use_graph 1, pipeline -1, autotune 1. */
 void hg_opts_default(hg_opts *opts);
 

@@ -3,6 +3,7 @@
 // metric reduction, weight fill).
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <cstdlib>
@@ -282,6 +283,8 @@ struct hg_plan_s {
     bool use_herm_col = false;                       // Hermitian loop: column pairs share transforms
     const PipeOps *hops = nullptr;                   // variant providing the column-pair pass
     bool ospr_herm = false;                          // binary OSPR in Hermitian form
+    float lt_start = 1.f;                            // LT window: initial side fraction, growth length
+    int lt_grow = 1;
     float *acc = nullptr;                            // adaptive OSPR: summed subframe intensities
     uint8_t *holo_tmp = nullptr;                     // adaptive OSPR: one subframe's holograms
     unsigned long long wait_ns = 2000000000ull;      // bound on a device-side wait
@@ -402,7 +405,19 @@ RowArgs row_args(hg_plan p) {
     a.invN2 = (float)(1.0 / (N * N));
     a.NN = (float)N;
     a.invSqrtN = (float)(1.0 / std::sqrt(N));
+    a.lt_amp = 0.f;
+    a.lt_hy = p->ny;
+    a.lt_hx = p->nx;
     return a;
+}
+
+// Liu-Taghizadeh window of constraint j (0: the first field) into a.
+void lt_set(hg_plan p, RowArgs &a, int j) {
+    if (p->algo != HG_LT) return;
+    const double f = std::min(1.0, (double)p->lt_start + (1.0 - (double)p->lt_start) * j / p->lt_grow);
+    a.lt_amp = (float)p->npx;  // target scaled to the replay's energy (unnormalised transforms)
+    a.lt_hy = (int)std::floor(f * p->ny / 2);
+    a.lt_hx = (int)std::floor(f * p->nx / 2);
 }
 
 ColArgs col_args(hg_plan p) {
@@ -556,6 +571,7 @@ void enqueue_loop(hg_plan p, int iters, cudaStream_t s) {
         else if (ca.half_in && p->use_herm_col) launch_col_herm(p, ca, s);
         else launch_col_gs(p, col_role_gs(p), ca, s);
         ra.part = p->part + (size_t)k * p->batch * p->ppt_max * NMET;
+        lt_set(p, ra, k + 1);
         launch_row_iter(p, ra, s);
     }
 }
@@ -654,6 +670,7 @@ hg_status enqueue_run(hg_plan p, const float *d_t, const float *d_ph, int iters,
             p->launches++;
         }
         ra.phase = d_ph;
+        lt_set(p, ra, 0);
         launch_row(p, ROW_HEAD, ra, p->stream);
         if (capturing) {
             enqueue_loop(p, iters, p->stream);
@@ -802,6 +819,8 @@ void hg_opts_default(hg_opts *o) {
     o->use_graph = 1;
     o->pipeline = -1;
     o->autotune = 1;
+    o->lt_start = 0.25f;
+    o->lt_grow = 10;
 }
 
 int hg_supported_length(int n) { return find_ops(n) != nullptr; }
@@ -842,12 +861,14 @@ hg_status hg_plan_create(hg_plan *out, int ny, int nx, int batch, hg_slm slm, hg
     hg_opts_default(&o);
     if (opts) o = *opts;
     if (batch < 1 || ny < 1 || nx < 1) return HG_ERR_INVALID_ARG;
-    if (algo != HG_GS && algo != HG_WGS && algo != HG_OSPR && algo != HG_ADOSPR) return HG_ERR_INVALID_ARG;
+    if (algo != HG_GS && algo != HG_WGS && algo != HG_OSPR && algo != HG_ADOSPR && algo != HG_LT)
+        return HG_ERR_INVALID_ARG;
+    if (algo == HG_LT && (!(o.lt_start > 0.f) || o.lt_start > 1.f || o.lt_grow < 1)) return HG_ERR_INVALID_ARG;
     if (slm.kind != HG_SLM_BINARY && slm.kind != HG_SLM_LLEVEL) return HG_ERR_INVALID_ARG;
     if (slm.kind == HG_SLM_LLEVEL && (slm.levels < 2 || slm.levels > 256)) return HG_ERR_INVALID_ARG;
     if (is_ospr(algo) && (slm.kind != HG_SLM_BINARY || o.subframes < 1)) return HG_ERR_INVALID_ARG;
     if (o.precision < 0 || o.precision > 4) return HG_ERR_INVALID_ARG;
-    if (o.precision > 0 && ((nx != 1024 && nx != 2048) || ny % (nx == 1024 ? 4 : 2) != 0 || is_ospr(algo)))
+    if (o.precision > 0 && ((nx != 1024 && nx != 2048) || ny % (nx == 1024 ? 4 : 2) != 0 || is_ospr(algo) || algo == HG_LT))
         return HG_ERR_UNSUPPORTED_SIZE;
     const LineOps *rops = find_ops(nx), *cops = find_ops(ny);
     if (!rops || !cops) return HG_ERR_UNSUPPORTED_SIZE;
@@ -871,6 +892,10 @@ hg_status hg_plan_create(hg_plan *out, int ny, int nx, int batch, hg_slm slm, hg
     p->nsub = nsub;
     p->nchains = batch * nsub;
     p->seed = o.seed;
+    if (algo == HG_LT) {
+        p->lt_start = o.lt_start;
+        p->lt_grow = o.lt_grow;
+    }
     p->stream = (cudaStream_t)o.stream;
     p->use_graph = o.use_graph ? 1 : 0;
     p->rops = rops;

@@ -43,7 +43,18 @@ struct RowArgs {
     int herm;              // paired binary rows: write only the Hermitian part of F (rows y <= ny/2)
     float *acc;            // ADAPT / ADFIN: summed normalised intensities [targets][ny][nx], DFT order
     int sub;               // ADAPT: subframes delivered so far (index of the next one)
+    // Liu-Taghizadeh window (HEAD / ITER): lt_amp > 0 constrains only replay pixels
+    // within lt_hy rows and lt_hx columns of the centre, with the target scaled by
+    // lt_amp; the field outside stays free.  lt_amp == 0: plain GS.
+    float lt_amp;
+    int lt_hy, lt_hx;
 };
+
+// Is DFT-order pixel (y, x) inside the Liu-Taghizadeh window?  Its replay
+// offsets from the centre are min(y, ny - y) and min(x, nx - x).
+__device__ __forceinline__ bool lt_in(const RowArgs &a, int y, int x) {
+    return min(y, a.ny - y) <= a.lt_hy && min(x, a.nx - x) <= a.lt_hx;
+}
 
 struct ColArgs {
     int ny, nx;
@@ -143,6 +154,7 @@ __device__ __forceinline__ void row_body(const RowArgs &a) {
                 const int ix = (x + NX / 2) % NX;
                 float amp = Tr[x];
                 if (wr) amp *= wr[x];
+                if (a.lt_amp > 0.f && !lt_in(a, yc, x)) amp = 0.f;
                 float s, c;
                 if (a.phase) {
                     // phase in half-turns: the reduction is exact, no large-argument path
@@ -213,8 +225,12 @@ __device__ __forceinline__ void row_body(const RowArgs &a) {
                     if (act) wr[x] = wv;
                 }
                 if constexpr (ROLE == ROW_ITER) {
-                    const float g = Tv * wv;
-                    v[e] = m2 > 0.f ? make_float2(g * r.x * rs, g * r.y * rs) : make_float2(g, 0.f);
+                    if (a.lt_amp > 0.f && !lt_in(a, yc, x)) {
+                        v[e] = r;  // outside the window: left free
+                    } else {
+                        const float g = (a.lt_amp > 0.f ? a.lt_amp : 1.f) * Tv * wv;
+                        v[e] = m2 > 0.f ? make_float2(g * r.x * rs, g * r.y * rs) : make_float2(g, 0.f);
+                    }
                 } else {
                     if (act) {
                         const int ix = (x + NX / 2) % NX;

@@ -263,8 +263,9 @@ __global__ void __launch_bounds__(RowPipeCfg<P, LINES, NG, D, SWZ>::THREADS, 1)
                 if (Tv > 0.f && m2 > 0.f) wv = wv * Tv * (a.NN * rs);
                 if (act) wr[x] = wv;
             }
-            const float gm = Tv * wv;
-            v[e] = m2 > 0.f ? make_float2(gm * r.x * rs, gm * r.y * rs) : make_float2(gm, 0.f);
+            const float gm = (a.lt_amp > 0.f ? a.lt_amp : 1.f) * Tv * wv;
+            if (a.lt_amp > 0.f && !lt_in(a, y, x)) v[e] = r;  // outside the window: left free
+            else v[e] = m2 > 0.f ? make_float2(gm * r.x * rs, gm * r.y * rs) : make_float2(gm, 0.f);
         });
         line_fft<P, +1, 1, LAY>(v, sf, a.tw, t, gsync);
         gsync();
@@ -296,7 +297,7 @@ __global__ void __launch_bounds__(RowPipeCfg<P, LINES, NG, D, SWZ>::THREADS, 1)
 // metric partials, optional weight update, F = w T R / |R| in place.
 template <class P>
 __device__ __forceinline__ void pair_constrain(float2 (&w)[P::E], const float *sT, float *wr,
-                                               const RowArgs &a, int t, float &acc0, float &acc1,
+                                               const RowArgs &a, int t, int yrow, float &acc0, float &acc1,
                                                float &acc2, float &acc3) {
     static_for<0, P::E>([&](auto ec) {
         constexpr int e = decltype(ec)::value;
@@ -319,8 +320,9 @@ __device__ __forceinline__ void pair_constrain(float2 (&w)[P::E], const float *s
             if (Tv > 0.f && m2 > 0.f) wv = wv * Tv * (a.NN * rs);
             wr[x] = wv;
         }
-        const float gm = Tv * wv;
-        w[e] = m2 > 0.f ? make_float2(gm * r.x * rs, gm * r.y * rs) : make_float2(gm, 0.f);
+        const float gm = (a.lt_amp > 0.f ? a.lt_amp : 1.f) * Tv * wv;
+        if (a.lt_amp > 0.f && !lt_in(a, yrow, x)) w[e] = r;  // outside the window: left free
+        else w[e] = m2 > 0.f ? make_float2(gm * r.x * rs, gm * r.y * rs) : make_float2(gm, 0.f);
     });
 }
 
@@ -351,7 +353,7 @@ __device__ __forceinline__ void pair_finish(float2 (&w)[P::E], float2 *xbuf, con
 template <class P>
 __device__ __forceinline__ void herm_constrain(float2 (&w)[P::E], const float *sT, const float *sTm, float *wr,
                                                const float *wold_m, float *wrm, bool partner,
-                                               const RowArgs &a, int t, float &acc0, float &acc1,
+                                               const RowArgs &a, int t, int yrow, float &acc0, float &acc1,
                                                float &acc2, float &acc3) {
     static_for<0, P::E>([&](auto ec) {
         constexpr int e = decltype(ec)::value;
@@ -385,8 +387,10 @@ __device__ __forceinline__ void herm_constrain(float2 (&w)[P::E], const float *s
             if (Tm > 0.f && m2 > 0.f) wm = wm * Tm * (a.NN * rs);
             if (partner) wrm[xm] = wm;
         }
-        const float gm = 0.5f * fmaf(Tv, wv, Tm * wm);
-        w[e] = m2 > 0.f ? make_float2(gm * r.x * rs, gm * r.y * rs) : make_float2(gm, 0.f);
+        const float gm = (a.lt_amp > 0.f ? a.lt_amp : 1.f) * 0.5f * fmaf(Tv, wv, Tm * wm);
+        // the window is symmetric under u -> -u: outside it F_H = R
+        if (a.lt_amp > 0.f && !lt_in(a, yrow, x)) w[e] = r;
+        else w[e] = m2 > 0.f ? make_float2(gm * r.x * rs, gm * r.y * rs) : make_float2(gm, 0.f);
     });
 }
 
@@ -500,8 +504,8 @@ __global__ void __launch_bounds__(PairPipeCfg<P, NG, D, SWZ>::THREADS, 1)
                 gsync();
                 wold = sW;
             }
-            herm_constrain<P>(v, sTa, partner ? sTa + NX : sTa, wrp, wold, wrm, partner, a, t, acc0, acc1, acc2,
-                              acc3);
+            herm_constrain<P>(v, sTa, partner ? sTa + NX : sTa, wrp, wold, wrm, partner, a, t, pan, acc0, acc1,
+                              acc2, acc3);
             pair_finish<P, LAY>(v, sf, a.tw, t, gsync, a.field + ((size_t)item * ny + pan) * NX);
             gsync();
             if (t == 0) issue(k + D);
@@ -527,8 +531,8 @@ __global__ void __launch_bounds__(PairPipeCfg<P, NG, D, SWZ>::THREADS, 1)
                 vb[e] = make_float2(q.x, -q.y);
             });
             pair_constrain<P>(vb, sTa + NX, a.w ? a.w + ((size_t)item * ny + ny - pan) * NX : nullptr, a,
-                              t, acc0, acc1, acc2, acc3);
-            pair_constrain<P>(v, sTa, a.w ? a.w + ((size_t)item * ny + pan) * NX : nullptr, a, t, acc0,
+                              t, ny - pan, acc0, acc1, acc2, acc3);
+            pair_constrain<P>(v, sTa, a.w ? a.w + ((size_t)item * ny + pan) * NX : nullptr, a, t, pan, acc0,
                               acc1, acc2, acc3);
             gsync();
             static_for<0, E>([&](auto ec) {
@@ -536,7 +540,7 @@ __global__ void __launch_bounds__(PairPipeCfg<P, NG, D, SWZ>::THREADS, 1)
                 park[t + TL * e] = vb[e];
             });
         } else {
-            pair_constrain<P>(v, sTa, a.w ? a.w + ((size_t)item * ny + pan) * NX : nullptr, a, t, acc0,
+            pair_constrain<P>(v, sTa, a.w ? a.w + ((size_t)item * ny + pan) * NX : nullptr, a, t, pan, acc0,
                               acc1, acc2, acc3);
         }
 #pragma unroll 1

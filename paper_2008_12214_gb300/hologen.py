@@ -17,7 +17,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libhologen.so")
 
 HG_SLM_BINARY, HG_SLM_LLEVEL = 0, 1
-HG_GS, HG_WGS, HG_OSPR, HG_ADOSPR = 0, 1, 2, 3
+HG_GS, HG_WGS, HG_OSPR, HG_ADOSPR, HG_LT = 0, 1, 2, 3, 4
 NMET = 4
 
 STATUS = {0: "HG_OK", 1: "HG_ERR_INVALID_ARG", 2: "HG_ERR_UNSUPPORTED_SIZE", 3: "HG_ERR_OOM",
@@ -34,7 +34,7 @@ class HgError(RuntimeError):
 class hg_opts(ctypes.Structure):
     _fields_ = [("stream", ctypes.c_void_p), ("seed", ctypes.c_uint64), ("subframes", ctypes.c_int),
                 ("precision", ctypes.c_int), ("use_graph", ctypes.c_int), ("pipeline", ctypes.c_int),
-                ("autotune", ctypes.c_int)]
+                ("autotune", ctypes.c_int), ("lt_start", ctypes.c_float), ("lt_grow", ctypes.c_int)]
 
 
 class hg_slm(ctypes.Structure):
@@ -149,7 +149,8 @@ def hg_status_string(st: int) -> str:
 
 
 def hg_plan_create(ny, nx, batch, slm_kind=HG_SLM_BINARY, levels=2, algo=HG_GS, stream=None,
-                   seed=0, subframes=24, precision=0, use_graph=True, pipeline=-1, autotune=True):
+                   seed=0, subframes=24, precision=0, use_graph=True, pipeline=-1, autotune=True,
+                   lt_start=None, lt_grow=None):
     o = hg_opts()
     lib().hg_opts_default(ctypes.byref(o))
     if stream is None and torch.cuda.is_available():
@@ -161,6 +162,10 @@ def hg_plan_create(ny, nx, batch, slm_kind=HG_SLM_BINARY, levels=2, algo=HG_GS, 
     o.use_graph = 1 if use_graph else 0
     o.pipeline = int(pipeline)
     o.autotune = int(autotune)
+    if lt_start is not None:
+        o.lt_start = float(lt_start)
+    if lt_grow is not None:
+        o.lt_grow = int(lt_grow)
     h = ctypes.c_void_p()
     _ck(lib().hg_plan_create(ctypes.byref(h), int(ny), int(nx), int(batch),
                              hg_slm(int(slm_kind), int(levels)), int(algo), ctypes.byref(o)),
