@@ -10,6 +10,11 @@ Every function cites the passage of arXiv:2008.12214 (HoloGen) it follows in
 the C source's header (adaptive OSPR, whose feedback the paper does not spell
 out, is a reading written here from the C steps).  Parity status: the FFT,
 quantiser, GS step, replay and Philox are pinned by ``tests/test_oracle.py``;
+the illumination / Fresnel / amplitude-SLM / region-of-interest functions
+(modulated_run, evaluate, roi_metrics, ssim_global) by
+``tests/test_oracle_modulation.py`` (hand-worked 4x4 ROI metrics, the SSIM
+closed form for an affine copy, the level-grid Fresnel and uniform
+illumination identities, binary amplitude = binary phase plus a zero order);
 the exact WGS trajectory, the OSPR mean intensity and the adaptive-OSPR
 sequence beyond its first subframe are "parity unpinned" beyond the
 qualitative and structural checks listed there.
@@ -294,3 +299,160 @@ def metrics(R2, T):
     out = np.empty(4, np.float64)
     _ck(_load().or_metrics(r.size, _p(r), _p(t), _p(out)))
     return out
+
+
+# ------------------------------------------------------------------------
+# Illumination, Fresnel holograms, amplitude SLMs, regions of interest
+# (Sections 2 and 3.1).  Plain numpy over the pinned primitives above.
+
+SLM_AMPLITUDE = 3
+
+
+def fresnel_phase(ny, nx, c):
+    """Section 2: a Fresnel (mid-field) hologram is the far-field one with an
+    extra quadratic phase on the SLM plane.  Reading: q(y, x) = c ((x -
+    nx//2)^2 + (y - ny//2)^2) radians, SLM pixel (y, x) in natural order, c
+    in radians per squared pixel (pi dx^2 / (lambda z) for pitch dx at
+    distance z; c = 0 is the far field)."""
+    y = (np.arange(ny) - ny // 2)[:, None].astype(np.float64)
+    x = (np.arange(nx) - nx // 2)[None, :].astype(np.float64)
+    return c * (x * x + y * y)
+
+
+def illumination(ny, nx, amp=None, phase=None, fresnel=0.0):
+    """Field E(y, x) lighting the SLM (natural order): amplitude `amp` (1 if
+    None) and phase `phase` (0 if None) plus the Fresnel term.  The Thrust
+    call of Section 4 hands the quantiser the illumination's phases and
+    magnitudes; the light leaving SLM pixel (y, x) is E(y, x) times the
+    pixel's modulation."""
+    a = np.ones((ny, nx)) if amp is None else np.asarray(amp, dtype=np.float64)
+    p = np.zeros((ny, nx)) if phase is None else np.asarray(phase, dtype=np.float64)
+    return a * np.exp(1j * (p + fresnel_phase(ny, nx, fresnel)))
+
+
+def round_half_away(v):
+    return np.sign(v) * np.floor(np.abs(v) + 0.5)
+
+
+def quantise_modulated(h, E, kind, levels=2, clip=2.0):
+    """Nearest SLM state for the wanted field h (unitary) under illumination E.
+    Returns (levels uint8, field leaving the SLM).
+
+    Phase SLMs (binary {0, pi} or L levels on the full circle): the state
+    nearest h / E in phase, i.e. the quantiser of Section 4 applied to
+    h conj(E) (its argument less the illumination's), giving E exp(i H).
+    Amplitude SLMs (transmittance l / (L - 1), l < L; Fig. 1's amplitude
+    modulation): the least-squares real transmittance m = Re(h conj E) /
+    |E|^2 (0 where E = 0) is mapped from [-clip, clip] to [0, 1] by
+    v = 1/2 + m / (2 clip) and rounded half away from zero to the nearest
+    level, clamped to [0, L - 1]; the field is E l / (L - 1).  With L = 2
+    that is l = 1 exactly where Re(h conj E) >= 0, whatever `clip`."""
+    h = np.asarray(h, dtype=np.complex128)
+    hm = h * np.conj(E)
+    if kind == SLM_AMPLITUDE:
+        e2 = np.abs(E) ** 2
+        m = np.where(e2 > 0, hm.real / np.where(e2 > 0, e2, 1.0), 0.0)
+        v = (levels - 1) * (0.5 + m / (2.0 * clip))
+        q = np.clip(round_half_away(v), 0, levels - 1).astype(np.uint8)
+        return q, E * (q / (levels - 1.0))
+    q = quantise(hm, kind, levels)
+    step = np.pi if kind == SLM_BINARY else 2 * np.pi / levels
+    return q, E * np.exp(1j * step * q)
+
+
+def modulated_field(holo, E, kind, levels=2):
+    """Field leaving the SLM for given levels under illumination E."""
+    q = np.asarray(holo, dtype=np.float64)
+    if kind == SLM_AMPLITUDE:
+        return E * (q / (levels - 1.0))
+    step = np.pi if kind == SLM_BINARY else 2 * np.pi / levels
+    return E * np.exp(1j * step * q)
+
+
+def ssim_global(x, y, k1=0.01, k2=0.03, L=1.0):
+    """SSIM of Section 3.1 over whole images: means, (population) variances
+    and covariance of x and y, c1 = (k1 L)^2, c2 = (k2 L)^2."""
+    x = np.asarray(x, dtype=np.float64).ravel()
+    y = np.asarray(y, dtype=np.float64).ravel()
+    mx, my = x.mean(), y.mean()
+    vx, vy = ((x - mx) ** 2).mean(), ((y - my) ** 2).mean()
+    cxy = ((x - mx) * (y - my)).mean()
+    c1, c2 = (k1 * L) ** 2, (k2 * L) ** 2
+    return (2 * mx * my + c1) * (2 * cxy + c2) / ((mx * mx + my * my + c1) * (vx + vy + c2))
+
+
+def roi_target(t_raw, roi=None):
+    """Target restricted to the region of interest (replay order) and
+    normalised there: sum over the ROI of T^2 = 1, T = 0 outside."""
+    t = np.asarray(t_raw, dtype=np.float64)
+    if roi is not None:
+        t = np.where(np.asarray(roi) != 0, t, 0.0)
+    return t / np.sqrt((t * t).sum())
+
+
+def roi_metrics(R2, Tn, roi=None):
+    """Metrics of Section 3.1 restricted to the region of interest, for an
+    unnormalised replay intensity R2 = |R|^2 and the ROI-normalised target
+    Tn (roi_target).  The scale freedom of Section 3 is taken over the ROI:
+    I = |R|^2 / sum_ROI |R|^2, so sum_ROI I = sum_ROI T^2 = 1.  Returns
+    (intensity MSE, amplitude MSE of eq. mse on sqrt(I) vs T, efficiency,
+    SSIM, sum |R|^2): means over the ROI's pixels; efficiency = energy on
+    the target's support inside the ROI over all replay energy; SSIM on the
+    amplitudes T / max T and sqrt(I) / max T over the ROI (dynamic range 1)."""
+    R2 = np.asarray(R2, dtype=np.float64)
+    Tn = np.asarray(Tn, dtype=np.float64)
+    m = np.ones(R2.shape, bool) if roi is None else np.asarray(roi) != 0
+    I = R2[m] / R2[m].sum()
+    t = Tn[m]
+    mse = ((I - t * t) ** 2).mean()
+    amp = ((np.sqrt(I) - t) ** 2).mean()
+    eff = R2[m][t > 0].sum() / R2.sum()
+    tmax = t.max()
+    ssim = ssim_global(t / tmax, np.sqrt(I) / tmax)
+    return np.array([mse, amp, eff, ssim, R2.sum()])
+
+
+def modulated_run(t_raw, phase0, iters, kind=SLM_BINARY, levels=2, E=None, roi=None, clip=2.0):
+    """GS (Section 3.2) with an illuminated (and Fresnel) SLM plane, phase or
+    amplitude SLM levels, and a region of interest.  Readings:
+      * the target is restricted to the ROI and normalised there (roi_target);
+        inside the ROI the replay constraint uses sqrt(N) T (the replay's
+        energy of a unit-modulus hologram, unitary transforms), outside it
+        the replay field is left free (Section 3's amplitude freedom);
+      * the initial field is sqrt(N) T exp(i phase0);
+      * h = IFFT2(ifftshift F) is quantised by quantise_modulated under the
+        illumination E (natural SLM order; uniform 1 if None), the replay is
+        R = fftshift(FFT2(field leaving the SLM));
+      * metrics per iteration: roi_metrics.
+    Returns dict(holo (last), mse, amp_mse, eff, ssim, sum_r2 [iters], R
+    (last replay field), F (the constraint field the next iteration starts
+    from))."""
+    Tn = roi_target(t_raw, roi)
+    ny, nx = Tn.shape
+    N = ny * nx
+    if E is None:
+        E = np.ones((ny, nx), np.complex128)
+    inside = np.ones((ny, nx), bool) if roi is None else np.asarray(roi) != 0
+    A = np.sqrt(N) * Tn
+    F = A * np.exp(1j * np.asarray(phase0, dtype=np.float64))
+    out = np.empty((5, iters))
+    for k in range(iters):
+        h = fft2(np.fft.ifftshift(F), +1)
+        q, s = quantise_modulated(h, E, kind, levels, clip)
+        R = np.fft.fftshift(fft2(s, -1))
+        out[:, k] = roi_metrics(np.abs(R) ** 2, Tn, roi)
+        mag = np.abs(R)
+        ph = np.where(mag > 0, R / np.where(mag > 0, mag, 1.0), 1.0)
+        F = np.where(inside, A * ph, R)
+    return dict(holo=q, mse=out[0], amp_mse=out[1], eff=out[2], ssim=out[3], sum_r2=out[4], R=R, F=F)
+
+
+def evaluate(holo, t_raw, kind=SLM_BINARY, levels=2, E=None, roi=None):
+    """roi_metrics of the replay of given holograms (levels, natural order)
+    under illumination E, against the ROI-normalised target."""
+    q = np.asarray(holo)
+    ny, nx = q.shape
+    if E is None:
+        E = np.ones((ny, nx), np.complex128)
+    R = np.fft.fftshift(fft2(modulated_field(q, E, kind, levels), -1))
+    return roi_metrics(np.abs(R) ** 2, roi_target(t_raw, roi), roi)
