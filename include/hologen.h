@@ -54,8 +54,15 @@ typedef enum {
 /* SLM modulation (Section 3; Fig. 1).  BINARY: levels {0, pi}, level 0 iff
  * Re h >= 0 for the back-propagated field h.  LLEVEL: `levels` phases
  * 2 pi q / levels over the full circle, q = round-half-away(arg h /
- * (2 pi / levels)) mod levels, 2 <= levels <= 256. */
-typedef enum { HG_SLM_BINARY = 0, HG_SLM_LLEVEL = 1 } hg_slm_kind;
+ * (2 pi / levels)) mod levels, 2 <= levels <= 256.  AMPLITUDE (Fig. 1's
+ * amplitude modulation; binary amplitude is levels = 2): transmittance
+ * q / (levels - 1), q = round-half-away((levels - 1) (1/2 + m / (2 amp_clip)))
+ * clamped to [0, levels - 1], where m = Re(h conj E) / |E|^2 is the
+ * least-squares real transmittance under the illumination E (0 where E = 0)
+ * and h is the unitary field of a target carrying sqrt(N) T; with levels = 2
+ * that is q = 1 exactly where Re(h conj E) >= 0.  AMPLITUDE makes the plan
+ * modulated (hg_opts.modulated). */
+typedef enum { HG_SLM_BINARY = 0, HG_SLM_LLEVEL = 1, HG_SLM_AMPLITUDE = 2 } hg_slm_kind;
 typedef struct {
     int kind;   /* hg_slm_kind */
     int levels; /* ignored for BINARY */
@@ -100,10 +107,33 @@ typedef struct {
                           (1 - lt_start) k / lt_grow) */
     int lt_grow;       /* LT: constraints over which the window grows to the full
                           field (>= 1, default 10) */
+    int modulated;     /* 1: a modulated plan (implied by an AMPLITUDE SLM or a
+                          non-zero fresnel).  Its SLM plane is lit by an
+                          illumination field E (hg_set_illumination; uniform 1
+                          until set) times the Fresnel term, and a region of
+                          interest (hg_set_roi; the whole field until set)
+                          limits the replay constraint and the metrics.  The
+                          target is restricted to the ROI and normalised there;
+                          inside the ROI the GS constraint uses sqrt(N) T (the
+                          replay energy of a unit-modulus hologram, unitary
+                          transforms), outside it the replay field is left free;
+                          the first field is sqrt(N) T e^{i phase}.  Metrics
+                          scale the replay to the ROI's energy, I = |R|^2 /
+                          sum_ROI |R|^2, and average over the ROI; efficiency is
+                          the energy on the target's support over all replay
+                          energy.  GS only, generic passes (not pipeline 1, not
+                          precision > 0), no hg_debug_step, else
+                          HG_ERR_INVALID_ARG.  Default 0. */
+    float fresnel;     /* Fresnel (mid-field) hologram, Section 2: the SLM-plane
+                          field gains the quadratic phase fresnel * ((x - nx/2)^2
+                          + (y - ny/2)^2) radians (pi dx^2 / (lambda z) for
+                          pixel pitch dx at distance z); 0 (default): far field */
+    float amp_clip;    /* AMPLITUDE SLM: the transmittance range [0, 1] spans
+                          m in [-amp_clip, amp_clip]; > 0, default 2 */
 } hg_opts;
 
 /* Fills *opts with the defaults: stream NULL, seed 0, subframes 24, lt_start
- * 0.25, lt_grow 10,
+ * 0.25, lt_grow 10, modulated 0, fresnel 0, amp_clip 2,
  * precision 0, use_graph 1, pipeline -1, autotune 1. */
 void hg_opts_default(hg_opts *opts);
 
@@ -156,6 +186,42 @@ hg_status hg_get_metrics(hg_plan plan, double *out, size_t count);
  * indices: holo [batch][ny][nx] (OSPR plans: [batch][subframes][ny][nx],
  * time-averaged per target); intensity_out [batch][ny][nx] float. */
 hg_status hg_replay(hg_plan plan, const uint8_t *holo, float *intensity_out);
+
+/* Illumination of the SLM plane of a modulated plan (Section 4: the
+ * quantiser is handed the illumination's phases and magnitudes; the paper
+ * gives no further rule).  amp and phase: [ny][nx] float, natural SLM order
+ * (NULL: 1 and 0).  The light leaving SLM pixel (y, x) is E = amp exp(i
+ * (phase + Fresnel term)) times the pixel's modulation; phase SLMs pick the
+ * level nearest arg(h conj E) and emit E e^{iH}, the AMPLITUDE SLM emits
+ * E q / (levels - 1).  Applies to later runs.  Synchronises the plan's
+ * stream.  Errors: HG_ERR_INVALID_ARG (NULL or unmodulated plan, a negative
+ * or non-finite amplitude, a non-finite phase), HG_ERR_CUDA. */
+hg_status hg_set_illumination(hg_plan plan, const float *amp, const float *phase);
+
+/* Region of interest of a modulated plan (Section 2: many applications use
+ * part of the replay field; metrics restricted to it give extra freedom):
+ * roi [ny][nx] uint8, replay order, nonzero inside; NULL = the whole field.
+ * Applies to later runs and hg_evaluate calls (the target is restricted to
+ * the ROI, so a ROI that misses the target gives HG_ERR_NUMERIC at the
+ * run).  Synchronises the plan's stream.  Errors: HG_ERR_INVALID_ARG (NULL
+ * or unmodulated plan), HG_ERR_CUDA. */
+hg_status hg_set_roi(hg_plan plan, const uint8_t *roi);
+
+/* Metrics of given holograms (Section 3.1), on any plan: the replay of holo
+ * (layout and SLM as in hg_replay, under the plan's illumination) against
+ * target ([batch][ny][nx] float, replay order, >= 0, normalised inside over
+ * the plan's region of interest), out [batch][5] double = {intensity MSE,
+ * amplitude MSE of eq. (mse), efficiency, SSIM, sum |R|^2 (unitary)}.  The
+ * replay intensity is scaled to the ROI's energy (I = |R|^2 / sum_ROI
+ * |R|^2) and the means run over the ROI's pixels (the whole field for
+ * unmodulated plans); efficiency = energy on the target's support in the
+ * ROI over all replay energy.  SSIM is Section 3.1's formula over the whole
+ * ROI (means, population variances and covariance; k1 = 0.01, k2 = 0.03,
+ * dynamic range 1) of x = T / max T and y = sqrt(I) / max T, i.e. the
+ * phase-insensitive (amplitude) variant.  Errors: HG_ERR_INVALID_ARG (NULL,
+ * negative / NaN / infinite target values, found on the device),
+ * HG_ERR_OOM, HG_ERR_CUDA. */
+hg_status hg_evaluate(hg_plan plan, const uint8_t *holo, const float *target, double *out);
 
 /* Replay phase arg R after the last GS/WGS run (0 where R = 0), replay order,
  * [batch][ny][nx] float radians: the state from which a run resumes. */

@@ -40,7 +40,8 @@ constexpr int PREP_BLOCKS = 64;  // per target
 // strided elements in float, threads and warps combine in double.  Flags
 // negative, NaN and infinite values.
 __global__ void __launch_bounds__(PREP_THREADS)
-k_prep_sum(const float *__restrict__ t_raw, int npx, double *part, unsigned *err) {
+k_prep_sum(const float *__restrict__ t_raw, int npx, const uint8_t *__restrict__ roi, double *part,
+           unsigned *err) {
     __shared__ double red[PREP_THREADS / 32];
     const int b = blockIdx.y;
     const float *tb = t_raw + (size_t)b * npx;
@@ -49,7 +50,7 @@ k_prep_sum(const float *__restrict__ t_raw, int npx, double *part, unsigned *err
     for (int i = blockIdx.x * PREP_THREADS + threadIdx.x; i < npx; i += PREP_BLOCKS * PREP_THREADS) {
         const float v = tb[i];
         if (!(v >= 0.f) || isinf(v)) bad = true;
-        sf = fmaf(v, v, sf);
+        if (!roi || roi[i]) sf = fmaf(v, v, sf);
     }
     double s = sf;
     if (bad) atomicOr(err, ERR_BAD_VALUE);
@@ -80,7 +81,7 @@ __global__ void k_prep_scale(const double *part, int batch, double *scale, unsig
 // Prepared target in DFT order: Tf[b][y][x] = T[b][(y+ny/2)%ny][(x+nx/2)%nx] * scale[b],
 // rounded to float with the support T > 0 preserved.
 __global__ void k_prep_apply(const float *__restrict__ t_raw, int ny, int nx, int batch,
-                             const double *scale, float *__restrict__ tf) {
+                             const double *scale, const uint8_t *__restrict__ roi, float *__restrict__ tf) {
     const size_t npx = (size_t)ny * nx, total = npx * batch;
     for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < total;
          i += (size_t)gridDim.x * blockDim.x) {
@@ -88,7 +89,8 @@ __global__ void k_prep_apply(const float *__restrict__ t_raw, int ny, int nx, in
         const int rem = (int)(i - (size_t)b * npx);
         const int y = rem / nx, x = rem - y * nx;
         const int iy = (y + ny / 2) % ny, ix = (x + nx / 2) % nx;
-        const float v = t_raw[(size_t)b * npx + (size_t)iy * nx + ix];
+        const size_t o = (size_t)iy * nx + ix;
+        const float v = (!roi || roi[o]) ? t_raw[(size_t)b * npx + o] : 0.f;  // target restricted to the ROI
         float tv = v * (float)scale[b];
         // keep the support {T > 0} of the input exactly: a positive value whose
         // scaled float underflows becomes the smallest positive float
@@ -156,6 +158,205 @@ __global__ void k_reduce(const double *part, int iters, int batch, int stride, i
     o[2] = s[3] > 0 ? s[2] / s[3] : 0.0;
     o[3] = s[3];
     if (mse_out) mse_out[(size_t)b * iters + k] = o[0];
+}
+
+// metrics[b][k][4] of a modulated plan from its eight per-panel sums (see
+// ROW_ITER): with g0 = sum_ROI |R|^2, g1 = sum_ROI |R|^4, g2 = sum_ROI |R|^2
+// T^2, g3 = sum_ROI |R| T, g4 = sum_{ROI, T>0} |R|^2, g5 = sum |R|^2, g6 =
+// sum T^4, g7 = sum T^2 (unitary |R|), the intensity I = s |R|^2 with the
+// ROI energy match s = g7 / g0 gives
+//   intensity MSE = (s^2 g1 - 2 s g2 + g6) / n_roi,
+//   amplitude MSE = (s g0 - 2 sqrt(s) g3 + g7) / n_roi,
+//   efficiency g4 / g5, and g5 itself.
+__global__ void k_reduce_gen(const double *part, int iters, int batch, int stride, int panels,
+                             int panels_last, const unsigned long long *nroi, double *metrics, double *mse_out) {
+    const int w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+    if (w >= iters * batch) return;
+    const int k = w / batch, b = w - k * batch;
+    const int np = k == iters - 1 ? panels_last : panels;
+    const double *p = part + ((size_t)k * batch * stride + (size_t)b * np) * NMET_GEN;
+    double g[NMET_GEN] = {0, 0, 0, 0, 0, 0, 0, 0};
+    for (int q = lane; q < np; q += 32)
+        for (int m = 0; m < NMET_GEN; ++m) g[m] += p[(size_t)q * NMET_GEN + m];
+    for (int off = 16; off; off >>= 1)
+        for (int m = 0; m < NMET_GEN; ++m) g[m] += __shfl_down_sync(0xffffffffu, g[m], off);
+    if (lane) return;
+    const double s = g[0] > 0 ? g[7] / g[0] : 0.0;
+    const double inv_nroi = *nroi ? 1.0 / (double)*nroi : 0.0;
+    double *o = metrics + ((size_t)b * iters + k) * NMET;
+    o[0] = fmax(s * s * g[1] - 2.0 * s * g[2] + g[6], 0.0) * inv_nroi;
+    o[1] = fmax(s * g[0] - 2.0 * sqrt(s) * g[3] + g[7], 0.0) * inv_nroi;
+    o[2] = g[5] > 0 ? g[4] / g[5] : 0.0;
+    o[3] = g[5];
+    if (mse_out) mse_out[(size_t)b * iters + k] = o[0];
+}
+
+// Illumination of the SLM plane: E = amp exp(i (phase + c ((x - nx/2)^2 +
+// (y - ny/2)^2))) in natural order, the phase summed in double (the Fresnel
+// term reaches millions of radians).  amp / phase may be null (1 / 0);
+// a negative or non-finite amplitude or phase sets ERR_BAD_VALUE.
+__global__ void k_illum(const float *amp, const float *phase, int ny, int nx, double c, float2 *E,
+                        unsigned *err) {
+    const size_t n = (size_t)ny * nx;
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+        const int y = (int)(i / nx), x = (int)(i - (size_t)y * nx);
+        const float a = amp ? amp[i] : 1.f, f = phase ? phase[i] : 0.f;
+        if (!(a >= 0.f) || isinf(a) || !isfinite(f)) atomicOr(err, ERR_BAD_VALUE);
+        const double dx = x - nx / 2, dy = y - ny / 2;
+        double sn, cs;
+        sincos((double)f + c * (dx * dx + dy * dy), &sn, &cs);
+        E[i] = make_float2((float)(a * cs), (float)(a * sn));
+    }
+}
+
+// Region of interest: DFT-order copy of a replay-order mask and its pixel
+// count (*count zeroed before; integer sums, so the order does not matter).
+__global__ void k_roi_dft(const uint8_t *roi, int ny, int nx, uint8_t *dft, unsigned long long *count) {
+    const size_t n = (size_t)ny * nx;
+    unsigned c = 0;
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+        const int y = (int)(i / nx), x = (int)(i - (size_t)y * nx);
+        const uint8_t v = roi[(size_t)((y + ny / 2) % ny) * nx + (x + nx / 2) % nx] ? 1 : 0;
+        dft[i] = v;
+        c += v;
+    }
+    for (int off = 16; off; off >>= 1) c += __shfl_down_sync(0xffffffffu, c, off);
+    if ((threadIdx.x & 31) == 0 && c) atomicAdd(count, (unsigned long long)c);
+}
+
+// ---------------------------------------------------- evaluation of holograms
+// Metrics of given holograms over the region of interest (Section 3.1): the
+// replay intensity (any scale) I0, the raw target t (replay order).  Pass 1
+// per (block, item): sum_ROI I0, sum I0, sum_ROI t^2, sum_{ROI, t>0} I0 and
+// max_ROI t.  Pass 2 scales I = I0 / sum_ROI I0 and T = t / sqrt(sum_ROI t^2)
+// and sums over the ROI (I - T^2)^2, (sqrt I - T)^2 and the moments of
+// x = T / max T, y = sqrt(I) / max T: x, y, x^2, y^2, x y.  Threads sum in
+// float over a fixed stride, blocks in double, items in a fixed order.
+constexpr int EV_THREADS = 256, EV_BLOCKS = 64, EV_S1 = 5, EV_S2 = 7;
+
+template <int K>
+__device__ void ev_block_sum(float (&v)[K], double *dst) {
+    __shared__ double red[EV_THREADS / 32][K];
+#pragma unroll
+    for (int m = 0; m < K; ++m) {
+        float x = v[m];
+        for (int off = 16; off; off >>= 1) x += __shfl_down_sync(0xffffffffu, x, off);
+        if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5][m] = x;
+    }
+    __syncthreads();
+    if (threadIdx.x < K) {
+        double s = 0;
+        for (int w = 0; w < EV_THREADS / 32; ++w) s += red[w][threadIdx.x];
+        dst[threadIdx.x] = s;
+    }
+}
+
+__global__ void __launch_bounds__(EV_THREADS)
+k_eval1(const float *I0, const float *t, const uint8_t *roi, int npx, double *part, unsigned *err) {
+    const int b = blockIdx.y;
+    const float *Ib = I0 + (size_t)b * npx;
+    const float *tb = t ? t + (size_t)b * npx : nullptr;
+    float v[4] = {0.f, 0.f, 0.f, 0.f};
+    float tmax = 0.f;
+    bool bad = false;
+    for (int i = blockIdx.x * EV_THREADS + threadIdx.x; i < npx; i += EV_BLOCKS * EV_THREADS) {
+        const float I = Ib[i];
+        v[1] += I;
+        if (roi && !roi[i]) continue;
+        v[0] += I;
+        if (tb) {
+            const float tv = tb[i];
+            if (!(tv >= 0.f) || isinf(tv)) bad = true;
+            v[2] = fmaf(tv, tv, v[2]);
+            if (tv > 0.f) v[3] += I;
+            tmax = fmaxf(tmax, tv);
+        }
+    }
+    if (bad) atomicOr(err, ERR_BAD_VALUE);
+    double *dst = part + ((size_t)b * EV_BLOCKS + blockIdx.x) * EV_S1;
+    ev_block_sum<4>(v, dst);
+    for (int off = 16; off; off >>= 1) tmax = fmaxf(tmax, __shfl_down_sync(0xffffffffu, tmax, off));
+    __shared__ float mx[EV_THREADS / 32];
+    if ((threadIdx.x & 31) == 0) mx[threadIdx.x >> 5] = tmax;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        float m = 0.f;
+        for (int w = 0; w < EV_THREADS / 32; ++w) m = fmaxf(m, mx[w]);
+        dst[4] = m;
+    }
+}
+
+// Item totals of pass 1: {sum_ROI I0, sum I0, sum_ROI t^2, sum_{ROI,t>0} I0, max t}.
+__device__ void ev_totals(const double *part1, int b, double (&g)[EV_S1]) {
+    for (int m = 0; m < EV_S1; ++m) g[m] = 0;
+    for (int k = 0; k < EV_BLOCKS; ++k) {
+        const double *q = part1 + ((size_t)b * EV_BLOCKS + k) * EV_S1;
+        for (int m = 0; m < 4; ++m) g[m] += q[m];
+        g[4] = fmax(g[4], q[4]);
+    }
+}
+
+// I_out (optional): I0 / sum I0 (normalised over the whole field).
+__global__ void __launch_bounds__(EV_THREADS)
+k_eval2(const float *I0, const float *t, const uint8_t *roi, int npx, const double *part1, double *part2,
+        float *I_out) {
+    const int b = blockIdx.y;
+    __shared__ float sc[4];
+    if (threadIdx.x == 0) {
+        double g[EV_S1];
+        ev_totals(part1, b, g);
+        const double tsc = g[2] > 0 ? 1.0 / sqrt(g[2]) : 0.0;
+        const double tm = g[4] * tsc;
+        sc[0] = g[0] > 0 ? (float)(1.0 / g[0]) : 0.f;  // ROI energy match (sum_ROI T^2 = 1)
+        sc[1] = (float)tsc;
+        sc[2] = tm > 0 ? (float)(1.0 / tm) : 0.f;
+        sc[3] = g[1] > 0 ? (float)(1.0 / g[1]) : 0.f;
+    }
+    __syncthreads();
+    const float s = sc[0], tsc = sc[1], inv_tm = sc[2], s_all = sc[3];
+    const float *Ib = I0 + (size_t)b * npx;
+    const float *tb = t ? t + (size_t)b * npx : nullptr;
+    float v[EV_S2] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+    for (int i = blockIdx.x * EV_THREADS + threadIdx.x; i < npx; i += EV_BLOCKS * EV_THREADS) {
+        const float I0v = Ib[i];
+        if (I_out) I_out[(size_t)b * npx + i] = I0v * s_all;
+        if (!tb || (roi && !roi[i])) continue;
+        const float I = I0v * s, T = tb[i] * tsc;
+        const float d = I - T * T, am = sqrtf(I) - T;
+        const float x = T * inv_tm, y = sqrtf(I) * inv_tm;
+        v[0] = fmaf(d, d, v[0]);
+        v[1] = fmaf(am, am, v[1]);
+        v[2] += x;
+        v[3] += y;
+        v[4] = fmaf(x, x, v[4]);
+        v[5] = fmaf(y, y, v[5]);
+        v[6] = fmaf(x, y, v[6]);
+    }
+    if (part2) ev_block_sum<EV_S2>(v, part2 + ((size_t)b * EV_BLOCKS + blockIdx.x) * EV_S2);
+}
+
+// out[b][5] = {intensity MSE, amplitude MSE, efficiency, SSIM, sum |R|^2}:
+// SSIM of Section 3.1 with c1 = 0.01^2, c2 = 0.03^2 (dynamic range 1);
+// sum |R|^2 in unitary units = N sum I0 for I0 = |R|^2 / N.
+__global__ void k_eval_fin(const double *part1, const double *part2, int batch, const unsigned long long *nroi,
+                           double N, double *out) {
+    const int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= batch) return;
+    const double n_roi = nroi ? (double)*nroi : N;
+    double g[EV_S1], h[EV_S2] = {0, 0, 0, 0, 0, 0, 0};
+    ev_totals(part1, b, g);
+    for (int k = 0; k < EV_BLOCKS; ++k)
+        for (int m = 0; m < EV_S2; ++m) h[m] += part2[((size_t)b * EV_BLOCKS + k) * EV_S2 + m];
+    const double mx = h[2] / n_roi, my = h[3] / n_roi;
+    const double vx = fmax(h[4] / n_roi - mx * mx, 0.0), vy = fmax(h[5] / n_roi - my * my, 0.0);
+    const double cxy = h[6] / n_roi - mx * my;
+    const double c1 = 1e-4, c2 = 9e-4;
+    double *o = out + (size_t)b * 5;
+    o[0] = h[0] / n_roi;
+    o[1] = h[1] / n_roi;
+    o[2] = g[1] > 0 ? g[3] / g[1] : 0.0;
+    o[3] = (2 * mx * my + c1) * (2 * cxy + c2) / ((mx * mx + my * my + c1) * (vx + vy + c2));
+    o[4] = g[1] * N;
 }
 
 // ------------------------------------------------------------ registry
@@ -285,6 +486,13 @@ struct hg_plan_s {
     bool ospr_herm = false;                          // binary OSPR in Hermitian form
     float lt_start = 1.f;                            // LT window: initial side fraction, growth length
     int lt_grow = 1;
+    bool mod = false;                                // illuminated / Fresnel / amplitude SLM / ROI plan
+    float2 *illum = nullptr;                         // modulated: SLM-plane illumination, natural order
+    uint8_t *roi_rep = nullptr, *roi_dft = nullptr;  // modulated: region of interest (null: whole field)
+    unsigned long long *nroi = nullptr;              // modulated: pixels in the region of interest (device)
+    float fresnel = 0.f, amp_clip = 2.f;
+    double *ev_part = nullptr;                       // hg_evaluate: pass partials
+    float *ev_buf = nullptr;                         // hg_evaluate: replay intensity
     float *acc = nullptr;                            // adaptive OSPR: summed subframe intensities
     uint8_t *holo_tmp = nullptr;                     // adaptive OSPR: one subframe's holograms
     unsigned long long wait_ns = 2000000000ull;      // bound on a device-side wait
@@ -367,12 +575,15 @@ hg_status ensure_stage(hg_plan p, size_t bytes) {
     return HG_OK;
 }
 
+// doubles per panel in the metric partials
+int part_stride(hg_plan p) { return p->mod ? NMET_GEN : NMET; }
+
 hg_status ensure_part(hg_plan p, int iters) {
     if (p->part_iters >= iters) return HG_OK;
     if (p->part) cudaFree(p->part);
     p->part = nullptr;
     p->part_iters = 0;
-    HG_CK(cudaMalloc(&p->part, sizeof(double) * NMET * (size_t)iters * p->batch * p->ppt_max));
+    HG_CK(cudaMalloc(&p->part, sizeof(double) * part_stride(p) * (size_t)iters * p->batch * p->ppt_max));
     p->part_iters = iters;
     return HG_OK;
 }
@@ -408,6 +619,11 @@ RowArgs row_args(hg_plan p) {
     a.lt_amp = 0.f;
     a.lt_hy = p->ny;
     a.lt_hx = p->nx;
+    if (p->mod) {
+        a.gen = 1;
+        a.roi = p->roi_dft;
+        a.lt_amp = (float)p->npx;  // target carrying the replay energy of a unit-modulus hologram
+    }
     return a;
 }
 
@@ -431,6 +647,10 @@ ColArgs col_args(hg_plan p) {
     a.qscale = (float)((double)p->levels / 6.283185307179586476925286766559005768);
     a.tw = p->twy;
     a.invSqrtN = (float)(1.0 / std::sqrt((double)p->npx));
+    a.illum = p->illum;
+    a.kind = p->kind;
+    // the column pass holds N times the unitary field of a target scaled by sqrt(N)
+    a.amp_gain = (float)(1.0 / (2.0 * (double)p->amp_clip * (double)p->npx));
     return a;
 }
 
@@ -538,16 +758,20 @@ int ew_grid(hg_plan p, size_t n) {
 // Target preparation (normalise to sum T^2 = 1, move to DFT order).
 void enqueue_prep(hg_plan p, const float *target) {
     dim3 g(PREP_BLOCKS, p->batch);
-    k_prep_sum<<<g, PREP_THREADS, 0, p->stream>>>(target, (int)p->npx, p->sum_part, p->err);
+    k_prep_sum<<<g, PREP_THREADS, 0, p->stream>>>(target, (int)p->npx, p->roi_rep, p->sum_part, p->err);
     k_prep_scale<<<(p->batch + 127) / 128, 128, 0, p->stream>>>(p->sum_part, p->batch, p->scale,
                                                                  p->err);
     k_prep_apply<<<ew_grid(p, p->npx * p->batch), 256, 0, p->stream>>>(
-        target, p->ny, p->nx, p->batch, p->scale, p->tf);
+        target, p->ny, p->nx, p->batch, p->scale, p->roi_rep, p->tf);
     p->launches += 3;
 }
 
-int col_role_gs(hg_plan p) { return p->kind == HG_SLM_BINARY ? COL_GS_BIN : COL_GS_LVL; }
-int col_role_holo(hg_plan p) { return p->kind == HG_SLM_BINARY ? COL_HOLO_BIN : COL_HOLO_LVL; }
+int col_role_gs(hg_plan p) {
+    return p->mod ? COL_GS_MOD : p->kind == HG_SLM_BINARY ? COL_GS_BIN : COL_GS_LVL;
+}
+int col_role_holo(hg_plan p) {
+    return p->mod ? COL_HOLO_MOD : p->kind == HG_SLM_BINARY ? COL_HOLO_BIN : COL_HOLO_LVL;
+}
 
 bool is_ospr(int algo) { return algo == HG_OSPR || algo == HG_ADOSPR; }
 
@@ -570,7 +794,7 @@ void enqueue_loop(hg_plan p, int iters, cudaStream_t s) {
         if (p->use_pack) launch_col_pack(p, ca, s);
         else if (ca.half_in && p->use_herm_col) launch_col_herm(p, ca, s);
         else launch_col_gs(p, col_role_gs(p), ca, s);
-        ra.part = p->part + (size_t)k * p->batch * p->ppt_max * NMET;
+        ra.part = p->part + (size_t)k * p->batch * p->ppt_max * part_stride(p);
         lt_set(p, ra, k + 1);
         launch_row_iter(p, ra, s);
     }
@@ -682,16 +906,20 @@ hg_status enqueue_run(hg_plan p, const float *d_t, const float *d_ph, int iters,
         if (ca.half_in && p->use_herm_col) launch_col_herm(p, ca, p->stream);
         else launch_col_gs(p, col_role_gs(p), ca, p->stream);
         RowArgs rt = row_args(p);
-        rt.part = p->part + (size_t)(iters - 1) * p->batch * p->ppt_max * NMET;
+        rt.part = p->part + (size_t)(iters - 1) * p->batch * p->ppt_max * part_stride(p);
         if (p->tc_prec) launch_row_tc(p, ROW_TAIL, rt, p->stream);
         else launch_row(p, ROW_TAIL, rt, p->stream);
     }
     const int panels_iter = p->tc_prec ? p->ppt_tc : p->prow ? p->ppt_pipe : p->ppt;
     int panels_last = (p->tc_prec && !is_ospr(p->algo)) ? p->ppt_tc : p->ppt;
     if (p->ospr_herm) panels_last = (p->ny / 2 + p->rops->row_lines) / p->rops->row_lines;  // rows <= ny/2
-    k_reduce<<<(iters * p->batch * 32 + 127) / 128, 128, 0, p->stream>>>(
-        p->part, iters, p->batch, p->ppt_max, panels_iter, panels_last, 1.0 / (double)p->npx, p->metrics,
-        d_mo);
+    if (p->mod)
+        k_reduce_gen<<<(iters * p->batch * 32 + 127) / 128, 128, 0, p->stream>>>(
+            p->part, iters, p->batch, p->ppt_max, panels_iter, panels_last, p->nroi, p->metrics, d_mo);
+    else
+        k_reduce<<<(iters * p->batch * 32 + 127) / 128, 128, 0, p->stream>>>(
+            p->part, iters, p->batch, p->ppt_max, panels_iter, panels_last, 1.0 / (double)p->npx, p->metrics,
+            d_mo);
     p->launches++;
     HG_CK(cudaGetLastError());
     p->weights_preset = false;
@@ -821,6 +1049,9 @@ void hg_opts_default(hg_opts *o) {
     o->autotune = 1;
     o->lt_start = 0.25f;
     o->lt_grow = 10;
+    o->modulated = 0;
+    o->fresnel = 0.f;
+    o->amp_clip = 2.f;
 }
 
 int hg_supported_length(int n) { return find_ops(n) != nullptr; }
@@ -847,7 +1078,8 @@ void hg_plan_destroy(hg_plan p) {
     if (p->cap_stream) cudaStreamDestroy(p->cap_stream);
     for (cudaEvent_t e : p->prof_ev) cudaEventDestroy(e);
     void *bufs[] = {p->field, p->tf, p->w, p->part, p->metrics, p->sum_part, p->scale,
-                    p->err, p->twx, p->twy, p->lvl, p->stage, p->tc_b, p->acc, p->holo_tmp};
+                    p->err, p->twx, p->twy, p->lvl, p->stage, p->tc_b, p->acc, p->holo_tmp,
+                    p->illum, p->roi_rep, p->roi_dft, p->nroi, p->ev_part, p->ev_buf};
     for (void *b : bufs)
         if (b) cudaFree(b);
     delete p;
@@ -864,8 +1096,13 @@ hg_status hg_plan_create(hg_plan *out, int ny, int nx, int batch, hg_slm slm, hg
     if (algo != HG_GS && algo != HG_WGS && algo != HG_OSPR && algo != HG_ADOSPR && algo != HG_LT)
         return HG_ERR_INVALID_ARG;
     if (algo == HG_LT && (!(o.lt_start > 0.f) || o.lt_start > 1.f || o.lt_grow < 1)) return HG_ERR_INVALID_ARG;
-    if (slm.kind != HG_SLM_BINARY && slm.kind != HG_SLM_LLEVEL) return HG_ERR_INVALID_ARG;
-    if (slm.kind == HG_SLM_LLEVEL && (slm.levels < 2 || slm.levels > 256)) return HG_ERR_INVALID_ARG;
+    if (slm.kind != HG_SLM_BINARY && slm.kind != HG_SLM_LLEVEL && slm.kind != HG_SLM_AMPLITUDE)
+        return HG_ERR_INVALID_ARG;
+    if (slm.kind != HG_SLM_BINARY && (slm.levels < 2 || slm.levels > 256)) return HG_ERR_INVALID_ARG;
+    const bool mod = o.modulated || slm.kind == HG_SLM_AMPLITUDE || o.fresnel != 0.f;
+    if (mod && (algo != HG_GS || o.precision != 0 || o.pipeline == 1 || !std::isfinite(o.fresnel) ||
+                !(o.amp_clip > 0.f) || !std::isfinite(o.amp_clip)))
+        return HG_ERR_INVALID_ARG;
     if (is_ospr(algo) && (slm.kind != HG_SLM_BINARY || o.subframes < 1)) return HG_ERR_INVALID_ARG;
     if (o.precision < 0 || o.precision > 4) return HG_ERR_INVALID_ARG;
     if (o.precision > 0 && ((nx != 1024 && nx != 2048) || ny % (nx == 1024 ? 4 : 2) != 0 || is_ospr(algo) || algo == HG_LT))
@@ -889,6 +1126,10 @@ hg_status hg_plan_create(hg_plan *out, int ny, int nx, int batch, hg_slm slm, hg
     p->algo = algo;
     p->kind = slm.kind;
     p->levels = slm.kind == HG_SLM_BINARY ? 2 : slm.levels;
+    p->mod = mod;
+    p->fresnel = o.fresnel;
+    p->amp_clip = o.amp_clip;
+
     p->nsub = nsub;
     p->nchains = batch * nsub;
     p->seed = o.seed;
@@ -927,13 +1168,14 @@ hg_status hg_plan_create(hg_plan *out, int ny, int nx, int batch, hg_slm slm, hg
     if ((st = make_twiddles(nx, &p->twx)) != HG_OK) return fail(st);
     if ((st = make_twiddles(ny, &p->twy)) != HG_OK) return fail(st);
     {
-        // SLM level phasors exp(2 pi i q / L), q < L
+        // SLM level phasors exp(2 pi i q / L), q < L; amplitude SLM: transmittance q / (L - 1)
         const int L = p->levels;
         float2 h[256];
         const long double two_pi = 6.283185307179586476925286766559005768L;
         for (int q = 0; q < L; ++q) {
             long double a = two_pi * (long double)q / (long double)L;
-            h[q] = make_float2((float)cosl(a), (float)sinl(a));
+            h[q] = slm.kind == HG_SLM_AMPLITUDE ? make_float2((float)((double)q / (L - 1)), 0.f)
+                                                : make_float2((float)cosl(a), (float)sinl(a));
         }
         ce = cudaMalloc(&p->lvl, sizeof(float2) * L);
         if (ce == cudaSuccess) ce = cudaMemcpy(p->lvl, h, sizeof(float2) * L, cudaMemcpyHostToDevice);
@@ -952,8 +1194,25 @@ hg_status hg_plan_create(hg_plan *out, int ny, int nx, int batch, hg_slm slm, hg
         free(hb);
         if (ce != cudaSuccess) return fail(map_err(ce));
     }
-    // Pass variants are chosen (and timed) only once every buffer they touch exists.
-    if (o.pipeline != 0) {
+    if (mod) {  // uniform illumination with the Fresnel term and the whole field as the ROI until set
+        const unsigned long long all = npx;
+        ce = cudaMalloc(&p->illum, sizeof(float2) * npx);
+        if (ce == cudaSuccess) ce = cudaMalloc(&p->roi_rep, npx);
+        if (ce == cudaSuccess) ce = cudaMalloc(&p->roi_dft, npx);
+        if (ce == cudaSuccess) ce = cudaMalloc(&p->nroi, sizeof(all));
+        if (ce == cudaSuccess) ce = cudaMemset(p->roi_rep, 1, npx);
+        if (ce == cudaSuccess) ce = cudaMemset(p->roi_dft, 1, npx);
+        if (ce == cudaSuccess) ce = cudaMemcpy(p->nroi, &all, sizeof(all), cudaMemcpyHostToDevice);
+        if (ce != cudaSuccess) return fail(map_err(ce));
+        k_illum<<<ew_grid(p, npx), 256, 0, p->cap_stream>>>(nullptr, nullptr, ny, nx, (double)o.fresnel, p->illum,
+                                                            p->err);
+        ce = cudaStreamSynchronize(p->cap_stream);
+        if (ce == cudaSuccess) ce = cudaGetLastError();
+        if (ce != cudaSuccess) return fail(map_err(ce));
+    }
+    // Pass variants are chosen (and timed) only once every buffer they touch exists;
+    // modulated plans run the generic passes.
+    if (o.pipeline != 0 && !mod) {
         // TMA-fed passes: row panels need 16-byte aligned rows of T (nx % 4 == 0);
         // the column tiles need a 16-byte multiple row pitch (nx even).
         const PipeOps *rc[8], *cc[8];
@@ -1267,6 +1526,13 @@ hg_status hg_replay(hg_plan p, const uint8_t *holo, float *intensity_out) {
     ra.w = nullptr;
     ra.I_out = d_i;
     launch_row(p, ROW_AVG, ra, p->stream);
+    if (p->mod) {  // the replay energy depends on the hologram: normalise by its sum
+        if (!p->ev_part) HG_CK(cudaMalloc(&p->ev_part, sizeof(double) * (EV_S1 + EV_S2) * EV_BLOCKS * p->batch));
+        const dim3 eg(EV_BLOCKS, p->batch);
+        k_eval1<<<eg, EV_THREADS, 0, p->stream>>>(d_i, nullptr, nullptr, (int)p->npx, p->ev_part, p->err);
+        k_eval2<<<eg, EV_THREADS, 0, p->stream>>>(d_i, nullptr, nullptr, (int)p->npx, p->ev_part, nullptr, d_i);
+        p->launches += 2;
+    }
     HG_CK(cudaGetLastError());
     if (i_host) {
         HG_CK(cudaMemcpyAsync(intensity_out, d_i, ibytes, cudaMemcpyDeviceToHost, p->stream));
@@ -1295,6 +1561,101 @@ hg_status hg_get_phase(hg_plan p, float *phase_out) {
         HG_CK(cudaMemcpyAsync(phase_out, d, bytes, cudaMemcpyDeviceToHost, p->stream));
         HG_CK(cudaStreamSynchronize(p->stream));
     }
+    return HG_OK;
+}
+
+hg_status hg_set_illumination(hg_plan p, const float *amp, const float *phase) {
+    NvtxRange nv("hg_set_illumination");
+    if (!p || !p->mod) return HG_ERR_INVALID_ARG;
+    DevGuard g(p->dev);
+    const size_t bytes = sizeof(float) * p->npx, off = (bytes + 255) & ~(size_t)255;
+    const bool ah = amp && !is_device_ptr(amp), fh = phase && !is_device_ptr(phase);
+    hg_status st;
+    if ((ah || fh) && (st = ensure_stage(p, 2 * off)) != HG_OK) return st;
+    const float *da = amp, *df = phase;
+    if (ah) {
+        HG_CK(cudaMemcpyAsync(p->stage, amp, bytes, cudaMemcpyHostToDevice, p->stream));
+        da = (const float *)p->stage;
+    }
+    if (fh) {
+        float *d = (float *)((char *)p->stage + off);
+        HG_CK(cudaMemcpyAsync(d, phase, bytes, cudaMemcpyHostToDevice, p->stream));
+        df = d;
+    }
+    HG_CK(cudaMemsetAsync(p->err, 0, sizeof(unsigned), p->stream));
+    k_illum<<<ew_grid(p, p->npx), 256, 0, p->stream>>>(da, df, p->ny, p->nx, (double)p->fresnel, p->illum, p->err);
+    HG_CK(cudaGetLastError());
+    return check_err_flag(p);
+}
+
+hg_status hg_set_roi(hg_plan p, const uint8_t *roi) {
+    NvtxRange nv("hg_set_roi");
+    if (!p || !p->mod) return HG_ERR_INVALID_ARG;
+    DevGuard g(p->dev);
+    if (!roi) {
+        const unsigned long long all = p->npx;
+        HG_CK(cudaMemsetAsync(p->roi_rep, 1, p->npx, p->stream));
+        HG_CK(cudaMemsetAsync(p->roi_dft, 1, p->npx, p->stream));
+        HG_CK(cudaMemcpyAsync(p->nroi, &all, sizeof(all), cudaMemcpyHostToDevice, p->stream));
+    } else {
+        HG_CK(cudaMemcpyAsync(p->roi_rep, roi, p->npx, cudaMemcpyDefault, p->stream));
+        HG_CK(cudaMemsetAsync(p->nroi, 0, sizeof(unsigned long long), p->stream));
+        k_roi_dft<<<ew_grid(p, p->npx), 256, 0, p->stream>>>(p->roi_rep, p->ny, p->nx, p->roi_dft, p->nroi);
+        HG_CK(cudaGetLastError());
+    }
+    HG_CK(cudaStreamSynchronize(p->stream));  // the caller's buffer may be reused on return
+    return HG_OK;
+}
+
+hg_status hg_evaluate(hg_plan p, const uint8_t *holo, const float *target, double *out) {
+    NvtxRange nv("hg_evaluate");
+    if (!p || !holo || !target || !out) return HG_ERR_INVALID_ARG;
+    DevGuard g(p->dev);
+    p->launches = 0;
+    const size_t hbytes = p->npx * p->nchains, tbytes = sizeof(float) * p->npx * p->batch,
+                 obytes = sizeof(double) * 5 * p->batch;
+    auto al = [](size_t n) { return (n + 255) & ~(size_t)255; };
+    const bool h_host = !is_device_ptr(holo), t_host = !is_device_ptr(target), o_host = !is_device_ptr(out);
+    hg_status st;
+    if ((h_host || t_host || o_host) && (st = ensure_stage(p, al(hbytes) + al(tbytes) + obytes)) != HG_OK)
+        return st;
+    if (!p->ev_buf) HG_CK(cudaMalloc(&p->ev_buf, sizeof(float) * p->npx * p->batch));
+    if (!p->ev_part) HG_CK(cudaMalloc(&p->ev_part, sizeof(double) * (EV_S1 + EV_S2) * EV_BLOCKS * p->batch));
+    const uint8_t *d_h = holo;
+    const float *d_t = target;
+    double *d_o = out;
+    if (h_host) {
+        HG_CK(cudaMemcpyAsync(p->stage, holo, hbytes, cudaMemcpyHostToDevice, p->stream));
+        d_h = (const uint8_t *)p->stage;
+    }
+    if (t_host) {
+        float *d = (float *)((char *)p->stage + al(hbytes));
+        HG_CK(cudaMemcpyAsync(d, target, tbytes, cudaMemcpyHostToDevice, p->stream));
+        d_t = d;
+    }
+    if (o_host) d_o = (double *)((char *)p->stage + al(hbytes) + al(tbytes));
+    HG_CK(cudaMemsetAsync(p->err, 0, sizeof(unsigned), p->stream));
+    p->field_from_run = false;
+    ColArgs ca = col_args(p);
+    ca.items = p->nchains;
+    ca.holo = const_cast<uint8_t *>(d_h);
+    launch_col(p, col_role_holo(p), ca, p->stream);
+    RowArgs ra = row_args(p);
+    ra.nsub = p->nsub;
+    ra.T = nullptr;
+    ra.w = nullptr;
+    ra.I_out = p->ev_buf;
+    launch_row(p, ROW_AVG, ra, p->stream);
+    double *part1 = p->ev_part, *part2 = p->ev_part + (size_t)EV_S1 * EV_BLOCKS * p->batch;
+    const dim3 eg(EV_BLOCKS, p->batch);
+    k_eval1<<<eg, EV_THREADS, 0, p->stream>>>(p->ev_buf, d_t, p->roi_rep, (int)p->npx, part1, p->err);
+    k_eval2<<<eg, EV_THREADS, 0, p->stream>>>(p->ev_buf, d_t, p->roi_rep, (int)p->npx, part1, part2, nullptr);
+    k_eval_fin<<<(p->batch + 127) / 128, 128, 0, p->stream>>>(part1, part2, p->batch, p->nroi, (double)p->npx,
+                                                               d_o);
+    p->launches += 3;
+    HG_CK(cudaGetLastError());
+    if (o_host) HG_CK(cudaMemcpyAsync(out, d_o, obytes, cudaMemcpyDeviceToHost, p->stream));
+    if (h_host || t_host || o_host) return hg_sync(p);
     return HG_OK;
 }
 
@@ -1338,7 +1699,7 @@ hg_status hg_get_weights(hg_plan p, float *w_out) {
 hg_status hg_debug_step(hg_plan p, const float *target, const float *phase_in, float *h_out,
                         uint8_t *holo_out, float *replay_out, double *metrics_out) {
     NvtxRange nv("hg_debug_step");
-    if (!p || !target || !phase_in || is_ospr(p->algo)) return HG_ERR_INVALID_ARG;
+    if (!p || !target || !phase_in || is_ospr(p->algo) || p->mod) return HG_ERR_INVALID_ARG;
     for (const void *q : {(const void *)target, (const void *)phase_in, (const void *)h_out,
                           (const void *)holo_out, (const void *)replay_out,
                           (const void *)metrics_out})

@@ -21,7 +21,7 @@
 namespace hg {
 
 enum RowRole { ROW_HEAD = 0, ROW_ITER = 1, ROW_TAIL = 2, ROW_AVG = 3, ROW_ADAPT = 4, ROW_ADFIN = 5 };
-enum ColRole { COL_GS_BIN = 0, COL_GS_LVL = 1, COL_HOLO_BIN = 2, COL_HOLO_LVL = 3 };
+enum ColRole { COL_GS_BIN = 0, COL_GS_LVL = 1, COL_HOLO_BIN = 2, COL_HOLO_LVL = 3, COL_GS_MOD = 4, COL_HOLO_MOD = 5 };
 
 constexpr int NMET = 4;  // per-panel partial sums: (I-T^2)^2, (sqrt I - T)^2, |R|^2 in T>0, |R|^2
 
@@ -48,7 +48,16 @@ struct RowArgs {
     // lt_amp; the field outside stays free.  lt_amp == 0: plain GS.
     float lt_amp;
     int lt_hy, lt_hx;
+    // Modulated plans (illuminated / Fresnel / amplitude SLM, region of
+    // interest): gen != 0 scores iterations with the eight sums of
+    // gen_sums8 (the replay energy is not known in advance), and roi (DFT
+    // order, shared by the items; null = the whole field) limits the replay
+    // constraint, with lt_amp as the target scale
+    const uint8_t *roi;
+    int gen;
 };
+
+constexpr int NMET_GEN = 8;  // modulated plans: per-panel sums, see the metrics of ROW_ITER
 
 // Is DFT-order pixel (y, x) inside the Liu-Taghizadeh window?  Its replay
 // offsets from the centre are min(y, ny - y) and min(x, nx - x).
@@ -71,6 +80,12 @@ struct ColArgs {
                            // row pass rebuilds rows ny - y from the Hermitian symmetry)
     int half_in;           // the field holds rows y <= ny/2 of a field whose columns are
                            // Hermitian: read those, take row ny - y as conj(row y)
+    // MOD roles: illumination E of the SLM plane (natural order [ny][nx]),
+    // SLM kind (0 binary phase, 1 L-level phase, 2 amplitude with lvl[q] =
+    // q / (L - 1)) and the amplitude map's gain 1 / (2 clip N)
+    const float2 *illum;
+    int kind;
+    float amp_gain;
 };
 
 // Sum four per-thread float partials over the block in a fixed order (lanes
@@ -154,7 +169,7 @@ __device__ __forceinline__ void row_body(const RowArgs &a) {
                 const int ix = (x + NX / 2) % NX;
                 float amp = Tr[x];
                 if (wr) amp *= wr[x];
-                if (a.lt_amp > 0.f && !lt_in(a, yc, x)) amp = 0.f;
+                if (a.lt_amp > 0.f) amp = lt_in(a, yc, x) ? amp * a.lt_amp : 0.f;
                 float s, c;
                 if (a.phase) {
                     // phase in half-turns: the reduction is exact, no large-argument path
@@ -201,21 +216,43 @@ __device__ __forceinline__ void row_body(const RowArgs &a) {
             const float *Tr = a.T + ((size_t)item * ny + yc) * NX;
             float *wr = a.w ? a.w + ((size_t)item * ny + yc) * NX : nullptr;
             float acc0 = 0.f, acc1 = 0.f, acc2 = 0.f, acc3 = 0.f;
+            float acc4 = 0.f, acc5 = 0.f, acc6 = 0.f, acc7 = 0.f;
+            const uint8_t *roir = a.roi ? a.roi + (size_t)yc * NX : nullptr;
             static_for<0, E>([&](auto ec) {
                 constexpr int e = decltype(ec)::value;
                 const int x = t + TL * e;
                 const float Tv = act ? Tr[x] : 0.f;
                 const float2 r = v[e];
                 const float m2 = fmaf(r.x, r.x, r.y * r.y);  // |R|^2 before the 1/N scale
-                const float I = m2 * a.invN2;                 // normalised intensity
-                const float d = I - Tv * Tv;
-                const float am = sqrtf(I) - Tv;
                 const float e2 = m2 * a.invN;                 // unitary |R|^2
-                if (act) {
-                    acc0 = fmaf(d, d, acc0);
-                    acc1 = fmaf(am, am, acc1);
-                    acc3 += e2;
-                    if (Tv > 0.f) acc2 += e2;
+                const bool in = !roir || roir[x] != 0;
+                if (a.gen) {
+                    // sums over the ROI of e2, e2^2, e2 T^2, sqrt(e2) T and e2 on T > 0,
+                    // e2 over the field, T^4 and T^2; the intensity scale (ROI
+                    // energy match) is applied when the panels are combined
+                    if (act) {
+                        acc5 += e2;
+                        if (in) {
+                            const float t2 = Tv * Tv;
+                            acc0 += e2;
+                            acc1 = fmaf(e2, e2, acc1);
+                            acc2 = fmaf(e2, t2, acc2);
+                            acc3 = fmaf(sqrtf(e2), Tv, acc3);
+                            if (Tv > 0.f) acc4 += e2;
+                            acc6 = fmaf(t2, t2, acc6);
+                            acc7 += t2;
+                        }
+                    }
+                } else {
+                    const float I = m2 * a.invN2;  // normalised intensity
+                    const float d = I - Tv * Tv;
+                    const float am = sqrtf(I) - Tv;
+                    if (act) {
+                        acc0 = fmaf(d, d, acc0);
+                        acc1 = fmaf(am, am, acc1);
+                        acc3 += e2;
+                        if (Tv > 0.f) acc2 += e2;
+                    }
                 }
                 const float rs = m2 > 0.f ? rsqrtf(m2) : 0.f;
                 float wv = 1.f;
@@ -225,8 +262,8 @@ __device__ __forceinline__ void row_body(const RowArgs &a) {
                     if (act) wr[x] = wv;
                 }
                 if constexpr (ROLE == ROW_ITER) {
-                    if (a.lt_amp > 0.f && !lt_in(a, yc, x)) {
-                        v[e] = r;  // outside the window: left free
+                    if (a.lt_amp > 0.f && (!in || !lt_in(a, yc, x))) {
+                        v[e] = r;  // outside the window / region of interest: left free
                     } else {
                         const float g = (a.lt_amp > 0.f ? a.lt_amp : 1.f) * Tv * wv;
                         v[e] = m2 > 0.f ? make_float2(g * r.x * rs, g * r.y * rs) : make_float2(g, 0.f);
@@ -250,9 +287,16 @@ __device__ __forceinline__ void row_body(const RowArgs &a) {
                     });
                 }
             }
-            if (a.part)
-                block_sum4(acc0, acc1, acc2, acc3, red,
-                           a.part + ((size_t)item * ppt + pan) * NMET, Cfg::THREADS);
+            if (a.part) {
+                if (a.gen) {
+                    double *dst = a.part + ((size_t)item * ppt + pan) * NMET_GEN;
+                    block_sum4(acc0, acc1, acc2, acc3, red, dst, Cfg::THREADS);
+                    block_sum4(acc4, acc5, acc6, acc7, red, dst + NMET, Cfg::THREADS);
+                } else {
+                    block_sum4(acc0, acc1, acc2, acc3, red,
+                               a.part + ((size_t)item * ppt + pan) * NMET, Cfg::THREADS);
+                }
+            }
         } else if constexpr (ROLE == ROW_ADAPT || ROLE == ROW_ADFIN) {
             // adaptive OSPR: replay of the subframe just quantised, its normalised
             // intensity added to the running sum; ADAPT then forms the next
@@ -406,7 +450,7 @@ __global__ void __launch_bounds__(P::TL *C) k_col(const ColArgs a) {
         const int xc = act ? x : nx - 1;
         const size_t base = (size_t)item * NY * nx;
         float2 v[E];
-        if constexpr (ROLE == COL_GS_BIN || ROLE == COL_GS_LVL) {
+        if constexpr (ROLE == COL_GS_BIN || ROLE == COL_GS_LVL || ROLE == COL_GS_MOD) {
             const float2 *fc = a.field + base + xc;
             static_for<0, E>([&](auto ec) {
                 constexpr int e = decltype(ec)::value;
@@ -419,7 +463,33 @@ __global__ void __launch_bounds__(P::TL *C) k_col(const ColArgs a) {
                 const float2 h = v[e];
                 int q;
                 float2 ph;
-                if constexpr (ROLE == COL_GS_BIN) {
+                if constexpr (ROLE == COL_GS_MOD) {
+                    // the level nearest h / E: phase SLMs decide on h conj(E), the
+                    // amplitude SLM on the least-squares transmittance
+                    // Re(h conj E) / |E|^2 mapped to [0, L - 1]; the light leaving
+                    // the SLM is E times the level
+                    const float2 E = __ldg(a.illum + (size_t)(t + TL * e) * nx + xc);
+                    const float hr = fmaf(h.x, E.x, h.y * E.y), hi = fmaf(h.y, E.x, -h.x * E.y);
+                    if (a.kind == 2) {
+                        const float e2 = fmaf(E.x, E.x, E.y * E.y);
+                        const float m = e2 > 0.f ? hr / e2 : 0.f;
+                        const float lv = (float)(a.levels - 1) * fmaf(m, a.amp_gain, 0.5f);
+                        q = (int)roundf(fminf(fmaxf(lv, 0.f), (float)(a.levels - 1)));
+                        const float tr = __ldg(a.lvl + q).x;
+                        ph = make_float2(E.x * tr, E.y * tr);
+                    } else {
+                        float2 l;
+                        if (a.kind == 0) {
+                            q = hr >= 0.f ? 0 : 1;
+                            l = make_float2(q ? -1.f : 1.f, 0.f);
+                        } else {
+                            q = (int)roundf(atan2f(hi, hr) * a.qscale) % a.levels;
+                            if (q < 0) q += a.levels;
+                            l = __ldg(a.lvl + q);
+                        }
+                        ph = make_float2(E.x * l.x - E.y * l.y, fmaf(E.x, l.y, E.y * l.x));
+                    }
+                } else if constexpr (ROLE == COL_GS_BIN) {
                     q = h.x >= 0.f ? 0 : 1;
                     ph = make_float2(q ? -1.f : 1.f, 0.f);
                 } else {
@@ -438,8 +508,16 @@ __global__ void __launch_bounds__(P::TL *C) k_col(const ColArgs a) {
             static_for<0, E>([&](auto ec) {
                 constexpr int e = decltype(ec)::value;
                 const int q = hc[(t + TL * e) * nx];
-                if constexpr (ROLE == COL_HOLO_BIN) v[e] = make_float2(q ? -1.f : 1.f, 0.f);
-                else v[e] = __ldg(a.lvl + (q < a.levels ? q : 0));
+                if constexpr (ROLE == COL_HOLO_BIN) {
+                    v[e] = make_float2(q ? -1.f : 1.f, 0.f);
+                } else if constexpr (ROLE == COL_HOLO_MOD) {
+                    const float2 E = __ldg(a.illum + (size_t)(t + TL * e) * nx + xc);
+                    const float2 l = a.kind == 0 ? make_float2(q ? -1.f : 1.f, 0.f)
+                                                 : __ldg(a.lvl + (q < a.levels ? q : 0));
+                    v[e] = make_float2(E.x * l.x - E.y * l.y, fmaf(E.x, l.y, E.y * l.x));
+                } else {
+                    v[e] = __ldg(a.lvl + (q < a.levels ? q : 0));
+                }
             });
         }
         line_fft<P, -1, C>(v, smb, a.tw, t, sync);
@@ -491,6 +569,8 @@ struct OpsImpl {
         set((const void *)k_col<P, COL_GS_LVL, C>, CC::SMEM);
         set((const void *)k_col<P, COL_HOLO_BIN, C>, CC::SMEM);
         set((const void *)k_col<P, COL_HOLO_LVL, C>, CC::SMEM);
+        set((const void *)k_col<P, COL_GS_MOD, C>, CC::SMEM);
+        set((const void *)k_col<P, COL_HOLO_MOD, C>, CC::SMEM);
         if (e != cudaSuccess) return e;
         int rb = 0, cb = 0;
         e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&rb, k_row<P, ROW_ITER, LINES>,
@@ -528,6 +608,8 @@ struct OpsImpl {
             case COL_GS_BIN: k_col<P, COL_GS_BIN, C><<<grid, CC::THREADS, CC::SMEM, s>>>(a); break;
             case COL_GS_LVL: k_col<P, COL_GS_LVL, C><<<grid, CC::THREADS, CC::SMEM, s>>>(a); break;
             case COL_HOLO_BIN: k_col<P, COL_HOLO_BIN, C><<<grid, CC::THREADS, CC::SMEM, s>>>(a); break;
+            case COL_GS_MOD: k_col<P, COL_GS_MOD, C><<<grid, CC::THREADS, CC::SMEM, s>>>(a); break;
+            case COL_HOLO_MOD: k_col<P, COL_HOLO_MOD, C><<<grid, CC::THREADS, CC::SMEM, s>>>(a); break;
             default: k_col<P, COL_HOLO_LVL, C><<<grid, CC::THREADS, CC::SMEM, s>>>(a); break;
         }
     }

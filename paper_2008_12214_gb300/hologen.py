@@ -16,7 +16,7 @@ import torch
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libhologen.so")
 
-HG_SLM_BINARY, HG_SLM_LLEVEL = 0, 1
+HG_SLM_BINARY, HG_SLM_LLEVEL, HG_SLM_AMPLITUDE = 0, 1, 2
 HG_GS, HG_WGS, HG_OSPR, HG_ADOSPR, HG_LT = 0, 1, 2, 3, 4
 NMET = 4
 
@@ -34,7 +34,8 @@ class HgError(RuntimeError):
 class hg_opts(ctypes.Structure):
     _fields_ = [("stream", ctypes.c_void_p), ("seed", ctypes.c_uint64), ("subframes", ctypes.c_int),
                 ("precision", ctypes.c_int), ("use_graph", ctypes.c_int), ("pipeline", ctypes.c_int),
-                ("autotune", ctypes.c_int), ("lt_start", ctypes.c_float), ("lt_grow", ctypes.c_int)]
+                ("autotune", ctypes.c_int), ("lt_start", ctypes.c_float), ("lt_grow", ctypes.c_int),
+                ("modulated", ctypes.c_int), ("fresnel", ctypes.c_float), ("amp_clip", ctypes.c_float)]
 
 
 class hg_slm(ctypes.Structure):
@@ -61,6 +62,9 @@ def lib():
         L.hg_get_metrics.argtypes = [P, P, Z]
         L.hg_replay.argtypes = [P, P, P]
         L.hg_get_phase.argtypes = [P, P]
+        L.hg_set_illumination.argtypes = [P, P, P]
+        L.hg_set_roi.argtypes = [P, P]
+        L.hg_evaluate.argtypes = [P, P, P, P]
         L.hg_set_weights.argtypes = [P, P]
         L.hg_get_weights.argtypes = [P, P]
         L.hg_debug_step.argtypes = [P, P, P, P, P, P, P]
@@ -115,7 +119,8 @@ def lib():
         L.hg_status_string.argtypes = [I]
         L.hg_status_string.restype = ctypes.c_char_p
         for name in ("hg_plan_create", "hg_run", "hg_get_metrics", "hg_replay", "hg_get_phase",
-                     "hg_set_weights", "hg_get_weights", "hg_debug_step", "hg_sync"):
+                     "hg_set_weights", "hg_get_weights", "hg_debug_step", "hg_sync", "hg_set_illumination",
+                     "hg_set_roi", "hg_evaluate"):
             getattr(L, name).restype = I
         _lib = L
     return _lib
@@ -150,7 +155,7 @@ def hg_status_string(st: int) -> str:
 
 def hg_plan_create(ny, nx, batch, slm_kind=HG_SLM_BINARY, levels=2, algo=HG_GS, stream=None,
                    seed=0, subframes=24, precision=0, use_graph=True, pipeline=-1, autotune=True,
-                   lt_start=None, lt_grow=None):
+                   lt_start=None, lt_grow=None, modulated=False, fresnel=0.0, amp_clip=None):
     o = hg_opts()
     lib().hg_opts_default(ctypes.byref(o))
     if stream is None and torch.cuda.is_available():
@@ -166,6 +171,10 @@ def hg_plan_create(ny, nx, batch, slm_kind=HG_SLM_BINARY, levels=2, algo=HG_GS, 
         o.lt_start = float(lt_start)
     if lt_grow is not None:
         o.lt_grow = int(lt_grow)
+    o.modulated = 1 if modulated else 0
+    o.fresnel = float(fresnel)
+    if amp_clip is not None:
+        o.amp_clip = float(amp_clip)
     h = ctypes.c_void_p()
     _ck(lib().hg_plan_create(ctypes.byref(h), int(ny), int(nx), int(batch),
                              hg_slm(int(slm_kind), int(levels)), int(algo), ctypes.byref(o)),
@@ -206,6 +215,20 @@ def hg_replay(plan, holo, intensity_out):
 
 def hg_get_phase(plan, phase_out):
     _ck(lib().hg_get_phase(plan, _ptr(phase_out, torch.float32, name="phase_out")), "hg_get_phase")
+
+
+def hg_set_illumination(plan, amp=None, phase=None):
+    _ck(lib().hg_set_illumination(plan, _ptr(amp, torch.float32, name="amp"),
+                                  _ptr(phase, torch.float32, name="phase")), "hg_set_illumination")
+
+
+def hg_set_roi(plan, roi=None):
+    _ck(lib().hg_set_roi(plan, _ptr(roi, torch.uint8, name="roi")), "hg_set_roi")
+
+
+def hg_evaluate(plan, holo, target, out):
+    _ck(lib().hg_evaluate(plan, _ptr(holo, torch.uint8, name="holo"), _ptr(target, torch.float32, name="target"),
+                          _ptr(out, torch.float64, name="out")), "hg_evaluate")
 
 
 def hg_set_weights(plan, w):
@@ -343,6 +366,18 @@ class Plan:
 
     def sync(self):
         hg_sync(self.h)
+
+    def set_illumination(self, amp=None, phase=None):
+        hg_set_illumination(self.h, amp, phase)
+
+    def set_roi(self, roi=None):
+        hg_set_roi(self.h, roi)
+
+    def evaluate(self, holo, target, device="cuda"):
+        """[batch][5] {intensity MSE, amplitude MSE, efficiency, SSIM, sum |R|^2}."""
+        out = torch.empty((self.batch, 5), dtype=torch.float64, device=device)
+        hg_evaluate(self.h, holo, target, out)
+        return out
 
 
 # ------------------------------------------------------------------ warm start

@@ -1,0 +1,212 @@
+"""Modulated plans (illumination, Fresnel phase, amplitude SLMs, region of
+interest) and hg_evaluate against the FP64 oracle, through the C ABI
+(marked gpu).
+
+Tolerances: holograms after two iterations all but 0.1% of pixels (decision
+boundaries: the GPU decides in FP32); per-iteration metrics after two
+iterations relative 1e-4; after six iterations within 2% (a flipped boundary
+pixel is carried forward, most of all outside a region of interest, where
+nothing resets the field); hg_evaluate's metrics on the same holograms
+relative 1e-5."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_2008_12214_gb300 import hologen as hg
+from paper_2008_12214_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+DEV = torch.device("cuda:0")
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    import __graft_entry__
+    __graft_entry__.build()
+
+
+def okind(kind):
+    return {hg.HG_SLM_BINARY: oracle.SLM_BINARY, hg.HG_SLM_LLEVEL: oracle.SLM_LLEVEL,
+            hg.HG_SLM_AMPLITUDE: oracle.SLM_AMPLITUDE}[kind]
+
+
+def gaussian_amp(ny, nx, frac=0.4):
+    y, x = np.mgrid[0:ny, 0:nx]
+    return np.exp(-((x - nx / 2) ** 2 / (frac * nx) ** 2 + (y - ny / 2) ** 2 / (frac * ny) ** 2)).astype(np.float32)
+
+
+def tilt_phase(ny, nx):
+    y, x = np.mgrid[0:ny, 0:nx]
+    return (0.3 * x + 0.17 * y + 0.5 * np.sin(x / 7.0)).astype(np.float32)
+
+
+def rect_roi(ny, nx):
+    roi = np.zeros((ny, nx), np.uint8)
+    roi[ny // 8: ny - ny // 5, nx // 6: nx - nx // 9] = 1
+    return roi
+
+
+def disc_roi(ny, nx):
+    y, x = np.mgrid[0:ny, 0:nx]
+    return (((y - ny / 2) ** 2 + (x - nx / 2) ** 2) <= (0.35 * min(ny, nx)) ** 2).astype(np.uint8)
+
+
+# (ny, nx, kind, levels, fresnel, illumination, roi)
+CASES = [
+    (64, 64, hg.HG_SLM_BINARY, 2, 0.05, "gauss+tilt", None),
+    (64, 64, hg.HG_SLM_LLEVEL, 8, 2 * np.pi * 3 / 8, None, "rect"),
+    (64, 64, hg.HG_SLM_AMPLITUDE, 2, 0.0, None, None),
+    (64, 64, hg.HG_SLM_AMPLITUDE, 16, 0.01, "gauss", "rect"),
+    (128, 256, hg.HG_SLM_LLEVEL, 4, 0.003, "tilt", "disc"),
+    (256, 256, hg.HG_SLM_AMPLITUDE, 4, 0.002, None, "disc"),
+    (512, 512, hg.HG_SLM_BINARY, 2, 0.0, "gauss", "rect"),
+]
+
+
+def case_id(c):
+    ny, nx, kind, levels, f, il, roi = c
+    return "%dx%d-k%d-L%d-f%g-%s-%s" % (ny, nx, kind, levels, f, il, roi)
+
+
+def setup_case(c):
+    ny, nx, kind, levels, f, il, roi_kind = c
+    f32 = float(np.float32(f))
+    amp = gaussian_amp(ny, nx) if il and "gauss" in il else None
+    ph = tilt_phase(ny, nx) if il and "tilt" in il else None
+    roi = {"rect": rect_roi, "disc": disc_roi, None: lambda a, b: None}[roi_kind](ny, nx)
+    E = oracle.illumination(ny, nx, amp, ph, fresnel=f32)
+    return f32, amp, ph, roi, E
+
+
+def run_gpu(c, t, ph0, iters, amp, ph, roi, f32):
+    ny, nx, kind, levels = c[:4]
+    batch = t.shape[0]
+    plan = hg.Plan(ny, nx, batch, kind, levels, hg.HG_GS, modulated=True, fresnel=f32)
+    try:
+        plan.set_illumination(None if amp is None else torch.from_numpy(amp).to(DEV),
+                              None if ph is None else torch.from_numpy(ph).to(DEV))
+        plan.set_roi(None if roi is None else torch.from_numpy(roi).to(DEV))
+        holo = torch.empty((batch, ny, nx), dtype=torch.uint8, device=DEV)
+        mse = torch.empty((batch, iters), dtype=torch.float64, device=DEV)
+        T = torch.from_numpy(t).to(DEV)
+        plan.run(T, torch.from_numpy(ph0).to(DEV), iters, holo, mse)
+        plan.sync()
+        met = plan.metrics().cpu().numpy()
+        ev = plan.evaluate(holo, T)
+        plan.sync()
+        assert hg.hg_plan_variant(plan.h, 0) == "generic"
+        return holo.cpu().numpy(), mse.cpu().numpy(), met, ev.cpu().numpy()
+    finally:
+        plan.close()
+
+
+@pytest.mark.parametrize("c", CASES, ids=case_id)
+def test_modulated_gs_matches_oracle(c):
+    ny, nx, kind, levels = c[:4]
+    f32, amp, ph, roi, E = setup_case(c)
+    batch = 2
+    t = synth.targets(batch, ny, nx, 5100)
+    ph0 = synth.init_phases(batch, ny, nx, 5100)
+    holo2, mse2, met2, ev2 = run_gpu(c, t, ph0, 2, amp, ph, roi, f32)
+    _, mse6, _, _ = run_gpu(c, t, ph0, 6, amp, ph, roi, f32)
+    for b in range(batch):
+        o2 = oracle.modulated_run(t[b], ph0[b].astype(np.float64), 2, okind(kind), levels, E=E, roi=roi)
+        bad = np.mean(holo2[b] != o2["holo"])
+        assert bad <= 1e-3, bad
+        assert np.allclose(mse2[b], o2["mse"], rtol=1e-4, atol=0), (mse2[b], o2["mse"])
+        assert np.allclose(met2[b, :, 1], o2["amp_mse"], rtol=1e-4, atol=0)
+        assert np.allclose(met2[b, :, 2], o2["eff"], rtol=1e-4, atol=0)
+        assert np.allclose(met2[b, :, 3], o2["sum_r2"], rtol=1e-4, atol=0)
+        # hg_evaluate of the GPU's own last hologram against the oracle's replay of it
+        oe = oracle.evaluate(holo2[b], t[b], okind(kind), levels, E=E, roi=roi)
+        assert np.allclose(ev2[b], oe, rtol=1e-5, atol=1e-12), (ev2[b], oe)
+        o6 = oracle.modulated_run(t[b], ph0[b].astype(np.float64), 6, okind(kind), levels, E=E, roi=roi)
+        assert np.allclose(mse6[b], o6["mse"], rtol=2e-2, atol=0), (mse6[b], o6["mse"])
+
+
+@pytest.mark.parametrize("kind,levels,algo", [(hg.HG_SLM_BINARY, 2, hg.HG_GS), (hg.HG_SLM_LLEVEL, 16, hg.HG_WGS),
+                                              (hg.HG_SLM_BINARY, 2, hg.HG_OSPR)])
+def test_evaluate_on_plain_plans_matches_oracle(kind, levels, algo):
+    """hg_evaluate on unmodulated plans: the whole field, uniform light; an
+    OSPR plan scores the time average of its subframes."""
+    ny, nx, batch, nsub = 128, 64, 3, 4
+    rng = np.random.default_rng(77)
+    t = synth.targets(batch, ny, nx, 6000)
+    kw = dict(subframes=nsub) if algo == hg.HG_OSPR else {}
+    plan = hg.Plan(ny, nx, batch, kind, levels, algo, **kw)
+    try:
+        shape = (batch, nsub, ny, nx) if algo == hg.HG_OSPR else (batch, ny, nx)
+        holo = rng.integers(0, levels, shape).astype(np.uint8)
+        ev = plan.evaluate(torch.from_numpy(holo).to(DEV), torch.from_numpy(t).to(DEV))
+        plan.sync()
+        ev = ev.cpu().numpy()
+    finally:
+        plan.close()
+    for b in range(batch):
+        if algo == hg.HG_OSPR:
+            R2 = sum(np.abs(oracle.replay_field(holo[b, n])) ** 2 for n in range(nsub)) / nsub
+            oe = oracle.roi_metrics(R2, oracle.roi_target(t[b]))
+        else:
+            oe = oracle.evaluate(holo[b], t[b], okind(kind), levels)
+        assert np.allclose(ev[b], oe, rtol=1e-5, atol=1e-12), (ev[b], oe)
+
+
+def test_modulated_replay_sums_to_one():
+    ny, nx = 64, 128
+    f32, amp, ph, roi, E = setup_case((ny, nx, hg.HG_SLM_AMPLITUDE, 8, 0.02, "gauss+tilt", "rect"))
+    rng = np.random.default_rng(3)
+    holo = rng.integers(0, 8, (2, ny, nx)).astype(np.uint8)
+    plan = hg.Plan(ny, nx, 2, hg.HG_SLM_AMPLITUDE, 8, hg.HG_GS, fresnel=f32)
+    try:
+        plan.set_illumination(torch.from_numpy(amp).to(DEV), torch.from_numpy(ph).to(DEV))
+        I = torch.empty((2, ny, nx), dtype=torch.float32, device=DEV)
+        hg.hg_replay(plan.h, torch.from_numpy(holo).to(DEV), I)
+        plan.sync()
+        I = I.cpu().numpy().astype(np.float64)
+    finally:
+        plan.close()
+    for b in range(2):
+        R = np.fft.fftshift(oracle.fft2(oracle.modulated_field(holo[b], E, oracle.SLM_AMPLITUDE, 8), -1))
+        P = np.abs(R) ** 2
+        assert abs(I[b].sum() - 1) < 1e-5
+        assert np.abs(I[b] - P / P.sum()).max() <= 1e-5 * (P / P.sum()).max()
+
+
+def test_modulated_plan_rules():
+    t = torch.from_numpy(synth.targets(1, 64, 64, 1)).to(DEV)
+    for kw in (dict(algo=hg.HG_WGS, modulated=True), dict(algo=hg.HG_GS, modulated=True, precision=4),
+               dict(algo=hg.HG_GS, fresnel=float("nan")), dict(algo=hg.HG_GS, slm_kind=hg.HG_SLM_AMPLITUDE,
+                                                              levels=1)):
+        algo = kw.pop("algo")
+        kind = kw.pop("slm_kind", hg.HG_SLM_BINARY)
+        levels = kw.pop("levels", 2)
+        with pytest.raises(hg.HgError):
+            hg.Plan(64, 64, 1, kind, levels, algo, **kw)
+    plain = hg.Plan(64, 64, 1)
+    try:
+        with pytest.raises(hg.HgError):
+            plain.set_roi(None)
+        with pytest.raises(hg.HgError):
+            plain.set_illumination(None, None)
+    finally:
+        plain.close()
+    plan = hg.Plan(64, 64, 1, hg.HG_SLM_LLEVEL, 4, hg.HG_GS, modulated=True)
+    try:
+        bad = torch.ones((64, 64), dtype=torch.float32, device=DEV)
+        bad[3, 5] = -1
+        with pytest.raises(hg.HgError):
+            plan.set_illumination(bad, None)
+        plan.set_illumination(None, None)
+        # a region of interest that misses the target: zero energy at the run
+        roi = torch.zeros((64, 64), dtype=torch.uint8, device=DEV)
+        plan.set_roi(roi)
+        plan.run(t, None, 2)
+        with pytest.raises(hg.HgError):
+            plan.sync()
+        plan.set_roi(None)
+        plan.run(t, None, 2)
+        plan.sync()
+    finally:
+        plan.close()
