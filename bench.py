@@ -58,12 +58,13 @@ def parse():
     ap.add_argument("--pipeline", type=int, default=-1)
     ap.add_argument("--autotune", type=int, default=1, help="1 tune, 0 first variant, 2+k variant k")
     ap.add_argument("--precision", type=int, default=0,
-                    help="0 FP32 engine; 1..4 tensor-core row pass (FP16 hi+lo, FP16, BF16 hi+lo, BF16)")
+                    help="0 FP32 engine; 1..4 tensor-core row pass (FP16 hi+lo, FP16, BF16 hi+lo, BF16); "
+                         "fresnel workload: 0 binary phase SLM, 1 16-level amplitude SLM")
     ap.add_argument("--batch", type=int, default=BATCH, help="targets per rank (profiling runs)")
     ap.add_argument("--quick", action="store_true", help="skip the e2e and CPU-baseline legs")
     ap.add_argument("--pairs", type=int, default=2048, help="warmstart: training pairs")
     ap.add_argument("--heldout", type=int, default=64, help="warmstart: held-out targets")
-    ap.add_argument("--workload", choices=["headline", "ospr", "adospr", "mixed", "warmstart", "gs2048", "wgs256"],
+    ap.add_argument("--workload", choices=["headline", "ospr", "adospr", "mixed", "warmstart", "gs2048", "wgs256", "fresnel", "lt"],
                     default="headline",
                     help="headline: binary GS 1024^2 x 64 (the benchmark line); ospr: 8 targets x 24 "
                          "subframes of 1024^2; mixed: 16 targets each of 512^2, 1024^2, 2048^2, 1080x1920")
@@ -306,6 +307,66 @@ def run_side_workload(args):
         out = dict(workload="wgs_llevel256_1024x1024_batch1", ms_per_run=ms, iterations_per_s=iters / (ms / 1e3),
                    final_mse=float(met[-1, 0]), final_amplitude_mse=float(met[-1, 1]),
                    diffraction_efficiency=float(met[-1, 2]), mse_iter_1_10_100=[float(met[i, 0]) for i in (0, 9, 99)],
+                   row_variant=hg.hg_plan_variant(plan.h, 0), column_variant=hg.hg_plan_variant(plan.h, 1))
+        plan.close()
+    elif args.workload == "lt":
+        # Liu-Taghizadeh GS, 64 binary holograms of 1024^2, window 0.25 -> 1 over 10 constraints
+        B, n = 64, 1024
+        T = torch.from_numpy(synth.targets(B, n, n, 7100)).to(dev)
+        P = torch.from_numpy(synth.init_phases(B, n, n, 7100)).to(dev)
+        mse = torch.empty((B, args.iters), dtype=torch.float64, device=dev)
+        plan = hg.Plan(n, n, B, hg.HG_SLM_BINARY, 2, hg.HG_LT, lt_start=0.25, lt_grow=10)
+        for _ in range(args.warmup):
+            plan.run(T, P, args.iters, None, mse)
+        plan.sync()
+        e0.record(s0)
+        for _ in range(args.steps):
+            plan.run(T, P, args.iters, None, mse)
+        e1.record(s0)
+        plan.sync()
+        ms = e0.elapsed_time(e1) / args.steps
+        it_ms = ms / args.iters
+        out = dict(workload="lt_binary_1024x1024_batch64", ms_per_step=ms, iters_per_step=args.iters,
+                   batched_iterations_per_s=1e3 / it_ms, gbs_at_36=36.0 * B * n * n / (it_ms / 1e3) / 1e9,
+                   final_mse_mean=float(mse[:, -1].mean().item()),
+                   row_variant=hg.hg_plan_variant(plan.h, 0), column_variant=hg.hg_plan_variant(plan.h, 1))
+        plan.close()
+    elif args.workload == "fresnel":
+        # modulated GS: 64 Fresnel holograms of 1024^2 (quadratic phase pi dx^2 / (lambda z) for
+        # 8 um pixels, 532 nm, 0.5 m), Gaussian illumination, disc region of interest, binary
+        # phase or 16-level amplitude SLM (--precision 0 / 1 selects), 50 iterations
+        B, n = 64, 1024
+        c = float(np.pi * (8e-6) ** 2 / (532e-9 * 0.5))
+        amp_slm = args.precision == 1
+        kind, levels = (hg.HG_SLM_AMPLITUDE, 16) if amp_slm else (hg.HG_SLM_BINARY, 2)
+        y, x = np.mgrid[0:n, 0:n]
+        A = np.exp(-((x - n / 2) ** 2 + (y - n / 2) ** 2) / (2 * (0.3 * n) ** 2)).astype(np.float32)
+        roi = (((y - n / 2) ** 2 + (x - n / 2) ** 2) <= (0.35 * n) ** 2).astype(np.uint8)
+        T = torch.from_numpy(synth.targets(B, n, n, 7000)).to(dev)
+        P = torch.from_numpy(synth.init_phases(B, n, n, 7000)).to(dev)
+        mse = torch.empty((B, args.iters), dtype=torch.float64, device=dev)
+        holo = torch.empty((B, n, n), dtype=torch.uint8, device=dev)
+        plan = hg.Plan(n, n, B, kind, levels, hg.HG_GS, fresnel=c, modulated=True)
+        plan.set_illumination(torch.from_numpy(A).to(dev), None)
+        plan.set_roi(torch.from_numpy(roi).to(dev))
+        for _ in range(args.warmup):
+            plan.run(T, P, args.iters, holo, mse)
+        plan.sync()
+        e0.record(s0)
+        for _ in range(args.steps):
+            plan.run(T, P, args.iters, holo, mse)
+        e1.record(s0)
+        plan.sync()
+        ms = e0.elapsed_time(e1) / args.steps
+        ev = plan.evaluate(holo, T).cpu().numpy()
+        it_ms = ms / args.iters
+        px = B * n * n
+        # generic passes: row 8 + 8 (field) + 4 (T) + 1 (ROI); column 8 + 8 (field) + 8 (illumination)
+        out = dict(workload="fresnel_%s_1024x1024_batch64" % ("amplitude16" if amp_slm else "binary"),
+                   ms_per_step=ms, iters_per_step=args.iters, batched_iterations_per_s=1e3 / it_ms,
+                   algorithmic_gbs_at_45=45.0 * px / (it_ms / 1e3) / 1e9,
+                   final_roi_mse_mean=float(mse[:, -1].mean().item()), roi_ssim_mean=float(ev[:, 3].mean()),
+                   efficiency_mean=float(ev[:, 2].mean()), fresnel_rad_per_px2=c,
                    row_variant=hg.hg_plan_variant(plan.h, 0), column_variant=hg.hg_plan_variant(plan.h, 1))
         plan.close()
     elif args.workload == "gs2048":
