@@ -15,6 +15,10 @@ the illumination / Fresnel / amplitude-SLM / region-of-interest functions
 ``tests/test_oracle_modulation.py`` (hand-worked 4x4 ROI metrics, the SSIM
 closed form for an affine copy, the level-grid Fresnel and uniform
 illumination identities, binary amplitude = binary phase plus a zero order);
+direct search / simulated annealing (search_run, search_delta) by
+``tests/test_oracle_search.py`` (the incremental error change against full
+recomputation, greedy descent to a one-flip minimum checked by enumeration,
+the zero- and high-temperature limits, the tracked replay field);
 the exact WGS trajectory, the OSPR mean intensity and the adaptive-OSPR
 sequence beyond its first subframe are "parity unpinned" beyond the
 qualitative and structural checks listed there.
@@ -456,3 +460,74 @@ def evaluate(holo, t_raw, kind=SLM_BINARY, levels=2, E=None, roi=None):
         E = np.ones((ny, nx), np.complex128)
     R = np.fft.fftshift(fft2(modulated_field(q, E, kind, levels), -1))
     return roi_metrics(np.abs(R) ** 2, roi_target(t_raw, roi), roi)
+
+
+# ------------------------------------------------------------------------
+# Holographic search algorithms (Section 3.3): direct search and simulated
+# annealing over single-pixel changes of a phase hologram.
+
+def _level_phasors(kind, levels):
+    step = np.pi if kind == SLM_BINARY else 2 * np.pi / levels
+    return np.exp(1j * step * np.arange(2 if kind == SLM_BINARY else levels))
+
+
+def search_delta(R, T2, y, x, ds):
+    """Change of the intensity MSE when SLM pixel (y, x) changes its field by
+    ds (unitary replay R in replay order, T2 = T^2 normalised, sum |R|^2 = N
+    for a phase hologram so I = |R|^2 / N).  The replay changes by
+    dR(ky, kx) = ds exp(-2 pi i (ky y / ny + kx x / nx)) / sqrt(N) with
+    (ky, kx) the frequency of replay pixel (iy, ix) = fftshift order, and
+    I by a = (2 Re(R conj dR) + |dR|^2) / N, so the MSE changes by
+    mean(a (2 (I - T2) + a)).  Returns (dE, dR)."""
+    ny, nx = R.shape
+    N = ny * nx
+    ky = ((np.arange(ny) - ny // 2) % ny).astype(np.int64)
+    kx = ((np.arange(nx) - nx // 2) % nx).astype(np.int64)
+    ph = ((ky * y) % ny)[:, None] / ny + ((kx * x) % nx)[None, :] / nx
+    dR = ds * np.exp(-2j * np.pi * ph) / np.sqrt(N)
+    a = (2 * (R.real * dR.real + R.imag * dR.imag) + (dR.real ** 2 + dR.imag ** 2)) / N
+    I = (R.real ** 2 + R.imag ** 2) / N
+    return float(np.mean(a * (2 * (I - T2) + a))), dR
+
+
+def search_run(t_raw, phase0, sweeps, kind=SLM_BINARY, levels=2, tau0=0.0, alpha=1.0, seed=0, t_index=0):
+    """Direct search (tau0 = 0) and simulated annealing (Section 3.3: trial
+    changes accepted when they lower Error(T, R), and under annealing also
+    with a temperature-dependent probability when they raise it).  Readings:
+      * the initial guess is the quantised back-propagation of the target with
+        phase0 (GS's first half-step): H0 = Q(IFFT2(ifftshift(T e^{i phase0})));
+      * a sweep visits every SLM pixel once in raster order (p = y nx + x);
+        the trial change is the other binary level, or for L levels level
+        (q + 1 + r1 mod (L - 1)) mod L;
+      * Error is the intensity MSE (energy normalised);
+      * accept when dE < 0, or when tau_s > 0 and u < exp(-dE / tau_s), with
+        tau_s = tau0 * MSE(H0) * alpha^s for sweep s;
+      * (u, r1): Philox4x32-10 words 0 and 1 at counter {p, s, t_index, 2},
+        key seed; u = (word0 >> 8) 2^-24.
+    Returns dict(holo, mse[sweeps] (after each sweep), accepted[sweeps],
+    mse0, R (tracked replay field, replay order))."""
+    Tn = prepare_target(t_raw)
+    ny, nx = Tn.shape
+    N = ny * nx
+    h = fft2(np.fft.ifftshift(Tn * np.exp(1j * np.asarray(phase0, dtype=np.float64))), +1)
+    q = quantise(h, kind, levels).astype(np.int64)
+    lv = _level_phasors(kind, levels)
+    R = np.fft.fftshift(fft2(lv[q], -1))
+    T2 = Tn * Tn
+    mse0 = float(np.mean(((R.real ** 2 + R.imag ** 2) / N - T2) ** 2))
+    key = np.array([seed & 0xFFFFFFFF, (seed >> 32) & 0xFFFFFFFF], np.uint32)
+    mse, acc = np.empty(sweeps), np.zeros(sweeps, np.int64)
+    for s in range(sweeps):
+        tau = tau0 * mse0 * alpha ** s
+        for p in range(N):
+            y, x = divmod(p, nx)
+            r = philox4x32_10(np.array([p, s, t_index, 2], np.uint32), key)
+            qn = 1 - q[y, x] if kind == SLM_BINARY else (q[y, x] + 1 + int(r[1]) % (levels - 1)) % levels
+            dE, dR = search_delta(R, T2, y, x, lv[qn] - lv[q[y, x]])
+            u = float(int(r[0]) >> 8) * (1.0 / 16777216.0)
+            if dE < 0 or (tau > 0 and u < np.exp(-dE / tau)):
+                R = R + dR
+                q[y, x] = qn
+                acc[s] += 1
+        mse[s] = np.mean(((R.real ** 2 + R.imag ** 2) / N - T2) ** 2)
+    return dict(holo=q.astype(np.uint8), mse=mse, accepted=acc, mse0=mse0, R=R)
