@@ -80,8 +80,22 @@ typedef struct {
  * centred window of the replay field is constrained at first, and the window
  * grows each iteration (hg_opts lt_start, lt_grow): inside it the GS
  * constraint with the target carrying the replay's total energy, outside it
- * the replay field is left free; the first field is the windowed target. */
-typedef enum { HG_GS = 0, HG_WGS = 1, HG_OSPR = 2, HG_ADOSPR = 3, HG_LT = 4 } hg_algo;
+ * the replay field is left free; the first field is the windowed target.
+ * DS / SA: the holographic search algorithms of Section 3.3, direct search
+ * and simulated annealing, for phase SLMs (binary or L-level).  The initial
+ * guess is the quantised back-propagation of the target with the initial
+ * phase (GS's first half-step).  Each sweep (`iters` counts sweeps) visits
+ * every SLM pixel once in raster order and tries the other binary level, or
+ * for L levels level (q + 1 + r1 mod (L - 1)) mod L; the change is kept when
+ * it lowers the intensity MSE, and under SA also when u < exp(-dE / tau_s)
+ * with tau_s = sa_temp * MSE(initial guess) * sa_cool^s.  (u, r1): Philox
+ * words 0 and 1 at counter {y*nx + x, sweep, target index, 2}, u = (word0 >>
+ * 8) 2^-24.  The replay field is updated incrementally in shared memory, one
+ * CTA per target, so ny * nx is limited to 16384 pixels and the thread
+ * layout to nx with lcm(32, nx) <= 1024 (else HG_ERR_UNSUPPORTED_SIZE).
+ * mse_out[b][s] is the MSE after sweep s; hg_get_metrics slot 3 holds the
+ * number of accepted changes of the sweep instead of sum |R|^2. */
+typedef enum { HG_GS = 0, HG_WGS = 1, HG_OSPR = 2, HG_ADOSPR = 3, HG_LT = 4, HG_DS = 5, HG_SA = 6 } hg_algo;
 
 typedef struct {
     void *stream;      /* cudaStream_t to enqueue on; NULL = legacy default stream */
@@ -130,10 +144,13 @@ typedef struct {
                           pixel pitch dx at distance z); 0 (default): far field */
     float amp_clip;    /* AMPLITUDE SLM: the transmittance range [0, 1] spans
                           m in [-amp_clip, amp_clip]; > 0, default 2 */
+    float sa_temp;     /* SA: initial temperature relative to the initial guess's
+                          MSE (> 0, default 1e-3) */
+    float sa_cool;     /* SA: temperature factor per sweep, in (0, 1] (default 0.9) */
 } hg_opts;
 
 /* Fills *opts with the defaults: stream NULL, seed 0, subframes 24, lt_start
- * 0.25, lt_grow 10, modulated 0, fresnel 0, amp_clip 2,
+ * 0.25, lt_grow 10, modulated 0, fresnel 0, amp_clip 2, sa_temp 1e-3, sa_cool 0.9,
  * precision 0, use_graph 1, pipeline -1, autotune 1. */
 void hg_opts_default(hg_opts *opts);
 

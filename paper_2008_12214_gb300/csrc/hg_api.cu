@@ -15,6 +15,7 @@
 #include <nvtx3/nvToolsExt.h>
 
 #include "hg_pipe.cuh"
+#include "hg_search.cuh"
 #include "hg_tc.cuh"
 #include "hologen.h"
 
@@ -493,6 +494,10 @@ struct hg_plan_s {
     float fresnel = 0.f, amp_clip = 2.f;
     double *ev_part = nullptr;                       // hg_evaluate: pass partials
     float *ev_buf = nullptr;                         // hg_evaluate: replay intensity
+    SearchLayout slay{};                             // direct search / annealing: CTA layout
+    float2 *rbuf = nullptr;                          // direct search / annealing: initial replay fields
+    uint8_t *sholo = nullptr;                        // direct search / annealing: holograms (no holo_out)
+    double sa_temp = 0, sa_cool = 1;
     float *acc = nullptr;                            // adaptive OSPR: summed subframe intensities
     uint8_t *holo_tmp = nullptr;                     // adaptive OSPR: one subframe's holograms
     unsigned long long wait_ns = 2000000000ull;      // bound on a device-side wait
@@ -774,6 +779,7 @@ int col_role_holo(hg_plan p) {
 }
 
 bool is_ospr(int algo) { return algo == HG_OSPR || algo == HG_ADOSPR; }
+bool is_search(int algo) { return algo == HG_DS || algo == HG_SA; }
 
 // Binary GS with the paired row pass and a TMA-fed column pass: the row pass
 // writes only the Hermitian part of F (rows ky <= ny/2) and the next column
@@ -888,6 +894,48 @@ hg_status enqueue_run(hg_plan p, const float *d_t, const float *d_ph, int iters,
         rt.part = p->part;
         rt.herm = p->ospr_herm;
         launch_row(p, ROW_AVG, rt, p->stream);
+    } else if (is_search(p->algo)) {
+        // initial guess: the quantised back-propagation of the target (head + column
+        // pass), its replay field (tail), then the sweeps in one kernel
+        ra.phase = d_ph;
+        launch_row(p, ROW_HEAD, ra, p->stream);
+        uint8_t *hb = d_ho ? d_ho : p->sholo;
+        ca.holo = hb;
+        launch_col(p, col_role_gs(p), ca, p->stream);
+        RowArgs rt = row_args(p);
+        rt.w = nullptr;
+        rt.R_out = p->rbuf;
+        launch_row(p, ROW_TAIL, rt, p->stream);
+        SearchArgs sa{};
+        sa.ny = p->ny;
+        sa.nx = p->nx;
+        sa.items = p->batch;
+        sa.R0 = p->rbuf;
+        sa.T = p->tf;
+        sa.holo = hb;
+        sa.lvl = p->lvl;
+        sa.levels = p->levels;
+        sa.binary = p->kind == HG_SLM_BINARY;
+        sa.twx = p->twx;
+        sa.twy = p->twy;
+        sa.sweeps = iters;
+        sa.tau0 = p->algo == HG_SA ? p->sa_temp : 0.0;
+        sa.alpha = p->sa_cool;
+        sa.seed_lo = (uint32_t)p->seed;
+        sa.seed_hi = (uint32_t)(p->seed >> 32);
+        sa.metrics = p->metrics;
+        sa.mse_out = d_mo;
+        sa.invN = (float)(1.0 / (double)p->npx);
+        sa.invSqrtN = (float)(1.0 / std::sqrt((double)p->npx));
+        sa.per_thread = p->slay.per_thread;
+        sa.off_twy = (unsigned)p->slay.off_twy;
+        sa.off_R = (unsigned)p->slay.off_R;
+        sa.off_T = (unsigned)p->slay.off_T;
+        sa.off_red = (unsigned)p->slay.off_red;
+        sa.off_dred = (unsigned)p->slay.off_dred;
+        sa.off_holo = (unsigned)p->slay.off_holo;
+        HG_CK(search_launch(sa, p->slay, p->stream));
+        p->launches++;
     } else {
         if (p->algo == HG_WGS && (!p->weights_preset || capturing)) {
             k_fill<<<ew_grid(p, p->npx * p->batch), 256, 0, p->stream>>>(p->w, p->npx * p->batch, 1.f);
@@ -913,18 +961,22 @@ hg_status enqueue_run(hg_plan p, const float *d_t, const float *d_ph, int iters,
     const int panels_iter = p->tc_prec ? p->ppt_tc : p->prow ? p->ppt_pipe : p->ppt;
     int panels_last = (p->tc_prec && !is_ospr(p->algo)) ? p->ppt_tc : p->ppt;
     if (p->ospr_herm) panels_last = (p->ny / 2 + p->rops->row_lines) / p->rops->row_lines;  // rows <= ny/2
-    if (p->mod)
+    if (is_search(p->algo)) {
+        // the search kernel wrote the metrics and mse_out itself
+    } else if (p->mod) {
         k_reduce_gen<<<(iters * p->batch * 32 + 127) / 128, 128, 0, p->stream>>>(
             p->part, iters, p->batch, p->ppt_max, panels_iter, panels_last, p->nroi, p->metrics, d_mo);
-    else
+        p->launches++;
+    } else {
         k_reduce<<<(iters * p->batch * 32 + 127) / 128, 128, 0, p->stream>>>(
             p->part, iters, p->batch, p->ppt_max, panels_iter, panels_last, 1.0 / (double)p->npx, p->metrics,
             d_mo);
-    p->launches++;
+        p->launches++;
+    }
     HG_CK(cudaGetLastError());
     p->weights_preset = false;
     p->have_run = true;
-    p->field_from_run = !is_ospr(p->algo);
+    p->field_from_run = !is_ospr(p->algo) && !is_search(p->algo);
     p->last_iters = iters;
     return st;
 }
@@ -1052,6 +1104,8 @@ void hg_opts_default(hg_opts *o) {
     o->modulated = 0;
     o->fresnel = 0.f;
     o->amp_clip = 2.f;
+    o->sa_temp = 1e-3f;
+    o->sa_cool = 0.9f;
 }
 
 int hg_supported_length(int n) { return find_ops(n) != nullptr; }
@@ -1079,7 +1133,7 @@ void hg_plan_destroy(hg_plan p) {
     for (cudaEvent_t e : p->prof_ev) cudaEventDestroy(e);
     void *bufs[] = {p->field, p->tf, p->w, p->part, p->metrics, p->sum_part, p->scale,
                     p->err, p->twx, p->twy, p->lvl, p->stage, p->tc_b, p->acc, p->holo_tmp,
-                    p->illum, p->roi_rep, p->roi_dft, p->nroi, p->ev_part, p->ev_buf};
+                    p->illum, p->roi_rep, p->roi_dft, p->nroi, p->ev_part, p->ev_buf, p->rbuf, p->sholo};
     for (void *b : bufs)
         if (b) cudaFree(b);
     delete p;
@@ -1093,7 +1147,8 @@ hg_status hg_plan_create(hg_plan *out, int ny, int nx, int batch, hg_slm slm, hg
     hg_opts_default(&o);
     if (opts) o = *opts;
     if (batch < 1 || ny < 1 || nx < 1) return HG_ERR_INVALID_ARG;
-    if (algo != HG_GS && algo != HG_WGS && algo != HG_OSPR && algo != HG_ADOSPR && algo != HG_LT)
+    if (algo != HG_GS && algo != HG_WGS && algo != HG_OSPR && algo != HG_ADOSPR && algo != HG_LT &&
+        algo != HG_DS && algo != HG_SA)
         return HG_ERR_INVALID_ARG;
     if (algo == HG_LT && (!(o.lt_start > 0.f) || o.lt_start > 1.f || o.lt_grow < 1)) return HG_ERR_INVALID_ARG;
     if (slm.kind != HG_SLM_BINARY && slm.kind != HG_SLM_LLEVEL && slm.kind != HG_SLM_AMPLITUDE)
@@ -1103,6 +1158,15 @@ hg_status hg_plan_create(hg_plan *out, int ny, int nx, int batch, hg_slm slm, hg
     if (mod && (algo != HG_GS || o.precision != 0 || o.pipeline == 1 || !std::isfinite(o.fresnel) ||
                 !(o.amp_clip > 0.f) || !std::isfinite(o.amp_clip)))
         return HG_ERR_INVALID_ARG;
+    const bool search = algo == HG_DS || algo == HG_SA;
+    SearchLayout slay{};
+    if (search) {
+        if (o.precision != 0 || o.pipeline == 1) return HG_ERR_INVALID_ARG;
+        if (algo == HG_SA && (!(o.sa_temp > 0.f) || !std::isfinite(o.sa_temp) || !(o.sa_cool > 0.f) ||
+                              o.sa_cool > 1.f))
+            return HG_ERR_INVALID_ARG;
+        if (!search_layout(ny, nx, &slay)) return HG_ERR_UNSUPPORTED_SIZE;
+    }
     if (is_ospr(algo) && (slm.kind != HG_SLM_BINARY || o.subframes < 1)) return HG_ERR_INVALID_ARG;
     if (o.precision < 0 || o.precision > 4) return HG_ERR_INVALID_ARG;
     if (o.precision > 0 && ((nx != 1024 && nx != 2048) || ny % (nx == 1024 ? 4 : 2) != 0 || is_ospr(algo) || algo == HG_LT))
@@ -1127,6 +1191,11 @@ hg_status hg_plan_create(hg_plan *out, int ny, int nx, int batch, hg_slm slm, hg
     p->kind = slm.kind;
     p->levels = slm.kind == HG_SLM_BINARY ? 2 : slm.levels;
     p->mod = mod;
+    p->slay = slay;
+    if (algo == HG_SA) {
+        p->sa_temp = o.sa_temp;
+        p->sa_cool = o.sa_cool;
+    }
     p->fresnel = o.fresnel;
     p->amp_clip = o.amp_clip;
 
@@ -1210,9 +1279,14 @@ hg_status hg_plan_create(hg_plan *out, int ny, int nx, int batch, hg_slm slm, hg
         if (ce == cudaSuccess) ce = cudaGetLastError();
         if (ce != cudaSuccess) return fail(map_err(ce));
     }
+    if (search) {
+        ce = cudaMalloc(&p->rbuf, sizeof(float2) * npx * batch);
+        if (ce == cudaSuccess) ce = cudaMalloc(&p->sholo, npx * batch);
+        if (ce != cudaSuccess) return fail(map_err(ce));
+    }
     // Pass variants are chosen (and timed) only once every buffer they touch exists;
-    // modulated plans run the generic passes.
-    if (o.pipeline != 0 && !mod) {
+    // modulated and search plans run the generic passes.
+    if (o.pipeline != 0 && !mod && !search) {
         // TMA-fed passes: row panels need 16-byte aligned rows of T (nx % 4 == 0);
         // the column tiles need a 16-byte multiple row pitch (nx even).
         const PipeOps *rc[8], *cc[8];
@@ -1699,7 +1773,7 @@ hg_status hg_get_weights(hg_plan p, float *w_out) {
 hg_status hg_debug_step(hg_plan p, const float *target, const float *phase_in, float *h_out,
                         uint8_t *holo_out, float *replay_out, double *metrics_out) {
     NvtxRange nv("hg_debug_step");
-    if (!p || !target || !phase_in || is_ospr(p->algo) || p->mod) return HG_ERR_INVALID_ARG;
+    if (!p || !target || !phase_in || is_ospr(p->algo) || is_search(p->algo) || p->mod) return HG_ERR_INVALID_ARG;
     for (const void *q : {(const void *)target, (const void *)phase_in, (const void *)h_out,
                           (const void *)holo_out, (const void *)replay_out,
                           (const void *)metrics_out})

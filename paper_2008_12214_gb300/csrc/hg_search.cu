@@ -1,0 +1,178 @@
+// hg_search.cu -- direct search and simulated annealing (Section 3.3); see
+// hg_search.cuh for the arithmetic and the shared-memory layout.
+#include "hg_search.cuh"
+
+namespace hg {
+namespace {
+
+// Sums four per-thread floats over the block (warps in double) and returns
+// the totals to every thread.  All threads must call.
+__device__ void search_sum4(float v0, float v1, float v2, float v3, double *dred, double out[4]) {
+    double d[4] = {v0, v1, v2, v3};
+#pragma unroll
+    for (int off = 16; off; off >>= 1)
+#pragma unroll
+        for (int m = 0; m < 4; ++m) d[m] += __shfl_down_sync(0xffffffffu, d[m], off);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    if (lane == 0)
+#pragma unroll
+        for (int m = 0; m < 4; ++m) dred[warp * 4 + m] = d[m];
+    __syncthreads();
+#pragma unroll
+    for (int m = 0; m < 4; ++m) {
+        double s = 0;
+        for (int w = 0; w < nw; ++w) s += dred[w * 4 + m];
+        out[m] = s;
+    }
+    __syncthreads();
+}
+
+__global__ void __launch_bounds__(SEARCH_MAX_THREADS) k_search(const SearchArgs a) {
+    extern __shared__ __align__(16) unsigned char sm[];
+    const int ny = a.ny, nx = a.nx, N = ny * nx, T = blockDim.x, tid = threadIdx.x, item = blockIdx.x;
+    float2 *twx = reinterpret_cast<float2 *>(sm);
+    float2 *twy = reinterpret_cast<float2 *>(sm + a.off_twy);
+    float2 *R = reinterpret_cast<float2 *>(sm + a.off_R);
+    float *Tt = reinterpret_cast<float *>(sm + a.off_T);
+    float *red = reinterpret_cast<float *>(sm + a.off_red);
+    double *dred = reinterpret_cast<double *>(sm + a.off_dred);
+    uint8_t *hq = sm + a.off_holo;
+    const size_t base = (size_t)item * N;
+    for (int i = tid; i < nx; i += T) twx[i] = a.twx[i];
+    for (int i = tid; i < ny; i += T) twy[i] = a.twy[i];
+    for (int k = tid; k < N; k += T) {
+        const int iy = k / nx, ix = k - iy * nx;
+        const int yc = (iy + ny - ny / 2) % ny, xc = (ix + nx - nx / 2) % nx;  // DFT index of replay pixel
+        R[k] = a.R0[base + k];
+        Tt[k] = a.T[base + (size_t)yc * nx + xc];
+        hq[k] = a.holo[base + k];
+    }
+    __syncthreads();
+    // pixel j of this thread: k = tid + T j, replay column ix, row iy0 + rstep j
+    const int ix = tid % nx, iy0 = tid / nx, rstep = T / nx;
+    const int kx = (ix - nx / 2 + nx) % nx, ky0 = (iy0 - ny / 2 + ny) % ny, rstep_m = rstep % ny;
+    const int J = a.per_thread, nw = T >> 5, lane = tid & 31, warp = tid >> 5;
+
+    auto metrics = [&](double out[4]) {
+        float m0 = 0.f, m1 = 0.f, m2 = 0.f, m3 = 0.f;
+        for (int j = 0; j < J; ++j) {
+            const int k = tid + T * j;
+            if (k >= N) break;
+            const float2 r = R[k];
+            const float e2 = fmaf(r.x, r.x, r.y * r.y), I = e2 * a.invN, t = Tt[k];
+            const float d = I - t * t, am = sqrtf(I) - t;
+            m0 = fmaf(d, d, m0);
+            m1 = fmaf(am, am, m1);
+            if (t > 0.f) m2 += e2;
+            m3 += e2;
+        }
+        search_sum4(m0, m1, m2, m3, dred, out);
+    };
+    double g[4];
+    metrics(g);
+    const double mse0 = g[0] / N;
+    int buf = 0;
+    for (int s = 0; s < a.sweeps; ++s) {
+        const float tau = (float)(a.tau0 * mse0 * pow(a.alpha, (double)s));
+        int accepted = 0;
+        int eyb = 0, st = 0;  // (ky0 y) mod ny and (rstep y) mod ny
+        for (int y = 0; y < ny; ++y) {
+            int ex = 0;  // (kx x) mod nx
+            for (int x = 0; x < nx; ++x) {
+                const int p = y * nx + x;
+                const uint2 r = philox_words01((uint32_t)p, (uint32_t)s, (uint32_t)item, 2u, a.seed_lo, a.seed_hi);
+                const int q = hq[p];
+                int qn;
+                float2 ds;
+                if (a.binary) {
+                    qn = 1 - q;
+                    ds = make_float2(q ? 2.f : -2.f, 0.f);
+                } else {
+                    qn = (q + 1 + (int)(r.y % (uint32_t)(a.levels - 1))) % a.levels;
+                    const float2 l1 = __ldg(a.lvl + qn), l0 = __ldg(a.lvl + q);
+                    ds = make_float2(l1.x - l0.x, l1.y - l0.y);
+                }
+                const float2 wx = twx[ex];
+                const float2 c = make_float2((ds.x * wx.x - ds.y * wx.y) * a.invSqrtN,
+                                             (ds.x * wx.y + ds.y * wx.x) * a.invSqrtN);
+                float part = 0.f;
+                int ey = eyb;
+                for (int j = 0; j < J; ++j) {
+                    const int k = tid + T * j;
+                    if (k < N) {
+                        const float2 w = twy[ey];
+                        const float dx = c.x * w.x - c.y * w.y, dy = fmaf(c.x, w.y, c.y * w.x);
+                        const float2 rv = R[k];
+                        const float I = fmaf(rv.x, rv.x, rv.y * rv.y) * a.invN, t = Tt[k];
+                        const float aa = fmaf(2.f, fmaf(rv.x, dx, rv.y * dy), fmaf(dx, dx, dy * dy)) * a.invN;
+                        part = fmaf(aa, fmaf(2.f, I - t * t, aa), part);
+                    }
+                    ey += st;
+                    if (ey >= ny) ey -= ny;
+                }
+#pragma unroll
+                for (int off = 16; off; off >>= 1) part += __shfl_down_sync(0xffffffffu, part, off);
+                if (lane == 0) red[buf * 32 + warp] = part;
+                __syncthreads();
+                float dE = 0.f;
+                for (int w = 0; w < nw; ++w) dE += red[buf * 32 + w];
+                dE *= a.invN;
+                buf ^= 1;
+                const float u = (float)(r.x >> 8) * (1.0f / 16777216.0f);
+                if (dE < 0.f || (tau > 0.f && u < expf(-dE / tau))) {
+                    ey = eyb;
+                    for (int j = 0; j < J; ++j) {
+                        const int k = tid + T * j;
+                        if (k < N) {
+                            const float2 w = twy[ey];
+                            R[k].x += c.x * w.x - c.y * w.y;
+                            R[k].y += fmaf(c.x, w.y, c.y * w.x);
+                        }
+                        ey += st;
+                        if (ey >= ny) ey -= ny;
+                    }
+                    if (tid == 0) hq[p] = (uint8_t)qn;
+                    ++accepted;
+                }
+                ex += kx;
+                if (ex >= nx) ex -= nx;
+            }
+            eyb += ky0;
+            if (eyb >= ny) eyb -= ny;
+            st += rstep_m;
+            if (st >= ny) st -= ny;
+        }
+        metrics(g);
+        if (tid == 0) {
+            double *o = a.metrics + ((size_t)item * a.sweeps + s) * 4;
+            o[0] = g[0] / N;
+            o[1] = g[1] / N;
+            o[2] = g[3] > 0 ? g[2] / g[3] : 0.0;
+            o[3] = accepted;
+            if (a.mse_out) a.mse_out[(size_t)item * a.sweeps + s] = o[0];
+        }
+    }
+    __syncthreads();
+    for (int k = tid; k < N; k += T) a.holo[base + k] = hq[k];
+}
+
+bool g_search_attr[64];
+
+}  // namespace
+
+cudaError_t search_launch(const SearchArgs &a, const SearchLayout &L, cudaStream_t s) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+    if (!g_search_attr[dev]) {
+        e = cudaFuncSetAttribute((const void *)k_search, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)SEARCH_MAX_SMEM);
+        if (e != cudaSuccess) return e;
+        g_search_attr[dev] = true;
+    }
+    k_search<<<a.items, L.threads, L.bytes, s>>>(a);
+    return cudaGetLastError();
+}
+
+}  // namespace hg

@@ -17,7 +17,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libhologen.so")
 
 HG_SLM_BINARY, HG_SLM_LLEVEL, HG_SLM_AMPLITUDE = 0, 1, 2
-HG_GS, HG_WGS, HG_OSPR, HG_ADOSPR, HG_LT = 0, 1, 2, 3, 4
+HG_GS, HG_WGS, HG_OSPR, HG_ADOSPR, HG_LT, HG_DS, HG_SA = 0, 1, 2, 3, 4, 5, 6
 NMET = 4
 
 STATUS = {0: "HG_OK", 1: "HG_ERR_INVALID_ARG", 2: "HG_ERR_UNSUPPORTED_SIZE", 3: "HG_ERR_OOM",
@@ -35,7 +35,8 @@ class hg_opts(ctypes.Structure):
     _fields_ = [("stream", ctypes.c_void_p), ("seed", ctypes.c_uint64), ("subframes", ctypes.c_int),
                 ("precision", ctypes.c_int), ("use_graph", ctypes.c_int), ("pipeline", ctypes.c_int),
                 ("autotune", ctypes.c_int), ("lt_start", ctypes.c_float), ("lt_grow", ctypes.c_int),
-                ("modulated", ctypes.c_int), ("fresnel", ctypes.c_float), ("amp_clip", ctypes.c_float)]
+                ("modulated", ctypes.c_int), ("fresnel", ctypes.c_float), ("amp_clip", ctypes.c_float),
+                ("sa_temp", ctypes.c_float), ("sa_cool", ctypes.c_float)]
 
 
 class hg_slm(ctypes.Structure):
@@ -155,7 +156,8 @@ def hg_status_string(st: int) -> str:
 
 def hg_plan_create(ny, nx, batch, slm_kind=HG_SLM_BINARY, levels=2, algo=HG_GS, stream=None,
                    seed=0, subframes=24, precision=0, use_graph=True, pipeline=-1, autotune=True,
-                   lt_start=None, lt_grow=None, modulated=False, fresnel=0.0, amp_clip=None):
+                   lt_start=None, lt_grow=None, modulated=False, fresnel=0.0, amp_clip=None, sa_temp=None,
+                   sa_cool=None):
     o = hg_opts()
     lib().hg_opts_default(ctypes.byref(o))
     if stream is None and torch.cuda.is_available():
@@ -175,6 +177,10 @@ def hg_plan_create(ny, nx, batch, slm_kind=HG_SLM_BINARY, levels=2, algo=HG_GS, 
     o.fresnel = float(fresnel)
     if amp_clip is not None:
         o.amp_clip = float(amp_clip)
+    if sa_temp is not None:
+        o.sa_temp = float(sa_temp)
+    if sa_cool is not None:
+        o.sa_cool = float(sa_cool)
     h = ctypes.c_void_p()
     _ck(lib().hg_plan_create(ctypes.byref(h), int(ny), int(nx), int(batch),
                              hg_slm(int(slm_kind), int(levels)), int(algo), ctypes.byref(o)),
