@@ -63,8 +63,9 @@ def parse():
     ap.add_argument("--batch", type=int, default=BATCH, help="targets per rank (profiling runs)")
     ap.add_argument("--quick", action="store_true", help="skip the e2e and CPU-baseline legs")
     ap.add_argument("--pairs", type=int, default=2048, help="warmstart: training pairs")
+    ap.add_argument("--search-waves", type=int, default=1, help="search: targets = waves x 4 x SMs")
     ap.add_argument("--heldout", type=int, default=64, help="warmstart: held-out targets")
-    ap.add_argument("--workload", choices=["headline", "ospr", "adospr", "mixed", "warmstart", "gs2048", "wgs256", "fresnel", "lt"],
+    ap.add_argument("--workload", choices=["headline", "ospr", "adospr", "mixed", "warmstart", "gs2048", "wgs256", "fresnel", "lt", "search"],
                     default="headline",
                     help="headline: binary GS 1024^2 x 64 (the benchmark line); ospr: 8 targets x 24 "
                          "subframes of 1024^2; mixed: 16 targets each of 512^2, 1024^2, 2048^2, 1080x1920")
@@ -309,6 +310,41 @@ def run_side_workload(args):
                    diffraction_efficiency=float(met[-1, 2]), mse_iter_1_10_100=[float(met[i, 0]) for i in (0, 9, 99)],
                    row_variant=hg.hg_plan_variant(plan.h, 0), column_variant=hg.hg_plan_variant(plan.h, 1))
         plan.close()
+    elif args.workload == "search":
+        # direct search (--precision 0) / simulated annealing (--precision 1): 64x64 binary holograms,
+        # one per CTA, 4 CTAs per SM resident (52 KB of shared memory each), 2 sweeps
+        n, sweeps = 64, 2
+        B = 4 * torch.cuda.get_device_properties(dev).multi_processor_count * args.search_waves
+        algo = hg.HG_SA if args.precision == 1 else hg.HG_DS
+        T = torch.from_numpy(synth.targets(B, n, n, 9000)).to(dev)
+        P = torch.from_numpy(synth.init_phases(B, n, n, 9000)).to(dev)
+        mse = torch.empty((B, sweeps), dtype=torch.float64, device=dev)
+        plan = hg.Plan(n, n, B, hg.HG_SLM_BINARY, 2, algo, seed=5, sa_temp=1e-3, sa_cool=0.5)
+        for _ in range(args.warmup):
+            plan.run(T, P, sweeps, None, mse)
+        plan.sync()
+        e0.record(s0)
+        for _ in range(args.steps):
+            plan.run(T, P, sweeps, None, mse)
+        e1.record(s0)
+        plan.sync()
+        ms = e0.elapsed_time(e1) / args.steps
+        met = plan.metrics().cpu().numpy()
+        trials = B * sweeps * n * n
+        px_evals = trials * n * n
+        # FP32 work per replay pixel per trial: dR = c w (6 flops), |R|^2 / N (4), the
+        # intensity change a (7), a (2 (I - T^2) + a) accumulated (6): 23 flops with FMA = 2
+        flops = 23.0 * px_evals
+        sms = torch.cuda.get_device_properties(dev).multi_processor_count
+        peak = sms * 128 * 2 * 2.07e9 / 1e12  # FP32 lanes x FMA x maximum SM clock
+        achieved = flops / (ms / 1e3) / 1e12
+        out = dict(workload="%s_binary_64x64_batch%d" % ("sa" if algo == hg.HG_SA else "ds", B), ms_per_step=ms,
+                   sweeps=sweeps, trials_per_s=trials / (ms / 1e3), pixel_evaluations_per_s=px_evals / (ms / 1e3),
+                   roofline=dict(bound="alu", achieved=achieved, peak=peak, unit="TFLOP/s", frac=achieved / peak,
+                                 flops_per_pixel_evaluation=23),
+                   mse_initial_to_final_mean=float((met[:, -1, 0]).mean()),
+                   accepted_per_sweep_mean=[float(met[:, k, 3].mean()) for k in range(sweeps)])
+        plan.close()
     elif args.workload == "lt":
         # Liu-Taghizadeh GS, 64 binary holograms of 1024^2, window 0.25 -> 1 over 10 constraints
         B, n = 64, 1024
@@ -543,12 +579,16 @@ def main():
         b_col = ((it - 1) * BYTES_COL_PAIRED + 16) / it  # last column pass writes every row
     else:
         b_row, b_col = BYTES_ROW, BYTES_COL
+    # "bytes": the algorithmic bytes of the fused schedule's pass (row 20, column 16 B/px),
+    # the per-unit figure of the roofline; "moved": what the running variant reads and writes
     passes = {
-        "row": dict(bytes=b_row * npx, ms=row_ms, launches=int(prof[1]), variant=variants[0]),
-        "column": dict(bytes=b_col * npx, ms=col_ms, launches=int(prof[3]), variant=variants[1]),
+        "row": dict(bytes=BYTES_ROW * npx, moved=b_row * npx, ms=row_ms, launches=int(prof[1]), variant=variants[0]),
+        "column": dict(bytes=BYTES_COL * npx, moved=b_col * npx, ms=col_ms, launches=int(prof[3]),
+                       variant=variants[1]),
     }
     for v in passes.values():
         v["gbs"] = v["bytes"] / (v["ms"] / 1e3) / 1e9 if v["ms"] > 0 else None
+        v["gbs_moved"] = v["moved"] / (v["ms"] / 1e3) / 1e9 if v["ms"] > 0 else None
     dom = max(passes, key=lambda k: passes[k]["ms"] * passes[k]["launches"])
     d = passes[dom]
     kernel_key = d["variant"] + (" row" if dom == "row" else " column")
@@ -556,7 +596,9 @@ def main():
     roofline = dict(bound="hbm", achieved=d["gbs"], peak=peak, unit="GB/s",
                     frac=(d["gbs"] / peak) if d["gbs"] else None, traffic=traffic,
                     kernel="%s pass (%s)" % (dom, kernel_key), peak_source=peak_src,
-                    algorithmic_bytes_per_launch=d["bytes"], avg_launch_ms=d["ms"])
+                    algorithmic_bytes_per_launch=d["bytes"], avg_launch_ms=d["ms"],
+                    variant_bytes_per_launch=d["moved"],
+                    frac_at_variant_bytes=(d["gbs_moved"] / peak) if d["gbs_moved"] else None)
     iter_ms = el_ms / (args.steps * args.iters)
     line = dict(
         metric=METRIC, value=value, unit=UNIT, n_gpus=world, steps=args.steps, warmup=args.warmup,
@@ -576,7 +618,9 @@ def main():
             frac_at_36=BYTES_SURVEY * npx / (iter_ms / 1e3) / 1e9 / peak),
         roofline=roofline,
         passes={k: dict(avg_ms=v["ms"], gbs=v["gbs"], frac=(v["gbs"] / peak if v["gbs"] else None),
-                        launches=v["launches"], bytes_per_px=v["bytes"] / npx, variant=v["variant"])
+                        launches=v["launches"], bytes_per_px=v["bytes"] / npx, variant=v["variant"],
+                        bytes_per_px_moved=v["moved"] / npx, gbs_moved=v["gbs_moved"],
+                        frac_moved=(v["gbs_moved"] / peak if v["gbs_moved"] else None))
                 for k, v in passes.items()},
         cpu_baseline=None if args.quick else cpu_oracle_sample(),
         e2e=e2e,
