@@ -933,6 +933,7 @@ hg_status enqueue_run(hg_plan p, const float *d_t, const float *d_ph, int iters,
         sa.off_T = (unsigned)p->slay.off_T;
         sa.off_red = (unsigned)p->slay.off_red;
         sa.off_dred = (unsigned)p->slay.off_dred;
+        sa.off_rnd = (unsigned)p->slay.off_rnd;
         sa.off_holo = (unsigned)p->slay.off_holo;
         HG_CK(search_launch(sa, p->slay, p->stream));
         p->launches++;

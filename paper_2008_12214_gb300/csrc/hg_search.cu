@@ -33,18 +33,16 @@ __global__ void __launch_bounds__(SEARCH_MAX_THREADS) k_search(const SearchArgs 
     float2 *twx = reinterpret_cast<float2 *>(sm);
     float2 *twy = reinterpret_cast<float2 *>(sm + a.off_twy);
     float2 *R = reinterpret_cast<float2 *>(sm + a.off_R);
-    float *Tt = reinterpret_cast<float *>(sm + a.off_T);
+    float *G = reinterpret_cast<float *>(sm + a.off_T);  // 2 (I - T^2) per replay pixel
     float *red = reinterpret_cast<float *>(sm + a.off_red);
     double *dred = reinterpret_cast<double *>(sm + a.off_dred);
     uint8_t *hq = sm + a.off_holo;
+    uint2 *rnd = reinterpret_cast<uint2 *>(sm + a.off_rnd);
     const size_t base = (size_t)item * N;
     for (int i = tid; i < nx; i += T) twx[i] = a.twx[i];
     for (int i = tid; i < ny; i += T) twy[i] = a.twy[i];
     for (int k = tid; k < N; k += T) {
-        const int iy = k / nx, ix = k - iy * nx;
-        const int yc = (iy + ny - ny / 2) % ny, xc = (ix + nx - nx / 2) % nx;  // DFT index of replay pixel
         R[k] = a.R0[base + k];
-        Tt[k] = a.T[base + (size_t)yc * nx + xc];
         hq[k] = a.holo[base + k];
     }
     __syncthreads();
@@ -52,15 +50,22 @@ __global__ void __launch_bounds__(SEARCH_MAX_THREADS) k_search(const SearchArgs 
     const int ix = tid % nx, iy0 = tid / nx, rstep = T / nx;
     const int kx = (ix - nx / 2 + nx) % nx, ky0 = (iy0 - ny / 2 + ny) % ny, rstep_m = rstep % ny;
     const int J = a.per_thread, nw = T >> 5, lane = tid & 31, warp = tid >> 5;
+    const bool full = J * T == N;  // every thread owns J pixels
 
+    // metrics of the current R, and G = 2 (I - T^2) recomputed from it (which
+    // also clears the rounding the in-place updates of G accumulate)
     auto metrics = [&](double out[4]) {
         float m0 = 0.f, m1 = 0.f, m2 = 0.f, m3 = 0.f;
         for (int j = 0; j < J; ++j) {
             const int k = tid + T * j;
             if (k >= N) break;
+            const int iy = k / nx, ixk = k - iy * nx;
+            const int yc = (iy + ny - ny / 2) % ny, xc = (ixk + nx - nx / 2) % nx;  // DFT index
+            const float t = __ldg(a.T + base + (size_t)yc * nx + xc);
             const float2 r = R[k];
-            const float e2 = fmaf(r.x, r.x, r.y * r.y), I = e2 * a.invN, t = Tt[k];
+            const float e2 = fmaf(r.x, r.x, r.y * r.y), I = e2 * a.invN;
             const float d = I - t * t, am = sqrtf(I) - t;
+            G[k] = 2.f * d;
             m0 = fmaf(d, d, m0);
             m1 = fmaf(am, am, m1);
             if (t > 0.f) m2 += e2;
@@ -68,6 +73,7 @@ __global__ void __launch_bounds__(SEARCH_MAX_THREADS) k_search(const SearchArgs 
         }
         search_sum4(m0, m1, m2, m3, dred, out);
     };
+    const bool need_rand = !a.binary || a.tau0 > 0.0;
     double g[4];
     metrics(g);
     const double mse0 = g[0] / N;
@@ -78,9 +84,17 @@ __global__ void __launch_bounds__(SEARCH_MAX_THREADS) k_search(const SearchArgs 
         int eyb = 0, st = 0;  // (ky0 y) mod ny and (rstep y) mod ny
         for (int y = 0; y < ny; ++y) {
             int ex = 0;  // (kx x) mod nx
+            if (need_rand) {
+                // the row's random words, drawn once by the block; every thread read
+                // the previous row's before the last trial's barrier
+                for (int xx = tid; xx < nx; xx += T)
+                    rnd[xx] = philox_words01((uint32_t)(y * nx + xx), (uint32_t)s, (uint32_t)item, 2u, a.seed_lo,
+                                             a.seed_hi);
+                __syncthreads();
+            }
             for (int x = 0; x < nx; ++x) {
                 const int p = y * nx + x;
-                const uint2 r = philox_words01((uint32_t)p, (uint32_t)s, (uint32_t)item, 2u, a.seed_lo, a.seed_hi);
+                const uint2 r = need_rand ? rnd[x] : make_uint2(0u, 0u);
                 const int q = hq[p];
                 int qn;
                 float2 ds;
@@ -93,19 +107,23 @@ __global__ void __launch_bounds__(SEARCH_MAX_THREADS) k_search(const SearchArgs 
                     ds = make_float2(l1.x - l0.x, l1.y - l0.y);
                 }
                 const float2 wx = twx[ex];
+                // dR_k = c w_k with |w_k| = 1, so the intensity change is
+                // a_k = Re(R_k conj(w_k) conj(c)) 2 / N + |c|^2 / N
                 const float2 c = make_float2((ds.x * wx.x - ds.y * wx.y) * a.invSqrtN,
                                              (ds.x * wx.y + ds.y * wx.x) * a.invSqrtN);
+                const float s2 = 2.f * a.invN;
+                const float2 c2 = make_float2(c.x * s2, c.y * s2);
+                const float cc = fmaf(c.x, c.x, c.y * c.y) * a.invN;
                 float part = 0.f;
                 int ey = eyb;
                 for (int j = 0; j < J; ++j) {
                     const int k = tid + T * j;
-                    if (k < N) {
+                    if (full || k < N) {
                         const float2 w = twy[ey];
-                        const float dx = c.x * w.x - c.y * w.y, dy = fmaf(c.x, w.y, c.y * w.x);
                         const float2 rv = R[k];
-                        const float I = fmaf(rv.x, rv.x, rv.y * rv.y) * a.invN, t = Tt[k];
-                        const float aa = fmaf(2.f, fmaf(rv.x, dx, rv.y * dy), fmaf(dx, dx, dy * dy)) * a.invN;
-                        part = fmaf(aa, fmaf(2.f, I - t * t, aa), part);
+                        const float zx = fmaf(rv.x, w.x, rv.y * w.y), zy = fmaf(rv.y, w.x, -rv.x * w.y);
+                        const float aa = fmaf(zx, c2.x, fmaf(zy, c2.y, cc));
+                        part = fmaf(aa, G[k] + aa, part);
                     }
                     ey += st;
                     if (ey >= ny) ey -= ny;
@@ -123,10 +141,12 @@ __global__ void __launch_bounds__(SEARCH_MAX_THREADS) k_search(const SearchArgs 
                     ey = eyb;
                     for (int j = 0; j < J; ++j) {
                         const int k = tid + T * j;
-                        if (k < N) {
+                        if (full || k < N) {
                             const float2 w = twy[ey];
-                            R[k].x += c.x * w.x - c.y * w.y;
-                            R[k].y += fmaf(c.x, w.y, c.y * w.x);
+                            const float2 rv = R[k];
+                            const float zx = fmaf(rv.x, w.x, rv.y * w.y), zy = fmaf(rv.y, w.x, -rv.x * w.y);
+                            G[k] += 2.f * fmaf(zx, c2.x, fmaf(zy, c2.y, cc));  // I gains a_k
+                            R[k] = make_float2(rv.x + (c.x * w.x - c.y * w.y), rv.y + fmaf(c.x, w.y, c.y * w.x));
                         }
                         ey += st;
                         if (ey >= ny) ey -= ny;

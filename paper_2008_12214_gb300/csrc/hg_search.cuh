@@ -7,7 +7,9 @@
 // by ds changes replay pixel (iy, ix), of frequency (ky, kx), by
 // dR = ds W_ny^(ky y) W_nx^(kx x) / sqrt(N), and the intensity MSE by
 // dE = mean(a (2 (I - T^2) + a)), a = (2 Re(R conj dR) + |dR|^2) / N,
-// I = |R|^2 / N (a phase hologram keeps sum |R|^2 = N).  Every thread sums
+// I = |R|^2 / N (a phase hologram keeps sum |R|^2 = N).  Shared memory holds
+// G = 2 (I - T^2) per replay pixel: an accepted change adds 2 a, and every
+// sweep recomputes G from R and T.  Every thread sums
 // its pixels' terms, warps reduce in float, and every thread adds the warp
 // partials in the same order, so all threads take the same decision after
 // one barrier per trial (the partials alternate between two buffers).
@@ -25,6 +27,7 @@ struct SearchArgs {
     const float2 *R0;   // [items][ny][nx] replay of the initial hologram, replay order, unitary
     const float *T;     // prepared targets [items][ny][nx], DFT order, sum T^2 = 1
     uint8_t *holo;      // [items][ny][nx] SLM order: initial levels in, final levels out
+                        // (T is read again at every sweep's metrics)
     const float2 *lvl;  // L-level phasors exp(2 pi i q / L)
     int levels, binary;
     const float2 *twx, *twy;  // W_n^e = exp(-2 pi i e / n)
@@ -36,12 +39,12 @@ struct SearchArgs {
     float invN, invSqrtN;
     // shared-memory layout (search_layout)
     int per_thread;
-    unsigned off_twy, off_R, off_T, off_red, off_dred, off_holo;
+    unsigned off_twy, off_R, off_T, off_red, off_dred, off_rnd, off_holo;
 };
 
 struct SearchLayout {
     int threads, per_thread;
-    size_t off_twy, off_R, off_T, off_red, off_dred, off_holo, bytes;
+    size_t off_twy, off_R, off_T, off_red, off_dred, off_rnd, off_holo, bytes;
 };
 
 // Thread t holds replay pixels t + threads j (j < per_thread), so `threads`
@@ -74,6 +77,8 @@ inline bool search_layout(int ny, int nx, SearchLayout *L) {
     o += 2 * 32 * sizeof(float);
     L->off_dred = o;
     o += 32 * 4 * sizeof(double);
+    L->off_rnd = o;  // Philox words 0 and 1 of one SLM row's trials
+    o += 8 * (size_t)nx;
     L->off_holo = o;
     o += (size_t)N;
     L->bytes = o;
