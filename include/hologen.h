@@ -135,9 +135,10 @@ typedef struct {
                           scale the replay to the ROI's energy, I = |R|^2 /
                           sum_ROI |R|^2, and average over the ROI; efficiency is
                           the energy on the target's support over all replay
-                          energy.  GS only, generic passes (not pipeline 1, not
-                          precision > 0), no hg_debug_step, else
-                          HG_ERR_INVALID_ARG.  Default 0. */
+                          energy.  GS only (not precision > 0), no
+                          hg_debug_step, else HG_ERR_INVALID_ARG.  Generic
+                          passes, or with pipeline 1 the TMA-fed passes without
+                          paired rows.  Default 0. */
     float fresnel;     /* Fresnel (mid-field) hologram, Section 2: the SLM-plane
                           field gains the quadratic phase fresnel * ((x - nx/2)^2
                           + (y - ny/2)^2) radians (pi dx^2 / (lambda z) for

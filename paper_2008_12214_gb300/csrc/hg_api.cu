@@ -386,7 +386,7 @@ int row_panels(const PipeOps *o, int ny) {
 
 // Autotuner cache: (device, ny, nx, items, slm kind) -> chosen candidates.
 struct TuneEntry {
-    int dev, ny, nx, items, kind;
+    int dev, ny, nx, items, kind;  // kind + 8 for modulated plans (no paired candidates)
     const PipeOps *row, *col;
 };
 std::mutex g_tune_mu;
@@ -1056,7 +1056,7 @@ float time_variant(hg_plan p, const PipeOps *o, bool row, bool pack = false, boo
         if (row) o->row_iter(ra, pa, grid, s);
         else if (herm_pairs) o->col_herm(ca, pa, m, grid, s);
         else if (pack) o->col_pack(ca, pa, m, grid, s);
-        else o->col_gs(p->kind == HG_SLM_BINARY ? COL_GS_BIN : COL_GS_LVL, ca, pa, m, grid, s);
+        else o->col_gs(p->mod ? COL_GS_MOD : p->kind == HG_SLM_BINARY ? COL_GS_BIN : COL_GS_LVL, ca, pa, m, grid, s);
         cudaEventRecord(e1, s);
         if (cudaEventSynchronize(e1) != cudaSuccess) break;
         float ms = 0;
@@ -1156,7 +1156,7 @@ hg_status hg_plan_create(hg_plan *out, int ny, int nx, int batch, hg_slm slm, hg
         return HG_ERR_INVALID_ARG;
     if (slm.kind != HG_SLM_BINARY && (slm.levels < 2 || slm.levels > 256)) return HG_ERR_INVALID_ARG;
     const bool mod = o.modulated || slm.kind == HG_SLM_AMPLITUDE || o.fresnel != 0.f;
-    if (mod && (algo != HG_GS || o.precision != 0 || o.pipeline == 1 || !std::isfinite(o.fresnel) ||
+    if (mod && (algo != HG_GS || o.precision != 0 || !std::isfinite(o.fresnel) ||
                 !(o.amp_clip > 0.f) || !std::isfinite(o.amp_clip)))
         return HG_ERR_INVALID_ARG;
     const bool search = algo == HG_DS || algo == HG_SA;
@@ -1286,8 +1286,10 @@ hg_status hg_plan_create(hg_plan *out, int ny, int nx, int batch, hg_slm slm, hg
         if (ce != cudaSuccess) return fail(map_err(ce));
     }
     // Pass variants are chosen (and timed) only once every buffer they touch exists;
-    // modulated and search plans run the generic passes.
-    if (o.pipeline != 0 && !mod && !search) {
+    // search plans run the generic passes.  Modulated plans run the generic passes unless
+    // pipeline is 1: their TMA-fed passes (unpaired: the light leaving the SLM, E e^{iH}, is
+    // complex, so no Hermitian symmetry) measured slower at 1024^2 x 64.
+    if (o.pipeline != 0 && !search && (!mod || o.pipeline == 1)) {
         // TMA-fed passes: row panels need 16-byte aligned rows of T (nx % 4 == 0);
         // the column tiles need a 16-byte multiple row pitch (nx even).
         const PipeOps *rc[8], *cc[8];
@@ -1298,7 +1300,7 @@ hg_status hg_plan_create(hg_plan *out, int ny, int nx, int batch, hg_slm slm, hg
             for (int i = 0; i < k; ++i) {
                 // paired rows need a binary SLM (real e^{iH}), an even column length and the
                 // GS/WGS loop
-                if (all[i]->paired && (slm.kind != HG_SLM_BINARY || ny % 2 || is_ospr(algo))) continue;
+                if (all[i]->paired && (slm.kind != HG_SLM_BINARY || ny % 2 || is_ospr(algo) || mod)) continue;
                 if (all[i]->row_iter && nx % 4 == 0 && ensure_pipe_init(p->dev, all[i]) == cudaSuccess)
                     rc[nr++] = all[i];
             }
@@ -1324,7 +1326,7 @@ hg_status hg_plan_create(hg_plan *out, int ny, int nx, int batch, hg_slm slm, hg
                 std::lock_guard<std::mutex> lk(g_tune_mu);
                 for (const TuneEntry &t : g_tune)
                     if (t.dev == p->dev && t.ny == ny && t.nx == nx && t.items == p->nchains &&
-                        t.kind == slm.kind) {
+                        t.kind == slm.kind + (mod ? 8 : 0)) {
                         row = t.row;
                         col = t.col;
                         cached = true;
@@ -1363,7 +1365,7 @@ hg_status hg_plan_create(hg_plan *out, int ny, int nx, int batch, hg_slm slm, hg
                     if (ms < best) best = ms, row = rc[i];
                 }
                 std::lock_guard<std::mutex> lk(g_tune_mu);
-                g_tune.push_back({p->dev, ny, nx, p->nchains, slm.kind, row, col});
+                g_tune.push_back({p->dev, ny, nx, p->nchains, slm.kind + (mod ? 8 : 0), row, col});
             }
         }
         if (row && !p->tc_prec) {

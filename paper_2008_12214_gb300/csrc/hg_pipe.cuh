@@ -239,7 +239,9 @@ __global__ void __launch_bounds__(RowPipeCfg<P, LINES, NG, D, SWZ>::THREADS, 1)
         });
         line_fft<P, -1, 1, LAY>(v, sf, a.tw, t, gsync);
         float *wr = a.w ? a.w + ((size_t)item * ny + (act ? y : ny - 1)) * NX : nullptr;
+        const uint8_t *roir = a.roi ? a.roi + (size_t)(act ? y : ny - 1) * NX : nullptr;
         float acc0 = 0.f, acc1 = 0.f, acc2 = 0.f, acc3 = 0.f;
+        float acc4 = 0.f, acc5 = 0.f, acc6 = 0.f, acc7 = 0.f;
         static_for<0, E>([&](auto ec) {
             constexpr int e = decltype(ec)::value;
             const int x = t + TL * e;
@@ -247,15 +249,32 @@ __global__ void __launch_bounds__(RowPipeCfg<P, LINES, NG, D, SWZ>::THREADS, 1)
             const float2 r = v[e];
             const float m2 = fmaf(r.x, r.x, r.y * r.y);
             const float rs = m2 > 0.f ? rsqrtf(m2) : 0.f;
-            const float I = m2 * a.invN2;
-            const float d = I - Tv * Tv;
-            const float am = fmaf(m2 * rs, a.invSqrtN * a.invSqrtN, -Tv);  // sqrt(I) - T
             const float e2 = m2 * a.invN;
-            if (act) {
-                acc0 = fmaf(d, d, acc0);
-                acc1 = fmaf(am, am, acc1);
-                acc3 += e2;
-                if (Tv > 0.f) acc2 += e2;
+            const bool in = !roir || roir[x] != 0;
+            if (a.gen) {  // modulated plan: the eight sums of the generic row pass
+                if (act) {
+                    acc5 += e2;
+                    if (in) {
+                        const float t2 = Tv * Tv;
+                        acc0 += e2;
+                        acc1 = fmaf(e2, e2, acc1);
+                        acc2 = fmaf(e2, t2, acc2);
+                        acc3 = fmaf(m2 * rs, Tv * a.invSqrtN, acc3);  // sqrt(e2) T
+                        if (Tv > 0.f) acc4 += e2;
+                        acc6 = fmaf(t2, t2, acc6);
+                        acc7 += t2;
+                    }
+                }
+            } else {
+                const float I = m2 * a.invN2;
+                const float d = I - Tv * Tv;
+                const float am = fmaf(m2 * rs, a.invSqrtN * a.invSqrtN, -Tv);  // sqrt(I) - T
+                if (act) {
+                    acc0 = fmaf(d, d, acc0);
+                    acc1 = fmaf(am, am, acc1);
+                    acc3 += e2;
+                    if (Tv > 0.f) acc2 += e2;
+                }
             }
             float wv = 1.f;
             if (wr) {
@@ -264,7 +283,7 @@ __global__ void __launch_bounds__(RowPipeCfg<P, LINES, NG, D, SWZ>::THREADS, 1)
                 if (act) wr[x] = wv;
             }
             const float gm = (a.lt_amp > 0.f ? a.lt_amp : 1.f) * Tv * wv;
-            if (a.lt_amp > 0.f && !lt_in(a, y, x)) v[e] = r;  // outside the window: left free
+            if (a.lt_amp > 0.f && (!in || !lt_in(a, y, x))) v[e] = r;  // outside the window / ROI: left free
             else v[e] = m2 > 0.f ? make_float2(gm * r.x * rs, gm * r.y * rs) : make_float2(gm, 0.f);
         });
         line_fft<P, +1, 1, LAY>(v, sf, a.tw, t, gsync);
@@ -277,9 +296,16 @@ __global__ void __launch_bounds__(RowPipeCfg<P, LINES, NG, D, SWZ>::THREADS, 1)
                 fw[t + TL * e] = v[e];
             });
         }
-        if (a.part)
-            group_sum4<GT>(acc0, acc1, acc2, acc3, red + (size_t)g * Cfg::GW * NMET,
-                           a.part + ((size_t)item * ppt + pan) * NMET, gt, gsync);
+        if (a.part) {
+            if (a.gen) {
+                double *dst = a.part + ((size_t)item * ppt + pan) * NMET_GEN;
+                group_sum4<GT>(acc0, acc1, acc2, acc3, red + (size_t)g * Cfg::GW * NMET, dst, gt, gsync);
+                group_sum4<GT>(acc4, acc5, acc6, acc7, red + (size_t)g * Cfg::GW * NMET, dst + NMET, gt, gsync);
+            } else {
+                group_sum4<GT>(acc0, acc1, acc2, acc3, red + (size_t)g * Cfg::GW * NMET,
+                               a.part + ((size_t)item * ppt + pan) * NMET, gt, gsync);
+            }
+        }
     }
 }
 
@@ -670,7 +696,30 @@ __global__ void __launch_bounds__(ColPipeCfg<P, C, NG, D, SWZ, BOXR>::THREADS, 1
             const float2 h = v[e];
             int q;
             float2 ph;
-            if constexpr (ROLE == COL_GS_BIN) {
+            if constexpr (ROLE == COL_GS_MOD) {
+                // as the generic column pass: the level nearest h / E, light E x level
+                const float2 E = __ldg(a.illum + (size_t)(t + TL * e) * nx + (act ? x : nx - 1));
+                const float hr = fmaf(h.x, E.x, h.y * E.y), hi = fmaf(h.y, E.x, -h.x * E.y);
+                if (a.kind == 2) {
+                    const float e2 = fmaf(E.x, E.x, E.y * E.y);
+                    const float m = e2 > 0.f ? hr / e2 : 0.f;
+                    const float lv = (float)(a.levels - 1) * fmaf(m, a.amp_gain, 0.5f);
+                    q = (int)roundf(fminf(fmaxf(lv, 0.f), (float)(a.levels - 1)));
+                    const float tr = __ldg(a.lvl + q).x;
+                    ph = make_float2(E.x * tr, E.y * tr);
+                } else {
+                    float2 l;
+                    if (a.kind == 0) {
+                        q = hr >= 0.f ? 0 : 1;
+                        l = make_float2(q ? -1.f : 1.f, 0.f);
+                    } else {
+                        q = (int)roundf(atan2f(hi, hr) * a.qscale) % a.levels;
+                        if (q < 0) q += a.levels;
+                        l = __ldg(a.lvl + q);
+                    }
+                    ph = make_float2(E.x * l.x - E.y * l.y, fmaf(E.x, l.y, E.y * l.x));
+                }
+            } else if constexpr (ROLE == COL_GS_BIN) {
                 q = h.x >= 0.f ? 0 : 1;
                 ph = make_float2(q ? -1.f : 1.f, 0.f);
             } else {
@@ -1034,6 +1083,9 @@ struct PipeImpl {
             e = cudaFuncSetAttribute((const void *)k_col_pipe<PC, COL_GS_LVL, C, NGC, DC, SWZC, BOXR>,
                                      cudaFuncAttributeMaxDynamicSharedMemorySize, (int)CC::SMEM);
         if (e == cudaSuccess)
+            e = cudaFuncSetAttribute((const void *)k_col_pipe<PC, COL_GS_MOD, C, NGC, DC, SWZC, BOXR>,
+                                     cudaFuncAttributeMaxDynamicSharedMemorySize, (int)CC::SMEM);
+        if (e == cudaSuccess)
             e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
                 &cb, k_col_pipe<PC, COL_GS_BIN, C, NGC, DC, SWZC, BOXR>, CC::THREADS, CC::SMEM);
         if (e != cudaSuccess) return e;
@@ -1052,6 +1104,8 @@ struct PipeImpl {
                        cudaStream_t s) {
         if (role == COL_GS_BIN)
             k_col_pipe<PC, COL_GS_BIN, C, NGC, DC, SWZC, BOXR><<<grid, CC::THREADS, CC::SMEM, s>>>(a, pa, m);
+        else if (role == COL_GS_MOD)
+            k_col_pipe<PC, COL_GS_MOD, C, NGC, DC, SWZC, BOXR><<<grid, CC::THREADS, CC::SMEM, s>>>(a, pa, m);
         else
             k_col_pipe<PC, COL_GS_LVL, C, NGC, DC, SWZC, BOXR><<<grid, CC::THREADS, CC::SMEM, s>>>(a, pa, m);
     }

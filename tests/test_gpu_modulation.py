@@ -80,10 +80,10 @@ def setup_case(c):
     return f32, amp, ph, roi, E
 
 
-def run_gpu(c, t, ph0, iters, amp, ph, roi, f32):
+def run_gpu(c, t, ph0, iters, amp, ph, roi, f32, pipe=-1):
     ny, nx, kind, levels = c[:4]
     batch = t.shape[0]
-    plan = hg.Plan(ny, nx, batch, kind, levels, hg.HG_GS, modulated=True, fresnel=f32)
+    plan = hg.Plan(ny, nx, batch, kind, levels, hg.HG_GS, modulated=True, fresnel=f32, pipeline=pipe)
     try:
         plan.set_illumination(None if amp is None else torch.from_numpy(amp).to(DEV),
                               None if ph is None else torch.from_numpy(ph).to(DEV))
@@ -96,21 +96,26 @@ def run_gpu(c, t, ph0, iters, amp, ph, roi, f32):
         met = plan.metrics().cpu().numpy()
         ev = plan.evaluate(holo, T)
         plan.sync()
-        assert hg.hg_plan_variant(plan.h, 0) == "generic"
+        assert "pair" not in hg.hg_plan_variant(plan.h, 0)
+        assert hg.hg_pipelined(plan.h) == (0 if pipe == 0 else 3)
         return holo.cpu().numpy(), mse.cpu().numpy(), met, ev.cpu().numpy()
     finally:
         plan.close()
 
 
+@pytest.mark.parametrize("pipe", [1, 0], ids=["tma", "generic"])
 @pytest.mark.parametrize("c", CASES, ids=case_id)
-def test_modulated_gs_matches_oracle(c):
+def test_modulated_gs_matches_oracle(c, pipe):
+    """Both the TMA-fed passes (where the size has them: 256, 512) and the generic ones."""
     ny, nx, kind, levels = c[:4]
+    if pipe == 1 and min(ny, nx) < 256:
+        pytest.skip("TMA-fed passes exist from 256 samples per line")
     f32, amp, ph, roi, E = setup_case(c)
     batch = 2
     t = synth.targets(batch, ny, nx, 5100)
     ph0 = synth.init_phases(batch, ny, nx, 5100)
-    holo2, mse2, met2, ev2 = run_gpu(c, t, ph0, 2, amp, ph, roi, f32)
-    _, mse6, _, _ = run_gpu(c, t, ph0, 6, amp, ph, roi, f32)
+    holo2, mse2, met2, ev2 = run_gpu(c, t, ph0, 2, amp, ph, roi, f32, pipe)
+    _, mse6, _, _ = run_gpu(c, t, ph0, 6, amp, ph, roi, f32, pipe)
     for b in range(batch):
         o2 = oracle.modulated_run(t[b], ph0[b].astype(np.float64), 2, okind(kind), levels, E=E, roi=roi)
         bad = np.mean(holo2[b] != o2["holo"])
