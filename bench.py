@@ -468,6 +468,7 @@ def main():
     import torch
     import __graft_entry__
     from paper_2008_12214_gb300 import hologen as hg
+    from paper_2008_12214_gb300 import shard
     from paper_2008_12214_gb300 import synth
 
     rank, local, world = dist_env()
@@ -484,7 +485,7 @@ def main():
     __graft_entry__.build()
 
     B = args.batch
-    base = 1000 + rank * B
+    base = shard.target_seeds(rank, B)[0]
     t_host = synth.targets(B, NY, NX, base)
     p_host = synth.init_phases(B, NY, NX, base)
     T = torch.from_numpy(t_host).to(dev)
@@ -520,11 +521,8 @@ def main():
     el_ms = e0.elapsed_time(e1)
     prof = hg.hg_profile_read(plan.h)
     hg.hg_profile_enable(plan.h, 0)
-    if world > 1:
-        t = torch.tensor([el_ms], device=dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        el_ms = float(t.item())
-    value = world * args.steps * args.iters / (el_ms / 1e3)
+    el_ms = shard.max_over_ranks(el_ms, dev)
+    value = shard.weak_scaling_rate(world, args.steps * args.iters, el_ms / 1e3)
 
     # end to end through the C ABI with pinned host buffers (copies inside)
     e2e = None
@@ -541,11 +539,8 @@ def main():
         for _ in range(e2e_steps):
             plan.run(tp, pp, args.iters, hp, mp)
         e2e_s = time.perf_counter() - w0
-        if world > 1:
-            t = torch.tensor([e2e_s], device=dev, dtype=torch.float64)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            e2e_s = float(t.item())
-        e2e = dict(value=world * e2e_steps * args.iters / e2e_s, unit=UNIT,
+        e2e_s = shard.max_over_ranks(e2e_s, dev)
+        e2e = dict(value=shard.weak_scaling_rate(world, e2e_steps * args.iters, e2e_s), unit=UNIT,
                    h2d_bytes_per_step=int(tp.numel() * 4 + pp.numel() * 4),
                    d2h_bytes_per_step=int(hp.numel() + mp.numel() * 8))
     variants = (hg.hg_plan_variant(plan.h, 0), hg.hg_plan_variant(plan.h, 1))
