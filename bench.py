@@ -77,9 +77,18 @@ def dist_env():
         os.environ.get("WORLD_SIZE", 1))
 
 
+# Sources of the GS passes that the roofline and the committed DRAM traffic
+# describe: the line engine, the passes, their instantiations and their
+# launches.  A change to any of them makes the committed traffic stale.
+GS_SOURCES = ("hg_fft.cuh", "hg_kernels.cuh", "hg_pipe.cuh", "hg_api.cu", "ops_*.cu")
+
+
 def src_hash():
     h = hashlib.sha256()
-    for f in sorted(glob.glob(os.path.join(ROOT, "paper_2008_12214_gb300", "csrc", "*"))):
+    files = set()
+    for pat in GS_SOURCES:
+        files.update(glob.glob(os.path.join(ROOT, "paper_2008_12214_gb300", "csrc", pat)))
+    for f in sorted(files):
         with open(f, "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]

@@ -88,6 +88,16 @@ hg_status hg_cnn_gradients(hg_cnn net, const float *target, const float *phase_l
 hg_status hg_cnn_train_step(hg_cnn net, const float *target, const float *phase_label, int batch, float lr,
                             double *loss_out);
 
+/* One Adam update of every parameter from the given gradient vector
+ * (HG_CNN_NPARAMS floats, device or host, parameter order above) with
+ * learning rate lr; the step counter advances and hg_cnn_get_grads then
+ * returns these gradients.  With the gradients of hg_cnn_gradients this is
+ * hg_cnn_train_step; data-parallel training averages each rank's gradients
+ * over the ranks (an all-reduce) in between.  The paper has no network, so
+ * no counterpart there.  Errors: HG_ERR_INVALID_ARG (NULL, lr <= 0),
+ * HG_ERR_CUDA. */
+hg_status hg_cnn_apply_grads(hg_cnn net, const float *grads, float lr);
+
 /* Waits for the net's stream; HG_ERR_TIMEOUT if a bounded device wait gave
  * up, HG_ERR_INVALID_ARG if a target held a negative / NaN / infinite value,
  * HG_ERR_NUMERIC for an all-zero target. */

@@ -856,6 +856,22 @@ hg_status hg_cnn_train_step(hg_cnn n, const float *T, const float *phi, int B, f
     return HG_OK;
 }
 
+hg_status hg_cnn_apply_grads(hg_cnn n, const float *grads, float lr) {
+    if (!n || !grads || !(lr > 0.f)) return HG_ERR_INVALID_ARG;
+    CnnGuard g(n->dev);
+    n->launches = 0;
+    CN_CK(cudaMemcpyAsync(n->grad, grads, sizeof(float) * kTab.n, cudaMemcpyDefault, n->s));
+    n->step++;
+    const double b1 = 0.9, b2 = 0.999;
+    const float bc1 = (float)(1.0 / (1.0 - std::pow(b1, (double)n->step)));
+    const float bc2 = (float)(1.0 / (1.0 - std::pow(b2, (double)n->step)));
+    k_adam<<<ew_blocks(kTab.n, n->nsm), 256, 0, n->s>>>(n->theta, n->grad, n->m, n->v, kTab.n, 1, lr, (float)b1,
+                                                        (float)b2, 1e-8f, bc1, bc2, n->wf, n->wt);
+    n->launches++;
+    CN_CK(cudaGetLastError());
+    return HG_OK;
+}
+
 hg_status hg_cnn_sync(hg_cnn n) {
     if (!n) return HG_ERR_INVALID_ARG;
     CnnGuard g(n->dev);

@@ -103,6 +103,7 @@ def lib():
                            ("hg_cnn_get_grads", [P, P]), ("hg_cnn_forward", [P, P, I, P, P]),
                            ("hg_cnn_gradients", [P, P, P, I, P]),
                            ("hg_cnn_train_step", [P, P, P, I, ctypes.c_float, P]), ("hg_cnn_sync", [P]),
+                           ("hg_cnn_apply_grads", [P, P, ctypes.c_float]),
                            ("hg_cnn_launch_count", [P]),
                            ("hg_conv3x3_forward", [P, I, I, I, I, P, I, P, I, P, P, P]),
                            ("hg_conv3x3_dgrad", [P, I, I, I, I, P, I, P, P, P]),
@@ -449,6 +450,11 @@ def hg_cnn_train_step(net, target, phase_label, batch, lr, loss_out=None):
     _ck(lib().hg_cnn_train_step(net, _ptr(target, torch.float32, name="target"),
                                 _ptr(phase_label, torch.float32, name="phase_label"), int(batch), float(lr),
                                 _ptr(loss_out, torch.float64, name="loss_out")), "hg_cnn_train_step")
+
+
+def hg_cnn_apply_grads(net, grads, lr):
+    _ck(lib().hg_cnn_apply_grads(net, _ptr(grads, torch.float32, HG_CNN_NPARAMS, name="grads"), float(lr)),
+        "hg_cnn_apply_grads")
 
 
 def hg_cnn_sync(net):

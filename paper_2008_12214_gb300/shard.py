@@ -57,6 +57,17 @@ def gather_rows(t: torch.Tensor, counts):
     return torch.cat([parts[r][: counts[r]] for r in range(world)])
 
 
+def average_over_ranks(t: torch.Tensor) -> torch.Tensor:
+    """In place: t becomes the mean of every rank's t (an all-reduce), the
+    exchange of data-parallel training (each rank's gradient of its shard's
+    mean loss; equal shards make the mean of the means the whole batch's)."""
+    import torch.distributed as dist
+    if dist.is_available() and dist.is_initialized() and dist.get_world_size() > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.SUM)
+        t.div_(dist.get_world_size())
+    return t
+
+
 def weak_scaling_rate(world: int, units_per_rank: float, max_seconds: float) -> float:
     """Whole-job throughput: the units all ranks processed over the slowest
     rank's time."""

@@ -27,6 +27,7 @@ import numpy as np
 import torch
 
 from . import hologen as hg
+from . import shard
 from . import synth
 
 HELDOUT_BASE = 10 ** 6
@@ -90,6 +91,19 @@ def train(H, W, pairs, batch=8, lr=1e-3, seed=0, chunk=64, label_iters=200, epoc
         plan.close()
     losses = lhist[:step].cpu().numpy().tolist()
     return net, losses, time.time() - t0
+
+
+def dp_train_step(net, T, phi, batch, lr, grad_buf, loss=None):
+    """One data-parallel training step: this rank's gradients of its batch
+    (hg_cnn_gradients), averaged over the ranks (shard.average_over_ranks,
+    an NCCL all-reduce on GPU ranks; nothing with one rank), then one Adam
+    update (hg_cnn_apply_grads), the same on every rank.  grad_buf: float32
+    [HG_CNN_NPARAMS] on the net's device; loss (double [1]) gets this rank's
+    loss.  Every call is on the current stream, as the net's calls are."""
+    hg.hg_cnn_gradients(net.h, T, phi, batch, loss)
+    hg.hg_cnn_get_grads(net.h, grad_buf)
+    shard.average_over_ranks(grad_buf)
+    hg.hg_cnn_apply_grads(net.h, grad_buf, lr)
 
 
 def evaluate(net, H, W, n, ref_iters=100, max_iters=100, chunk=64, base_seed=HELDOUT_BASE,

@@ -291,3 +291,32 @@ def test_checkpoint_resume_continues_training_bit_for_bit():
         a.close()
         b.close()
     assert torch.equal(pa, pb)
+
+
+def test_data_parallel_step_with_one_rank_is_the_fused_step():
+    """warmstart.dp_train_step (gradients, the rank average, hg_cnn_apply_grads)
+    with one rank equals hg_cnn_train_step bit for bit over three steps; the
+    average over ranks itself is tested on two gloo ranks on CPU."""
+    from paper_2008_12214_gb300 import warmstart
+    B, H, W = 2, 128, 128
+    T, phi = net_inputs(B, H, W, 610)
+    Td, Pd = torch.from_numpy(T).to(DEV), torch.from_numpy(phi).to(DEV)
+    a, b = hg.CNN(H, W, B, seed=6), hg.CNN(H, W, B, seed=6)
+    try:
+        g = torch.empty(hg.HG_CNN_NPARAMS, dtype=torch.float32, device=DEV)
+        la = torch.zeros(1, dtype=torch.float64, device=DEV)
+        lb = torch.zeros(1, dtype=torch.float64, device=DEV)
+        for _ in range(3):
+            hg.hg_cnn_train_step(a.h, Td, Pd, B, 1e-3, la)
+            warmstart.dp_train_step(b, Td, Pd, B, 1e-3, g, lb)
+        sa = torch.empty(3 * hg.HG_CNN_NPARAMS, dtype=torch.float32, device=DEV)
+        sb = torch.empty_like(sa)
+        ka = hg.hg_cnn_get_state(a.h, sa)
+        kb = hg.hg_cnn_get_state(b.h, sb)
+        hg.hg_cnn_sync(a.h)
+        hg.hg_cnn_sync(b.h)
+    finally:
+        a.close()
+        b.close()
+    assert ka == kb == 3
+    assert torch.equal(sa, sb) and torch.equal(la, lb)
