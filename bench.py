@@ -43,7 +43,7 @@ BATCH = 64
 BYTES_ROW, BYTES_COL = 20, 16
 BYTES_ROW_PAIRED, BYTES_COL_PAIRED = 16, 12
 BYTES_ROW_HERM, BYTES_COL_HERM = 12, 8
-BYTES_SURVEY = 36
+BYTES_FUSED = 36
 DATA = ("synthetic: seeded targets of 16 Gaussian blobs + 8 rectangles per 1024x1024 field "
         "(seeds 1000 + rank*64 + b), initial phase U[0, 2 pi)")
 
@@ -617,9 +617,9 @@ def main():
         whole_iteration=dict(
             ms=iter_ms, bytes_per_px_moved=b_row + b_col,
             gbs_moved=(b_row + b_col) * npx / (iter_ms / 1e3) / 1e9,
-            bytes_per_px_36=BYTES_SURVEY,
-            gbs_at_36=BYTES_SURVEY * npx / (iter_ms / 1e3) / 1e9,
-            frac_at_36=BYTES_SURVEY * npx / (iter_ms / 1e3) / 1e9 / peak),
+            bytes_per_px_36=BYTES_FUSED,
+            gbs_at_36=BYTES_FUSED * npx / (iter_ms / 1e3) / 1e9,
+            frac_at_36=BYTES_FUSED * npx / (iter_ms / 1e3) / 1e9 / peak),
         roofline=roofline,
         passes={k: dict(avg_ms=v["ms"], gbs=v["gbs"], frac=(v["gbs"] / peak if v["gbs"] else None),
                         launches=v["launches"], bytes_per_px=v["bytes"] / npx, variant=v["variant"],

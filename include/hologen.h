@@ -343,7 +343,7 @@ void hg_group_destroy(hg_group group);
  * within a fixed frame time (cudaMalloc and cudaFree may synchronise the
  * whole device and take milliseconds, stalling every other stream); an
  * application whose device memory is owned by another framework's pool or
- * capped by a budget it may not exceed; code that must not meet an
+ * capped at a size it may not exceed; code that must not meet an
  * out-of-memory error once it is running.  hg_run cannot serve them because
  * creating a plan allocates its workspace.
  *

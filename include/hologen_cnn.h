@@ -7,7 +7,7 @@
  * The paper (HoloGen, arXiv:2008.12214) has no network: GS and its variants
  * (Section 3.2) start from a free replay phase, and this net only proposes
  * that phase; GS still iterates to its error as before.  Plain random-phase
- * GS stays the fallback and the judge of the net's value.
+ * GS stays the fallback and the measure of the net's value.
  *
  * Network (all 3x3 convolutions zero-padded and followed by ReLU):
  *   encoder levels 0..3 of widths 32, 64, 128, 256, two convolutions each,

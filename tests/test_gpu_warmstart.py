@@ -1,7 +1,7 @@
 """The learned warm start end to end (labels from the engine's own GS,
 training through the tensor-core kernels, time-to-MSE evaluation), at a
 size that trains in seconds.  GS started from the network's phase must
-still reach plain GS's quality (GS remains the judge and the fallback);
+still reach plain GS's quality (GS remains the yardstick and the fallback);
 the gain itself is printed and is measured at full size by bench.py."""
 import numpy as np
 import pytest
