@@ -237,8 +237,9 @@ hg_status hg_set_roi(hg_plan plan, const uint8_t *roi);
  * ROI (means, population variances and covariance; k1 = 0.01, k2 = 0.03,
  * dynamic range 1) of x = T / max T and y = sqrt(I) / max T, i.e. the
  * phase-insensitive (amplitude) variant.  Errors: HG_ERR_INVALID_ARG (NULL,
- * negative / NaN / infinite target values, found on the device),
- * HG_ERR_OOM, HG_ERR_CUDA. */
+ * negative / NaN / infinite target values), HG_ERR_NUMERIC (a target with
+ * no energy in the region of interest) -- both found on the device, so with
+ * device pointers returned by hg_sync -- HG_ERR_OOM, HG_ERR_CUDA. */
 hg_status hg_evaluate(hg_plan plan, const uint8_t *holo, const float *target, double *out);
 
 /* Replay phase arg R after the last GS/WGS run (0 where R = 0), replay order,

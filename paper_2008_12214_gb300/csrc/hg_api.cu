@@ -340,12 +340,13 @@ k_eval2(const float *I0, const float *t, const uint8_t *roi, int npx, const doub
 // SSIM of Section 3.1 with c1 = 0.01^2, c2 = 0.03^2 (dynamic range 1);
 // sum |R|^2 in unitary units = N sum I0 for I0 = |R|^2 / N.
 __global__ void k_eval_fin(const double *part1, const double *part2, int batch, const unsigned long long *nroi,
-                           double N, double *out) {
+                           double N, double *out, unsigned *err) {
     const int b = blockIdx.x * blockDim.x + threadIdx.x;
     if (b >= batch) return;
     const double n_roi = nroi ? (double)*nroi : N;
     double g[EV_S1], h[EV_S2] = {0, 0, 0, 0, 0, 0, 0};
     ev_totals(part1, b, g);
+    if (!(g[2] > 0)) atomicOr(err, ERR_ZERO_ENERGY);  // no target energy in the region of interest
     for (int k = 0; k < EV_BLOCKS; ++k)
         for (int m = 0; m < EV_S2; ++m) h[m] += part2[((size_t)b * EV_BLOCKS + k) * EV_S2 + m];
     const double mx = h[2] / n_roi, my = h[3] / n_roi;
@@ -1728,7 +1729,7 @@ hg_status hg_evaluate(hg_plan p, const uint8_t *holo, const float *target, doubl
     k_eval1<<<eg, EV_THREADS, 0, p->stream>>>(p->ev_buf, d_t, p->roi_rep, (int)p->npx, part1, p->err);
     k_eval2<<<eg, EV_THREADS, 0, p->stream>>>(p->ev_buf, d_t, p->roi_rep, (int)p->npx, part1, part2, nullptr);
     k_eval_fin<<<(p->batch + 127) / 128, 128, 0, p->stream>>>(part1, part2, p->batch, p->nroi, (double)p->npx,
-                                                               d_o);
+                                                               d_o, p->err);
     p->launches += 3;
     HG_CK(cudaGetLastError());
     if (o_host) HG_CK(cudaMemcpyAsync(out, d_o, obytes, cudaMemcpyDeviceToHost, p->stream));

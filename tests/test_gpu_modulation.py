@@ -215,3 +215,31 @@ def test_modulated_plan_rules():
         plan.sync()
     finally:
         plan.close()
+
+
+def test_evaluate_reports_bad_and_empty_targets():
+    plan = hg.Plan(64, 64, 2, hg.HG_SLM_BINARY, 2, hg.HG_GS, modulated=True)
+    try:
+        holo = torch.zeros((2, 64, 64), dtype=torch.uint8, device=DEV)
+        t = torch.from_numpy(synth.targets(2, 64, 64, 3)).to(DEV)
+        out = torch.empty((2, 5), dtype=torch.float64, device=DEV)
+        hg.hg_evaluate(plan.h, holo, t, out)
+        plan.sync()
+        bad = t.clone()
+        bad[1, 5, 5] = float("nan")
+        hg.hg_evaluate(plan.h, holo, bad, out)
+        with pytest.raises(hg.HgError):
+            plan.sync()
+        roi = torch.zeros((64, 64), dtype=torch.uint8, device=DEV)
+        roi[0, 0] = 1
+        t2 = t.clone()
+        t2[:, 0, 0] = 0
+        plan.set_roi(roi)
+        hg.hg_evaluate(plan.h, holo, t2, out)
+        with pytest.raises(hg.HgError):
+            plan.sync()
+        plan.set_roi(None)
+        hg.hg_evaluate(plan.h, holo, t, out)
+        plan.sync()
+    finally:
+        plan.close()
