@@ -27,6 +27,10 @@ __device__ void search_sum4(float v0, float v1, float v2, float v3, double *dred
     __syncthreads();
 }
 
+// KK trials per pass over the pixels: SEARCH_K for direct search, whose trials
+// are mostly rejected, 1 for annealing, which accepts too many for speculation
+// to pay.
+template <int KK>
 __global__ void __launch_bounds__(SEARCH_MAX_THREADS) k_search(const SearchArgs a) {
     extern __shared__ __align__(16) unsigned char sm[];
     const int ny = a.ny, nx = a.nx, N = ny * nx, T = blockDim.x, tid = threadIdx.x, item = blockIdx.x;
@@ -92,70 +96,142 @@ __global__ void __launch_bounds__(SEARCH_MAX_THREADS) k_search(const SearchArgs 
                                              a.seed_hi);
                 __syncthreads();
             }
-            for (int x = 0; x < nx; ++x) {
-                const int p = y * nx + x;
-                const uint2 r = need_rand ? rnd[x] : make_uint2(0u, 0u);
-                const int q = hq[p];
-                int qn;
-                float2 ds;
-                if (a.binary) {
-                    qn = 1 - q;
-                    ds = make_float2(q ? 2.f : -2.f, 0.f);
-                } else {
-                    qn = (q + 1 + (int)(r.y % (uint32_t)(a.levels - 1))) % a.levels;
-                    const float2 l1 = __ldg(a.lvl + qn), l0 = __ldg(a.lvl + q);
-                    ds = make_float2(l1.x - l0.x, l1.y - l0.y);
-                }
-                const float2 wx = twx[ex];
-                // dR_k = c w_k with |w_k| = 1, so the intensity change is
-                // a_k = Re(R_k conj(w_k) conj(c)) 2 / N + |c|^2 / N
-                const float2 c = make_float2((ds.x * wx.x - ds.y * wx.y) * a.invSqrtN,
-                                             (ds.x * wx.y + ds.y * wx.x) * a.invSqrtN);
-                const float s2 = 2.f * a.invN;
-                const float2 c2 = make_float2(c.x * s2, c.y * s2);
-                const float cc = fmaf(c.x, c.x, c.y * c.y) * a.invN;
-                float part = 0.f;
-                int ey = eyb;
-                for (int j = 0; j < J; ++j) {
-                    const int k = tid + T * j;
-                    if (full || k < N) {
-                        const float2 w = twy[ey];
-                        const float2 rv = R[k];
-                        const float zx = fmaf(rv.x, w.x, rv.y * w.y), zy = fmaf(rv.y, w.x, -rv.x * w.y);
-                        const float aa = fmaf(zx, c2.x, fmaf(zy, c2.y, cc));
-                        part = fmaf(aa, G[k] + aa, part);
-                    }
-                    ey += st;
-                    if (ey >= ny) ey -= ny;
-                }
+            // KK trials (pixels x0 .. x0 + kb - 1 of the row) are evaluated from the
+            // same state in one pass; the first accepted one is applied and the search
+            // resumes after it, so every decision is the sequential search's
+            {
+                for (int x0 = 0; x0 < nx;) {
+                    const int kb = min(KK, nx - x0);
+                    const float s2 = 2.f * a.invN;
+                    float2 c2[KK];
+                    float cc[KK], part[KK];
+                    int exs[KK];        // x twiddle index of each trial
+                    unsigned qpk = 0u;  // each trial's current level, one byte per trial
+                    float2 c1 = make_float2(0.f, 0.f);  // KK == 1: the trial's dR coefficient
+                    int qn[KK];
+                    float u[KK];  // acceptance draws
+                    int exk = ex;
 #pragma unroll
-                for (int off = 16; off; off >>= 1) part += __shfl_down_sync(0xffffffffu, part, off);
-                if (lane == 0) red[buf * 32 + warp] = part;
-                __syncthreads();
-                float dE = 0.f;
-                for (int w = 0; w < nw; ++w) dE += red[buf * 32 + w];
-                dE *= a.invN;
-                buf ^= 1;
-                const float u = (float)(r.x >> 8) * (1.0f / 16777216.0f);
-                if (dE < 0.f || (tau > 0.f && u < expf(-dE / tau))) {
-                    ey = eyb;
+                    for (int k = 0; k < KK; ++k) {
+                        part[k] = 0.f;
+                        c2[k] = make_float2(0.f, 0.f);
+                        exs[k] = 0;
+                        cc[k] = 0.f;
+                        qn[k] = 0;
+                        u[k] = 0.f;
+                        if (k < kb) {
+                            const uint2 r = need_rand ? rnd[x0 + k] : make_uint2(0u, 0u);
+                            u[k] = (float)(r.x >> 8) * (1.0f / 16777216.0f);
+                            const int q = hq[y * nx + x0 + k];
+                            qpk |= (unsigned)q << (8 * k);
+                            float2 ds;
+                            if (a.binary) {
+                                qn[k] = 1 - q;
+                                ds = make_float2(q ? 2.f : -2.f, 0.f);
+                            } else {
+                                qn[k] = (q + 1 + (int)(r.y % (uint32_t)(a.levels - 1))) % a.levels;
+                                const float2 l1 = __ldg(a.lvl + qn[k]), l0 = __ldg(a.lvl + q);
+                                ds = make_float2(l1.x - l0.x, l1.y - l0.y);
+                            }
+                            // dR_i = c w_i with |w_i| = 1, so the intensity change is
+                            // a_i = Re(R_i conj(w_i) conj(c)) 2 / N + |c|^2 / N
+                            const float2 wx = twx[exk];
+                            const float2 ck = make_float2((ds.x * wx.x - ds.y * wx.y) * a.invSqrtN,
+                                                          (ds.x * wx.y + ds.y * wx.x) * a.invSqrtN);
+                            c2[k] = make_float2(ck.x * s2, ck.y * s2);
+                            cc[k] = fmaf(ck.x, ck.x, ck.y * ck.y) * a.invN;
+                            exs[k] = exk;
+                            if constexpr (KK == 1) c1 = ck;
+                            exk += kx;
+                            if (exk >= nx) exk -= nx;
+                        }
+                    }
+                    int ey = eyb;
                     for (int j = 0; j < J; ++j) {
-                        const int k = tid + T * j;
-                        if (full || k < N) {
+                        const int i = tid + T * j;
+                        if (full || i < N) {
                             const float2 w = twy[ey];
-                            const float2 rv = R[k];
+                            const float2 rv = R[i];
+                            const float g = G[i];
                             const float zx = fmaf(rv.x, w.x, rv.y * w.y), zy = fmaf(rv.y, w.x, -rv.x * w.y);
-                            G[k] += 2.f * fmaf(zx, c2.x, fmaf(zy, c2.y, cc));  // I gains a_k
-                            R[k] = make_float2(rv.x + (c.x * w.x - c.y * w.y), rv.y + fmaf(c.x, w.y, c.y * w.x));
+#pragma unroll
+                            for (int k = 0; k < KK; ++k) {
+                                const float aa = fmaf(zx, c2[k].x, fmaf(zy, c2[k].y, cc[k]));
+                                part[k] = fmaf(aa, g + aa, part[k]);
+                            }
                         }
                         ey += st;
                         if (ey >= ny) ey -= ny;
                     }
-                    if (tid == 0) hq[p] = (uint8_t)qn;
-                    ++accepted;
+#pragma unroll
+                    for (int k = 0; k < KK; ++k) {
+#pragma unroll
+                        for (int off = 16; off; off >>= 1) part[k] += __shfl_down_sync(0xffffffffu, part[k], off);
+                        if (lane == 0) red[(buf * SEARCH_K + k) * 32 + warp] = part[k];
+                    }
+                    __syncthreads();
+                    int jacc = -1;
+                    for (int k = 0; k < kb; ++k) {
+                        float dE = 0.f;
+                        for (int w = 0; w < nw; ++w) dE += red[(buf * SEARCH_K + k) * 32 + w];
+                        dE *= a.invN;
+                        if (dE < 0.f || (tau > 0.f && u[k] < expf(-dE / tau))) {
+                            jacc = k;
+                            break;
+                        }
+                    }
+                    buf ^= 1;
+                    if (jacc >= 0) {
+                        float2 c2j = c2[0];
+                        float ccj = cc[0];
+                        int qj = qn[0], exj = exs[0];
+#pragma unroll
+                        for (int k = 1; k < KK; ++k)
+                            if (k == jacc) {
+                                c2j = c2[k];
+                                ccj = cc[k];
+                                qj = qn[k];
+                                exj = exs[k];
+                            }
+                        // the accepted trial's dR coefficient, as computed for its evaluation
+                        // (its old level was read before the barrier: thread 0 rewrites it below)
+                        float2 cj = c1;
+                        if constexpr (KK > 1) {
+                            const int q = (int)((qpk >> (8 * jacc)) & 0xffu);
+                            float2 ds;
+                            if (a.binary) {
+                                ds = make_float2(q ? 2.f : -2.f, 0.f);
+                            } else {
+                                const float2 l1 = __ldg(a.lvl + qj), l0 = __ldg(a.lvl + q);
+                                ds = make_float2(l1.x - l0.x, l1.y - l0.y);
+                            }
+                            const float2 wx = twx[exj];
+                            cj = make_float2((ds.x * wx.x - ds.y * wx.y) * a.invSqrtN,
+                                             (ds.x * wx.y + ds.y * wx.x) * a.invSqrtN);
+                        }
+                        ey = eyb;
+                        for (int j = 0; j < J; ++j) {
+                            const int i = tid + T * j;
+                            if (full || i < N) {
+                                const float2 w = twy[ey];
+                                const float2 rv = R[i];
+                                const float zx = fmaf(rv.x, w.x, rv.y * w.y), zy = fmaf(rv.y, w.x, -rv.x * w.y);
+                                G[i] += 2.f * fmaf(zx, c2j.x, fmaf(zy, c2j.y, ccj));  // I gains a_i
+                                R[i] = make_float2(rv.x + (cj.x * w.x - cj.y * w.y), rv.y + fmaf(cj.x, w.y, cj.y * w.x));
+                            }
+                            ey += st;
+                            if (ey >= ny) ey -= ny;
+                        }
+                        if (tid == 0) hq[y * nx + x0 + jacc] = (uint8_t)qj;
+                        ++accepted;
+                    }
+                    const int adv = jacc >= 0 ? jacc + 1 : kb;
+                    for (int k = 0; k < adv; ++k) {
+                        ex += kx;
+                        if (ex >= nx) ex -= nx;
+                    }
+                    x0 += adv;
                 }
-                ex += kx;
-                if (ex >= nx) ex -= nx;
             }
             eyb += ky0;
             if (eyb >= ny) eyb -= ny;
@@ -176,7 +252,7 @@ __global__ void __launch_bounds__(SEARCH_MAX_THREADS) k_search(const SearchArgs 
     for (int k = tid; k < N; k += T) a.holo[base + k] = hq[k];
 }
 
-bool g_search_attr[64];
+bool g_search_attr[64][2];
 
 }  // namespace
 
@@ -185,13 +261,15 @@ cudaError_t search_launch(const SearchArgs &a, const SearchLayout &L, cudaStream
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
     if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
-    if (!g_search_attr[dev]) {
-        e = cudaFuncSetAttribute((const void *)k_search, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)SEARCH_MAX_SMEM);
+    const int spec = a.tau0 > 0.0 ? 0 : 1;
+    const void *fn = spec ? (const void *)k_search<SEARCH_K> : (const void *)k_search<1>;
+    if (!g_search_attr[dev][spec]) {
+        e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SEARCH_MAX_SMEM);
         if (e != cudaSuccess) return e;
-        g_search_attr[dev] = true;
+        g_search_attr[dev][spec] = true;
     }
-    k_search<<<a.items, L.threads, L.bytes, s>>>(a);
+    if (spec) k_search<SEARCH_K><<<a.items, L.threads, L.bytes, s>>>(a);
+    else k_search<1><<<a.items, L.threads, L.bytes, s>>>(a);
     return cudaGetLastError();
 }
 

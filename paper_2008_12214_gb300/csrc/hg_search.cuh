@@ -7,18 +7,24 @@
 // by ds changes replay pixel (iy, ix), of frequency (ky, kx), by
 // dR = ds W_ny^(ky y) W_nx^(kx x) / sqrt(N), and the intensity MSE by
 // dE = mean(a (2 (I - T^2) + a)), a = (2 Re(R conj dR) + |dR|^2) / N,
-// I = |R|^2 / N (a phase hologram keeps sum |R|^2 = N).  Shared memory holds
+// I = |R|^2 / N (a phase hologram keeps sum |R|^2 = N).  SEARCH_K
+// consecutive trials are evaluated from the same state in one pass over the
+// pixels; the first one accepted is applied and the next pass starts after
+// it, so the decisions are those of the one-trial-at-a-time search.  Shared
+// memory holds
 // G = 2 (I - T^2) per replay pixel: an accepted change adds 2 a, and every
 // sweep recomputes G from R and T.  Every thread sums
 // its pixels' terms, warps reduce in float, and every thread adds the warp
 // partials in the same order, so all threads take the same decision after
-// one barrier per trial (the partials alternate between two buffers).
+// one barrier per pass of SEARCH_K trials (the partials alternate between
+// two buffers).
 #pragma once
 #include "hg_fft.cuh"
 
 namespace hg {
 
 constexpr int SEARCH_PX = 16;  // replay pixels per thread at most
+constexpr int SEARCH_K = 4;    // trials evaluated per barrier
 constexpr int SEARCH_MAX_THREADS = 1024;
 constexpr size_t SEARCH_MAX_SMEM = 227 * 1024;
 
@@ -74,7 +80,7 @@ inline bool search_layout(int ny, int nx, SearchLayout *L) {
     o += 4 * (size_t)N;
     o = (o + 7) & ~(size_t)7;
     L->off_red = o;
-    o += 2 * 32 * sizeof(float);
+    o += 2 * SEARCH_K * 32 * sizeof(float);
     L->off_dred = o;
     o += 32 * 4 * sizeof(double);
     L->off_rnd = o;  // Philox words 0 and 1 of one SLM row's trials
