@@ -137,13 +137,14 @@ def run_reference(args):
         ph = oracle.gs_step(T, ph)["phase"]
     el = time.perf_counter() - t0
     per = el / args.steps
-    value = 1.0 / (BATCH * per)
+    B = args.batch
+    value = 1.0 / (B * per)
     line = dict(impl="reference", metric=METRIC, value=value, unit=UNIT, n_gpus=world, steps=args.steps,
                 warmup=args.warmup, ms_per_step=per * 1e3, higher_is_better=True, scaling="weak",
                 vs_baseline=None, dtype="f64", data=DATA,
                 config=dict(workload="gs_binary_1024x1024_batch%d" % B, ny=NY, nx=NX, batch=B,
                             step="one GS iteration of one 1024x1024 target (bounded sample), "
-                                 "scaled to 64 targets"),
+                                 "scaled to %d targets" % B),
                 cpu_baseline=dict(kind="oracle", cores=cores, value=value, unit=UNIT,
                                   sample="%d x one 1024x1024 target-iteration" % args.steps),
                 e2e=dict(value=value, unit=UNIT, h2d_bytes_per_step=0, d2h_bytes_per_step=0))
