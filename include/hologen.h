@@ -150,6 +150,11 @@ typedef struct {
     float sa_cool;     /* SA: temperature factor per sweep, in (0, 1] (default 0.9) */
 } hg_opts;
 
+/* sizeof(hg_opts) as this library was built: a binding that lays the
+ * structure out itself compares it with its own before the first call (no
+ * counterpart in the paper). */
+size_t hg_opts_size(void);
+
 /* Fills *opts with the defaults: stream NULL, seed 0, subframes 24, lt_start
  * 0.25, lt_grow 10, modulated 0, fresnel 0, amp_clip 2, sa_temp 1e-3, sa_cool 0.9,
  * precision 0, use_graph 1, pipeline -1, autotune 1. */

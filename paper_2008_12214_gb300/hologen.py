@@ -54,6 +54,11 @@ def lib():
             raise RuntimeError("libhologen.so is not built (run paper_2008_12214_gb300.build.build())")
         L = ctypes.CDLL(LIB_PATH)
         P, I, Z = ctypes.c_void_p, ctypes.c_int, ctypes.c_size_t
+        L.hg_opts_size.argtypes = []
+        L.hg_opts_size.restype = Z
+        if L.hg_opts_size() != ctypes.sizeof(hg_opts):
+            raise RuntimeError("libhologen.so was built with another hg_opts layout (%d bytes, binding %d): "
+                               "rebuild it" % (L.hg_opts_size(), ctypes.sizeof(hg_opts)))
         L.hg_opts_default.argtypes = [ctypes.POINTER(hg_opts)]
         L.hg_opts_default.restype = None
         L.hg_supported_length.argtypes = [I]
