@@ -92,3 +92,21 @@ def test_null_handles_are_rejected(lib):
     assert lib.hg_replay(None, None, None) == 1
     assert lib.hg_last_launch_count(None) == 0
     lib.hg_plan_destroy(None)
+
+
+def test_plain_c_client_builds_and_runs(tmp_path):
+    """The boundary is a C ABI: a C program compiled with gcc against
+    include/*.h alone, linked to libhologen.so, runs the calls that need no
+    GPU."""
+    import shutil
+    import subprocess
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    pkg = os.path.join(root, "paper_2008_12214_gb300")
+    if not os.path.exists(os.path.join(pkg, "libhologen.so")) or shutil.which("gcc") is None:
+        pytest.skip("library or gcc missing")
+    exe = str(tmp_path / "c_abi_check")
+    subprocess.check_call(["gcc", "-std=c11", "-Wall", "-Werror", "-I", os.path.join(root, "include"),
+                           os.path.join(root, "tests", "c_abi_check.c"), "-L", pkg, "-lhologen",
+                           "-Wl,-rpath," + pkg, "-o", exe])
+    out = subprocess.run([exe], capture_output=True, text=True, timeout=120)
+    assert out.returncode == 0 and "c abi ok" in out.stdout, (out.returncode, out.stdout, out.stderr)
