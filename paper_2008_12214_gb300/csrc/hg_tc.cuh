@@ -65,7 +65,19 @@ constexpr int TC_N = 1024;      // row length served
 constexpr int TC_B = 8192;      // one 64 x 64 16-bit matrix
 constexpr int TC_A0 = 16384;    // 128 x 64, K-major
 constexpr int TC_A1 = 18432;    // 128 x 64, MN-major with padding
-constexpr int TC_SMEM = 1024 + 4 * TC_B + 2 * TC_A0 + 2 * TC_A1 + 256;  // + barrier, slots, reduction
+// Shared-memory layout per precision: the 4 B matrices, then the stage-0 and
+// stage-1 A operands (a low half of each only for the hi+lo precisions), then
+// the barrier, TMEM slot, flag and reduction.  Without the low halves a CTA
+// needs 69 KB instead of 104 KB, so three fit on an SM instead of two.
+template <bool SPLIT>
+struct TcLayout {
+    static constexpr int NA = SPLIT ? 2 : 1;
+    static constexpr int A0 = 4 * TC_B;
+    static constexpr int A1 = A0 + NA * TC_A0;
+    static constexpr int BAR = A1 + NA * TC_A1;
+    static constexpr int SMEM = 1024 + BAR + 256;
+    static_assert(TC_A0 + TC_A1 >= 4 * 1024 * 8, "the 2048 exchange buffer reuses the operand memory");
+};
 
 struct TcArgs {
     const uint4 *bmats;  // [fwd hi, fwd lo, inv hi, inv lo], each 64 x 64 K-major canonical
@@ -192,9 +204,10 @@ __device__ __forceinline__ void tc_fft(float2 (&v)[32], TcCtx &c, const float2 *
     using PR = TcPrec<PREC>;
     using T = typename PR::T;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    using L = TcLayout<PR::SPLIT>;
     unsigned char *B0 = c.sm + (DIR < 0 ? 0 : 2 * TC_B);
-    unsigned char *A0h = c.sm + 4 * TC_B, *A0l = A0h + TC_A0;
-    unsigned char *A1h = A0l + TC_A0, *A1l = A1h + TC_A1;
+    unsigned char *A0h = c.sm + L::A0, *A0l = A0h + TC_A0;  // low halves: hi+lo precisions only
+    unsigned char *A1h = c.sm + L::A1, *A1l = A1h + TC_A1;
     T *tag = nullptr;
 
     // ---- stage 0: vector (warp, lane), DFT over n2 = e
@@ -313,7 +326,7 @@ __global__ void __launch_bounds__(128, 1) k_row_tc(const RowArgs a, const TcArgs
     static_assert(NX == 1024 || NX == 2048, "tensor-core rows are 1024 or 2048 samples");
     extern __shared__ unsigned char smraw[];
     unsigned char *sm = smraw + ((1024 - (smem_addr(smraw) & 1023)) & 1023);
-    uint64_t *bar = reinterpret_cast<uint64_t *>(sm + 4 * TC_B + 2 * TC_A0 + 2 * TC_A1);
+    uint64_t *bar = reinterpret_cast<uint64_t *>(sm + TcLayout<TcPrec<PREC>::SPLIT>::BAR);
     uint32_t *tslot = reinterpret_cast<uint32_t *>(bar + 1);
     volatile int *flag = reinterpret_cast<volatile int *>(tslot + 1);
     double *red = reinterpret_cast<double *>(bar + 2);  // [4 warps][NMET]

@@ -8,30 +8,52 @@
 namespace hg {
 
 namespace {
+template <int PREC>
+constexpr int tc_smem() {
+    return TcLayout<TcPrec<PREC>::SPLIT>::SMEM;
+}
+
 template <int PREC, int NX>
 cudaError_t set_attr_n() {
     cudaError_t e = cudaFuncSetAttribute((const void *)k_row_tc<PREC, ROW_ITER, NX>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, TC_SMEM);
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, tc_smem<PREC>());
     if (e == cudaSuccess)
         e = cudaFuncSetAttribute((const void *)k_row_tc<PREC, ROW_TAIL, NX>,
-                                 cudaFuncAttributeMaxDynamicSharedMemorySize, TC_SMEM);
-    return e;
-}
-template <int PREC>
-cudaError_t set_attr() {
-    cudaError_t e = set_attr_n<PREC, 1024>();
-    if (e == cudaSuccess) e = set_attr_n<PREC, 2048>();
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize, tc_smem<PREC>());
     return e;
 }
 
+// resident CTAs per SM of each precision's kernel, per device (set by tc_init)
+int g_tc_occ[64][5];
+int g_tc_nsm[64];
+
+template <int PREC>
+cudaError_t set_attr(int dev) {
+    cudaError_t e = set_attr_n<PREC, 1024>();
+    if (e == cudaSuccess) e = set_attr_n<PREC, 2048>();
+    if (e == cudaSuccess)
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&g_tc_occ[dev][PREC], k_row_tc<PREC, ROW_ITER, 1024>, 128,
+                                                          tc_smem<PREC>());
+    return e;
+}
+
+// The grid fills the SMs with this precision's resident CTAs (the caller's
+// grid assumes the hi+lo layout's occupancy).
 template <int PREC>
 void launch(int role, const RowArgs &a, const TcArgs &ta, int grid, cudaStream_t s) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) == cudaSuccess && dev >= 0 && dev < 64 && g_tc_occ[dev][PREC] > 0 && g_tc_nsm[dev] > 0) {
+        const long work = (long)a.items * (a.ny / (a.nx == 2048 ? 2 : 4));
+        const long g = (long)g_tc_occ[dev][PREC] * g_tc_nsm[dev];
+        grid = (int)(g < work ? g : (work > 0 ? work : 1));
+    }
+    constexpr int SM = tc_smem<PREC>();
     if (a.nx == 2048) {
-        if (role == ROW_ITER) k_row_tc<PREC, ROW_ITER, 2048><<<grid, 128, TC_SMEM, s>>>(a, ta);
-        else k_row_tc<PREC, ROW_TAIL, 2048><<<grid, 128, TC_SMEM, s>>>(a, ta);
+        if (role == ROW_ITER) k_row_tc<PREC, ROW_ITER, 2048><<<grid, 128, SM, s>>>(a, ta);
+        else k_row_tc<PREC, ROW_TAIL, 2048><<<grid, 128, SM, s>>>(a, ta);
     } else {
-        if (role == ROW_ITER) k_row_tc<PREC, ROW_ITER, 1024><<<grid, 128, TC_SMEM, s>>>(a, ta);
-        else k_row_tc<PREC, ROW_TAIL, 1024><<<grid, 128, TC_SMEM, s>>>(a, ta);
+        if (role == ROW_ITER) k_row_tc<PREC, ROW_ITER, 1024><<<grid, 128, SM, s>>>(a, ta);
+        else k_row_tc<PREC, ROW_TAIL, 1024><<<grid, 128, SM, s>>>(a, ta);
     }
 }
 
@@ -48,12 +70,16 @@ uint16_t bits_of(float x, int prec, float *back) {
 }  // namespace
 
 cudaError_t tc_init(int *blocks_per_sm) {
-    cudaError_t e = set_attr<1>();
-    if (e == cudaSuccess) e = set_attr<2>();
-    if (e == cudaSuccess) e = set_attr<3>();
-    if (e == cudaSuccess) e = set_attr<4>();
-    if (e == cudaSuccess)
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k_row_tc<1, ROW_ITER, 1024>, 128, TC_SMEM);
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+    e = cudaDeviceGetAttribute(&g_tc_nsm[dev], cudaDevAttrMultiProcessorCount, dev);
+    if (e == cudaSuccess) e = set_attr<1>(dev);
+    if (e == cudaSuccess) e = set_attr<2>(dev);
+    if (e == cudaSuccess) e = set_attr<3>(dev);
+    if (e == cudaSuccess) e = set_attr<4>(dev);
+    if (e == cudaSuccess) *blocks_per_sm = g_tc_occ[dev][1];
     return e;
 }
 
