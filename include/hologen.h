@@ -136,9 +136,10 @@ typedef struct {
                           sum_ROI |R|^2, and average over the ROI; efficiency is
                           the energy on the target's support over all replay
                           energy.  GS only (not precision > 0), no
-                          hg_debug_step, else HG_ERR_INVALID_ARG.  Generic
-                          passes, or with pipeline 1 the TMA-fed passes without
-                          paired rows.  Default 0. */
+                          hg_debug_step, else HG_ERR_INVALID_ARG.  TMA-fed
+                          row passes without paired rows where the size has them
+                          and the generic column pass (pipeline 0: generic
+                          passes only; 1: both TMA-fed).  Default 0. */
     float fresnel;     /* Fresnel (mid-field) hologram, Section 2: the SLM-plane
                           field gains the quadratic phase fresnel * ((x - nx/2)^2
                           + (y - ny/2)^2) radians (pi dx^2 / (lambda z) for

@@ -387,7 +387,8 @@ int row_panels(const PipeOps *o, int ny) {
 
 // Autotuner cache: (device, ny, nx, items, slm kind) -> chosen candidates.
 struct TuneEntry {
-    int dev, ny, nx, items, kind;  // kind + 8 for modulated plans (no paired candidates)
+    int dev, ny, nx, items, kind;  // kind, + 8 for modulated plans (no paired candidates), + 16 more
+                                   // when their column pass stays generic
     const PipeOps *row, *col;
 };
 std::mutex g_tune_mu;
@@ -1287,10 +1288,12 @@ hg_status hg_plan_create(hg_plan *out, int ny, int nx, int batch, hg_slm slm, hg
         if (ce != cudaSuccess) return fail(map_err(ce));
     }
     // Pass variants are chosen (and timed) only once every buffer they touch exists;
-    // search plans run the generic passes.  Modulated plans run the generic passes unless
-    // pipeline is 1: their TMA-fed passes (unpaired: the light leaving the SLM, E e^{iH}, is
-    // complex, so no Hermitian symmetry) measured slower at 1024^2 x 64.
-    if (o.pipeline != 0 && !search && (!mod || o.pipeline == 1)) {
+    // search plans run the generic passes.  Modulated plans take unpaired TMA-fed rows (the
+    // light leaving the SLM, E e^{iH}, is complex, so no Hermitian symmetry) and the generic
+    // column pass, which measured faster than their TMA-fed one at 1024^2 x 64 (pipeline 1
+    // forces both TMA-fed passes).
+    const bool mod_col_generic = mod && o.pipeline != 1;
+    if (o.pipeline != 0 && !search) {
         // TMA-fed passes: row panels need 16-byte aligned rows of T (nx % 4 == 0);
         // the column tiles need a 16-byte multiple row pitch (nx even).
         const PipeOps *rc[8], *cc[8];
@@ -1310,7 +1313,7 @@ hg_status hg_plan_create(hg_plan *out, int ny, int nx, int batch, hg_slm slm, hg
             const PipeOps *all[8];
             const int k = pipe_candidates(ny, all, 8);
             CUtensorMap m;
-            for (int i = 0; i < k; ++i)
+            for (int i = 0; i < k && !mod_col_generic; ++i)
                 if (!all[i]->paired && all[i]->col_gs && nx % 2 == 0 &&
                     ensure_pipe_init(p->dev, all[i]) == cudaSuccess && make_cmap(p, all[i], &m))
                     cc[nc++] = all[i];
@@ -1327,7 +1330,7 @@ hg_status hg_plan_create(hg_plan *out, int ny, int nx, int batch, hg_slm slm, hg
                 std::lock_guard<std::mutex> lk(g_tune_mu);
                 for (const TuneEntry &t : g_tune)
                     if (t.dev == p->dev && t.ny == ny && t.nx == nx && t.items == p->nchains &&
-                        t.kind == slm.kind + (mod ? 8 : 0)) {
+                        t.kind == slm.kind + (mod ? (mod_col_generic ? 24 : 8) : 0)) {
                         row = t.row;
                         col = t.col;
                         cached = true;
@@ -1355,7 +1358,7 @@ hg_status hg_plan_create(hg_plan *out, int ny, int nx, int batch, hg_slm slm, hg
                     const bool hm = rc[i]->paired && !pk && col && slm.kind == HG_SLM_BINARY;
                     float ms = time_variant(p, rc[i], true, false, hm);
                     if (i < 4) p->tune_ms[i] = ms;
-                    float cm = best_col;
+                    float cm = nc ? best_col : 0.f;
                     if (pk) cm = time_variant(p, rc[i], false, true);
                     else if (hm) {
                         cm = time_variant(p, col, false, false, true);
@@ -1366,7 +1369,8 @@ hg_status hg_plan_create(hg_plan *out, int ny, int nx, int batch, hg_slm slm, hg
                     if (ms < best) best = ms, row = rc[i];
                 }
                 std::lock_guard<std::mutex> lk(g_tune_mu);
-                g_tune.push_back({p->dev, ny, nx, p->nchains, slm.kind + (mod ? 8 : 0), row, col});
+                g_tune.push_back({p->dev, ny, nx, p->nchains, slm.kind + (mod ? (mod_col_generic ? 24 : 8) : 0), row,
+                                  col});
             }
         }
         if (row && !p->tc_prec) {

@@ -97,16 +97,18 @@ def run_gpu(c, t, ph0, iters, amp, ph, roi, f32, pipe=-1):
         ev = plan.evaluate(holo, T)
         plan.sync()
         assert "pair" not in hg.hg_plan_variant(plan.h, 0)
-        assert hg.hg_pipelined(plan.h) == (0 if pipe == 0 else 3)
+        want = {0: 0, 1: 3, -1: 1 if nx >= 256 else 0}[pipe]  # auto: TMA-fed rows of >= 256 samples
+        assert hg.hg_pipelined(plan.h) == want, (hg.hg_pipelined(plan.h), want)
         return holo.cpu().numpy(), mse.cpu().numpy(), met, ev.cpu().numpy()
     finally:
         plan.close()
 
 
-@pytest.mark.parametrize("pipe", [1, 0], ids=["tma", "generic"])
+@pytest.mark.parametrize("pipe", [1, -1, 0], ids=["tma", "auto", "generic"])
 @pytest.mark.parametrize("c", CASES, ids=case_id)
 def test_modulated_gs_matches_oracle(c, pipe):
-    """Both the TMA-fed passes (where the size has them: 256, 512) and the generic ones."""
+    """TMA-fed passes (rows and columns of 256 samples and up), the default
+    (TMA-fed rows, generic columns) and the generic passes."""
     ny, nx, kind, levels = c[:4]
     if pipe == 1 and min(ny, nx) < 256:
         pytest.skip("TMA-fed passes exist from 256 samples per line")
