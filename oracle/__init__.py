@@ -19,9 +19,11 @@ direct search / simulated annealing (search_run, search_delta) by
 ``tests/test_oracle_search.py`` (the incremental error change against full
 recomputation, greedy descent to a one-flip minimum checked by enumeration,
 the zero- and high-temperature limits, the tracked replay field);
-the exact WGS trajectory, the OSPR mean intensity and the adaptive-OSPR
-sequence beyond its first subframe are "parity unpinned" beyond the
-qualitative and structural checks listed there.
+the OSPR mean intensity by its closed-form expectation (the arcsine law for
+the signs of Gaussian pairs), to which the time average converges as
+1/sqrt(subframes); the exact WGS trajectory and the adaptive-OSPR sequence
+beyond its first subframe are "parity unpinned" beyond the qualitative and
+structural checks listed there.
 """
 from __future__ import annotations
 

@@ -424,3 +424,27 @@ def test_lt_leaves_the_field_outside_the_window_free():
         return np.mean((I_w - T_w) ** 2)
 
     assert win_err(lt["holo"]) < win_err(gs["holo"])
+
+
+def test_ospr_mean_intensity_follows_the_arcsine_law():
+    """The expected replay of binary OSPR subframes in closed form.  With an
+    i.i.d. uniform random phase, h = IFFT2(T e^{i phi}) is (by the central
+    limit theorem) circular Gaussian with E[h(x) conj h(x + d)] = C(d) =
+    (1/N) sum_u T(u)^2 e^{-2 pi i u d / N}, so Re h has correlation rho(d) =
+    Re C(d) / C(0), and the signs b = sign(Re h) of the binary hologram have
+    E[b(x) b(x + d)] = (2 / pi) arcsin(rho(d)) (the arcsine law for Gaussian
+    pairs).  Then E|R(u)|^2 = sum_d (2 / pi) arcsin(rho(d)) e^{-2 pi i u d / N}.
+    The oracle's time average converges to it as 1 / sqrt(subframes)."""
+    t = synth.target(32, 32, 77)
+    T = oracle.prepare_target(t)
+    Td = np.fft.ifftshift(T)
+    C = np.fft.fft2(Td * Td) / T.size
+    rho = np.real(C) / np.real(C[0, 0])
+    P = np.fft.fftshift(np.real(np.fft.fft2((2 / np.pi) * np.arcsin(np.clip(rho, -1, 1)))))
+    E = P / P.sum()
+    err = []
+    for nsub in (2000, 8000):
+        I = oracle.ospr_run(t, nsub, 5)["I"]
+        err.append(np.linalg.norm(I - E) / np.linalg.norm(E))
+    assert err[0] < 0.03 and err[1] < 0.015, err
+    assert err[1] < 0.7 * err[0]  # the subframe noise averages out
