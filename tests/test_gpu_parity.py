@@ -644,3 +644,30 @@ def test_liu_taghizadeh_matches_oracle(n, kind, levels, pipe):
         assert np.allclose(out[2][1][b], o2["mse"], rtol=1e-4, atol=0), (out[2][1][b], o2["mse"])
         assert np.mean(out[2][0][b] != o2["holo"]) <= 1e-3, np.mean(out[2][0][b] != o2["holo"])
         assert np.allclose(out[6][1][b], o6["mse"], rtol=2e-2, atol=0), (out[6][1][b], o6["mse"])
+
+
+def test_ospr_time_average_follows_the_arcsine_law_at_size():
+    """A property that holds at any size: the time-averaged replay of binary
+    OSPR subframes converges to its closed-form expectation (the arcsine law,
+    see tests/test_oracle.py), here 2000 subframes of a 256^2 target on the
+    GPU, within the 1/sqrt(subframes) speckle noise."""
+    n, nsub = 256, 2000
+    t = synth.targets(1, n, n, 3300)
+    plan = hg.Plan(n, n, 1, hg.HG_SLM_BINARY, 2, hg.HG_OSPR, subframes=nsub, seed=9)
+    try:
+        holo = torch.empty((1, nsub, n, n), dtype=torch.uint8, device=DEV)
+        plan.run(torch.from_numpy(t).to(DEV), None, 1, holo, None)
+        I = torch.empty((1, n, n), dtype=torch.float32, device=DEV)
+        hg.hg_replay(plan.h, holo, I)
+        plan.sync()
+        I = I.cpu().numpy()[0].astype(np.float64)
+    finally:
+        plan.close()
+    T = oracle.prepare_target(t[0])
+    Td = np.fft.ifftshift(T)
+    C = np.fft.fft2(Td * Td) / T.size
+    rho = np.real(C) / np.real(C[0, 0])
+    P = np.fft.fftshift(np.real(np.fft.fft2((2 / np.pi) * np.arcsin(np.clip(rho, -1, 1)))))
+    E = P / P.sum()
+    err = np.linalg.norm(I - E) / np.linalg.norm(E)
+    assert err < 0.04, err
