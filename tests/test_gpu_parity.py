@@ -671,3 +671,34 @@ def test_ospr_time_average_follows_the_arcsine_law_at_size():
     E = P / P.sum()
     err = np.linalg.norm(I - E) / np.linalg.norm(E)
     assert err < 0.04, err
+
+
+def test_bench_configuration_sampled_against_the_oracle():
+    """The benchmark's own configuration: one autotuned plan of 64 binary
+    targets of 1024^2 (seeds 1000 + b, the bench's targets and phases), run
+    for 3 and for 50 iterations.  Three sampled targets go through the
+    oracle: holograms after 3 iterations (all but 0.1% of pixels) with their
+    metrics to 1e-4, and the 50-iteration MSE curve within 1%."""
+    n, B = 1024, 64
+    t = synth.targets(B, n, n, 1000)
+    ph = synth.init_phases(B, n, n, 1000)
+    T, P = torch.from_numpy(t).to(DEV), torch.from_numpy(ph).to(DEV)
+    plan = hg.Plan(n, n, B)
+    try:
+        holo3 = torch.empty((B, n, n), dtype=torch.uint8, device=DEV)
+        mse3 = torch.empty((B, 3), dtype=torch.float64, device=DEV)
+        plan.run(T, P, 3, holo3, mse3)
+        mse50 = torch.empty((B, 50), dtype=torch.float64, device=DEV)
+        plan.run(T, P, 50, None, mse50)
+        plan.sync()
+        variant = hg.hg_plan_variant(plan.h, 0)
+    finally:
+        plan.close()
+    assert "+herm" in variant, variant  # the loop the bench times
+    h3, m3, m50 = holo3.cpu().numpy(), mse3.cpu().numpy(), mse50.cpu().numpy()
+    for b in (0, 31, 63):
+        o3 = oracle.gs_run(t[b], ph[b].astype(np.float64), 3)
+        assert np.mean(h3[b] != o3["holo"]) <= 1e-3
+        assert np.allclose(m3[b], o3["mse"], rtol=1e-4, atol=0), (m3[b], o3["mse"])
+        o50 = oracle.gs_run(t[b], ph[b].astype(np.float64), 50)
+        assert np.allclose(m50[b], o50["mse"], rtol=1e-2, atol=0), (b, np.abs(m50[b] / o50["mse"] - 1).max())
