@@ -702,3 +702,46 @@ def test_bench_configuration_sampled_against_the_oracle():
         assert np.allclose(m3[b], o3["mse"], rtol=1e-4, atol=0), (m3[b], o3["mse"])
         o50 = oracle.gs_run(t[b], ph[b].astype(np.float64), 50)
         assert np.allclose(m50[b], o50["mse"], rtol=1e-2, atol=0), (b, np.abs(m50[b] / o50["mse"] - 1).max())
+
+
+def test_ospr_and_2048_configurations_sampled_against_the_oracle():
+    """The OSPR workload (8 targets x 24 subframes of 1024^2, Hermitian form)
+    and the 2048^2 x 16 GS workload, sampled: OSPR target 5's subframe
+    holograms (all but 0.1% of pixels) and its time-averaged MSE (1e-4); GS
+    target 9 of 16 at 2048^2, holograms after 3 iterations and the 20-iteration
+    MSE curve within 1%."""
+    n, B, NS = 1024, 8, 24
+    t = synth.targets(B, n, n, 1000)
+    plan = hg.Plan(n, n, B, hg.HG_SLM_BINARY, 2, hg.HG_OSPR, subframes=NS, seed=7)
+    try:
+        holo = torch.empty((B, NS, n, n), dtype=torch.uint8, device=DEV)
+        mse = torch.empty(B, dtype=torch.float64, device=DEV)
+        plan.run(torch.from_numpy(t).to(DEV), None, 1, holo, mse)
+        plan.sync()
+        h5, m5 = holo[5].cpu().numpy(), float(mse[5].item())
+    finally:
+        plan.close()
+    o = oracle.ospr_run(t[5], NS, 7, t_index=5)
+    assert np.mean(h5 != o["holo"]) <= 1e-3
+    assert abs(m5 - o["mse"]) <= 1e-4 * o["mse"], (m5, o["mse"])
+
+    n, B = 2048, 16
+    t = synth.targets(B, n, n, 5000)
+    ph = synth.init_phases(B, n, n, 5000)
+    plan = hg.Plan(n, n, B)
+    try:
+        T, P = torch.from_numpy(t).to(DEV), torch.from_numpy(ph).to(DEV)
+        holo3 = torch.empty((B, n, n), dtype=torch.uint8, device=DEV)
+        mse3 = torch.empty((B, 3), dtype=torch.float64, device=DEV)
+        plan.run(T, P, 3, holo3, mse3)
+        mse20 = torch.empty((B, 20), dtype=torch.float64, device=DEV)
+        plan.run(T, P, 20, None, mse20)
+        plan.sync()
+        h9, m3, m20 = holo3[9].cpu().numpy(), mse3[9].cpu().numpy(), mse20[9].cpu().numpy()
+    finally:
+        plan.close()
+    o3 = oracle.gs_run(t[9], ph[9].astype(np.float64), 3)
+    assert np.mean(h9 != o3["holo"]) <= 1e-3
+    assert np.allclose(m3, o3["mse"], rtol=1e-4, atol=0)
+    o20 = oracle.gs_run(t[9], ph[9].astype(np.float64), 20)
+    assert np.allclose(m20, o20["mse"], rtol=1e-2, atol=0)
