@@ -110,3 +110,29 @@ def test_plain_c_client_builds_and_runs(tmp_path):
                            "-Wl,-rpath," + pkg, "-o", exe])
     out = subprocess.run([exe], capture_output=True, text=True, timeout=120)
     assert out.returncode == 0 and "c abi ok" in out.stdout, (out.returncode, out.stdout, out.stderr)
+
+
+@pytest.mark.parametrize("ny,nx,kind,levels,algo,opt,value,want", [
+    (256, 256, 0, 2, 5, None, None, 2),        # direct search: 65536 pixels exceed one CTA's shared memory
+    (32, 32, 0, 2, 6, "sa_temp", 0.0, 1),      # annealing needs a positive temperature
+    (32, 32, 0, 2, 6, "sa_cool", 1.5, 1),      # and a cooling factor in (0, 1]
+    (32, 32, 2, 4, 5, None, None, 1),          # search plans are phase-SLM plans
+    (64, 64, 0, 2, 1, "modulated", 1, 1),      # modulated plans run GS only
+    (64, 64, 0, 2, 0, "fresnel", float("nan"), 1),
+    (64, 64, 2, 8, 0, "amp_clip", 0.0, 1),     # amplitude SLM needs a positive clip
+    (64, 64, 2, 257, 0, None, None, 1),        # amplitude SLM with L > 256
+    (1024, 1024, 0, 2, 0, "precision", 5, 1),  # precision outside 0..4
+    (64, 64, 0, 2, 4, "lt_start", 0.0, 1),     # Liu-Taghizadeh window fraction in (0, 1]
+])
+def test_variant_options_rejected_before_device_work(lib, ny, nx, kind, levels, algo, opt, value, want):
+    from paper_2008_12214_gb300 import hologen as hg
+    o = hg.hg_opts()
+    lib.hg_opts_default(ctypes.byref(o))
+    if opt is not None:
+        setattr(o, opt, value)
+    if opt == "precision":
+        o.modulated = 1
+    h = ctypes.c_void_p(123)
+    st = lib.hg_plan_create(ctypes.byref(h), ny, nx, 1, hg.hg_slm(kind, levels), algo, ctypes.byref(o))
+    assert st == want, st
+    assert h.value is None
