@@ -4,8 +4,8 @@ FP64 oracle, through the C ABI (marked gpu).
 The GPU sums each trial's error change in FP32 and tracks R in FP32, the
 oracle in FP64: a trial whose change is within rounding of zero (or of the
 annealing threshold) can go the other way, and the search then continues
-from a different hologram.  Small fields (16^2, 32^2) must follow the oracle
-trial for trial; larger ones are held to a hologram mismatch of 1% and the
+from a different hologram.  Small fields (16^2 to 60^2) must follow the
+oracle trial for trial; larger ones are held to a hologram mismatch of 1% and the
 per-sweep MSE within 1%.  The GPU's reported MSE of its own final hologram
 is checked against the oracle's fresh evaluation of that hologram to 1e-4
 (the FP32 tracking of R)."""
@@ -55,6 +55,7 @@ CASES = [  # ny, nx, batch, kind, levels, algo, sweeps, tau0, alpha, exact
     (16, 16, 2, hg.HG_SLM_LLEVEL, 4, hg.HG_DS, 3, None, None, True),
     (32, 32, 2, hg.HG_SLM_BINARY, 2, hg.HG_SA, 3, 1e-3, 0.5, True),
     (32, 64, 1, hg.HG_SLM_LLEVEL, 8, hg.HG_SA, 2, 3e-4, 0.7, True),
+    (60, 60, 1, hg.HG_SLM_BINARY, 2, hg.HG_DS, 2, None, None, True),     # 480 threads, last pixel group partial
     (64, 64, 2, hg.HG_SLM_BINARY, 2, hg.HG_DS, 2, None, None, False),
     (128, 128, 1, hg.HG_SLM_BINARY, 2, hg.HG_SA, 1, 1e-4, 0.9, False),
 ]
