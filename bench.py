@@ -94,59 +94,93 @@ def src_hash():
     return h.hexdigest()[:16]
 
 
-def cpu_oracle_sample(seconds_hint: float = 10.0):
-    """The FP64 oracle as it stands, timed on this host's cores over a bounded
-    sample: whole GS iterations (oracle.gs_step) on single 1024^2 targets."""
+def _oracle_worker(seed, steps, barrier, queue):
+    """One host core: the oracle on its own 1024^2 target, single-threaded
+    (OMP_NUM_THREADS = 1 before the oracle library loads), one warm-up GS
+    iteration, then `steps` timed ones started together with the other
+    workers.  Puts (start, end) wall times on `queue`."""
+    os.environ["OMP_NUM_THREADS"] = "1"
     import oracle
     from paper_2008_12214_gb300 import synth
-    oracle.build()
-    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
-    t = synth.target(NY, NX, 1000)
-    ph = synth.init_phase(NY, NX, 1000).astype(np.float64)
+    t = synth.target(NY, NX, seed)
+    ph = synth.init_phase(NY, NX, seed).astype(np.float64)
     T = oracle.prepare_target(t)
-    oracle.gs_step(T, ph)  # warm-up (library load, first-touch)
-    n, t0 = 0, time.perf_counter()
-    while True:
-        o = oracle.gs_step(T, ph)
-        ph = o["phase"]
-        n += 1
-        el = time.perf_counter() - t0
-        if el * cores >= seconds_hint or n >= 40:
-            break
-    per_target_iter = el / n
-    return dict(value=1.0 / (BATCH * per_target_iter), unit=UNIT, cores=cores, kind="oracle",
-                sample="%d GS iterations of one 1024x1024 binary target (oracle.gs_step), "
-                       "%.3f s each; scaled to one batched iteration = 64 target-iterations" % (n, per_target_iter))
+    ph = oracle.gs_step(T, ph)["phase"]
+    barrier.wait()
+    t0 = time.time()
+    for _ in range(steps):
+        ph = oracle.gs_step(T, ph)["phase"]
+    queue.put((t0, time.time()))
+
+
+def oracle_per_core(workers: int, steps: int, seed0: int = 1000):
+    """The FP64 oracle as it stands, one target per host core: `workers`
+    single-threaded processes (spawned, so no process is forked from one that
+    holds a CUDA context) each run `steps` GS iterations of their own 1024^2
+    binary target.  Returns target-iterations per second over the common
+    timed span."""
+    import multiprocessing as mp
+    import oracle
+    oracle.build()
+    ctx = mp.get_context("spawn")
+    barrier = ctx.Barrier(workers)
+    queue = ctx.Queue()
+    procs = [ctx.Process(target=_oracle_worker, args=(seed0 + i, steps, barrier, queue)) for i in range(workers)]
+    for pr in procs:
+        pr.start()
+    spans = [queue.get() for _ in procs]
+    for pr in procs:
+        pr.join()
+    t0, t1 = min(a for a, _ in spans), max(b for _, b in spans)
+    return workers * steps / (t1 - t0)
+
+
+def host_cores():
+    try:
+        return len(os.sched_getaffinity(0))
+    except Exception:
+        return os.cpu_count() or 1
+
+
+def cpu_oracle_sample(steps: int = 2):
+    """CPU baseline: the oracle threaded one target per core on all host
+    cores, and alone on one core, each core running `steps` whole GS
+    iterations of a 1024^2 binary target (oracle.gs_step); scaled to the
+    benchmark's unit, one batched iteration = 64 target-iterations."""
+    cores = host_cores()
+    all_rate = oracle_per_core(cores, steps)
+    one_rate = oracle_per_core(1, steps)
+    return dict(value=all_rate / BATCH, unit=UNIT, cores=cores, kind="oracle",
+                single_core_value=one_rate / BATCH, single_core_s_per_target_iteration=1.0 / one_rate,
+                sample="one target per core: %d single-threaded processes x %d GS iterations of their own "
+                       "1024x1024 binary target (oracle.gs_step, FP64), %.2f target-iterations/s in all; "
+                       "single core %.2f s per target-iteration; scaled to one batched iteration = %d "
+                       "target-iterations" % (cores, steps, all_rate, 1.0 / one_rate, BATCH))
 
 
 def run_reference(args):
+    """The reference arm: the oracle, one target per host core.  Each step is
+    one GS iteration on every core's own 1024^2 target (a bounded sample of
+    the 64-target batch), scaled to batched iterations of 64 targets."""
     rank, _, world = dist_env()
     if rank != 0:
         return
-    import oracle
-    from paper_2008_12214_gb300 import synth
-    oracle.build()
-    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
-    t = synth.target(NY, NX, 1000)
-    ph = synth.init_phase(NY, NX, 1000).astype(np.float64)
-    T = oracle.prepare_target(t)
-    for _ in range(args.warmup):
-        ph = oracle.gs_step(T, ph)["phase"]
-    t0 = time.perf_counter()
-    for _ in range(args.steps):
-        ph = oracle.gs_step(T, ph)["phase"]
-    el = time.perf_counter() - t0
-    per = el / args.steps
+    cores = host_cores()
+    if args.warmup:
+        oracle_per_core(cores, 1)
+    rate = oracle_per_core(cores, args.steps)
     B = args.batch
-    value = 1.0 / (B * per)
+    value = rate / B
+    per = cores / rate  # wall seconds per step (one iteration on every core)
     line = dict(impl="reference", metric=METRIC, value=value, unit=UNIT, n_gpus=world, steps=args.steps,
                 warmup=args.warmup, ms_per_step=per * 1e3, higher_is_better=True, scaling="weak",
                 vs_baseline=None, dtype="f64", data=DATA,
                 config=dict(workload="gs_binary_1024x1024_batch%d" % B, ny=NY, nx=NX, batch=B,
-                            step="one GS iteration of one 1024x1024 target (bounded sample), "
-                                 "scaled to %d targets" % B),
+                            step="one GS iteration of one 1024x1024 target on each of %d host cores "
+                                 "(bounded sample), scaled to %d targets" % (cores, B)),
                 cpu_baseline=dict(kind="oracle", cores=cores, value=value, unit=UNIT,
-                                  sample="%d x one 1024x1024 target-iteration" % args.steps),
+                                  sample="%d steps x %d single-threaded processes, one 1024x1024 target "
+                                         "each" % (args.steps, cores)),
                 e2e=dict(value=value, unit=UNIT, h2d_bytes_per_step=0, d2h_bytes_per_step=0))
     print(json.dumps(line), flush=True)
 
@@ -510,8 +544,8 @@ def main():
         plan.run(T, P, args.iters, holo, mse)
     plan.sync()
 
-    # timed region: K steps, per-pass event timing inside the library
-    hg.hg_profile_enable(plan.h, 2 * args.steps * args.iters + 8)
+    # timed region: K steps as the library runs them (the iteration loop
+    # replayed as one CUDA graph), bracketed by CUDA events on the plan's stream
     if world > 1:
         dist.barrier()
     torch.cuda.synchronize(dev)
@@ -526,11 +560,18 @@ def main():
     torch.cuda.synchronize(dev)
     if world > 1:
         dist.barrier()
-    clk = clocks.stop() if clocks else None
     plan.sync()
     el_ms = e0.elapsed_time(e1)
+    # per-pass durations for the roofline: the same K steps again with an event
+    # pair around every row and column pass (the loop is then launched pass by
+    # pass instead of as the graph)
+    hg.hg_profile_enable(plan.h, 2 * args.steps * args.iters + 8)
+    for _ in range(args.steps):
+        plan.run(T, P, args.iters, holo, mse)
     prof = hg.hg_profile_read(plan.h)
     hg.hg_profile_enable(plan.h, 0)
+    torch.cuda.synchronize(dev)
+    clk = clocks.stop() if clocks else None
     el_ms = shard.max_over_ranks(el_ms, dev)
     value = shard.weak_scaling_rate(world, args.steps * args.iters, el_ms / 1e3)
 
@@ -601,9 +642,13 @@ def main():
     roofline = dict(bound="hbm", achieved=d["gbs"], peak=peak, unit="GB/s",
                     frac=(d["gbs"] / peak) if d["gbs"] else None, traffic=traffic,
                     kernel="%s pass (%s)" % (dom, kernel_key), peak_source=peak_src,
+                    frac_basis="equivalent bandwidth: the fused schedule's algorithmic bytes (%d B/px for the "
+                               "%s pass) over the launch time; frac_moved uses the bytes this variant reads "
+                               "and writes" % (BYTES_ROW if dom == "row" else BYTES_COL, dom),
                     algorithmic_bytes_per_launch=d["bytes"], avg_launch_ms=d["ms"],
                     variant_bytes_per_launch=d["moved"],
-                    frac_at_variant_bytes=(d["gbs_moved"] / peak) if d["gbs_moved"] else None)
+                    frac_moved=(d["gbs_moved"] / peak) if d["gbs_moved"] else None,
+                    timing="per-pass CUDA events on the plan's stream over a second K-step region")
     iter_ms = el_ms / (args.steps * args.iters)
     line = dict(
         metric=METRIC, value=value, unit=UNIT, n_gpus=world, steps=args.steps, warmup=args.warmup,
@@ -616,7 +661,8 @@ def main():
                     l2="inputs larger than L2: field 512 MiB + prepared targets 256 MiB per rank"),
         holograms_per_s=value * B / args.iters,
         whole_iteration=dict(
-            ms=iter_ms, bytes_per_px_moved=b_row + b_col,
+            ms=iter_ms, loop_row_plus_column_ms=row_ms + col_ms,
+            bytes_per_px_moved=b_row + b_col,
             gbs_moved=(b_row + b_col) * npx / (iter_ms / 1e3) / 1e9,
             bytes_per_px_36=BYTES_FUSED,
             gbs_at_36=BYTES_FUSED * npx / (iter_ms / 1e3) / 1e9,

@@ -166,7 +166,12 @@ void hg_opts_default(hg_opts *opts);
 int hg_supported_length(int n);
 
 /* Creates a plan for `batch` targets of ny x nx pixels on the current CUDA
- * device.  Allocates the plan's device workspace (the field, the prepared
+ * device.  The parameters are those of the problem the paper states: its
+ * program summary (two-dimensional Fourier holograms for SLMs with binary or
+ * multi-level control, by one of the listed algorithm variants), Section 2
+ * (an ny x nx field) and Section 4.7, whose quantiser is constructed from the
+ * SLM's level range and level count before it is applied to any field.
+ * Allocates the plan's device workspace (the field, the prepared
  * targets, weights, twiddle tables and metric partials).  opts may be NULL
  * (defaults).  Errors: HG_ERR_INVALID_ARG (out NULL, batch < 1, bad slm or
  * algo, OSPR with a non-binary SLM, subframes < 1, precision outside 0..4),
@@ -207,7 +212,9 @@ hg_status hg_run(hg_plan plan, const float *target, const float *init_phase, int
 hg_status hg_get_metrics(hg_plan plan, double *out, size_t count);
 
 /* Normalised replay intensity (sums to 1, replay order) of holograms of level
- * indices: holo [batch][ny][nx] (OSPR plans: [batch][subframes][ny][nx],
+ * indices, i.e. |fftshift(FFT2(e^{iH}))|^2 / sum, the replay field of
+ * Section 2, eq. (fouriertrans2d5c), under the scale freedom of Section 3.1
+ * (OSPR plans time-average the subframes' intensities, Section 3.4): holo [batch][ny][nx] (OSPR plans: [batch][subframes][ny][nx],
  * time-averaged per target); intensity_out [batch][ny][nx] float. */
 hg_status hg_replay(hg_plan plan, const uint8_t *holo, float *intensity_out);
 
@@ -249,7 +256,12 @@ hg_status hg_set_roi(hg_plan plan, const uint8_t *roi);
 hg_status hg_evaluate(hg_plan plan, const uint8_t *holo, const float *target, double *out);
 
 /* Replay phase arg R after the last GS/WGS run (0 where R = 0), replay order,
- * [batch][ny][nx] float radians: the state from which a run resumes. */
+ * [batch][ny][nx] float radians: the state from which a run resumes.  In
+ * Section 3.2's loop this is the phase the replay-plane constraint keeps
+ * when it replaces |R| by the target amplitude; the next iteration starts
+ * from F = T e^{i arg R}.  Errors: HG_ERR_INVALID_ARG (NULL, no GS/WGS run
+ * since the plan was created or since hg_replay / hg_debug_loop_step reused
+ * the field, OSPR plans). */
 hg_status hg_get_phase(hg_plan plan, float *phase_out);
 
 /* WGS weights, replay order, [batch][ny][nx] float.  hg_set_weights makes the
@@ -270,6 +282,43 @@ hg_status hg_get_weights(hg_plan plan, float *w_out);
  */
 hg_status hg_debug_step(hg_plan plan, const float *target, const float *phase_in, float *h_out,
                         uint8_t *holo_out, float *replay_out, double *metrics_out);
+
+/*
+ * One iteration of the fused LOOP (the row and column passes that hg_run
+ * repeats between its first and last iteration, in the variants the plan
+ * chose), started from a given hologram H_k, for checking the loop kernels
+ * against one step of Section 3.2 (unitary DFT of Section 2, eqs.
+ * fouriertrans2d5c/d).  GS, WGS, LT and modulated plans; DEVICE pointers only.
+ *  holo_in     [batch][ny][nx] uint8 level indices H_k, natural SLM order.
+ *  k           iteration index of H_k (LT: the row pass applies the window
+ *              of constraint k + 1; ignored otherwise).
+ *  row_out     [batch][ny][nx] complex64: the field the row pass leaves,
+ *              G[ky][x] = sum_kx F[ky][kx] exp(+2 pi i kx x / nx) (an
+ *              unnormalised inverse row DFT), ky and kx in DFT order, x in
+ *              natural order, where F = A w T R / |R| (F = A for R = 0) with
+ *              R = FFT2(E e^{iH_k}) unnormalised (E = 1 unless the plan is
+ *              modulated), T the normalised target moved to DFT order, w the
+ *              updated WGS weight (1 otherwise) and A = 1 (GS, WGS) or N
+ *              (LT and modulated plans, where F = R outside the window or the
+ *              region of interest).  When the plan runs the binary loop in
+ *              Hermitian form (hg_plan_variant(plan, 0) contains "+herm") F
+ *              is replaced by F_H(u) = (F(u) + conj F(-u)) / 2 and only rows
+ *              ky <= ny/2 are defined.
+ *  holo_out    [batch][ny][nx] uint8: H_{k+1}, the column pass's quantisation.
+ *  col_out     [batch][ny][nx] complex64: the field the column pass leaves,
+ *              sum_y E e^{iH_{k+1}[y][x]} exp(-2 pi i ky y / ny) (unnormalised
+ *              forward column DFT); only rows ky <= ny/2 are defined when the
+ *              row pass is paired (variant name contains "pair").
+ *  metrics_out [batch][4] double: the metrics of iteration k (the replay of
+ *              H_k), as in hg_get_metrics.
+ * WGS starts from the weights set by hg_set_weights (else 1); the updated
+ * weights are returned by hg_get_weights.  Any output may be NULL.  Errors:
+ * HG_ERR_INVALID_ARG (NULL plan, target or holo_in, k < 0, OSPR or search
+ * plans, a host pointer), HG_ERR_CUDA; device-detected value errors at
+ * hg_sync.
+ */
+hg_status hg_debug_loop_step(hg_plan plan, const float *target, const uint8_t *holo_in, int k, float *row_out,
+                             uint8_t *holo_out, float *col_out, double *metrics_out);
 
 /* Waits for the plan's stream and reports errors found on the device since
  * the last run started (invalid or zero-energy targets, CUDA faults). */
@@ -341,9 +390,9 @@ int hg_group_launch_count(hg_group group);
 void hg_group_destroy(hg_group group);
 
 /*
- * hg_run_noalloc -- one GS or WGS run (Section 3.2) of ONE target that
- * allocates no device memory.  The paper has no counterpart: it is a
- * deployment variant of hg_run, not part of the method.
+ * hg_run_noalloc -- one GS or WGS run of ONE target that allocates no
+ * device memory.  The paper has no counterpart: it is a deployment variant
+ * of hg_run, not part of the method.
  *
  * Who needs it: callers that must not allocate device memory at the moment
  * they compute a hologram.  Examples: a display loop that refreshes an SLM

@@ -1824,6 +1824,66 @@ hg_status hg_debug_step(hg_plan p, const float *target, const float *phase_in, f
     return HG_OK;
 }
 
+// One row pass and one column pass of the iteration loop, fed a hologram:
+// the column spectra of the hologram's SLM field (generic HOLO role, all
+// rows), then exactly the launches enqueue_loop makes for an iteration k >= 1
+// (the plan's own row-pass and column-pass variants), then the metric
+// reduction of the row pass's panels.
+hg_status hg_debug_loop_step(hg_plan p, const float *target, const uint8_t *holo_in, int k, float *row_out,
+                             uint8_t *holo_out, float *col_out, double *metrics_out) {
+    NvtxRange nv("hg_debug_loop_step");
+    if (!p || !target || !holo_in || k < 0 || is_ospr(p->algo) || is_search(p->algo)) return HG_ERR_INVALID_ARG;
+    for (const void *q : {(const void *)target, (const void *)holo_in, (const void *)row_out,
+                          (const void *)holo_out, (const void *)col_out, (const void *)metrics_out})
+        if (q && !is_device_ptr(q)) return HG_ERR_INVALID_ARG;  // device buffers only
+    DevGuard g(p->dev);
+    p->launches = 0;
+    hg_status st;
+    if ((st = ensure_part(p, 1)) != HG_OK) return st;
+    if ((st = ensure_metrics(p, 1)) != HG_OK) return st;
+    const size_t fbytes = sizeof(float2) * p->npx * p->batch;
+    HG_CK(cudaMemsetAsync(p->err, 0, sizeof(unsigned), p->stream));
+    enqueue_prep(p, target);
+    if (p->algo == HG_WGS && !p->weights_preset) {
+        k_fill<<<ew_grid(p, p->npx * p->batch), 256, 0, p->stream>>>(p->w, p->npx * p->batch, 1.f);
+        p->launches++;
+    }
+    ColArgs ch = col_args(p);
+    ch.holo = const_cast<uint8_t *>(holo_in);
+    launch_col(p, col_role_holo(p), ch, p->stream);
+    ColArgs ca = col_args(p);
+    RowArgs ra = row_args(p);
+    ca.half = p->prow && p->prow->paired;
+    ra.herm = herm_loop(p);
+    ca.half_in = ra.herm;
+    ra.part = p->part;
+    lt_set(p, ra, k + 1);
+    launch_row_iter(p, ra, p->stream);
+    if (row_out) HG_CK(cudaMemcpyAsync(row_out, p->field, fbytes, cudaMemcpyDeviceToDevice, p->stream));
+    ca.holo = holo_out;
+    if (p->use_pack) launch_col_pack(p, ca, p->stream);
+    else if (ca.half_in && p->use_herm_col) launch_col_herm(p, ca, p->stream);
+    else launch_col_gs(p, col_role_gs(p), ca, p->stream);
+    if (col_out) HG_CK(cudaMemcpyAsync(col_out, p->field, fbytes, cudaMemcpyDeviceToDevice, p->stream));
+    const int pl = p->tc_prec ? p->ppt_tc : p->prow ? p->ppt_pipe : p->ppt;
+    if (p->mod)
+        k_reduce_gen<<<(p->batch * 32 + 127) / 128, 128, 0, p->stream>>>(p->part, 1, p->batch, p->ppt_max, pl, pl,
+                                                                     p->nroi, p->metrics, nullptr);
+    else
+        k_reduce<<<(p->batch * 32 + 127) / 128, 128, 0, p->stream>>>(p->part, 1, p->batch, p->ppt_max, pl, pl,
+                                                                 1.0 / (double)p->npx, p->metrics, nullptr);
+    p->launches++;
+    if (metrics_out)
+        HG_CK(cudaMemcpyAsync(metrics_out, p->metrics, sizeof(double) * NMET * p->batch,
+                              cudaMemcpyDeviceToDevice, p->stream));
+    HG_CK(cudaGetLastError());
+    p->weights_preset = false;
+    p->have_run = true;
+    p->field_from_run = false;
+    p->last_iters = 1;
+    return HG_OK;
+}
+
 }  // extern "C"
 
 // ------------------------------------------------------------------ groups

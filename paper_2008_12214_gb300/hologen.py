@@ -74,6 +74,7 @@ def lib():
         L.hg_set_weights.argtypes = [P, P]
         L.hg_get_weights.argtypes = [P, P]
         L.hg_debug_step.argtypes = [P, P, P, P, P, P, P]
+        L.hg_debug_loop_step.argtypes = [P, P, P, I, P, P, P, P]
         L.hg_sync.argtypes = [P]
         L.hg_last_launch_count.argtypes = [P]
         L.hg_last_launch_count.restype = I
@@ -126,8 +127,8 @@ def lib():
         L.hg_status_string.argtypes = [I]
         L.hg_status_string.restype = ctypes.c_char_p
         for name in ("hg_plan_create", "hg_run", "hg_get_metrics", "hg_replay", "hg_get_phase",
-                     "hg_set_weights", "hg_get_weights", "hg_debug_step", "hg_sync", "hg_set_illumination",
-                     "hg_set_roi", "hg_evaluate"):
+                     "hg_set_weights", "hg_get_weights", "hg_debug_step", "hg_debug_loop_step", "hg_sync",
+                     "hg_set_illumination", "hg_set_roi", "hg_evaluate"):
             getattr(L, name).restype = I
         _lib = L
     return _lib
@@ -259,6 +260,16 @@ def hg_debug_step(plan, target, phase_in, h_out=None, holo_out=None, replay_out=
                             _ptr(holo_out, torch.uint8, name="holo_out"),
                             _ptr(replay_out, torch.complex64, name="replay_out"),
                             _ptr(metrics_out, torch.float64, name="metrics_out")), "hg_debug_step")
+
+
+def hg_debug_loop_step(plan, target, holo_in, k=0, row_out=None, holo_out=None, col_out=None,
+                       metrics_out=None):
+    _ck(lib().hg_debug_loop_step(plan, _ptr(target, torch.float32, name="target"),
+                                 _ptr(holo_in, torch.uint8, name="holo_in"), int(k),
+                                 _ptr(row_out, torch.complex64, name="row_out"),
+                                 _ptr(holo_out, torch.uint8, name="holo_out"),
+                                 _ptr(col_out, torch.complex64, name="col_out"),
+                                 _ptr(metrics_out, torch.float64, name="metrics_out")), "hg_debug_loop_step")
 
 
 def hg_sync(plan):

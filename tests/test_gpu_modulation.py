@@ -245,3 +245,70 @@ def test_evaluate_reports_bad_and_empty_targets():
         plan.sync()
     finally:
         plan.close()
+
+
+def mod_boundary_mask(h, E, kind, levels, bound=1e-5):
+    """Pixels whose quantiser input lies within `bound` of a decision
+    boundary: phase SLMs decide on the phase of h conj(E) (1e-5 rad), the
+    binary amplitude SLM on the sign of Re(h conj E) (the same rule)."""
+    hm = h * np.conj(E)
+    if kind in (oracle.SLM_BINARY, oracle.SLM_AMPLITUDE):
+        return np.abs(hm.real) <= np.sin(bound) * np.abs(hm)
+    x = np.angle(hm) * levels / (2 * np.pi)
+    return np.abs(x - np.floor(x) - 0.5) <= bound * levels / (2 * np.pi)
+
+
+@pytest.mark.parametrize("c", [CASES[0], CASES[1], CASES[2], CASES[6],
+                               (1024, 1024, hg.HG_SLM_BINARY, 2, 0.002, "gauss", "disc")], ids=case_id)
+def test_modulated_loop_step_from_oracle_state(c):
+    """The loop's row and column passes of a modulated plan, fed the oracle's
+    hologram H_k (k = 0 and 2) through hg_debug_loop_step: the metrics of
+    iteration k to 1e-4; the row pass's field against sqrt(N) times the
+    oracle's next constraint field F_{k+1} (the unnormalised inverse row DFT,
+    relative L2 1e-5); H_{k+1} bit-exact except decision-boundary pixels; the
+    column pass's field against the column DFT of E e^{iH_{k+1}} of the GPU's
+    own hologram (relative L2 1e-5)."""
+    ny, nx, kind, levels = c[:4]
+    if kind == hg.HG_SLM_AMPLITUDE and levels != 2:
+        pytest.skip("boundary rule stated for phase and binary amplitude SLMs")
+    ok = okind(kind)
+    f32, amp, ph, roi, E = setup_case(c)
+    batch, N = 2, ny * nx
+    t = synth.targets(batch, ny, nx, 5200)
+    ph0 = synth.init_phases(batch, ny, nx, 5200)
+    plan = hg.Plan(ny, nx, batch, kind, levels, hg.HG_GS, modulated=True, fresnel=f32)
+    try:
+        plan.set_illumination(None if amp is None else torch.from_numpy(amp).to(DEV),
+                              None if ph is None else torch.from_numpy(ph).to(DEV))
+        plan.set_roi(None if roi is None else torch.from_numpy(roi).to(DEV))
+        for k in (0, 2):
+            runs = [oracle.modulated_run(t[b], ph0[b].astype(np.float64), k + 1, ok, levels, E=E, roi=roi)
+                    for b in range(batch)]
+            holos = np.stack([r["holo"] for r in runs]).astype(np.uint8)
+            T = torch.from_numpy(t).to(DEV)
+            row = torch.empty((batch, ny, nx), dtype=torch.complex64, device=DEV)
+            col = torch.empty((batch, ny, nx), dtype=torch.complex64, device=DEV)
+            hout = torch.empty((batch, ny, nx), dtype=torch.uint8, device=DEV)
+            met = torch.empty((batch, 4), dtype=torch.float64, device=DEV)
+            hg.hg_debug_loop_step(plan.h, T, torch.from_numpy(holos).to(DEV), k, row, hout, col, met)
+            plan.sync()
+            row, col, hout, met = row.cpu().numpy(), col.cpu().numpy(), hout.cpu().numpy(), met.cpu().numpy()
+            for b in range(batch):
+                r = runs[b]
+                want = np.array([r["mse"][-1], r["amp_mse"][-1], r["eff"][-1], r["sum_r2"][-1]])
+                assert np.allclose(met[b], want, rtol=1e-4, atol=0), (k, b, met[b], want)
+                G = np.fft.ifft(np.fft.ifftshift(np.sqrt(N) * r["F"]), axis=1) * nx
+                e_row = np.linalg.norm(row[b] - G) / np.linalg.norm(G)
+                assert e_row <= 1e-5, (k, b, e_row)
+                h = oracle.fft2(np.fft.ifftshift(r["F"]), +1)
+                q, _ = oracle.quantise_modulated(h, E, ok, levels)
+                mism = hout[b] != q
+                bnd = mod_boundary_mask(h, E, ok, levels)
+                assert not np.any(mism & ~bnd), (k, b, int(np.sum(mism & ~bnd)))
+                C = np.fft.fft(oracle.modulated_field(hout[b], E, ok, levels), axis=0)
+                e_col = np.linalg.norm(col[b] - C) / np.linalg.norm(C)
+                assert e_col <= 1e-5, (k, b, e_col)
+                print("%s k=%d target %d: row rel-L2 %.2e, column rel-L2 %.2e, %d boundary pixels, %d quantised "
+                      "differently" % (case_id(c), k, b, e_row, e_col, int(np.sum(bnd)), int(np.sum(mism))))
+    finally:
+        plan.close()

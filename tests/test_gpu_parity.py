@@ -179,6 +179,23 @@ def test_whole_run_batch_graph_and_no_graph_identical():
         assert abs(a["mse"][i, -1] - o["mse"][-1]) <= 0.01 * o["mse"][-1]
 
 
+def test_wgs_1024_256_levels_100_iterations_whole_run():
+    """Weighted GS at 1024^2 with a 256-level SLM, 100 iterations from the
+    seeded target and phase, whole run on each side: the final intensity MSE
+    and diffraction efficiency within 1% of the oracle's."""
+    ny = nx = 1024
+    t = synth.targets(1, ny, nx, 1000)
+    ph = synth.init_phases(1, ny, nx, 1000)
+    g = run_gpu(t, ph, 100, hg.HG_SLM_LLEVEL, 256, hg.HG_WGS)
+    o = oracle.gs_run(t[0], ph[0].astype(np.float64), 100, kind=oracle.SLM_LLEVEL, levels=256, wgs=True)
+    gap = abs(g["mse"][0, -1] - o["mse"][-1]) / o["mse"][-1]
+    print("WGS 1024^2 / 256 levels / 100 iterations: final MSE gpu %.6e oracle %.6e (gap %.2e), efficiency "
+          "gpu %.6f oracle %.6f" % (g["mse"][0, -1], o["mse"][-1], gap, g["met"][0, -1, 2], o["eff"][-1]))
+    assert np.allclose(g["mse"][0, :2], o["mse"][:2], rtol=1e-4, atol=0)
+    assert gap <= 0.01
+    assert abs(g["met"][0, -1, 2] - o["eff"][-1]) <= 0.01 * o["eff"][-1]
+
+
 def test_wgs_fed_oracle_state_every_iteration():
     """Weighted GS with 64 levels: at each of 6 iterations the GPU is fed the
     oracle's (phase, weights) and one step is checked.  Whole WGS runs are
@@ -707,7 +724,8 @@ def test_bench_configuration_sampled_against_the_oracle():
 def test_ospr_and_2048_configurations_sampled_against_the_oracle():
     """The OSPR workload (8 targets x 24 subframes of 1024^2, Hermitian form)
     and the 2048^2 x 16 GS workload, sampled: OSPR target 5's subframe
-    holograms (all but 0.1% of pixels) and its time-averaged MSE (1e-4); GS
+    holograms (bit-exact except decision-boundary pixels: every subframe is
+    one step from its own Philox phase) and its time-averaged MSE (1e-4); GS
     target 9 of 16 at 2048^2, holograms after 3 iterations and the 20-iteration
     MSE curve within 1%."""
     n, B, NS = 1024, 8, 24
@@ -722,7 +740,14 @@ def test_ospr_and_2048_configurations_sampled_against_the_oracle():
     finally:
         plan.close()
     o = oracle.ospr_run(t[5], NS, 7, t_index=5)
-    assert np.mean(h5 != o["holo"]) <= 1e-3
+    Tn = oracle.prepare_target(t[5])
+    flips = 0
+    for s in range(NS):  # each subframe is one step from its Philox phase
+        h = oracle.gs_step(Tn, oracle.random_phase(n, n, 7, 5, s, 0))["h"]
+        mism = h5[s] != o["holo"][s]
+        assert not np.any(mism & ~boundary_mask(h, hg.HG_SLM_BINARY, 2)), (s, int(np.sum(mism)))
+        flips += int(np.sum(mism))
+    print("OSPR 8 x 24 x 1024^2, target 5: %d boundary pixels quantised differently" % flips)
     assert abs(m5 - o["mse"]) <= 1e-4 * o["mse"], (m5, o["mse"])
 
     n, B = 2048, 16
