@@ -790,6 +790,19 @@ bool herm_loop(hg_plan p) {
     return p->prow && p->prow->paired && p->pcol && !p->use_pack && p->kind == HG_SLM_BINARY;
 }
 
+// The Hermitian binary loop also starts and ends in Hermitian form: the head
+// writes rows ky <= ny/2 of F_H, and the tail reads rows ky <= ny/2 of the
+// last column pass (both on the paired row kernel).
+bool herm_ends(hg_plan p) { return herm_loop(p) && p->prow->row_head && p->prow->row_tail; }
+
+void launch_pair_end(hg_plan p, bool head, const RowArgs &a, cudaStream_t s) {
+    const long work = (long)a.items * p->ppt_pipe;
+    const int grid = grid_for(p->prow->row_blocks_per_sm, p->nsm, work);
+    if (head) p->prow->row_head(a, pipe_args(p), grid, s);
+    else p->prow->row_tail(a, pipe_args(p), grid, s);
+    p->launches++;
+}
+
 // The middle of a GS run: for k = 0 .. iters-2, column pass k then row pass
 // k (metrics of iteration k, constraint for iteration k+1).
 void enqueue_loop(hg_plan p, int iters, cudaStream_t s) {
@@ -797,8 +810,9 @@ void enqueue_loop(hg_plan p, int iters, cudaStream_t s) {
     RowArgs ra = row_args(p);
     ca.half = p->prow && p->prow->paired;  // the paired row pass rebuilds rows ny - ky
     ra.herm = herm_loop(p);
+    const bool half_head = herm_ends(p);
     for (int k = 0; k + 1 < iters; ++k) {
-        ca.half_in = ra.herm && k > 0;  // column pass 0 follows the (full) head pass
+        ca.half_in = ra.herm && (k > 0 || half_head);  // after a full head, column pass 0 reads every row
         if (p->use_pack) launch_col_pack(p, ca, s);
         else if (ca.half_in && p->use_herm_col) launch_col_herm(p, ca, s);
         else launch_col_gs(p, col_role_gs(p), ca, s);
@@ -946,23 +960,32 @@ hg_status enqueue_run(hg_plan p, const float *d_t, const float *d_ph, int iters,
         }
         ra.phase = d_ph;
         lt_set(p, ra, 0);
-        launch_row(p, ROW_HEAD, ra, p->stream);
+        const bool ends = herm_ends(p);
+        if (ends) {
+            ra.herm = 1;
+            launch_pair_end(p, true, ra, p->stream);
+        } else {
+            launch_row(p, ROW_HEAD, ra, p->stream);
+        }
         if (capturing) {
             enqueue_loop(p, iters, p->stream);
         } else if ((st = run_loop(p, iters)) != HG_OK) {
             return st;
         }
         ca.holo = d_ho;
-        ca.half_in = herm_loop(p) && iters >= 2;
+        ca.half_in = herm_loop(p) && (iters >= 2 || ends);
+        ca.half = ends;  // the Hermitian tail reads rows ky <= ny/2 only
         if (ca.half_in && p->use_herm_col) launch_col_herm(p, ca, p->stream);
         else launch_col_gs(p, col_role_gs(p), ca, p->stream);
         RowArgs rt = row_args(p);
         rt.part = p->part + (size_t)(iters - 1) * p->batch * p->ppt_max * part_stride(p);
         if (p->tc_prec) launch_row_tc(p, ROW_TAIL, rt, p->stream);
+        else if (ends) launch_pair_end(p, false, rt, p->stream);
         else launch_row(p, ROW_TAIL, rt, p->stream);
     }
     const int panels_iter = p->tc_prec ? p->ppt_tc : p->prow ? p->ppt_pipe : p->ppt;
     int panels_last = (p->tc_prec && !is_ospr(p->algo)) ? p->ppt_tc : p->ppt;
+    if (!is_ospr(p->algo) && !is_search(p->algo) && herm_ends(p)) panels_last = p->ppt_pipe;  // Hermitian tail
     if (p->ospr_herm) panels_last = (p->ny / 2 + p->rops->row_lines) / p->rops->row_lines;  // rows <= ny/2
     if (is_search(p->algo)) {
         // the search kernel wrote the metrics and mse_out itself
@@ -1509,8 +1532,10 @@ const char *hg_plan_variant(hg_plan p, int pass) {
     }
     const PipeOps *o = pass == 0 ? p->prow : p->pcol;
     if (o && herm_loop(p)) {  // Hermitian form of the binary loop
-        snprintf(p->vname[pass], sizeof p->vname[pass], "%s+herm%s", o->name,
-                 pass == 1 && p->use_herm_col ? "-colpairs" : "");
+        // the column-pair pass may come from another variant than the per-column pass
+        const bool pairs = pass == 1 && p->use_herm_col;
+        snprintf(p->vname[pass], sizeof p->vname[pass], "%s+herm%s", pairs ? p->hops->name : o->name,
+                 pairs ? "-colpairs" : "");
         return p->vname[pass];
     }
     return o ? o->name : "generic";
@@ -1637,7 +1662,9 @@ hg_status hg_get_phase(hg_plan p, float *phase_out) {
     RowArgs ra = row_args(p);
     ra.w = nullptr;  // no weight update
     ra.phase_out = d;
-    launch_row(p, ROW_TAIL, ra, p->stream);
+    // after a run of the Hermitian loop the field holds rows ky <= ny/2 only
+    if (herm_ends(p)) launch_pair_end(p, false, ra, p->stream);
+    else launch_row(p, ROW_TAIL, ra, p->stream);
     HG_CK(cudaGetLastError());
     if (host) {
         HG_CK(cudaMemcpyAsync(phase_out, d, bytes, cudaMemcpyDeviceToHost, p->stream));

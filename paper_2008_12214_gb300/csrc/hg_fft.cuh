@@ -344,6 +344,21 @@ __device__ __forceinline__ void stage_next(float2 (&v)[P::E], float2 *smb,
     if constexpr (!TO_REGS) sync();
 }
 
+// A plan whose stage roots are loaded afresh by every line transform.  In a
+// persistent kernel each thread's roots are the same for every line it
+// transforms, so the compiler keeps them in registers across the whole loop
+// (about 2 (R_0 - 1) + 2 (R_1 - 1) registers for a three-stage plan); this
+// wrapper trades those registers for L1-resident reloads, raising the number
+// of warps an SM can hold.
+template <class P>
+struct Reload : P {
+    static constexpr bool TW_RELOAD = true;
+};
+template <class P, class = void>
+struct tw_reload : std::false_type {};
+template <class P>
+struct tw_reload<P, std::void_t<decltype(P::TW_RELOAD)>> : std::bool_constant<P::TW_RELOAD> {};
+
 // Whole line transform: thread t holds samples t + TL e in v on entry and the
 // transform's outputs t + TL e on exit.  `sync` must order shared-memory
 // accesses of all threads of the line.  Shared memory may be reused between
@@ -351,6 +366,11 @@ __device__ __forceinline__ void stage_next(float2 (&v)[P::E], float2 *smb,
 template <class P, int DIR, int STRIDE, class LAY = Pad, class SYNC>
 __device__ __forceinline__ void line_fft(float2 (&v)[P::E], float2 *smb,
                                          const float2 *__restrict__ tw, int t, SYNC sync) {
+    if constexpr (tw_reload<P>::value) {
+        // an opaque copy of the table pointer: loads through it cannot be
+        // hoisted out of the caller's loop
+        asm volatile("mov.b64 %0, %0;" : "+l"(tw));
+    }
     if constexpr (P::NS == 1) {
         stage_first<P, DIR, STRIDE, LAY>(v, smb, tw, t);
     } else {

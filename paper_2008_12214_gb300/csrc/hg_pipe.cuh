@@ -376,7 +376,7 @@ __device__ __forceinline__ void pair_finish(float2 (&w)[P::E], float2 *xbuf, con
 // row's weights before this pass (for self-mirrored rows a shared-memory
 // copy, since other threads update the row in place); store_m: write the
 // mirror's updated weight (partner rows only).
-template <class P>
+template <class P, bool GEN>
 __device__ __forceinline__ void herm_constrain(float2 (&w)[P::E], const float *sT, const float *sTm, float *wr,
                                                const float *wold_m, float *wrm, bool partner,
                                                const RowArgs &a, int t, int yrow, float &acc0, float &acc1,
@@ -404,19 +404,24 @@ __device__ __forceinline__ void herm_constrain(float2 (&w)[P::E], const float *s
             acc3 += e2;
             if (Tm > 0.f) acc2 += e2;
         }
-        float wv = 1.f, wm = 1.f;
-        if (wr) {
-            wv = wr[x];
-            if (Tv > 0.f && m2 > 0.f) wv = wv * Tv * (a.NN * rs);
-            wr[x] = wv;
-            wm = wold_m[xm];
-            if (Tm > 0.f && m2 > 0.f) wm = wm * Tm * (a.NN * rs);
-            if (partner) wrm[xm] = wm;
+        if constexpr (GEN) {
+            float wv = 1.f, wm = 1.f;
+            if (wr) {
+                wv = wr[x];
+                if (Tv > 0.f && m2 > 0.f) wv = wv * Tv * (a.NN * rs);
+                wr[x] = wv;
+                wm = wold_m[xm];
+                if (Tm > 0.f && m2 > 0.f) wm = wm * Tm * (a.NN * rs);
+                if (partner) wrm[xm] = wm;
+            }
+            const float gm = (a.lt_amp > 0.f ? a.lt_amp : 1.f) * 0.5f * fmaf(Tv, wv, Tm * wm);
+            // the window is symmetric under u -> -u: outside it F_H = R
+            if (a.lt_amp > 0.f && !lt_in(a, yrow, x)) w[e] = r;
+            else w[e] = m2 > 0.f ? make_float2(gm * r.x * rs, gm * r.y * rs) : make_float2(gm, 0.f);
+        } else {  // plain GS: no weights, no window
+            const float gm = 0.5f * (Tv + Tm);
+            w[e] = m2 > 0.f ? make_float2(gm * r.x * rs, gm * r.y * rs) : make_float2(gm, 0.f);
         }
-        const float gm = (a.lt_amp > 0.f ? a.lt_amp : 1.f) * 0.5f * fmaf(Tv, wv, Tm * wm);
-        // the window is symmetric under u -> -u: outside it F_H = R
-        if (a.lt_amp > 0.f && !lt_in(a, yrow, x)) w[e] = r;
-        else w[e] = m2 > 0.f ? make_float2(gm * r.x * rs, gm * r.y * rs) : make_float2(gm, 0.f);
     });
 }
 
@@ -432,9 +437,18 @@ struct PairPipeCfg {
     static constexpr size_t SMEM = 1024 + (size_t)NG * D * SLOT + RED + NG * D * 8 + 4 * (NG + 1) + 256;
 };
 
-template <class P, int NG, int D, int SWZ, bool HERM>
-__global__ void __launch_bounds__(PairPipeCfg<P, NG, D, SWZ>::THREADS, 1)
+// MODE 0: paired rows (full F); 1: Hermitian form, any plan (weights, window);
+// 2: Hermitian form of plain GS (no weights, no window), compiled without
+// those paths; 3: Hermitian HEAD, the first field F_H of a run from the
+// target and the initial replay phase (or Philox phases), rows ky <= ny/2,
+// inverse row FFT; 4: Hermitian TAIL, the forward row FFT of a binary
+// column-transformed field (rows ky <= ny/2), metrics and weights of both
+// pixels u and -u, and optionally arg R and R at both (no inverse FFT, no
+// store).
+template <class P, int NG, int D, int SWZ, int MODE, int MINB = 1>
+__global__ void __launch_bounds__(PairPipeCfg<P, NG, D, SWZ>::THREADS, MINB)
     k_row_pipe_pair(const RowArgs a, const PipeArgs pa) {
+    constexpr bool HERM = MODE != 0;
     using Cfg = PairPipeCfg<P, NG, D, SWZ>;
     using LAY = Swz<SWZ>;
     constexpr int TL = P::TL, E = P::E, NX = P::N, GT = Cfg::GT;
@@ -472,6 +486,21 @@ __global__ void __launch_bounds__(PairPipeCfg<P, NG, D, SWZ>::THREADS, 1)
         const int item = j / ppt, pan = j - item * ppt;
         const bool partner = pan != 0 && pan != hy;
         unsigned char *sl = ring + (size_t)(k % D) * Cfg::SLOT;
+        if constexpr (MODE == 3) {
+            // replay rows of DFT rows pan and ny - pan: phases, then the targets
+            const int b = item / a.nsub, ym = (ny - pan) % ny;
+            const int iy = (pan + hy) % ny, iym = (ym + hy) % ny;
+            const uint32_t rows = partner ? 2u : 1u;
+            mbar_expect_tx(gfull + k % D, (uint32_t)(NX * 4) * rows * (a.phase ? 2u : 1u));
+            if (a.phase) {
+                bulk_g2s(sl, a.phase + ((size_t)b * ny + iy) * NX, NX * 4, gfull + k % D);
+                if (partner) bulk_g2s(sl + NX * 4, a.phase + ((size_t)b * ny + iym) * NX, NX * 4, gfull + k % D);
+            }
+            bulk_g2s(sl + Cfg::SLOT_F, a.T + ((size_t)b * ny + pan) * NX, NX * 4, gfull + k % D);
+            if (partner)
+                bulk_g2s(sl + Cfg::SLOT_F + NX * 4, a.T + ((size_t)b * ny + ym) * NX, NX * 4, gfull + k % D);
+            return;
+        }
         mbar_expect_tx(gfull + k % D, (uint32_t)(NX * (partner ? 16 : 12)));
         bulk_g2s(sl, a.field + ((size_t)item * ny + pan) * NX, NX * 8, gfull + k % D);
         bulk_g2s(sl + Cfg::SLOT_F, a.T + ((size_t)item * ny + pan) * NX, NX * 4, gfull + k % D);
@@ -511,28 +540,101 @@ __global__ void __launch_bounds__(PairPipeCfg<P, NG, D, SWZ>::THREADS, 1)
         const float *sTa = reinterpret_cast<const float *>(sl + Cfg::SLOT_F);
         float2 *park = reinterpret_cast<float2 *>(sl + Cfg::SLOT_F);  // row ny - p after use of T
         float2 v[E];
+        if constexpr (MODE == 3) {
+            // F_H(u) = (F(u) + conj F(-u)) / 2 with F = w T e^{i phi} (A w T inside
+            // the Liu-Taghizadeh window, 0 outside; the window is symmetric)
+            const float *sP = reinterpret_cast<const float *>(sl);
+            const float *sPm = partner ? sP + NX : sP;
+            const float *sTm = partner ? sTa + NX : sTa;
+            const int b = item / a.nsub, sub = item - b * a.nsub;
+            const int ym = (ny - pan) % ny, iy = (pan + hy) % ny, iym = (ym + hy) % ny;
+            const float *wr = a.w ? a.w + ((size_t)b * ny + pan) * NX : nullptr;
+            const float *wrm = a.w ? a.w + ((size_t)b * ny + ym) * NX : nullptr;
+            static_for<0, E>([&](auto ec) {
+                constexpr int e = decltype(ec)::value;
+                const int x = t + TL * e, xm = mirror_idx<NX>(x);
+                const int ix = (x + NX / 2) % NX, ixm = (xm + NX / 2) % NX;
+                float amp = sTa[x], am = sTm[xm];
+                if (wr) {
+                    amp *= wr[x];
+                    am *= wrm[xm];
+                }
+                if (a.lt_amp > 0.f) {
+                    const bool in = lt_in(a, pan, x);
+                    amp = in ? amp * a.lt_amp : 0.f;
+                    am = in ? am * a.lt_amp : 0.f;
+                }
+                float s, c, sm, cm;
+                if (a.phase) {
+                    // phase in half-turns: the reduction is exact, no large-argument path
+                    sincospif(sP[ix] * 0.318309886183790672f, &s, &c);
+                    sincospif(sPm[ixm] * 0.318309886183790672f, &sm, &cm);
+                } else {
+                    const uint32_t r = philox_word0((uint32_t)(iy * NX + ix), (uint32_t)sub, (uint32_t)b,
+                                                    a.stream_id, a.seed_lo, a.seed_hi);
+                    const uint32_t rm = philox_word0((uint32_t)(iym * NX + ixm), (uint32_t)sub, (uint32_t)b,
+                                                     a.stream_id, a.seed_lo, a.seed_hi);
+                    sincospif((float)(r >> 8) * (1.0f / 8388608.0f), &s, &c);  // pi * 2u
+                    sincospif((float)(rm >> 8) * (1.0f / 8388608.0f), &sm, &cm);
+                }
+                v[e] = make_float2(0.5f * fmaf(am, cm, amp * c), 0.5f * fmaf(-am, sm, amp * s));
+            });
+            pair_finish<P, LAY>(v, sf, a.tw, t, gsync, a.field + ((size_t)item * ny + pan) * NX);
+            gsync();
+            if (t == 0) issue(k + D);
+            continue;
+        }
         static_for<0, E>([&](auto ec) {
             constexpr int e = decltype(ec)::value;
             v[e] = sf[t + TL * e];
         });
         line_fft<P, -1, 1, LAY>(v, sf, a.tw, t, gsync);
         float acc0 = 0.f, acc1 = 0.f, acc2 = 0.f, acc3 = 0.f;
-        if constexpr (HERM) {
-            float *wrp = a.w ? a.w + ((size_t)item * ny + pan) * NX : nullptr;
-            float *wrm = a.w && partner ? a.w + ((size_t)item * ny + ny - pan) * NX : nullptr;
-            const float *wold = wrm;
-            if (a.w && !partner) {  // self-mirrored row: keep its old weights for the mirror reads
-                float *sW = const_cast<float *>(sTa) + NX;
+        if constexpr (MODE == 4) {
+            // outputs at u (this row) and -u (row ny - pan, R(-u) = conj R(u));
+            // the mirror pixels of the self-conjugate rows are this row's own
+            if (a.phase_out || a.R_out) {
+                const int ym = (ny - pan) % ny, iy = (pan + hy) % ny, iym = (ym + hy) % ny;
+                const size_t ob = (size_t)item * ny * NX;
                 static_for<0, E>([&](auto ec) {
                     constexpr int e = decltype(ec)::value;
-                    sW[t + TL * e] = wrp[t + TL * e];
+                    const int x = t + TL * e, xm = mirror_idx<NX>(x);
+                    const int ix = (x + NX / 2) % NX, ixm = (xm + NX / 2) % NX;
+                    const float2 r = v[e];
+                    const bool nz = fmaf(r.x, r.x, r.y * r.y) > 0.f;
+                    if (a.phase_out) {
+                        a.phase_out[ob + (size_t)iy * NX + ix] = nz ? atan2f(r.y, r.x) : 0.f;
+                        if (partner) a.phase_out[ob + (size_t)iym * NX + ixm] = nz ? atan2f(-r.y, r.x) : 0.f;
+                    }
+                    if (a.R_out) {
+                        a.R_out[ob + (size_t)iy * NX + ix] = make_float2(r.x * a.invSqrtN, r.y * a.invSqrtN);
+                        if (partner)
+                            a.R_out[ob + (size_t)iym * NX + ixm] = make_float2(r.x * a.invSqrtN, -r.y * a.invSqrtN);
+                    }
                 });
-                gsync();
-                wold = sW;
             }
-            herm_constrain<P>(v, sTa, partner ? sTa + NX : sTa, wrp, wold, wrm, partner, a, t, pan, acc0, acc1,
-                              acc2, acc3);
-            pair_finish<P, LAY>(v, sf, a.tw, t, gsync, a.field + ((size_t)item * ny + pan) * NX);
+        }
+        if constexpr (HERM) {
+            float *wrp = nullptr, *wrm = nullptr;
+            const float *wold = nullptr;
+            if constexpr (MODE == 1 || MODE == 4) {
+                wrp = a.w ? a.w + ((size_t)item * ny + pan) * NX : nullptr;
+                wrm = a.w && partner ? a.w + ((size_t)item * ny + ny - pan) * NX : nullptr;
+                wold = wrm;
+                if (a.w && !partner) {  // self-mirrored row: keep its old weights for the mirror reads
+                    float *sW = const_cast<float *>(sTa) + NX;
+                    static_for<0, E>([&](auto ec) {
+                        constexpr int e = decltype(ec)::value;
+                        sW[t + TL * e] = wrp[t + TL * e];
+                    });
+                    gsync();
+                    wold = sW;
+                }
+            }
+            herm_constrain<P, MODE != 2>(v, sTa, partner ? sTa + NX : sTa, wrp, wold, wrm, partner, a, t, pan,
+                                         acc0, acc1, acc2, acc3);
+            if constexpr (MODE != 4)
+                pair_finish<P, LAY>(v, sf, a.tw, t, gsync, a.field + ((size_t)item * ny + pan) * NX);
             gsync();
             if (t == 0) issue(k + D);
             if (a.part)
@@ -772,8 +874,8 @@ struct ColHermCfg {
     static constexpr size_t SMEM = 1024 + (size_t)D * SLOT + D * 8 + 16 + 256;
 };
 
-template <class P, int C, int D, int SWZ, int BOXR>
-__global__ void __launch_bounds__(ColHermCfg<P, C, D, SWZ, BOXR>::THREADS, 1)
+template <class P, int C, int D, int SWZ, int BOXR, int MINB = 1>
+__global__ void __launch_bounds__(ColHermCfg<P, C, D, SWZ, BOXR>::THREADS, MINB)
     k_col_pipe_herm(const ColArgs a, const PipeArgs pa, const __grid_constant__ CUtensorMap tmap) {
     using Cfg = ColHermCfg<P, C, D, SWZ, BOXR>;
     using LAY = Swz<SWZ>;
@@ -1056,6 +1158,10 @@ struct PipeOps {
     // its tensor map has boxes of herm_c columns x herm_boxr rows
     void (*col_herm)(const ColArgs &a, const PipeArgs &pa, const CUtensorMap &m, int grid, cudaStream_t s);
     int herm_c, herm_boxr, herm_blocks_per_sm;
+    // Hermitian head and tail of the binary loop on the paired row kernel
+    // (rows ky <= ny/2; may be null)
+    void (*row_head)(const RowArgs &a, const PipeArgs &pa, int grid, cudaStream_t s);
+    void (*row_tail)(const RowArgs &a, const PipeArgs &pa, int grid, cudaStream_t s);
 };
 
 // Row pass: plan P, LINES rows per group, NGR groups, ring depth DR, swizzle
@@ -1132,24 +1238,38 @@ struct PipeImpl {
 
 
 // A paired-row variant: plan P (TL a multiple of 32), NG groups, ring depth D,
-// swizzle SWZ, and the column pass of another variant `col`.
-template <class P, int NG, int D, int SWZ>
+// swizzle SWZ, at least MINB CTAs per SM (the register budget), and the
+// column pass of another variant `col`.
+template <class P, int NG, int D, int SWZ, int MINB = 1>
 struct PairImpl {
     using RC = PairPipeCfg<P, NG, D, SWZ>;
     static cudaError_t init_row(int *blocks) {
-        cudaError_t e = cudaFuncSetAttribute((const void *)k_row_pipe_pair<P, NG, D, SWZ, false>,
-                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)RC::SMEM);
+        cudaError_t e = cudaSuccess;
+        for (const void *f : {(const void *)k_row_pipe_pair<P, NG, D, SWZ, 0, MINB>,
+                              (const void *)k_row_pipe_pair<P, NG, D, SWZ, 1, MINB>,
+                              (const void *)k_row_pipe_pair<P, NG, D, SWZ, 2, MINB>,
+                              (const void *)k_row_pipe_pair<P, NG, D, SWZ, 3, MINB>,
+                              (const void *)k_row_pipe_pair<P, NG, D, SWZ, 4, MINB>})
+            if (e == cudaSuccess)
+                e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)RC::SMEM);
+        // the block count of the general Hermitian kernel (the most registers)
+        // sizes the grid of every mode
         if (e == cudaSuccess)
-            e = cudaFuncSetAttribute((const void *)k_row_pipe_pair<P, NG, D, SWZ, true>,
-                                     cudaFuncAttributeMaxDynamicSharedMemorySize, (int)RC::SMEM);
-        if (e == cudaSuccess)
-            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, k_row_pipe_pair<P, NG, D, SWZ, false>,
+            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, k_row_pipe_pair<P, NG, D, SWZ, 1, MINB>,
                                                               RC::THREADS, RC::SMEM);
         return e;
     }
     static void row_iter(const RowArgs &a, const PipeArgs &pa, int grid, cudaStream_t s) {
-        if (a.herm) k_row_pipe_pair<P, NG, D, SWZ, true><<<grid, RC::THREADS, RC::SMEM, s>>>(a, pa);
-        else k_row_pipe_pair<P, NG, D, SWZ, false><<<grid, RC::THREADS, RC::SMEM, s>>>(a, pa);
+        if (!a.herm) k_row_pipe_pair<P, NG, D, SWZ, 0, MINB><<<grid, RC::THREADS, RC::SMEM, s>>>(a, pa);
+        else if (a.w || a.lt_amp > 0.f)
+            k_row_pipe_pair<P, NG, D, SWZ, 1, MINB><<<grid, RC::THREADS, RC::SMEM, s>>>(a, pa);
+        else k_row_pipe_pair<P, NG, D, SWZ, 2, MINB><<<grid, RC::THREADS, RC::SMEM, s>>>(a, pa);
+    }
+    static void row_head(const RowArgs &a, const PipeArgs &pa, int grid, cudaStream_t s) {
+        k_row_pipe_pair<P, NG, D, SWZ, 3, MINB><<<grid, RC::THREADS, RC::SMEM, s>>>(a, pa);
+    }
+    static void row_tail(const RowArgs &a, const PipeArgs &pa, int grid, cudaStream_t s) {
+        k_row_pipe_pair<P, NG, D, SWZ, 4, MINB><<<grid, RC::THREADS, RC::SMEM, s>>>(a, pa);
     }
 };
 
@@ -1170,21 +1290,22 @@ struct PackImpl {
     }
 };
 
-// Column-pair Hermitian column pass launcher (see k_col_pipe_herm).
-template <class P, int C, int D, int SWZ, int BOXR>
+// Column-pair Hermitian column pass launcher (see k_col_pipe_herm); MINB:
+// at least that many CTAs per SM (the register budget).
+template <class P, int C, int D, int SWZ, int BOXR, int MINB = 1>
 struct HermImpl {
     using CC = ColHermCfg<P, C, D, SWZ, BOXR>;
     static constexpr int COLS = C, BOX_ROWS = BOXR;
     static cudaError_t init(int *blocks) {
-        cudaError_t e = cudaFuncSetAttribute((const void *)k_col_pipe_herm<P, C, D, SWZ, BOXR>,
+        cudaError_t e = cudaFuncSetAttribute((const void *)k_col_pipe_herm<P, C, D, SWZ, BOXR, MINB>,
                                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)CC::SMEM);
         if (e == cudaSuccess)
-            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, k_col_pipe_herm<P, C, D, SWZ, BOXR>,
+            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, k_col_pipe_herm<P, C, D, SWZ, BOXR, MINB>,
                                                               CC::THREADS, CC::SMEM);
         return e;
     }
     static void launch(const ColArgs &a, const PipeArgs &pa, const CUtensorMap &m, int grid, cudaStream_t s) {
-        k_col_pipe_herm<P, C, D, SWZ, BOXR><<<grid, CC::THREADS, CC::SMEM, s>>>(a, pa, m);
+        k_col_pipe_herm<P, C, D, SWZ, BOXR, MINB><<<grid, CC::THREADS, CC::SMEM, s>>>(a, pa, m);
     }
 };
 
@@ -1236,6 +1357,8 @@ struct PairedOps {
         o.row_threads = PAIR::RC::THREADS;
         o.row_smem = PAIR::RC::SMEM;
         o.row_iter = &PAIR::row_iter;
+        o.row_head = &PAIR::row_head;
+        o.row_tail = &PAIR::row_tail;
         o.col_pack = PACK::launch;
         o.col_herm = HERM::launch;
         o.herm_c = HERM::COLS;

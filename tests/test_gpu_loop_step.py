@@ -18,10 +18,12 @@ target:
   * the field the column pass leaves, against the column DFT of the SLM field
     of the GPU's own H_{k+1}: relative L2 <= 1e-5;
   * WGS: the updated weights against the oracle's where I is above 1% of its
-    mean (elsewhere w T / sqrt(I) divides by a near-zero |R|).  The row field
-    and the next hologram of a WGS plan are checked with the GPU's updated
-    weights, so that only the transforms, the constraint and the quantiser
-    are under test there.
+    mean (elsewhere w T / sqrt(I) divides by a near-zero |R|); the constrained
+    field F (the row pass's output transformed back along x) with the GPU's
+    weights on those pixels, relative L2 <= 1e-5; the next hologram against
+    the quantisation of the exact inverse DFT of the GPU's own F, bit-exact
+    except pixels within 1e-5 rad of a boundary or closer to it than 1e-6 of
+    the field's RMS magnitude (wgs_floor_mask: the weights' dynamic range).
 The plans are those the workloads use (autotuned, default options); targets
 that are not sampled get seeded random holograms and only their metrics are
 checked.
@@ -56,6 +58,19 @@ def boundary_mask(h, kind, levels):
         return np.abs(h.real) <= np.sin(BOUND_RAD) * np.abs(h)
     x = np.angle(h) * levels / (2 * np.pi)
     return np.abs(x - np.floor(x) - 0.5) <= BOUND_RAD * levels / (2 * np.pi)
+
+
+def wgs_floor_mask(h, kind, levels, rel=1e-6):
+    """Pixels whose distance to a decision boundary, in field units, is below
+    rel x the field's RMS magnitude (about ten times the FP32 transform's
+    absolute error).  Weighted GS gives F a dynamic range in which a fixed
+    angle band does not cover that error at pixels of small |h|."""
+    floor = rel * np.sqrt(np.mean(np.abs(h) ** 2))
+    if kind == oracle.SLM_BINARY:
+        return np.abs(h.real) <= floor
+    x = np.angle(h) * levels / (2 * np.pi)
+    margin = np.abs(x - np.floor(x) - 0.5) * 2 * np.pi / levels  # rad to the boundary
+    return np.abs(h) * np.sin(np.minimum(margin, np.pi / 2)) <= floor
 
 
 def okind(kind):
@@ -131,6 +146,7 @@ def check_sample(g, b, st, kind, levels, wgs, herm, half_col, tag):
     ny, nx = st["Tn"].shape
     assert np.allclose(g["met"][b], st["met"], rtol=1e-4, atol=0), (tag, g["met"][b], st["met"])
     w = np.ones((ny, nx))
+    good = None
     if wgs:
         R2 = np.abs(st["R"]) ** 2
         I = R2 / R2.sum()
@@ -141,11 +157,34 @@ def check_sample(g, b, st, kind, levels, wgs, herm, half_col, tag):
     F = w * st["Tn"] * phasor(st["R"])
     G = row_field(F, herm)
     rows = slice(0, ny // 2 + 1) if herm else slice(0, ny)
-    e_row = rel_l2(g["row"][b][rows], G[rows])
-    assert e_row <= 1e-5, (tag, "row field", e_row)
-    nxt = oracle.gs_step(st["Tn"], st["phase_next"], w if wgs else None, kind, levels, False)
-    mism = g["holo"][b] != nxt["holo"]
-    bnd = boundary_mask(nxt["h"], kind, levels)
+    if not wgs:
+        e_row = rel_l2(g["row"][b][rows], G[rows])
+        assert e_row <= 1e-5, (tag, "row field", e_row)
+        nxt = oracle.gs_step(st["Tn"], st["phase_next"], None, kind, levels, False)
+        h_next = nxt["h"]
+        H_next = nxt["holo"]
+        bnd = boundary_mask(h_next, kind, levels)
+    else:
+        # The literal weight rule divides by |R|, so the largest weights sit
+        # where |R| is smallest and its phasor least determined: F's FP32
+        # error concentrates on a few pixels that dominate its norm.  The
+        # row pass is therefore checked on the constrained field F (its
+        # output transformed back along x) where I is above 1% of its mean,
+        # and the column pass on the GPU's own F: H_{k+1} against the
+        # quantisation of the exact inverse DFT of that F.
+        Fg = np.fft.fft(g["row"][b].astype(np.complex128), axis=1) / nx
+        Fr = np.fft.ifftshift(F)
+        if herm:
+            Fr = 0.5 * (Fr + np.conj(mirror(Fr)))
+        good = np.fft.ifftshift(good)[rows]
+        e_row = rel_l2(Fg[rows][good], Fr[rows][good])
+        assert e_row <= 1e-5, (tag, "constrained field where I > 1% of its mean", e_row)
+        if herm:
+            Fg[ny // 2 + 1:] = np.conj(mirror(Fg))[ny // 2 + 1:]
+        h_next = oracle.fft2(Fg, +1)
+        H_next = oracle.quantise(h_next, kind, levels)
+        bnd = boundary_mask(h_next, kind, levels) | wgs_floor_mask(h_next, kind, levels)
+    mism = g["holo"][b] != H_next
     assert not np.any(mism & ~bnd), (tag, "hologram mismatch off the boundary", int(np.sum(mism & ~bnd)))
     step = np.pi if kind == oracle.SLM_BINARY else 2 * np.pi / levels
     C = col_field(np.exp(1j * step * g["holo"][b].astype(np.float64)))
