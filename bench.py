@@ -480,19 +480,44 @@ def run_side_workload(args):
             Ps.append(torch.from_numpy(synth.init_phases(16, ny, nx, 3000 + 16 * i)).to(dev))
             Ms.append(torch.empty((16, args.iters), dtype=torch.float64, device=dev))
         g = hg.hg_group_create(plans)
-        for _ in range(args.warmup):
-            hg.hg_group_run(g, Ts, Ps, args.iters, None, Ms)
-        hg.hg_group_sync(g)
-        e0.record(s0)
-        for _ in range(args.steps):
-            hg.hg_group_run(g, Ts, Ps, args.iters, None, Ms)
-        e1.record(s0)
-        hg.hg_group_sync(g)
-        ms = e0.elapsed_time(e1) / args.steps
+        sched_ms = {}
+        for name, sched in (("concurrent", hg.HG_GROUP_CONCURRENT), ("serial", hg.HG_GROUP_SERIAL)):
+            hg.hg_group_set_schedule(g, sched)
+            for _ in range(args.warmup):
+                hg.hg_group_run(g, Ts, Ps, args.iters, None, Ms)
+            hg.hg_group_sync(g)
+            e0.record(s0)
+            for _ in range(args.steps):
+                hg.hg_group_run(g, Ts, Ps, args.iters, None, Ms)
+            e1.record(s0)
+            hg.hg_group_sync(g)
+            sched_ms[name] = e0.elapsed_time(e1) / args.steps
+        ms = sched_ms["serial"]  # the default schedule
         px = 16 * sum(a * b for a, b in shapes)
+        # each size alone (its plan's own hg_run), and its loop passes one by one
+        alone = []
+        for i, p in enumerate(plans):
+            for _ in range(2):
+                p.run(Ts[i], Ps[i], args.iters, None, Ms[i])
+            p.sync()
+            e0.record(s0)
+            for _ in range(args.steps):
+                p.run(Ts[i], Ps[i], args.iters, None, Ms[i])
+            e1.record(s0)
+            p.sync()
+            ms_i = e0.elapsed_time(e1) / args.steps
+            hg.hg_profile_enable(p.h, 2 * args.iters + 8)
+            p.run(Ts[i], Ps[i], args.iters, None, Ms[i])
+            prof = hg.hg_profile_read(p.h)
+            hg.hg_profile_enable(p.h, 0)
+            alone.append(dict(shape="%dx%d" % shapes[i], ms_per_run=ms_i,
+                              row_ms=prof[0] / max(prof[1], 1), column_ms=prof[2] / max(prof[3], 1),
+                              gbs_at_36=36.0 * 16 * shapes[i][0] * shapes[i][1] * args.iters / (ms_i / 1e3) / 1e9))
         out = dict(workload="mixed_64_targets_one_graph", ms_per_step=ms, iters_per_step=args.iters,
                    batched_iterations_per_s=args.iters / (ms / 1e3),
                    algorithmic_gbs_at_36=36.0 * px * args.iters / (ms / 1e3) / 1e9,
+                   ms_per_step_by_schedule=sched_ms,
+                   sum_of_sizes_alone_ms=sum(a["ms_per_run"] for a in alone), sizes_alone=alone,
                    variants=[(hg.hg_plan_variant(p.h, 0), hg.hg_plan_variant(p.h, 1)) for p in plans],
                    launches_per_step=hg.hg_group_launch_count(g))
         hg.hg_group_destroy(g)

@@ -360,7 +360,8 @@ const char *hg_status_string(hg_status st);
 
 /*
  * Groups: targets of different sizes (each size a plan) run as ONE CUDA graph
- * whose branches are the plans' whole GS/WGS runs, executed concurrently.
+ * holding the plans' whole GS/WGS runs, one after another or as concurrent
+ * branches (hg_group_set_schedule).
  * This serves mixed batches such as 512^2, 1024^2, 2048^2 and 1080 x 1920
  * targets side by side (Section 2 notes that field size is a free parameter;
  * the batch mix itself has no counterpart in the paper).
@@ -387,6 +388,15 @@ hg_status hg_group_run(hg_group group, const float *const *targets, const float 
                        int iters, uint8_t *const *holo_out, double *const *mse_out, void *stream);
 hg_status hg_group_sync(hg_group group, void *stream);
 int hg_group_launch_count(hg_group group);
+/* Order of the plans' runs inside the group's graph: HG_GROUP_SERIAL (the
+ * default) runs them one after another, HG_GROUP_CONCURRENT as concurrent
+ * branches.  Every pass of a size of 512^2 and up fills the GPU on its own,
+ * so concurrent branches only contend for the SMs and the L2; concurrency can
+ * pay for many small plans.  The next hg_group_run captures the graph again.
+ * Errors: HG_ERR_INVALID_ARG (NULL group, unknown schedule). */
+#define HG_GROUP_SERIAL 0
+#define HG_GROUP_CONCURRENT 1
+hg_status hg_group_set_schedule(hg_group group, int schedule);
 void hg_group_destroy(hg_group group);
 
 /*

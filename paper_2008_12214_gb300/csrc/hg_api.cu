@@ -80,23 +80,25 @@ __global__ void k_prep_scale(const double *part, int batch, double *scale, unsig
 }
 
 // Prepared target in DFT order: Tf[b][y][x] = T[b][(y+ny/2)%ny][(x+nx/2)%nx] * scale[b],
-// rounded to float with the support T > 0 preserved.
+// rounded to float with the support T > 0 preserved.  One CTA per output row
+// (block b * ny + y): the source row is read as two contiguous halves.
 __global__ void k_prep_apply(const float *__restrict__ t_raw, int ny, int nx, int batch,
                              const double *scale, const uint8_t *__restrict__ roi, float *__restrict__ tf) {
-    const size_t npx = (size_t)ny * nx, total = npx * batch;
-    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < total;
-         i += (size_t)gridDim.x * blockDim.x) {
-        const int b = (int)(i / npx);
-        const int rem = (int)(i - (size_t)b * npx);
-        const int y = rem / nx, x = rem - y * nx;
-        const int iy = (y + ny / 2) % ny, ix = (x + nx / 2) % nx;
-        const size_t o = (size_t)iy * nx + ix;
-        const float v = (!roi || roi[o]) ? t_raw[(size_t)b * npx + o] : 0.f;  // target restricted to the ROI
-        float tv = v * (float)scale[b];
+    const int b = blockIdx.x / ny, y = blockIdx.x - b * ny;
+    if (b >= batch) return;
+    const int iy = y + ny / 2 < ny ? y + ny / 2 : y + ny / 2 - ny;
+    const float sc = (float)scale[b];
+    const float *src = t_raw + ((size_t)b * ny + iy) * nx;
+    const uint8_t *rr = roi ? roi + (size_t)iy * nx : nullptr;
+    float *dst = tf + ((size_t)b * ny + y) * nx;
+    for (int x = threadIdx.x; x < nx; x += blockDim.x) {
+        const int ix = x + nx / 2 < nx ? x + nx / 2 : x + nx / 2 - nx;
+        const float v = (!rr || rr[ix]) ? src[ix] : 0.f;  // target restricted to the ROI
+        float tv = v * sc;
         // keep the support {T > 0} of the input exactly: a positive value whose
         // scaled float underflows becomes the smallest positive float
         if (v > 0.f && !(tv > 0.f)) tv = __int_as_float(1);
-        tf[i] = tv;
+        dst[x] = tv;
     }
 }
 
@@ -768,8 +770,8 @@ void enqueue_prep(hg_plan p, const float *target) {
     k_prep_sum<<<g, PREP_THREADS, 0, p->stream>>>(target, (int)p->npx, p->roi_rep, p->sum_part, p->err);
     k_prep_scale<<<(p->batch + 127) / 128, 128, 0, p->stream>>>(p->sum_part, p->batch, p->scale,
                                                                  p->err);
-    k_prep_apply<<<ew_grid(p, p->npx * p->batch), 256, 0, p->stream>>>(
-        target, p->ny, p->nx, p->batch, p->scale, p->roi_rep, p->tf);
+    k_prep_apply<<<(unsigned)(p->ny * p->batch), 256, 0, p->stream>>>(target, p->ny, p->nx, p->batch, p->scale,
+                                                                      p->roi_rep, p->tf);
     p->launches += 3;
 }
 
@@ -1424,6 +1426,12 @@ hg_status hg_plan_create(hg_plan *out, int ny, int nx, int batch, hg_slm slm, hg
             }
             const PipeOps *best = nullptr;
             float best_ms = 1e30f;
+            // a forced candidate k of another column length takes that length's k-th
+            // column-pair variant (the last one if it has fewer)
+            if (o.autotune >= 2 && nh > 1 && p->prow->N != ny) {
+                hc[0] = hc[std::min(o.autotune - 2, nh - 1)];
+                nh = 1;
+            }
             for (int i = 0; i < nh; ++i) {
                 CUtensorMap m;
                 if (!make_cmap_box(p, hc[i]->herm_c, hc[i]->herm_boxr, &m)) continue;
@@ -1928,6 +1936,7 @@ struct hg_group_s {
     int iters = -1;
     const void *key[4 * HG_GROUP_MAX] = {};
     int launches = 0;
+    int schedule = HG_GROUP_SERIAL;  // branches in sequence, or concurrent
 };
 
 extern "C" {
@@ -2000,13 +2009,16 @@ hg_status hg_group_run(hg_group g, const float *const *targets, const float *con
         HG_CK(cudaStreamBeginCapture(g->cap, cudaStreamCaptureModeThreadLocal));
         cudaError_t e = cudaEventRecord(g->fork, g->cap);
         g->launches = 0;
+        const bool conc = g->schedule == HG_GROUP_CONCURRENT;
         for (int i = 0; i < g->n && e == cudaSuccess; ++i) {
             hg_plan p = g->plans[i];
-            e = cudaStreamWaitEvent(g->branch[i], g->fork, 0);
+            // serial: every plan's run on the capture stream, one after another;
+            // concurrent: each run a branch forked from the capture stream
+            if (conc) e = cudaStreamWaitEvent(g->branch[i], g->fork, 0);
             if (e != cudaSuccess) break;
             cudaStream_t keep = p->stream;
             const bool prof = p->prof_on;
-            p->stream = g->branch[i];
+            p->stream = conc ? g->branch[i] : g->cap;
             p->prof_on = false;
             p->launches = 0;
             st = enqueue_run(p, (const float *)key[4 * i], (const float *)key[4 * i + 1], iters,
@@ -2015,8 +2027,8 @@ hg_status hg_group_run(hg_group g, const float *const *targets, const float *con
             p->stream = keep;
             p->prof_on = prof;
             if (st != HG_OK) e = cudaErrorUnknown;
-            if (e == cudaSuccess) e = cudaEventRecord(g->join[i], g->branch[i]);
-            if (e == cudaSuccess) e = cudaStreamWaitEvent(g->cap, g->join[i], 0);
+            if (conc && e == cudaSuccess) e = cudaEventRecord(g->join[i], g->branch[i]);
+            if (conc && e == cudaSuccess) e = cudaStreamWaitEvent(g->cap, g->join[i], 0);
         }
         cudaGraph_t graph = nullptr;
         cudaError_t e2 = cudaStreamEndCapture(g->cap, &graph);
@@ -2054,6 +2066,19 @@ hg_status hg_group_sync(hg_group g, void *stream) {
 }
 
 int hg_group_launch_count(hg_group g) { return g ? g->launches : 0; }
+
+hg_status hg_group_set_schedule(hg_group g, int schedule) {
+    if (!g || (schedule != HG_GROUP_SERIAL && schedule != HG_GROUP_CONCURRENT)) return HG_ERR_INVALID_ARG;
+    if (schedule != g->schedule) {
+        g->schedule = schedule;
+        if (g->exec) {  // captured with the other schedule: capture again at the next run
+            DevGuard dg(g->dev);
+            cudaGraphExecDestroy(g->exec);
+            g->exec = nullptr;
+        }
+    }
+    return HG_OK;
+}
 
 }  // extern "C"
 

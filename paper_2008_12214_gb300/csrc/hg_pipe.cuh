@@ -110,8 +110,8 @@ __device__ __forceinline__ void named_sync(int id, int nthreads) {
 // Sum four per-thread float partials over a consumer group of GT threads in a
 // fixed order: lanes and warps combine in float (at most GT partial sums of
 // E terms each), the group total is stored as double by thread 0 and every
-// reduction across panels is done in double.  (Double shuffles would occupy
-// the FP64 pipe, which is narrow on this GPU.)
+// reduction across panels is done in double.  (Double shuffles or additions
+// here would occupy the FP64 pipe, which is narrow on this GPU.)
 template <int GT, class SYNC>
 __device__ __forceinline__ void group_sum4(float a0, float a1, float a2, float a3, double *red,
                                            double *dst, int gt, SYNC gsync) {
@@ -132,12 +132,16 @@ __device__ __forceinline__ void group_sum4(float a0, float a1, float a2, float a
             for (int m = 0; m < NMET; ++m) redf[w * NMET + m] = d[m];
         gsync();
         if (gt == 0) {
-            double s[NMET] = {0, 0, 0, 0};
+            // the group's few warp sums in float (one rounding each), then one
+            // conversion: this thread's FP64 work would hold the group's
+            // barrier on the narrow FP64 pipe
+            float s[NMET] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
             for (int q = 0; q < GT / 32; ++q)
 #pragma unroll
-                for (int m = 0; m < NMET; ++m) s[m] += (double)redf[q * NMET + m];
+                for (int m = 0; m < NMET; ++m) s[m] += redf[q * NMET + m];
 #pragma unroll
-            for (int m = 0; m < NMET; ++m) dst[m] = s[m];
+            for (int m = 0; m < NMET; ++m) dst[m] = (double)s[m];
         }
         gsync();
     }

@@ -98,6 +98,8 @@ def lib():
         L.hg_group_sync.restype = I
         L.hg_group_launch_count.argtypes = [P]
         L.hg_group_launch_count.restype = I
+        L.hg_group_set_schedule.argtypes = [P, I]
+        L.hg_group_set_schedule.restype = I
         L.hg_group_destroy.argtypes = [P]
         L.hg_group_destroy.restype = None
         L.hg_run_noalloc.argtypes = [I, I, hg_slm, I, P, P, I, P, P, P]
@@ -349,6 +351,13 @@ def hg_group_sync(group, stream=None):
 
 def hg_group_launch_count(group) -> int:
     return lib().hg_group_launch_count(group)
+
+
+HG_GROUP_SERIAL, HG_GROUP_CONCURRENT = 0, 1
+
+
+def hg_group_set_schedule(group, schedule):
+    _ck(lib().hg_group_set_schedule(group, int(schedule)), "hg_group_set_schedule")
 
 
 def hg_group_destroy(group):

@@ -448,9 +448,10 @@ def test_paired_rows_weighted_gs_binary(cand):
 
 
 def test_group_mixed_sizes_one_graph():
-    """Mixed batch (512^2, 1024^2, 2048^2, 1080 x 1920) as one CUDA graph with
-    concurrent branches: identical to the plans run one by one, stable across
-    graph replays, and iteration 0 matches the oracle for every size."""
+    """Mixed batch (512^2, 1024^2, 2048^2, 1080 x 1920) as one CUDA graph, the
+    runs in sequence and as concurrent branches: identical to the plans run
+    one by one, stable across graph replays, and iteration 0 matches the
+    oracle for every size."""
     shapes = [(512, 512, 3), (1024, 1024, 2), (2048, 2048, 1), (1080, 1920, 1)]
     iters = 3
     plans, T, P, H, M, host = [], [], [], [], [], []
@@ -473,6 +474,14 @@ def test_group_mixed_sizes_one_graph():
     hg.hg_group_sync(g)
     for i in range(len(shapes)):
         assert np.array_equal(M[i].cpu().numpy(), first[i])
+    hg.hg_group_set_schedule(g, hg.HG_GROUP_CONCURRENT)  # the same runs as concurrent branches
+    hg.hg_group_run(g, T, P, iters, H, M)
+    hg.hg_group_sync(g)
+    for i in range(len(shapes)):
+        assert np.array_equal(M[i].cpu().numpy(), first[i])
+        assert np.array_equal(H[i].cpu().numpy(), holos[i])
+    with pytest.raises(hg.HgError):
+        hg.hg_group_set_schedule(g, 7)
     for i, p in enumerate(plans):
         h2 = torch.empty_like(H[i])
         m2 = torch.empty_like(M[i])
@@ -532,7 +541,7 @@ def test_tensor_core_row_pass_precision(n, prec, tol):
 
 @pytest.mark.parametrize("n,cand,wgs", [(1024, 2, False), (1024, 3, False), (1024, 5, False), (1024, 2, True),
                                         (512, 2, False), (512, 3, False), (2048, 2, False), (2048, 3, False),
-                                        ((1080, 1920), 0, False)])
+                                        ((1080, 1920), 0, False), ((1080, 1920), 1, False)])
 def test_hermitian_binary_loop_matches_generic(n, cand, wgs):
     """Binary GS in Hermitian form (paired rows write only the Hermitian part
     of F, rows ky <= ny/2; the column passes read those rows back, two columns
