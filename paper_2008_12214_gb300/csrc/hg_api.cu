@@ -797,6 +797,18 @@ bool herm_loop(hg_plan p) {
 // last column pass (both on the paired row kernel).
 bool herm_ends(hg_plan p) { return herm_loop(p) && p->prow->row_head && p->prow->row_tail; }
 
+// Binary OSPR in Hermitian form: head and time average on the paired row
+// kernel of the variant that provides the column-pair pass.
+bool ospr_pair_ends(hg_plan p) { return p->ospr_herm && p->hops->row_head && p->hops->row_avg; }
+
+void launch_ospr_end(hg_plan p, bool head, const RowArgs &a, cudaStream_t s) {
+    const long work = (long)a.items * (p->ny / 2 + 1);
+    const int grid = grid_for(p->hops->row_blocks_per_sm, p->nsm, work);
+    if (head) p->hops->row_head(a, pipe_args(p), grid, s);
+    else p->hops->row_avg(a, pipe_args(p), grid, s);
+    p->launches++;
+}
+
 void launch_pair_end(hg_plan p, bool head, const RowArgs &a, cudaStream_t s) {
     const long work = (long)a.items * p->ppt_pipe;
     const int grid = grid_for(p->prow->row_blocks_per_sm, p->nsm, work);
@@ -898,7 +910,8 @@ hg_status enqueue_run(hg_plan p, const float *d_t, const float *d_ph, int iters,
         ra.phase = nullptr;
         ra.stream_id = 0;
         ra.herm = p->ospr_herm;
-        launch_row(p, ROW_HEAD, ra, p->stream);
+        if (ospr_pair_ends(p)) launch_ospr_end(p, true, ra, p->stream);
+        else launch_row(p, ROW_HEAD, ra, p->stream);
         ca.items = p->nchains;
         ca.holo = d_ho;
         if (p->ospr_herm) {
@@ -911,7 +924,8 @@ hg_status enqueue_run(hg_plan p, const float *d_t, const float *d_ph, int iters,
         rt.nsub = p->nsub;
         rt.part = p->part;
         rt.herm = p->ospr_herm;
-        launch_row(p, ROW_AVG, rt, p->stream);
+        if (ospr_pair_ends(p)) launch_ospr_end(p, false, rt, p->stream);
+        else launch_row(p, ROW_AVG, rt, p->stream);
     } else if (is_search(p->algo)) {
         // initial guess: the quantised back-propagation of the target (head + column
         // pass), its replay field (tail), then the sweeps in one kernel
@@ -989,6 +1003,7 @@ hg_status enqueue_run(hg_plan p, const float *d_t, const float *d_ph, int iters,
     int panels_last = (p->tc_prec && !is_ospr(p->algo)) ? p->ppt_tc : p->ppt;
     if (!is_ospr(p->algo) && !is_search(p->algo) && herm_ends(p)) panels_last = p->ppt_pipe;  // Hermitian tail
     if (p->ospr_herm) panels_last = (p->ny / 2 + p->rops->row_lines) / p->rops->row_lines;  // rows <= ny/2
+    if (is_ospr(p->algo) && ospr_pair_ends(p)) panels_last = p->ny / 2 + 1;  // one panel per row
     if (is_search(p->algo)) {
         // the search kernel wrote the metrics and mse_out itself
     } else if (p->mod) {
@@ -1450,13 +1465,23 @@ hg_status hg_plan_create(hg_plan *out, int ny, int nx, int batch, hg_slm slm, hg
         // Binary OSPR: one pass per subframe in Hermitian form with the column-pair
         // pass of any paired variant of this column length (square power-of-two fields)
         if (algo == HG_OSPR && ny == nx && ny % 2 == 0) {
+            // the fastest column-pair pass of the paired variants (the first when not tuning)
             const PipeOps *all[8];
             const int k = pipe_candidates(ny, all, 8);
-            for (int i = 0; i < k && !p->hops; ++i)
-                if (all[i]->paired && all[i]->col_herm && ensure_pipe_init(p->dev, all[i]) == cudaSuccess &&
-                    all[i]->herm_blocks_per_sm > 0 &&
-                    make_cmap_box(p, all[i]->herm_c, all[i]->herm_boxr, &p->cmap_herm))
+            float best_ms = 1e30f;
+            for (int i = 0; i < k; ++i) {
+                CUtensorMap m;
+                if (!(all[i]->paired && all[i]->col_herm && ensure_pipe_init(p->dev, all[i]) == cudaSuccess &&
+                      all[i]->herm_blocks_per_sm > 0 && make_cmap_box(p, all[i]->herm_c, all[i]->herm_boxr, &m)))
+                    continue;
+                const float ms = o.autotune == 1 ? time_variant(p, all[i], false, false, true, true) : 0.f;
+                if (!p->hops || ms < best_ms) {
                     p->hops = all[i];
+                    p->cmap_herm = m;
+                    best_ms = ms;
+                }
+                if (o.autotune != 1) break;
+            }
             p->ospr_herm = p->hops != nullptr;
         }
     }

@@ -448,7 +448,10 @@ struct PairPipeCfg {
 // inverse row FFT; 4: Hermitian TAIL, the forward row FFT of a binary
 // column-transformed field (rows ky <= ny/2), metrics and weights of both
 // pixels u and -u, and optionally arg R and R at both (no inverse FFT, no
-// store).
+// store); 5: Hermitian time average (binary OSPR, Section 3.4): a job is one
+// row ky <= ny/2 of one target, whose nsub subframe rows the group streams in
+// order, summing |R|^2 in registers; after the last one it writes the
+// normalised intensity of u and -u and the metrics.
 template <class P, int NG, int D, int SWZ, int MODE, int MINB = 1>
 __global__ void __launch_bounds__(PairPipeCfg<P, NG, D, SWZ>::THREADS, MINB)
     k_row_pipe_pair(const RowArgs a, const PipeArgs pa) {
@@ -484,12 +487,30 @@ __global__ void __launch_bounds__(PairPipeCfg<P, NG, D, SWZ>::THREADS, MINB)
         else named_sync(1 + g, GT);
     };
     auto job = [&](int k) { return (int)blockIdx.x + (g + NG * k) * (int)gridDim.x; };
+    // the group's k-th panel belongs to job jstep(k); MODE 5 takes nsub panels
+    // (the job's subframes, in order) per job
+    const int per = MODE == 5 ? a.nsub : 1;
+    auto jstep = [&](int k) { return job(k / per); };
     auto issue = [&](int k) {
-        const int j = job(k);
+        const int j = jstep(k);
         if (j >= J || j == pa.drop_job) return;
         const int item = j / ppt, pan = j - item * ppt;
         const bool partner = pan != 0 && pan != hy;
         unsigned char *sl = ring + (size_t)(k % D) * Cfg::SLOT;
+        if constexpr (MODE == 5) {
+            // subframe n's row, and with the last subframe the target rows
+            const int n = k % per;
+            const bool last = n == per - 1;
+            mbar_expect_tx(gfull + k % D, (uint32_t)(NX * 8 + (last ? NX * 4 * (partner ? 2 : 1) : 0)));
+            bulk_g2s(sl, a.field + ((size_t)(item * per + n) * ny + pan) * NX, NX * 8, gfull + k % D);
+            if (last) {
+                bulk_g2s(sl + Cfg::SLOT_F, a.T + ((size_t)item * ny + pan) * NX, NX * 4, gfull + k % D);
+                if (partner)
+                    bulk_g2s(sl + Cfg::SLOT_F + NX * 4, a.T + ((size_t)item * ny + ny - pan) * NX, NX * 4,
+                             gfull + k % D);
+            }
+            return;
+        }
         if constexpr (MODE == 3) {
             // replay rows of DFT rows pan and ny - pan: phases, then the targets
             const int b = item / a.nsub, ym = (ny - pan) % ny;
@@ -514,15 +535,16 @@ __global__ void __launch_bounds__(PairPipeCfg<P, NG, D, SWZ>::THREADS, MINB)
     };
     auto drain = [&](int k0, int k1) {
         for (int q = k0; q < k1; ++q) {
-            const int j = job(q);
+            const int j = jstep(q);
             if (j < J && j != pa.drop_job) mbar_wait(gfull + q % D, (q / D) & 1, pa.wait_ns, nullptr);
         }
     };
     if (t == 0)
         for (int k = 0; k < D; ++k) issue(k);
 
+    float accI[E];  // MODE 5: sum over the subframes of |R|^2
     for (int k = 0;; ++k) {
-        const int j = job(k);
+        const int j = jstep(k);
         if (j >= J) break;
         if (t == 0) {
             bool ok = !*abort && mbar_wait(gfull + k % D, (k / D) & 1, pa.wait_ns, abort);
@@ -593,6 +615,49 @@ __global__ void __launch_bounds__(PairPipeCfg<P, NG, D, SWZ>::THREADS, MINB)
             v[e] = sf[t + TL * e];
         });
         line_fft<P, -1, 1, LAY>(v, sf, a.tw, t, gsync);
+        if constexpr (MODE == 5) {
+            const int n = k % per;
+            static_for<0, E>([&](auto ec) {
+                constexpr int e = decltype(ec)::value;
+                accI[e] = fmaf(v[e].x, v[e].x, fmaf(v[e].y, v[e].y, n ? accI[e] : 0.f));
+            });
+            if (n == per - 1) {
+                // normalised time-averaged intensity of u and of -u (the same), metrics
+                const float inv_sub = 1.0f / (float)per;
+                const float *sTm = partner ? sTa + NX : sTa;
+                const int ym = (ny - pan) % ny, iy = (pan + hy) % ny, iym = (ym + hy) % ny;
+                float *Io = a.I_out ? a.I_out + (size_t)item * ny * NX : nullptr;
+                float m0 = 0.f, m1 = 0.f, m2s = 0.f, m3 = 0.f;
+                static_for<0, E>([&](auto ec) {
+                    constexpr int e = decltype(ec)::value;
+                    const int x = t + TL * e, xm = mirror_idx<NX>(x);
+                    const float I = accI[e] * inv_sub * a.invN2;
+                    const float e2 = accI[e] * inv_sub * a.invN;
+                    const float Tv = sTa[x];
+                    const float d = I - Tv * Tv, am = sqrtf(I) - Tv;
+                    m0 = fmaf(d, d, m0);
+                    m1 = fmaf(am, am, m1);
+                    m3 += e2;
+                    if (Tv > 0.f) m2s += e2;
+                    if (Io) Io[(size_t)iy * NX + (x + NX / 2) % NX] = I;
+                    if (partner) {
+                        const float Tm = sTm[xm];
+                        const float dm = I - Tm * Tm, amm = sqrtf(I) - Tm;
+                        m0 = fmaf(dm, dm, m0);
+                        m1 = fmaf(amm, amm, m1);
+                        m3 += e2;
+                        if (Tm > 0.f) m2s += e2;
+                        if (Io) Io[(size_t)iym * NX + (xm + NX / 2) % NX] = I;
+                    }
+                });
+                if (a.part)
+                    group_sum4<GT>(m0, m1, m2s, m3, red + (size_t)g * Cfg::GW * NMET,
+                                   a.part + ((size_t)item * ppt + pan) * NMET, t, gsync);
+            }
+            gsync();
+            if (t == 0) issue(k + D);
+            continue;
+        }
         float acc0 = 0.f, acc1 = 0.f, acc2 = 0.f, acc3 = 0.f;
         if constexpr (MODE == 4) {
             // outputs at u (this row) and -u (row ny - pan, R(-u) = conj R(u));
@@ -1166,6 +1231,8 @@ struct PipeOps {
     // (rows ky <= ny/2; may be null)
     void (*row_head)(const RowArgs &a, const PipeArgs &pa, int grid, cudaStream_t s);
     void (*row_tail)(const RowArgs &a, const PipeArgs &pa, int grid, cudaStream_t s);
+    // Hermitian OSPR time average on the paired row kernel (may be null)
+    void (*row_avg)(const RowArgs &a, const PipeArgs &pa, int grid, cudaStream_t s);
 };
 
 // Row pass: plan P, LINES rows per group, NGR groups, ring depth DR, swizzle
@@ -1253,7 +1320,8 @@ struct PairImpl {
                               (const void *)k_row_pipe_pair<P, NG, D, SWZ, 1, MINB>,
                               (const void *)k_row_pipe_pair<P, NG, D, SWZ, 2, MINB>,
                               (const void *)k_row_pipe_pair<P, NG, D, SWZ, 3, MINB>,
-                              (const void *)k_row_pipe_pair<P, NG, D, SWZ, 4, MINB>})
+                              (const void *)k_row_pipe_pair<P, NG, D, SWZ, 4, MINB>,
+                              (const void *)k_row_pipe_pair<P, NG, D, SWZ, 5, MINB>})
             if (e == cudaSuccess)
                 e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)RC::SMEM);
         // the block count of the general Hermitian kernel (the most registers)
@@ -1274,6 +1342,9 @@ struct PairImpl {
     }
     static void row_tail(const RowArgs &a, const PipeArgs &pa, int grid, cudaStream_t s) {
         k_row_pipe_pair<P, NG, D, SWZ, 4, MINB><<<grid, RC::THREADS, RC::SMEM, s>>>(a, pa);
+    }
+    static void row_avg(const RowArgs &a, const PipeArgs &pa, int grid, cudaStream_t s) {
+        k_row_pipe_pair<P, NG, D, SWZ, 5, MINB><<<grid, RC::THREADS, RC::SMEM, s>>>(a, pa);
     }
 };
 
@@ -1363,6 +1434,7 @@ struct PairedOps {
         o.row_iter = &PAIR::row_iter;
         o.row_head = &PAIR::row_head;
         o.row_tail = &PAIR::row_tail;
+        o.row_avg = &PAIR::row_avg;
         o.col_pack = PACK::launch;
         o.col_herm = HERM::launch;
         o.herm_c = HERM::COLS;

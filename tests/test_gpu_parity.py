@@ -503,8 +503,9 @@ def test_tensor_core_row_pass_precision(n, prec, tol):
     """Row-pass DFT stages as tcgen05 GEMMs (1 FP16 hi+lo, 2 FP16, 3 BF16
     hi+lo, 4 BF16): the replay field the tensor-core pass computes from the
     GPU's hologram, against the oracle's replay of that hologram (single-step
-    relative L2), and a 6-iteration run's final MSE against the FP32 engine.
-    2048-sample rows run as two 1024-point halves joined by a radix-2 step."""
+    relative L2), and a 6-iteration whole run's final MSE against the FP64
+    oracle's (within 1%; the FP32 engine's is printed beside it).  2048-sample
+    rows run as two 1024-point halves joined by a radix-2 step."""
     batch = 2 if n == 1024 else 1
     t = synth.targets(batch, n, n)
     ph = synth.init_phases(batch, n, n)
@@ -534,9 +535,12 @@ def test_tensor_core_row_pass_precision(n, prec, tol):
         mref = oracle.metrics(np.abs(Rref) ** 2, oracle.prepare_target(t[b]))
         assert abs(met[b, 0] - mref[0]) <= max(10 * tol, 1e-4) * mref[0]
     d = np.abs(mse.cpu().numpy()[:, -1] - mse32.cpu().numpy()[:, -1]) / mse32.cpu().numpy()[:, -1]
-    print("n %d precision %d: single-step rel-L2 %s, final-MSE delta vs FP32 %s" % (n, prec, errs, d))
+    o6 = np.array([oracle.gs_run(t[b], ph[b].astype(np.float64), 6)["mse"][-1] for b in range(batch)])
+    do = np.abs(mse.cpu().numpy()[:, -1] - o6) / o6
+    print("n %d precision %d: single-step rel-L2 %s, final-MSE delta vs the FP64 oracle %s (FP32 engine: %s)"
+          % (n, prec, errs, do, d))
     assert max(errs) <= tol
-    assert np.all(d < 0.05)
+    assert np.all(do <= 0.01)
 
 
 @pytest.mark.parametrize("n,cand,wgs", [(1024, 2, False), (1024, 3, False), (1024, 5, False), (1024, 2, True),
