@@ -483,8 +483,6 @@ struct hg_plan_s {
     uint4 *tc_b = nullptr;                           // DFT-32 operand matrices
     int tc_blocks = 1, ppt_tc = 0;
     CUtensorMap cmap;                                // field as [chains*ny][2*nx] floats
-    CUtensorMap cmap_pack;                           // same field, tiles of the packed column pass
-    bool use_pack = false;                           // binary: packed column pass in the loop
     CUtensorMap cmap_herm;                           // same field, tiles of the column-pair Hermitian pass
     bool use_herm_col = false;                       // Hermitian loop: column pairs share transforms
     const PipeOps *hops = nullptr;                   // variant providing the column-pair pass
@@ -731,13 +729,6 @@ void launch_row_iter(hg_plan p, const RowArgs &a, cudaStream_t s) {
     }
 }
 
-void launch_col_pack(hg_plan p, const ColArgs &a, cudaStream_t s) {
-    ProfScope ps(p, s, 1);
-    const long work = (long)a.items * ((p->nx + p->prow->col_c - 1) / p->prow->col_c);
-    p->prow->col_pack(a, pipe_args(p), p->cmap_pack, grid_for(p->prow->pack_blocks_per_sm, p->nsm, work), s);
-    p->launches++;
-}
-
 void launch_col_herm(hg_plan p, const ColArgs &a, cudaStream_t s) {
     ProfScope ps(p, s, 1);
     const PipeOps *h = p->hops;
@@ -789,7 +780,7 @@ bool is_search(int algo) { return algo == HG_DS || algo == HG_SA; }
 // writes only the Hermitian part of F (rows ky <= ny/2) and the next column
 // pass reads those rows back (see herm_constrain).
 bool herm_loop(hg_plan p) {
-    return p->prow && p->prow->paired && p->pcol && !p->use_pack && p->kind == HG_SLM_BINARY;
+    return p->prow && p->prow->paired && p->pcol && p->kind == HG_SLM_BINARY;
 }
 
 // The Hermitian binary loop also starts and ends in Hermitian form: the head
@@ -827,8 +818,7 @@ void enqueue_loop(hg_plan p, int iters, cudaStream_t s) {
     const bool half_head = herm_ends(p);
     for (int k = 0; k + 1 < iters; ++k) {
         ca.half_in = ra.herm && (k > 0 || half_head);  // after a full head, column pass 0 reads every row
-        if (p->use_pack) launch_col_pack(p, ca, s);
-        else if (ca.half_in && p->use_herm_col) launch_col_herm(p, ca, s);
+        if (ca.half_in && p->use_herm_col) launch_col_herm(p, ca, s);
         else launch_col_gs(p, col_role_gs(p), ca, s);
         ra.part = p->part + (size_t)k * p->batch * p->ppt_max * part_stride(p);
         lt_set(p, ra, k + 1);
@@ -1060,8 +1050,7 @@ bool make_cmap(hg_plan p, const PipeOps *pc, CUtensorMap *m) {
 
 // Best-of-3 launch time (ms, after one warm-up launch) of one pass variant on
 // the plan's own zeroed buffers, on the private capture stream.
-float time_variant(hg_plan p, const PipeOps *o, bool row, bool pack = false, bool herm = false,
-                   bool herm_pairs = false) {
+float time_variant(hg_plan p, const PipeOps *o, bool row, bool herm = false, bool herm_pairs = false) {
     if (!p->field || !p->tf || !p->twx || !p->twy || !p->lvl || !p->err) return 1e30f;
     cudaStream_t s = p->cap_stream;
     RowArgs ra = row_args(p);
@@ -1075,13 +1064,11 @@ float time_variant(hg_plan p, const PipeOps *o, bool row, bool pack = false, boo
     } else if (!row && !make_cmap(p, o, &m)) {
         return 1e30f;
     }
-    if (pack) ca.half = 1;
     if (!row && herm) ca.half = ca.half_in = 1;
     const int ppt = row ? row_panels(o, p->ny) : (p->nx + (herm_pairs ? o->herm_c : o->col_c) - 1) /
                                                      (herm_pairs ? o->herm_c : o->col_c);
     const int grid = grid_for(row ? o->row_blocks_per_sm
-                                  : pack ? o->pack_blocks_per_sm
-                                         : herm_pairs ? o->herm_blocks_per_sm : o->col_blocks_per_sm,
+                                  : herm_pairs ? o->herm_blocks_per_sm : o->col_blocks_per_sm,
                               p->nsm, (long)p->batch * ppt);
     PipeArgs pa = pipe_args(p);
     cudaEvent_t e0, e1;
@@ -1097,7 +1084,6 @@ float time_variant(hg_plan p, const PipeOps *o, bool row, bool pack = false, boo
         cudaEventRecord(e0, s);
         if (row) o->row_iter(ra, pa, grid, s);
         else if (herm_pairs) o->col_herm(ca, pa, m, grid, s);
-        else if (pack) o->col_pack(ca, pa, m, grid, s);
         else o->col_gs(p->mod ? COL_GS_MOD : p->kind == HG_SLM_BINARY ? COL_GS_BIN : COL_GS_LVL, ca, pa, m, grid, s);
         cudaEventRecord(e1, s);
         if (cudaEventSynchronize(e1) != cudaSuccess) break;
@@ -1385,7 +1371,8 @@ hg_status hg_plan_create(hg_plan *out, int ny, int nx, int batch, hg_slm slm, hg
                 if (ce == cudaSuccess) ce = cudaGetLastError();
                 if (ce != cudaSuccess) return fail(map_err(ce));
                 // columns first; a row candidate is scored by its own time plus
-                // the column pass it implies (its packed column pass, if any)
+                // the column pass it implies (in Hermitian form, the faster of the
+                // per-column pass and its own column-pair pass)
                 float best = 1e30f, best_col = 1e30f;
                 for (int i = 0; i < nc; ++i) {
                     const float ms = nc > 1 || nr > 1 ? time_variant(p, cc[i], false) : 0.f;
@@ -1393,17 +1380,15 @@ hg_status hg_plan_create(hg_plan *out, int ny, int nx, int batch, hg_slm slm, hg
                     if (ms < best_col) best_col = ms, col = cc[i];
                 }
                 for (int i = 0; i < nr; ++i) {
-                    const bool pk = rc[i]->paired && rc[i]->col_pack && slm.kind == HG_SLM_BINARY;
                     // a paired row pass with a TMA-fed column pass runs in Hermitian form
-                    const bool hm = rc[i]->paired && !pk && col && slm.kind == HG_SLM_BINARY;
-                    float ms = time_variant(p, rc[i], true, false, hm);
+                    const bool hm = rc[i]->paired && col && slm.kind == HG_SLM_BINARY;
+                    float ms = time_variant(p, rc[i], true, hm);
                     if (i < 4) p->tune_ms[i] = ms;
                     float cm = nc ? best_col : 0.f;
-                    if (pk) cm = time_variant(p, rc[i], false, true);
-                    else if (hm) {
-                        cm = time_variant(p, col, false, false, true);
+                    if (hm) {
+                        cm = time_variant(p, col, false, true);
                         if (rc[i]->col_herm && rc[i]->N == ny)
-                            cm = fminf(cm, time_variant(p, rc[i], false, false, true, true));
+                            cm = fminf(cm, time_variant(p, rc[i], false, true, true));
                     }
                     ms += cm;
                     if (ms < best) best = ms, row = rc[i];
@@ -1415,8 +1400,6 @@ hg_status hg_plan_create(hg_plan *out, int ny, int nx, int batch, hg_slm slm, hg
         }
         if (row && !p->tc_prec) {
             p->prow = row;
-            p->use_pack = row->paired && row->col_pack && slm.kind == HG_SLM_BINARY && nx % 2 == 0 &&
-                          ny == row->N && make_cmap(p, row, &p->cmap_pack);
             p->ppt_pipe = row_panels(row, ny);
             if (p->ppt_pipe > p->ppt_max) p->ppt_max = p->ppt_pipe;
         }
@@ -1450,12 +1433,12 @@ hg_status hg_plan_create(hg_plan *out, int ny, int nx, int batch, hg_slm slm, hg
             for (int i = 0; i < nh; ++i) {
                 CUtensorMap m;
                 if (!make_cmap_box(p, hc[i]->herm_c, hc[i]->herm_boxr, &m)) continue;
-                const float ms = (o.autotune == 1 && nh > 0) ? time_variant(p, hc[i], false, false, true, true) : 0.f;
+                const float ms = (o.autotune == 1 && nh > 0) ? time_variant(p, hc[i], false, true, true) : 0.f;
                 if (!best || ms < best_ms) best = hc[i], best_ms = ms;
             }
             if (best) {
                 bool take = true;
-                if (o.autotune == 1) take = best_ms <= time_variant(p, p->pcol, false, false, true);
+                if (o.autotune == 1) take = best_ms <= time_variant(p, p->pcol, false, true);
                 if (take && make_cmap_box(p, best->herm_c, best->herm_boxr, &p->cmap_herm)) {
                     p->use_herm_col = true;
                     p->hops = best;
@@ -1474,7 +1457,7 @@ hg_status hg_plan_create(hg_plan *out, int ny, int nx, int batch, hg_slm slm, hg
                 if (!(all[i]->paired && all[i]->col_herm && ensure_pipe_init(p->dev, all[i]) == cudaSuccess &&
                       all[i]->herm_blocks_per_sm > 0 && make_cmap_box(p, all[i]->herm_c, all[i]->herm_boxr, &m)))
                     continue;
-                const float ms = o.autotune == 1 ? time_variant(p, all[i], false, false, true, true) : 0.f;
+                const float ms = o.autotune == 1 ? time_variant(p, all[i], false, true, true) : 0.f;
                 if (!p->hops || ms < best_ms) {
                     p->hops = all[i];
                     p->cmap_herm = m;
@@ -1551,7 +1534,6 @@ hg_status hg_profile_read(hg_plan p, double *out4) {
 
 const char *hg_plan_variant(hg_plan p, int pass) {
     if (!p) return "";
-    if (pass == 1 && p->use_pack) return "packed-binary-columns (with the row variant)";
     if (pass == 1 && p->ospr_herm) {
         snprintf(p->vname[1], sizeof p->vname[1], "%s+herm-colpairs (OSPR)", p->hops->name);
         return p->vname[1];
@@ -1921,8 +1903,7 @@ hg_status hg_debug_loop_step(hg_plan p, const float *target, const uint8_t *holo
     launch_row_iter(p, ra, p->stream);
     if (row_out) HG_CK(cudaMemcpyAsync(row_out, p->field, fbytes, cudaMemcpyDeviceToDevice, p->stream));
     ca.holo = holo_out;
-    if (p->use_pack) launch_col_pack(p, ca, p->stream);
-    else if (ca.half_in && p->use_herm_col) launch_col_herm(p, ca, p->stream);
+    if (ca.half_in && p->use_herm_col) launch_col_herm(p, ca, p->stream);
     else launch_col_gs(p, col_role_gs(p), ca, p->stream);
     if (col_out) HG_CK(cudaMemcpyAsync(col_out, p->field, fbytes, cudaMemcpyDeviceToDevice, p->stream));
     const int pl = p->tc_prec ? p->ppt_tc : p->prow ? p->ppt_pipe : p->ppt;

@@ -1058,155 +1058,6 @@ __global__ void __launch_bounds__(ColHermCfg<P, C, D, SWZ, BOXR>::THREADS, MINB)
     }
 }
 
-// ------------------------------------- packed column pass (binary, half rows)
-// After binary quantisation every column of e^{iH} is real, so two columns a
-// and b are transformed by one complex FFT of z = a + i b: with Z = FFT(z),
-// A[k] = (Z[k] + conj(Z[N-k])) / 2 and B[k] = (Z[k] - conj(Z[N-k])) / (2i).
-// Only rows k <= ny/2 are produced (the paired row pass rebuilds the rest), so
-// this pass runs inside the iteration loop when the row pass is paired.  The
-// inverse transforms use plan P (TL x C threads, C columns); the forward ones
-// use plan PB on C/2 packed columns with the same threads (PB::TL = 2 P::TL).
-template <class P, class PB, int C, int NG, int D, int SWZ, int SWZB, int BOXR>
-struct ColPackCfg {
-    static constexpr int GT = P::TL * C;
-    static_assert(PB::TL * (C / 2) == GT && PB::N == P::N, "packed plan must use the same threads");
-    static_assert(GT % 32 == 0, "column group must be whole warps");
-    static_assert(P::N % BOXR == 0 && BOXR <= 256, "box rows must tile the column");
-    static constexpr int THREADS = NG * GT;
-    static constexpr int SLOT = P::N * C * 8;
-    static constexpr size_t SMEM = 1024 + (size_t)NG * D * SLOT + NG * D * 8 + 4 * (NG + 1) + 256;
-};
-
-template <class P, class PB, int C, int NG, int D, int SWZ, int SWZB, int BOXR>
-__global__ void __launch_bounds__(ColPackCfg<P, PB, C, NG, D, SWZ, SWZB, BOXR>::THREADS, 1)
-    k_col_pipe_pack(const ColArgs a, const PipeArgs pa, const __grid_constant__ CUtensorMap tmap) {
-    using Cfg = ColPackCfg<P, PB, C, NG, D, SWZ, SWZB, BOXR>;
-    using LAY = Swz<SWZ>;
-    using LAYB = Swz<SWZB>;
-    constexpr int TL = P::TL, E = P::E, NY = P::N, GT = Cfg::GT, CP = C / 2;
-    constexpr int TLB = PB::TL, EB = PB::E;
-    extern __shared__ unsigned char smraw[];
-    unsigned char *base = smraw + ((1024 - (smem_addr(smraw) & 1023)) & 1023);
-    uint64_t *full = reinterpret_cast<uint64_t *>(base + (size_t)NG * D * Cfg::SLOT);
-    volatile int *flags = reinterpret_cast<volatile int *>(full + NG * D);
-    volatile int *abort = flags + NG;
-
-    const int tid = threadIdx.x;
-    if (tid == 0) {
-        for (int i = 0; i < NG * D; ++i) mbar_init(full + i, 1);
-        *abort = 0;
-        fence_mbar_init();
-    }
-    __syncthreads();
-
-    const int nx = a.nx;
-    const int ppt = (nx + C - 1) / C;
-    const int J = a.items * ppt;
-    const int g = tid / GT, gt = tid - g * GT;
-    const int c = gt % C, t = gt / C;       // inverse-transform mapping
-    const int cp = gt % CP, tb = gt / CP;   // packed forward-transform mapping
-    unsigned char *ring = base + (size_t)g * D * Cfg::SLOT;
-    uint64_t *gfull = full + g * D;
-    auto gsync = [g]() { named_sync(1 + g, GT); };
-    auto job = [&](int k) { return (int)blockIdx.x + (g + NG * k) * (int)gridDim.x; };
-    auto issue = [&](int k) {
-        const int j = job(k);
-        if (j >= J || j == pa.drop_job) return;
-        const int item = j / ppt, pan = j - item * ppt;
-        unsigned char *sl = ring + (size_t)(k % D) * Cfg::SLOT;
-        mbar_expect_tx(gfull + k % D, (uint32_t)Cfg::SLOT);
-#pragma unroll 1
-        for (int r = 0; r < NY / BOXR; ++r)
-            tma_load_2d(sl + (size_t)r * BOXR * C * 8, &tmap, 2 * pan * C, item * NY + r * BOXR,
-                        gfull + k % D);
-    };
-    auto drain = [&](int k0, int k1) {
-        for (int q = k0; q < k1; ++q) {
-            const int j = job(q);
-            if (j < J && j != pa.drop_job) mbar_wait(gfull + q % D, (q / D) & 1, pa.wait_ns, nullptr);
-        }
-    };
-    if (gt == 0)
-        for (int k = 0; k < D; ++k) issue(k);
-
-    for (int k = 0;; ++k) {
-        const int j = job(k);
-        if (j >= J) break;
-        if (gt == 0) {
-            bool ok = !*abort && mbar_wait(gfull + k % D, (k / D) & 1, pa.wait_ns, abort);
-            if (!ok) {
-                atomicOr(pa.err, ERR_TIMEOUT_BIT);
-                *abort = 1;
-            }
-            flags[g] = ok;
-        }
-        gsync();
-        if (!flags[g]) {
-            if (gt == 0) drain(k, k + D);
-            break;
-        }
-        const int item = j / ppt, pan = j - item * ppt;
-        const int x = pan * C + c;
-        const bool act = x < nx;
-        float2 *sl = reinterpret_cast<float2 *>(ring + (size_t)(k % D) * Cfg::SLOT);
-        float *slf = reinterpret_cast<float *>(sl);
-        const size_t base_o = (size_t)item * NY * nx;
-        {
-            float2 v[E];
-            static_for<0, E>([&](auto ec) {
-                constexpr int e = decltype(ec)::value;
-                v[e] = sl[(t + TL * e) * C + c];
-            });
-            line_fft<P, +1, C, LAY>(v, sl + c, a.tw, t, gsync);
-            // binary quantisation; the real phasors go to the packed layout
-            // z[y][cp] = (col 2cp, col 2cp+1), float index (y * CP + c/2) * 2 + (c & 1)
-            gsync();
-            static_for<0, E>([&](auto ec) {
-                constexpr int e = decltype(ec)::value;
-                const int y = t + TL * e;
-                const float2 h = v[e];
-                const int q = h.x >= 0.f ? 0 : 1;
-                if (act) {
-                    if (a.h_out) a.h_out[base_o + (size_t)y * nx + x] = make_float2(h.x * a.invSqrtN, h.y * a.invSqrtN);
-                    if (a.holo) a.holo[base_o + (size_t)y * nx + x] = (uint8_t)q;
-                }
-                slf[(y * CP + (c >> 1)) * 2 + (c & 1)] = q ? -1.f : 1.f;
-            });
-        }
-        gsync();
-        float2 w[EB];
-        static_for<0, EB>([&](auto ec) {
-            constexpr int e = decltype(ec)::value;
-            w[e] = sl[(tb + TLB * e) * CP + cp];
-        });
-        line_fft<PB, -1, CP, LAYB>(w, sl + cp, a.tw, tb, gsync);
-        // Z to the dense [k][cp] layout, then unpack rows k <= ny/2
-        gsync();
-        static_for<0, EB>([&](auto ec) {
-            constexpr int e = decltype(ec)::value;
-            sl[(tb + TLB * e) * CP + cp] = w[e];
-        });
-        gsync();
-        const int xa = pan * C + 2 * cp;  // the two columns of this packed pair
-        static_for<0, EB>([&](auto ec) {
-            constexpr int e = decltype(ec)::value;
-            const int kk = tb + TLB * e;
-            if (kk <= NY / 2) {
-                const float2 z = w[e];
-                const float2 zm = sl[mirror_idx<NY>(kk) * CP + cp];  // Z[N - k]
-                // A = (Z + conj(Zm)) / 2, B = (Z - conj(Zm)) / (2i)
-                const float2 A = make_float2(0.5f * (z.x + zm.x), 0.5f * (z.y - zm.y));
-                const float2 B = make_float2(0.5f * (z.y + zm.y), -0.5f * (z.x - zm.x));
-                float2 *row = a.field + base_o + (size_t)kk * nx;
-                if (xa < nx) row[xa] = A;
-                if (xa + 1 < nx) row[xa + 1] = B;
-            }
-        });
-        gsync();
-        if (gt == 0) issue(k + D);  // slot fully consumed: refill it
-    }
-}
-
 // --------------------------------------------------------- dispatch glue
 
 struct PipeOps {
@@ -1220,9 +1071,6 @@ struct PipeOps {
     void (*row_iter)(const RowArgs &a, const PipeArgs &pa, int grid, cudaStream_t s);  // may be null
     void (*col_gs)(int role, const ColArgs &a, const PipeArgs &pa, const CUtensorMap &m, int grid,
                    cudaStream_t s);  // may be null
-    // binary column pass with packed forward transforms, half rows (may be null)
-    void (*col_pack)(const ColArgs &a, const PipeArgs &pa, const CUtensorMap &m, int grid, cudaStream_t s);
-    int pack_blocks_per_sm;
     // column pass of the Hermitian binary loop, two columns per transform (may be null);
     // its tensor map has boxes of herm_c columns x herm_boxr rows
     void (*col_herm)(const ColArgs &a, const PipeArgs &pa, const CUtensorMap &m, int grid, cudaStream_t s);
@@ -1348,23 +1196,6 @@ struct PairImpl {
     }
 };
 
-// Packed binary column pass launcher (see k_col_pipe_pack).
-template <class P, class PB, int C, int NG, int D, int SWZ, int SWZB, int BOXR>
-struct PackImpl {
-    using CC = ColPackCfg<P, PB, C, NG, D, SWZ, SWZB, BOXR>;
-    static cudaError_t init(int *blocks) {
-        cudaError_t e = cudaFuncSetAttribute((const void *)k_col_pipe_pack<P, PB, C, NG, D, SWZ, SWZB, BOXR>,
-                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)CC::SMEM);
-        if (e == cudaSuccess)
-            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-                blocks, k_col_pipe_pack<P, PB, C, NG, D, SWZ, SWZB, BOXR>, CC::THREADS, CC::SMEM);
-        return e;
-    }
-    static void launch(const ColArgs &a, const PipeArgs &pa, const CUtensorMap &m, int grid, cudaStream_t s) {
-        k_col_pipe_pack<P, PB, C, NG, D, SWZ, SWZB, BOXR><<<grid, CC::THREADS, CC::SMEM, s>>>(a, pa, m);
-    }
-};
-
 // Column-pair Hermitian column pass launcher (see k_col_pipe_herm); MINB:
 // at least that many CTAs per SM (the register budget).
 template <class P, int C, int D, int SWZ, int BOXR, int MINB = 1>
@@ -1394,33 +1225,21 @@ struct NoHerm {
                                     cudaStream_t) = nullptr;
 };
 
-struct NoPack {
-    static cudaError_t init(int *blocks) {
-        *blocks = 0;
-        return cudaSuccess;
-    }
-    static constexpr void (*launch)(const ColArgs &, const PipeArgs &, const CUtensorMap &, int,
-                                    cudaStream_t) = nullptr;
-};
-
-// Combines a paired row pass with the column pass of an existing variant (and
-// optionally a packed binary column pass with the same tile shape).
-template <class PAIR, const PipeOps *COL, class PACK = NoPack, class HERM = NoHerm>
+// Combines a paired row pass with the column pass of an existing variant and
+// optionally a column-pair pass for the Hermitian binary loop.
+template <class PAIR, const PipeOps *COL, class HERM = NoHerm>
 struct PairedOps {
     static cudaError_t init(PipeOps *self) {
         cudaError_t e = COL->init(const_cast<PipeOps *>(COL));
         if (e != cudaSuccess) return e;
-        int rb = 0, pb = 0, hb = 0;
+        int rb = 0, hb = 0;
         e = PAIR::init_row(&rb);
-        if (e == cudaSuccess) e = PACK::init(&pb);
         if (e == cudaSuccess) e = HERM::init(&hb);
         if (e != cudaSuccess) return e;
         if (rb < 1) return cudaErrorInvalidConfiguration;
         self->row_blocks_per_sm = rb;
         self->col_blocks_per_sm = COL->col_blocks_per_sm;
-        self->pack_blocks_per_sm = pb;
         self->herm_blocks_per_sm = hb;
-        if (pb < 1) self->col_pack = nullptr;
         if (hb < 1) self->col_herm = nullptr;
         return cudaSuccess;
     }
@@ -1435,7 +1254,6 @@ struct PairedOps {
         o.row_head = &PAIR::row_head;
         o.row_tail = &PAIR::row_tail;
         o.row_avg = &PAIR::row_avg;
-        o.col_pack = PACK::launch;
         o.col_herm = HERM::launch;
         o.herm_c = HERM::COLS;
         o.herm_boxr = HERM::BOX_ROWS;

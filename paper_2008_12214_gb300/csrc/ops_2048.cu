@@ -14,9 +14,9 @@ PipeOps p2048b = PipeImpl<Plan<2048, 64, 32, 32, 8, 8>, 1, 4, 2, 5, Plan<2048, 6
 // with 16 samples per thread, or 8 columns with 32 samples per thread
 using Herm2048a = HermImpl<Plan<2048, 128, 16, 16, 16, 8>, 4, 3, 4, 256>;
 using Herm2048b = HermImpl<Plan<2048, 64, 32, 32, 8, 8>, 8, 3, 5, 256>;
-PipeOps p2048c = PairedOps<PairImpl<Plan<2048, 128, 16, 16, 16, 8>, 3, 2, 4>, &p2048a, NoPack, Herm2048a>::make(
+PipeOps p2048c = PairedOps<PairImpl<Plan<2048, 128, 16, 16, 16, 8>, 3, 2, 4>, &p2048a, Herm2048a>::make(
     "2048:pair16x16x8e16+c16x16x8e16");
-PipeOps p2048d = PairedOps<PairImpl<Plan<2048, 128, 16, 16, 16, 8>, 3, 2, 4>, &p2048a, NoPack, Herm2048b>::make(
+PipeOps p2048d = PairedOps<PairImpl<Plan<2048, 128, 16, 16, 16, 8>, 3, 2, 4>, &p2048a, Herm2048b>::make(
     "2048:pair16x16x8e16+c16x16x8e16/h32");
 }  // namespace
 

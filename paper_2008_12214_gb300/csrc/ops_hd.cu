@@ -2,10 +2,12 @@
 // Generic passes: 1080 = 30 x 6 x 6 (36 threads per line), 1920 = 30 x 8 x 8
 // (64 threads per line; its last stage returns through shared memory).
 // TMA-fed variants: 1080-sample columns (8 per CTA, 288 threads, boxes of 180
-// rows) with column-pair passes (16 columns of 30 samples per thread, or 8
-// columns of 15), 1920-sample columns (4 per CTA, boxes of 240 rows), and
-// paired row passes on 1920-sample rows (3 lines of 30 samples per thread,
-// or 2 lines of 15 samples per thread, 15 x 16 x 8).
+// rows) with a column-pair pass of 8 columns on a 15 x 8 x 9 plan (72 threads
+// per column pair, stage roots reloaded per line), 1920-sample columns (4 per
+// CTA, boxes of 240 rows), and the paired row pass on 1920-sample rows (2
+// lines of 128 threads, 15 x 16 x 8).  The 30-samples-per-thread plans spill
+// as TMA-fed paired or column-pair passes (255 and 168 registers plus 0.8-0.9
+// KB per thread) and measured 1.6x (rows) and 1.2x (column pairs) slower.
 #include "hg_pipe.cuh"
 
 namespace hg {
@@ -17,10 +19,8 @@ using P1920b = Plan<1920, 128, 16, 15, 16, 8>;
 LineOps o1080 = OpsImpl<P1080, 8, 16>::make();
 LineOps o1920 = OpsImpl<P1920, 4, 8>::make();
 PipeOps p1080c = PipeImpl<P1080, 0, 1, 1, 3, P1080, 8, 1, 3, 3, 180>::make("1080:c30x6x6");
-PipeOps p1080h = WithHerm<&p1080c, HermImpl<P1080, 16, 3, 3, 180>>::make("1080:c30x6x6/h30c16");
 PipeOps p1080k = WithHerm<&p1080c, HermImpl<Reload<P1080b>, 8, 3, 0, 180>>::make("1080:c30x6x6/h15c8");
 PipeOps p1920c = PipeImpl<P1920, 0, 1, 1, 4, P1920, 4, 1, 3, 4, 240>::make("1920:c30x8x8");
-PipeOps p1920p = PairedOps<PairImpl<P1920, 3, 2, 4>, &p1920c>::make("1920:pair30x8x8+c30x8x8");
 PipeOps p1920q = PairedOps<PairImpl<Reload<P1920b>, 2, 2, 0>, &p1920c>::make("1920:pair15x16x8w8+c30x8x8");
 }  // namespace
 
@@ -35,12 +35,10 @@ const LineOps *ops_hd(int n) {
 int pipe_ops_hd(int n, const PipeOps **out, int max) {
     int k = 0;
     if (n == 1080) {
-        if (k < max) out[k++] = &p1080h;
         if (k < max) out[k++] = &p1080k;
     }
     if (n == 1920) {
         if (k < max) out[k++] = &p1920c;
-        if (k < max) out[k++] = &p1920p;
         if (k < max) out[k++] = &p1920q;
     }
     return k;

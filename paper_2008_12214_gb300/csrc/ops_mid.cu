@@ -15,9 +15,9 @@ PipeOps p512b = PipeImpl<Plan<512, 32, 16, 16, 16, 2>, 1, 16, 2, 4, Plan<512, 32
 // with 16 samples per thread, or 32 columns with 32 samples per thread
 using Herm512a = HermImpl<Plan<512, 32, 16, 16, 16, 2>, 16, 3, 4, 256>;
 using Herm512b = HermImpl<Plan<512, 16, 32, 32, 16>, 32, 3, 5, 256>;
-PipeOps p512c = PairedOps<PairImpl<Plan<512, 32, 16, 16, 16, 2>, 12, 2, 4>, &p512a, NoPack, Herm512a>::make(
+PipeOps p512c = PairedOps<PairImpl<Plan<512, 32, 16, 16, 16, 2>, 12, 2, 4>, &p512a, Herm512a>::make(
     "512:pair16x16x2e16+c32x16e32");
-PipeOps p512d = PairedOps<PairImpl<Plan<512, 32, 16, 16, 16, 2>, 12, 2, 4>, &p512a, NoPack, Herm512b>::make(
+PipeOps p512d = PairedOps<PairImpl<Plan<512, 32, 16, 16, 16, 2>, 12, 2, 4>, &p512a, Herm512b>::make(
     "512:pair16x16x2e16+c32x16e32/h32");
 }  // namespace
 
