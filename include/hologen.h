@@ -185,8 +185,10 @@ hg_status hg_plan_create(hg_plan *out, int ny, int nx, int batch, hg_slm slm, hg
  *              per target.  Normalised inside to sum T^2 = 1.
  *  init_phase  GS/WGS: [batch][ny][nx] float radians, replay order, the
  *              starting replay phase; NULL draws U[0, 2 pi) from Philox with
- *              counter {y*nx + x, 0, target index, 1}.  OSPR: must be NULL
- *              (subframe n of target t uses counter {y*nx + x, n, t, 0}).
+ *              counter {(y*nx + x) / 4, 0, target index, 1}, replay pixel
+ *              y*nx + x taking output word (y*nx + x) mod 4.  OSPR: must be
+ *              NULL (subframe n of target t: counter {(y*nx + x) / 4, n, t, 0},
+ *              the same word).
  *  iters       GS/WGS iterations, >= 1.  OSPR / ADOSPR: ignored.
  *  holo_out    GS/WGS: [batch][ny][nx] uint8 level indices of the last
  *              iteration's hologram; OSPR: [batch][subframes][ny][nx].  NULL

@@ -198,6 +198,8 @@ def philox4x32_10(ctr, key) -> np.ndarray:
 
 
 def random_phase(ny, nx, seed, t, sub, stream) -> np.ndarray:
+    """Seeded U[0, 2 pi) phase map (replay order): pixel r = y nx + x takes
+    word r mod 4 of Philox4x32-10 at counter {r // 4, sub, t, stream}."""
     out = np.empty((ny, nx), np.float64)
     _ck(_load().or_random_phase(int(ny), int(nx), int(seed), int(t), int(sub), int(stream), _p(out)))
     return out

@@ -473,19 +473,23 @@ void or_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t out
 }
 
 /*
- * Seeded random phase in [0, 2 pi) for every replay pixel (y, x), replay order:
- *   u = (philox(ctr = {y*nx + x, sub, t, stream}, key = {seed lo, seed hi})[0] >> 8) * 2^-24
- *   phase = 2 pi u.
+ * Seeded random phase in [0, 2 pi) for every replay pixel (y, x), replay order.
+ * Pixel r = y*nx + x takes output word (r mod 4) of one generator call per
+ * group of four consecutive pixels:
+ *   w = philox(ctr = {floor(r / 4), sub, t, stream}, key = {seed lo, seed hi})
+ *   u = (w[r mod 4] >> 8) * 2^-24,  phase = 2 pi u.
  * stream 0: OSPR subframe `sub` of target t; stream 1: GS initial phase.
+ * (The paper asks only for random phases, Section 3.4; the counter layout is
+ * this implementation's.)
  */
 int or_random_phase(int ny, int nx, uint64_t seed, uint32_t t, uint32_t sub, uint32_t stream,
                     double *phase_out) {
     if (ny < 1 || nx < 1 || !phase_out) return OR_ERR_ARG;
     uint32_t key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32)};
     for (size_t i = 0; i < (size_t)nx * ny; ++i) {
-        uint32_t ctr[4] = {(uint32_t)i, sub, t, stream}, r[4];
+        uint32_t ctr[4] = {(uint32_t)(i / 4), sub, t, stream}, r[4];
         or_philox4x32_10(ctr, key, r);
-        double u = (double)(r[0] >> 8) * (1.0 / 16777216.0);
+        double u = (double)(r[i % 4] >> 8) * (1.0 / 16777216.0);
         phase_out[i] = (double)(OR_TWO_PI * (long double)u);
     }
     return OR_OK;

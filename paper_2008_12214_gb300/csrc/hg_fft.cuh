@@ -415,6 +415,38 @@ __device__ __forceinline__ uint32_t philox_word0(uint32_t c0, uint32_t c1, uint3
     return c0;
 }
 
+// All four output words of the same generator.
+__device__ __forceinline__ uint4 philox4(uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3, uint32_t k0,
+                                         uint32_t k1) {
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        if (r) {
+            k0 += 0x9E3779B9u;
+            k1 += 0xBB67AE85u;
+        }
+        const uint32_t lo0 = 0xD2511F53u * c0, hi0 = __umulhi(0xD2511F53u, c0);
+        const uint32_t lo1 = 0xCD9E8D57u * c2, hi1 = __umulhi(0xCD9E8D57u, c2);
+        const uint32_t n0 = hi1 ^ c1 ^ k0, n2 = hi0 ^ c3 ^ k1;
+        c0 = n0;
+        c1 = lo1;
+        c2 = n2;
+        c3 = lo0;
+    }
+    return make_uint4(c0, c1, c2, c3);
+}
+
+// The random phase of replay pixel r (= y nx + x) of a drawn phase map, as
+// 2u with u = (word >> 8) 2^-24 in [0, 1), ready for sincospif: every group
+// of four consecutive pixels shares one generator call, counter {r / 4, sub,
+// target, stream}, pixel r taking output word r mod 4.
+__device__ __forceinline__ float philox_phase2u(uint32_t r, uint32_t sub, uint32_t target, uint32_t stream,
+                                                uint32_t k0, uint32_t k1) {
+    const uint4 w = philox4(r >> 2, sub, target, stream, k0, k1);
+    const uint32_t q = r & 3u;
+    const uint32_t v = q == 0 ? w.x : q == 1 ? w.y : q == 2 ? w.z : w.w;
+    return (float)(v >> 8) * (1.0f / 8388608.0f);
+}
+
 // Output words 0 and 1 of the same generator.
 __device__ __forceinline__ uint2 philox_words01(uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3, uint32_t k0,
                                                 uint32_t k1) {

@@ -176,9 +176,9 @@ __device__ __forceinline__ void row_body(const RowArgs &a) {
                     sincospif(__ldg(a.phase + ((size_t)b * ny + iy) * NX + ix) * 0.318309886183790672f,
                               &s, &c);
                 } else {
-                    const uint32_t r = philox_word0((uint32_t)(iy * NX + ix), (uint32_t)sub,
-                                                    (uint32_t)b, a.stream_id, a.seed_lo, a.seed_hi);
-                    sincospif((float)(r >> 8) * (1.0f / 8388608.0f), &s, &c);  // pi * 2u
+                    sincospif(philox_phase2u((uint32_t)(iy * NX + ix), (uint32_t)sub, (uint32_t)b, a.stream_id,
+                                             a.seed_lo, a.seed_hi),
+                              &s, &c);  // pi * 2u
                 }
                 v[e] = make_float2(amp * c, amp * s);
                 if constexpr (H) {  // F_H = (F(u) + conj F(-u)) / 2, u' = (ny - y, nx - x)
@@ -189,9 +189,9 @@ __device__ __forceinline__ void row_body(const RowArgs &a) {
                         sincospif(__ldg(a.phase + ((size_t)b * ny + iym) * NX + ixm) * 0.318309886183790672f,
                                   &snm, &csm);
                     } else {
-                        const uint32_t r = philox_word0((uint32_t)(iym * NX + ixm), (uint32_t)sub,
-                                                        (uint32_t)b, a.stream_id, a.seed_lo, a.seed_hi);
-                        sincospif((float)(r >> 8) * (1.0f / 8388608.0f), &snm, &csm);
+                        sincospif(philox_phase2u((uint32_t)(iym * NX + ixm), (uint32_t)sub, (uint32_t)b,
+                                                 a.stream_id, a.seed_lo, a.seed_hi),
+                                  &snm, &csm);
                     }
                     float am = a.T[((size_t)b * ny + ym) * NX + xm];
                     if (a.w) am *= a.w[((size_t)b * ny + ym) * NX + xm];
@@ -323,10 +323,10 @@ __device__ __forceinline__ void row_body(const RowArgs &a) {
                     if (act) ar[x] = sum;
                     const float amp = sqrtf(fmaxf(fmaf((float)(a.sub + 1), Tv * Tv, -sum), 0.f));
                     const int ix = (x + NX / 2) % NX;
-                    const uint32_t r = philox_word0((uint32_t)(iy * NX + ix), (uint32_t)a.sub, (uint32_t)item,
-                                                    a.stream_id, a.seed_lo, a.seed_hi);
                     float s, c;
-                    sincospif((float)(r >> 8) * (1.0f / 8388608.0f), &s, &c);  // pi * 2u
+                    sincospif(philox_phase2u((uint32_t)(iy * NX + ix), (uint32_t)a.sub, (uint32_t)item,
+                                             a.stream_id, a.seed_lo, a.seed_hi),
+                              &s, &c);  // pi * 2u
                     v[e] = make_float2(amp * c, amp * s);
                 } else {
                     const float I = sum * inv_sub;

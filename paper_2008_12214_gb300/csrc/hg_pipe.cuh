@@ -576,6 +576,21 @@ __global__ void __launch_bounds__(PairPipeCfg<P, NG, D, SWZ>::THREADS, MINB)
             const int ym = (ny - pan) % ny, iy = (pan + hy) % ny, iym = (ym + hy) % ny;
             const float *wr = a.w ? a.w + ((size_t)b * ny + pan) * NX : nullptr;
             const float *wrm = a.w ? a.w + ((size_t)b * ny + ym) * NX : nullptr;
+            if (!a.phase) {
+                // drawn phases: one generator call per four pixels of each replay row
+                // (the phase map's definition), stored as 2u where the phase rows would be
+                float4 *wP = reinterpret_cast<float4 *>(sl);
+                const int nrow = partner ? 2 : 1;
+                for (int gi = t; gi < nrow * (NX / 4); gi += TL) {
+                    const int rr = gi / (NX / 4), g4 = gi - rr * (NX / 4);
+                    const uint4 w = philox4((uint32_t)((rr ? iym : iy) * (NX / 4) + g4), (uint32_t)sub, (uint32_t)b,
+                                            a.stream_id, a.seed_lo, a.seed_hi);
+                    constexpr float k = 1.0f / 8388608.0f;
+                    wP[gi] = make_float4((float)(w.x >> 8) * k, (float)(w.y >> 8) * k, (float)(w.z >> 8) * k,
+                                         (float)(w.w >> 8) * k);
+                }
+                gsync();
+            }
             static_for<0, E>([&](auto ec) {
                 constexpr int e = decltype(ec)::value;
                 const int x = t + TL * e, xm = mirror_idx<NX>(x);
@@ -596,12 +611,8 @@ __global__ void __launch_bounds__(PairPipeCfg<P, NG, D, SWZ>::THREADS, MINB)
                     sincospif(sP[ix] * 0.318309886183790672f, &s, &c);
                     sincospif(sPm[ixm] * 0.318309886183790672f, &sm, &cm);
                 } else {
-                    const uint32_t r = philox_word0((uint32_t)(iy * NX + ix), (uint32_t)sub, (uint32_t)b,
-                                                    a.stream_id, a.seed_lo, a.seed_hi);
-                    const uint32_t rm = philox_word0((uint32_t)(iym * NX + ixm), (uint32_t)sub, (uint32_t)b,
-                                                     a.stream_id, a.seed_lo, a.seed_hi);
-                    sincospif((float)(r >> 8) * (1.0f / 8388608.0f), &s, &c);  // pi * 2u
-                    sincospif((float)(rm >> 8) * (1.0f / 8388608.0f), &sm, &cm);
+                    sincospif(sP[ix], &s, &c);  // pi * 2u
+                    sincospif(sPm[ixm], &sm, &cm);
                 }
                 v[e] = make_float2(0.5f * fmaf(am, cm, amp * c), 0.5f * fmaf(-am, sm, amp * s));
             });

@@ -295,9 +295,12 @@ def test_philox_known_answers():
 def test_random_phase_layout_and_range():
     ph = oracle.random_phase(4, 6, 0x1234_5678_9ABC, 3, 5, 0)
     key = [0x5678_9ABC, 0x1234]
-    for i in (0, 7, 23):
-        r = oracle.philox4x32_10([i, 5, 3, 0], key)
-        assert ph.flat[i] == pytest.approx(2 * np.pi * (int(r[0]) >> 8) / 2 ** 24, abs=1e-15)
+    # one generator call per four consecutive replay pixels, pixel i taking word i mod 4
+    for i in (0, 1, 2, 3, 7, 22, 23):
+        r = oracle.philox4x32_10([i // 4, 5, 3, 0], key)
+        assert ph.flat[i] == pytest.approx(2 * np.pi * (int(r[i % 4]) >> 8) / 2 ** 24, abs=1e-15)
+    # the four words of a call are independent draws: no two pixels of a group coincide
+    assert len(set(np.round(ph.flat[:4], 12))) == 4
     big = oracle.random_phase(512, 512, 7, 0, 0, 0)
     assert big.min() >= 0 and big.max() < 2 * np.pi
     sigma = 2 * np.pi / np.sqrt(12) / 512          # std of the mean of U[0, 2 pi)
