@@ -454,7 +454,7 @@ def run_side_workload(args):
         T = torch.from_numpy(synth.targets(B, n, n, 5000)).to(dev)
         P = torch.from_numpy(synth.init_phases(B, n, n, 5000)).to(dev)
         mse = torch.empty((B, args.iters), dtype=torch.float64, device=dev)
-        plan = hg.Plan(n, n, B, hg.HG_SLM_BINARY, 2, hg.HG_GS, precision=args.precision)
+        plan = hg.Plan(n, n, B, hg.HG_SLM_BINARY, 2, hg.HG_GS, precision=args.precision, autotune=args.autotune)
         for _ in range(args.warmup):
             plan.run(T, P, args.iters, None, mse)
         plan.sync()

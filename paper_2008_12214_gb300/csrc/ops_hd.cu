@@ -4,10 +4,12 @@
 // TMA-fed variants: 1080-sample columns (8 per CTA, 288 threads, boxes of 180
 // rows) with a column-pair pass of 8 columns on a 15 x 8 x 9 plan (72 threads
 // per column pair, stage roots reloaded per line), 1920-sample columns (4 per
-// CTA, boxes of 240 rows), and the paired row pass on 1920-sample rows (2
-// lines of 128 threads, 15 x 16 x 8).  The 30-samples-per-thread plans spill
-// as TMA-fed paired or column-pair passes (255 and 168 registers plus 0.8-0.9
-// KB per thread) and measured 1.6x (rows) and 1.2x (column pairs) slower.
+// CTA, boxes of 240 rows), and the paired row pass on 1920-sample rows (3
+// single-slot lines of 128 threads, 15 x 16 x 8, reloaded roots: 168
+// registers; 0.146 ms per launch at 16 fields, against 0.161 for 2 lines of
+// two slots).  The 30-samples-per-thread plans spill as TMA-fed paired or
+// column-pair passes (255 and 168 registers plus 0.8-0.9 KB per thread) and
+// measured 1.6x (rows) and 1.2x (column pairs) slower.
 #include "hg_pipe.cuh"
 
 namespace hg {
@@ -21,7 +23,7 @@ LineOps o1920 = OpsImpl<P1920, 4, 8>::make();
 PipeOps p1080c = PipeImpl<P1080, 0, 1, 1, 3, P1080, 8, 1, 3, 3, 180>::make("1080:c30x6x6");
 PipeOps p1080k = WithHerm<&p1080c, HermImpl<Reload<P1080b>, 8, 3, 0, 180>>::make("1080:c30x6x6/h15c8");
 PipeOps p1920c = PipeImpl<P1920, 0, 1, 1, 4, P1920, 4, 1, 3, 4, 240>::make("1920:c30x8x8");
-PipeOps p1920q = PairedOps<PairImpl<Reload<P1920b>, 2, 2, 0>, &p1920c>::make("1920:pair15x16x8w8+c30x8x8");
+PipeOps p1920r = PairedOps<PairImpl<Reload<P1920b>, 3, 1, 0>, &p1920c>::make("1920:pair15x16x8w12+c30x8x8");
 }  // namespace
 
 const LineOps *ops_hd(int n) {
@@ -39,7 +41,7 @@ int pipe_ops_hd(int n, const PipeOps **out, int max) {
     }
     if (n == 1920) {
         if (k < max) out[k++] = &p1920c;
-        if (k < max) out[k++] = &p1920q;
+        if (k < max) out[k++] = &p1920r;
     }
     return k;
 }

@@ -387,8 +387,8 @@ def test_bounded_wait_reports_timeout_and_plan_recovers():
         assert np.allclose(mse[b].cpu().numpy(), o["mse"], rtol=1e-4)
 
 
-@pytest.mark.parametrize("n,cand", [(256, 0), (512, 0), (512, 1), (512, 2), (1024, 0), (1024, 1), (1024, 2),
-                                    (1024, 3), (512, 3), (2048, 0), (2048, 1), (2048, 2), (2048, 3)])
+@pytest.mark.parametrize("n,cand", [(256, 0), (512, 0), (512, 1), (512, 2), (512, 3), (1024, 0), (1024, 1),
+                                    (1024, 2), (1024, 3), (2048, 0), (2048, 1), (2048, 2), (2048, 3)])
 def test_every_pipelined_variant_against_oracle(n, cand):
     """Each TMA-fed candidate the autotuner may pick, forced in turn: the
     column pass through a single step, the row pass through the metrics it
@@ -544,7 +544,7 @@ def test_tensor_core_row_pass_precision(n, prec, tol):
 
 @pytest.mark.parametrize("n,cand,wgs", [(1024, 2, False), (1024, 3, False), (1024, 2, True), (1024, 3, True),
                                         (512, 2, False), (512, 3, False), (2048, 2, False), (2048, 3, False),
-                                        ((1080, 1920), 0, False)])
+                                        (2048, 3, True), ((1080, 1920), 0, False)])
 def test_hermitian_binary_loop_matches_generic(n, cand, wgs):
     """Binary GS in Hermitian form (paired rows write only the Hermitian part
     of F, rows ky <= ny/2; the column passes read those rows back, two columns
