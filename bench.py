@@ -426,7 +426,7 @@ def run_side_workload(args):
         P = torch.from_numpy(synth.init_phases(B, n, n, 7000)).to(dev)
         mse = torch.empty((B, args.iters), dtype=torch.float64, device=dev)
         holo = torch.empty((B, n, n), dtype=torch.uint8, device=dev)
-        plan = hg.Plan(n, n, B, kind, levels, hg.HG_GS, fresnel=c, modulated=True)
+        plan = hg.Plan(n, n, B, kind, levels, hg.HG_GS, fresnel=c, modulated=True, pipeline=args.pipeline)
         plan.set_illumination(torch.from_numpy(A).to(dev), None)
         plan.set_roi(torch.from_numpy(roi).to(dev))
         for _ in range(args.warmup):
@@ -438,6 +438,10 @@ def run_side_workload(args):
         e1.record(s0)
         plan.sync()
         ms = e0.elapsed_time(e1) / args.steps
+        hg.hg_profile_enable(plan.h, 2 * args.iters + 8)
+        plan.run(T, P, args.iters, holo, mse)
+        prof = hg.hg_profile_read(plan.h)
+        hg.hg_profile_enable(plan.h, 0)
         ev = plan.evaluate(holo, T).cpu().numpy()
         it_ms = ms / args.iters
         px = B * n * n
@@ -447,6 +451,7 @@ def run_side_workload(args):
                    algorithmic_gbs_at_45=45.0 * px / (it_ms / 1e3) / 1e9,
                    final_roi_mse_mean=float(mse[:, -1].mean().item()), roi_ssim_mean=float(ev[:, 3].mean()),
                    efficiency_mean=float(ev[:, 2].mean()), fresnel_rad_per_px2=c,
+                   row_ms=prof[0] / max(prof[1], 1), column_ms=prof[2] / max(prof[3], 1),
                    row_variant=hg.hg_plan_variant(plan.h, 0), column_variant=hg.hg_plan_variant(plan.h, 1))
         plan.close()
     elif args.workload == "gs2048":

@@ -23,6 +23,7 @@ using P16b = Plan<1024, 64, 16, 16, 8, 8>;
 LineOps o1024 = OpsImpl<P32, 8, 16, true>::make();
 PipeOps p1024a = PipeImpl<P32, 1, 8, 2, 5, P32, 8, 1, 3, 5, 256>::make("1024:r32x32e32");
 PipeOps p1024b = PipeImpl<P16, 1, 8, 2, 4, P16, 8, 1, 3, 4, 256>::make("1024:r16x16x4e16");
+PipeOps p1024e = PipeImpl<Reload<P16b>, 1, 8, 1, 4, Reload<P16b>, 8, 1, 2, 4, 256>::make("1024:r16x8x8w16");
 PipeOps p1024c = PairedOps<PairImpl<Reload<P16b>, 8, 1, 4>, &p1024a, HermImpl<Reload<P16b>, 8, 2, 4, 256, 2>>::make(
     "1024:pair16x8x8w16+c32x32e32/h16c8x2");
 PipeOps p1024d = PairedOps<PairImpl<P16, 6, 2, 4>, &p1024a, HermImpl<P32, 16, 3, 5, 256>>::make(
@@ -33,7 +34,7 @@ const LineOps *ops_1024(int n) { return n == 1024 ? &o1024 : nullptr; }
 
 int pipe_ops_1024(int n, const PipeOps **out, int max) {
     if (n != 1024) return 0;
-    const PipeOps *c[] = {&p1024a, &p1024b, &p1024c, &p1024d};
+    const PipeOps *c[] = {&p1024a, &p1024b, &p1024c, &p1024d, &p1024e};
     int k = 0;
     for (const PipeOps *o : c)
         if (k < max) out[k++] = o;
