@@ -791,6 +791,13 @@ bool herm_ends(hg_plan p) { return herm_loop(p) && p->prow->row_head && p->prow-
 // Binary OSPR in Hermitian form: head and time average on the paired row
 // kernel of the variant that provides the column-pair pass.
 bool ospr_pair_ends(hg_plan p) { return p->ospr_herm && p->hops->row_head && p->hops->row_avg; }
+bool adospr_pair(hg_plan p) { return p->algo == HG_ADOSPR && ospr_pair_ends(p) && p->hops->row_adapt; }
+
+void launch_adapt(hg_plan p, const RowArgs &a, bool last, cudaStream_t s) {
+    const long work = (long)a.items * (p->ny / 2 + 1);
+    p->hops->row_adapt(a, pipe_args(p), grid_for(p->hops->row_blocks_per_sm, p->nsm, work), s, last);
+    p->launches++;
+}
 
 void launch_ospr_end(hg_plan p, bool head, const RowArgs &a, cudaStream_t s) {
     const long work = (long)a.items * (p->ny / 2 + 1);
@@ -874,24 +881,31 @@ hg_status enqueue_run(hg_plan p, const float *d_t, const float *d_ph, int iters,
         ra.nsub = 1;  // the head draws subframe 0 of target `item`
         ra.phase = nullptr;
         ra.stream_id = 0;
-        launch_row(p, ROW_HEAD, ra, p->stream);
+        // Hermitian form: the running intensity sum is symmetric, rows ky <= ny/2 suffice
+        const bool hm = adospr_pair(p);
+        if (hm) launch_ospr_end(p, true, ra, p->stream);
+        else launch_row(p, ROW_HEAD, ra, p->stream);
         ca.items = p->batch;
+        ca.half_in = ca.half = hm;
         RowArgs rn = row_args(p);
         rn.acc = p->acc;
         rn.stream_id = 0;
         rn.nsub = p->nsub;
         for (int n = 0; n < p->nsub; ++n) {
             ca.holo = d_ho ? p->holo_tmp : nullptr;
-            launch_col_gs(p, COL_GS_BIN, ca, p->stream);
+            if (hm) launch_col_herm(p, ca, p->stream);
+            else launch_col_gs(p, COL_GS_BIN, ca, p->stream);
             if (d_ho)  // subframe n of each target: [batch][subframes][ny][nx]
                 HG_CK(cudaMemcpy2DAsync(d_ho + (size_t)n * p->npx, p->npx * p->nsub, p->holo_tmp, p->npx, p->npx,
                                         p->batch, cudaMemcpyDeviceToDevice, p->stream));
             rn.sub = n + 1;
             if (n + 1 < p->nsub) {
-                launch_row(p, ROW_ADAPT, rn, p->stream);
+                if (hm) launch_adapt(p, rn, false, p->stream);
+                else launch_row(p, ROW_ADAPT, rn, p->stream);
             } else {
                 rn.part = p->part;
-                launch_row(p, ROW_ADFIN, rn, p->stream);
+                if (hm) launch_adapt(p, rn, true, p->stream);
+                else launch_row(p, ROW_ADFIN, rn, p->stream);
             }
         }
     } else if (p->algo == HG_OSPR) {
@@ -1447,7 +1461,7 @@ hg_status hg_plan_create(hg_plan *out, int ny, int nx, int batch, hg_slm slm, hg
         }
         // Binary OSPR: one pass per subframe in Hermitian form with the column-pair
         // pass of any paired variant of this column length (square power-of-two fields)
-        if (algo == HG_OSPR && ny == nx && ny % 2 == 0) {
+        if (is_ospr(algo) && ny == nx && ny % 2 == 0) {
             // the fastest column-pair pass of the paired variants (the first when not tuning)
             const PipeOps *all[8];
             const int k = pipe_candidates(ny, all, 8);
@@ -1466,6 +1480,8 @@ hg_status hg_plan_create(hg_plan *out, int ny, int nx, int batch, hg_slm slm, hg
                 if (o.autotune != 1) break;
             }
             p->ospr_herm = p->hops != nullptr;
+            // the Hermitian head and averages keep one metric panel per row ky <= ny/2
+            if (p->ospr_herm && p->ppt_max < ny / 2 + 1) p->ppt_max = ny / 2 + 1;
         }
     }
     if ((st = ensure_part(p, is_ospr(algo) ? 1 : 8)) != HG_OK) return fail(st);

@@ -451,7 +451,11 @@ struct PairPipeCfg {
 // store); 5: Hermitian time average (binary OSPR, Section 3.4): a job is one
 // row ky <= ny/2 of one target, whose nsub subframe rows the group streams in
 // order, summing |R|^2 in registers; after the last one it writes the
-// normalised intensity of u and -u and the metrics.
+// normalised intensity of u and -u and the metrics; 6 and 7: adaptive OSPR in
+// Hermitian form, 6 the replay of the subframe just quantised added to the
+// running intensity sum, then the next subframe's deficit target with its
+// Philox phases and the inverse row FFT, 7 the last subframe's replay and the
+// metrics of the time average.
 template <class P, int NG, int D, int SWZ, int MODE, int MINB = 1>
 __global__ void __launch_bounds__(PairPipeCfg<P, NG, D, SWZ>::THREADS, MINB)
     k_row_pipe_pair(const RowArgs a, const PipeArgs pa) {
@@ -644,6 +648,87 @@ __global__ void __launch_bounds__(PairPipeCfg<P, NG, D, SWZ>::THREADS, MINB)
                     const int x = t + TL * e, xm = mirror_idx<NX>(x);
                     const float I = accI[e] * inv_sub * a.invN2;
                     const float e2 = accI[e] * inv_sub * a.invN;
+                    const float Tv = sTa[x];
+                    const float d = I - Tv * Tv, am = sqrtf(I) - Tv;
+                    m0 = fmaf(d, d, m0);
+                    m1 = fmaf(am, am, m1);
+                    m3 += e2;
+                    if (Tv > 0.f) m2s += e2;
+                    if (Io) Io[(size_t)iy * NX + (x + NX / 2) % NX] = I;
+                    if (partner) {
+                        const float Tm = sTm[xm];
+                        const float dm = I - Tm * Tm, amm = sqrtf(I) - Tm;
+                        m0 = fmaf(dm, dm, m0);
+                        m1 = fmaf(amm, amm, m1);
+                        m3 += e2;
+                        if (Tm > 0.f) m2s += e2;
+                        if (Io) Io[(size_t)iym * NX + (xm + NX / 2) % NX] = I;
+                    }
+                });
+                if (a.part)
+                    group_sum4<GT>(m0, m1, m2s, m3, red + (size_t)g * Cfg::GW * NMET,
+                                   a.part + ((size_t)item * ppt + pan) * NMET, t, gsync);
+            }
+            gsync();
+            if (t == 0) issue(k + D);
+            continue;
+        }
+        if constexpr (MODE == 6 || MODE == 7) {
+            // adaptive OSPR: every subframe's replay is Hermitian, so the running
+            // sum S of the energy-normalised intensities is symmetric, S(-u) = S(u),
+            // and is kept for rows ky <= ny/2 only (a.acc, DFT order)
+            float *ar = a.acc + ((size_t)item * ny + pan) * NX;
+            const float *sTm = partner ? sTa + NX : sTa;
+            const int ym = (ny - pan) % ny, iy = (pan + hy) % ny, iym = (ym + hy) % ny;
+            float sum[E];
+            static_for<0, E>([&](auto ec) {
+                constexpr int e = decltype(ec)::value;
+                const float2 r = v[e];
+                sum[e] = ar[t + TL * e] + fmaf(r.x, r.x, r.y * r.y) * a.invN2;
+            });
+            if constexpr (MODE == 6) {
+                static_for<0, E>([&](auto ec) {
+                    constexpr int e = decltype(ec)::value;
+                    ar[t + TL * e] = sum[e];
+                });
+                // the next subframe: target sqrt(max((sub + 1) T^2 - S, 0)) at u and -u,
+                // its Philox phases drawn four per call into the (consumed) field area
+                gsync();
+                float4 *wP = reinterpret_cast<float4 *>(sl);
+                for (int gi = t; gi < (partner ? 2 : 1) * (NX / 4); gi += TL) {
+                    const int rr = gi / (NX / 4), g4 = gi - rr * (NX / 4);
+                    const uint4 w = philox4((uint32_t)((rr ? iym : iy) * (NX / 4) + g4), (uint32_t)a.sub,
+                                            (uint32_t)item, a.stream_id, a.seed_lo, a.seed_hi);
+                    constexpr float kk = 1.0f / 8388608.0f;
+                    wP[gi] = make_float4((float)(w.x >> 8) * kk, (float)(w.y >> 8) * kk, (float)(w.z >> 8) * kk,
+                                         (float)(w.w >> 8) * kk);
+                }
+                gsync();
+                const float *sP = reinterpret_cast<const float *>(sl);
+                const float *sPm = partner ? sP + NX : sP;
+                const float nn = (float)(a.sub + 1);
+                static_for<0, E>([&](auto ec) {
+                    constexpr int e = decltype(ec)::value;
+                    const int x = t + TL * e, xm = mirror_idx<NX>(x);
+                    const float Tv = sTa[x], Tm = sTm[xm];
+                    const float amp = sqrtf(fmaxf(fmaf(nn, Tv * Tv, -sum[e]), 0.f));
+                    const float am = sqrtf(fmaxf(fmaf(nn, Tm * Tm, -sum[e]), 0.f));
+                    float sn, cs, snm, csm;
+                    sincospif(sP[(x + NX / 2) % NX], &sn, &cs);  // pi * 2u
+                    sincospif(sPm[(xm + NX / 2) % NX], &snm, &csm);
+                    v[e] = make_float2(0.5f * fmaf(am, csm, amp * cs), 0.5f * fmaf(-am, snm, amp * sn));
+                });
+                pair_finish<P, LAY>(v, sf, a.tw, t, gsync, a.field + ((size_t)item * ny + pan) * NX);
+            } else {
+                // the time average S / nsub of u and -u, scored as in the plain OSPR average
+                const float inv_sub = 1.0f / (float)a.nsub;
+                float *Io = a.I_out ? a.I_out + (size_t)item * ny * NX : nullptr;
+                float m0 = 0.f, m1 = 0.f, m2s = 0.f, m3 = 0.f;
+                static_for<0, E>([&](auto ec) {
+                    constexpr int e = decltype(ec)::value;
+                    const int x = t + TL * e, xm = mirror_idx<NX>(x);
+                    const float I = sum[e] * inv_sub;
+                    const float e2 = I * a.NN;
                     const float Tv = sTa[x];
                     const float d = I - Tv * Tv, am = sqrtf(I) - Tv;
                     m0 = fmaf(d, d, m0);
@@ -1092,6 +1177,8 @@ struct PipeOps {
     void (*row_tail)(const RowArgs &a, const PipeArgs &pa, int grid, cudaStream_t s);
     // Hermitian OSPR time average on the paired row kernel (may be null)
     void (*row_avg)(const RowArgs &a, const PipeArgs &pa, int grid, cudaStream_t s);
+    // Hermitian adaptive-OSPR step (last: the final average) on the paired row kernel (may be null)
+    void (*row_adapt)(const RowArgs &a, const PipeArgs &pa, int grid, cudaStream_t s, bool last);
 };
 
 // Row pass: plan P, LINES rows per group, NGR groups, ring depth DR, swizzle
@@ -1180,7 +1267,9 @@ struct PairImpl {
                               (const void *)k_row_pipe_pair<P, NG, D, SWZ, 2, MINB>,
                               (const void *)k_row_pipe_pair<P, NG, D, SWZ, 3, MINB>,
                               (const void *)k_row_pipe_pair<P, NG, D, SWZ, 4, MINB>,
-                              (const void *)k_row_pipe_pair<P, NG, D, SWZ, 5, MINB>})
+                              (const void *)k_row_pipe_pair<P, NG, D, SWZ, 5, MINB>,
+                              (const void *)k_row_pipe_pair<P, NG, D, SWZ, 6, MINB>,
+                              (const void *)k_row_pipe_pair<P, NG, D, SWZ, 7, MINB>})
             if (e == cudaSuccess)
                 e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)RC::SMEM);
         // the block count of the general Hermitian kernel (the most registers)
@@ -1204,6 +1293,10 @@ struct PairImpl {
     }
     static void row_avg(const RowArgs &a, const PipeArgs &pa, int grid, cudaStream_t s) {
         k_row_pipe_pair<P, NG, D, SWZ, 5, MINB><<<grid, RC::THREADS, RC::SMEM, s>>>(a, pa);
+    }
+    static void row_adapt(const RowArgs &a, const PipeArgs &pa, int grid, cudaStream_t s, bool last) {
+        if (last) k_row_pipe_pair<P, NG, D, SWZ, 7, MINB><<<grid, RC::THREADS, RC::SMEM, s>>>(a, pa);
+        else k_row_pipe_pair<P, NG, D, SWZ, 6, MINB><<<grid, RC::THREADS, RC::SMEM, s>>>(a, pa);
     }
 };
 
@@ -1265,6 +1358,7 @@ struct PairedOps {
         o.row_head = &PAIR::row_head;
         o.row_tail = &PAIR::row_tail;
         o.row_avg = &PAIR::row_avg;
+        o.row_adapt = &PAIR::row_adapt;
         o.col_herm = HERM::launch;
         o.herm_c = HERM::COLS;
         o.herm_boxr = HERM::BOX_ROWS;

@@ -611,7 +611,7 @@ def test_gs_resumes_from_its_returned_phase(n, pipe):
     assert np.allclose(rest, full[:, k:], rtol=2e-2, atol=0), (rest, full)
 
 
-@pytest.mark.parametrize("ny,nsub", [(64, 5), (512, 3)])
+@pytest.mark.parametrize("ny,nsub", [(64, 5), (512, 3), (1024, 4)])
 def test_adaptive_ospr_matches_oracle(ny, nsub):
     """Adaptive OSPR: subframes in order, each aiming at the intensity deficit
     of the earlier ones.  The first subframe is OSPR's (bit-exact off the
