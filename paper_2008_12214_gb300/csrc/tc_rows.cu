@@ -23,8 +23,9 @@ cudaError_t set_attr_n() {
     return e;
 }
 
-// resident CTAs per SM of each precision's kernel, per device (set by tc_init)
-int g_tc_occ[64][5];
+// resident CTAs per SM of each precision's kernel for 1024- and 2048-sample
+// rows, per device (set by tc_init)
+int g_tc_occ[64][5][2];
 int g_tc_nsm[64];
 
 template <int PREC>
@@ -32,8 +33,11 @@ cudaError_t set_attr(int dev) {
     cudaError_t e = set_attr_n<PREC, 1024>();
     if (e == cudaSuccess) e = set_attr_n<PREC, 2048>();
     if (e == cudaSuccess)
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&g_tc_occ[dev][PREC], k_row_tc<PREC, ROW_ITER, 1024>, 128,
-                                                          tc_smem<PREC>());
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&g_tc_occ[dev][PREC][0], k_row_tc<PREC, ROW_ITER, 1024>,
+                                                          128, tc_smem<PREC>());
+    if (e == cudaSuccess)
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&g_tc_occ[dev][PREC][1], k_row_tc<PREC, ROW_ITER, 2048>,
+                                                          128, tc_smem<PREC>());
     return e;
 }
 
@@ -42,9 +46,11 @@ cudaError_t set_attr(int dev) {
 template <int PREC>
 void launch(int role, const RowArgs &a, const TcArgs &ta, int grid, cudaStream_t s) {
     int dev = 0;
-    if (cudaGetDevice(&dev) == cudaSuccess && dev >= 0 && dev < 64 && g_tc_occ[dev][PREC] > 0 && g_tc_nsm[dev] > 0) {
-        const long work = (long)a.items * (a.ny / (a.nx == 2048 ? 2 : 4));
-        const long g = (long)g_tc_occ[dev][PREC] * g_tc_nsm[dev];
+    const int wide = a.nx == 2048;
+    if (cudaGetDevice(&dev) == cudaSuccess && dev >= 0 && dev < 64 && g_tc_occ[dev][PREC][wide] > 0 &&
+        g_tc_nsm[dev] > 0) {
+        const long work = (long)a.items * (a.ny / (wide ? 2 : 4));
+        const long g = (long)g_tc_occ[dev][PREC][wide] * g_tc_nsm[dev];
         grid = (int)(g < work ? g : (work > 0 ? work : 1));
     }
     constexpr int SM = tc_smem<PREC>();
@@ -79,7 +85,7 @@ cudaError_t tc_init(int *blocks_per_sm) {
     if (e == cudaSuccess) e = set_attr<2>(dev);
     if (e == cudaSuccess) e = set_attr<3>(dev);
     if (e == cudaSuccess) e = set_attr<4>(dev);
-    if (e == cudaSuccess) *blocks_per_sm = g_tc_occ[dev][1];
+    if (e == cudaSuccess) *blocks_per_sm = g_tc_occ[dev][1][0];
     return e;
 }
 
