@@ -21,9 +21,13 @@ recomputation, greedy descent to a one-flip minimum checked by enumeration,
 the zero- and high-temperature limits, the tracked replay field);
 the OSPR mean intensity by its closed-form expectation (the arcsine law for
 the signs of Gaussian pairs), to which the time average converges as
-1/sqrt(subframes); the exact WGS trajectory and the adaptive-OSPR sequence
-beyond its first subframe are "parity unpinned" beyond the qualitative and
-structural checks listed there.
+1/sqrt(subframes); whole WGS trajectories by a hand-derived run whose
+hologram is stationary while the weight compounds as sqrt(2)^k, and
+adaptive-OSPR sequences by hand-derived delta targets (exact reproduction at
+the replay centre; off the centre the twin's negative deficit clipped at
+every subframe) -- WGS on general targets and the adaptive deficit's effect on
+general targets beyond those cases rest on the single-step pins and the
+qualitative checks listed there.
 """
 from __future__ import annotations
 

@@ -188,6 +188,62 @@ def test_gs_step_hand_worked_4x4(case):
         assert np.abs(I - expect).max() < 1e-15
 
 
+def test_wgs_run_hand_worked_twin_image():
+    """A whole WGS trajectory derived by hand (binary 4x4, the twin_image case
+    of the golden file): the target's single pixel at replay [2][3] with phase
+    pi/4.  Each iteration's field is w T e^{i arg R} at that pixel only, so h
+    keeps the phases e^{i(pi/4 + pi x/2)} (scaled by w / 4), the hologram stays
+    the golden one and the replay splits equally into the pixel and its twin
+    [2][1]: I = 1/2 at both and MSE 1/32 at every iteration.  The weight there
+    compounds, w_k = w_{k-1} T / sqrt(I) = sqrt(2)^k, and the replay phase
+    stays pi/4 at [2][3], -pi/4 at [2][1] and 0 where R = 0."""
+    t = np.zeros((4, 4), np.float32)
+    t[2, 3] = 1
+    ph = np.zeros((4, 4))
+    ph[2, 3] = np.pi / 4
+    holo = np.array([int(ch) for ch in "0110011001100110"]).reshape(4, 4)
+    for k in (1, 2, 3, 5):
+        run = oracle.gs_run(t, ph, k, kind=oracle.SLM_BINARY, wgs=True)
+        assert np.allclose(run["mse"], 1 / 32, rtol=1e-13, atol=0), run["mse"]
+        assert np.array_equal(run["holo"], holo)
+        w = np.ones((4, 4))
+        w[2, 3] = np.sqrt(2) ** k
+        assert np.abs(run["w"] - w).max() < 1e-13 * w.max()
+        expect = np.zeros((4, 4))
+        expect[2, 3], expect[2, 1] = np.pi / 4, -np.pi / 4
+        assert np.abs(run["phase"] - expect).max() < 1e-14
+        assert np.allclose(run["eff"], 0.5, rtol=1e-14)
+
+
+def test_adaptive_ospr_hand_worked_deltas():
+    """Adaptive OSPR sequences derived by hand on 4x4 binary targets, for any
+    random phases.  A delta at the replay centre is reproduced exactly by every
+    subframe (h is constant, H constant, R = 4 at the centre), so each deficit
+    target equals T and the time average is T^2: MSE 0.  A delta off the centre
+    (replay [2][3]) always splits into itself and its twin [2][1], I = 1/2 at
+    both; the deficit at the twin, (n + 1) 0 - S < 0, is clipped to zero, so
+    every later subframe aims at the same delta, and the time average keeps
+    I = 1/2 at both pixels: MSE 1/32."""
+    for r, c, mse in ((2, 2, 0.0), (2, 3, 1 / 32)):
+        t = np.zeros((4, 4), np.float32)
+        t[r, c] = 1
+        for seed in (3, 11):
+            out = oracle.adaptive_ospr_run(t, 5, seed, 1)
+            assert abs(out["mse"] - mse) < 1e-15, (r, c, seed, out["mse"])
+            expect = np.zeros((4, 4))
+            if (r, c) == (2, 2):
+                expect[2, 2] = 1.0
+            else:
+                expect[2, 3] = expect[2, 1] = 0.5
+            assert np.abs(out["I"] - expect).max() < 1e-15
+            for n in range(5):
+                Tn = oracle.adaptive_target(oracle.prepare_target(t), out["I"] * n, n + 1) if n else None
+                if Tn is not None:
+                    assert np.isfinite(Tn).all() and abs(Tn[r, c] - 1.0) < 1e-15
+                # each subframe's hologram depends on the column only (h has one frequency)
+                assert (out["holo"][n] == out["holo"][n][0]).all()
+
+
 def test_gs_step_delta_target_any_phase():
     rng = np.random.default_rng(0)
     t = np.zeros((8, 8), np.float32)
