@@ -426,7 +426,8 @@ def run_side_workload(args):
         P = torch.from_numpy(synth.init_phases(B, n, n, 7000)).to(dev)
         mse = torch.empty((B, args.iters), dtype=torch.float64, device=dev)
         holo = torch.empty((B, n, n), dtype=torch.uint8, device=dev)
-        plan = hg.Plan(n, n, B, kind, levels, hg.HG_GS, fresnel=c, modulated=True, pipeline=args.pipeline)
+        plan = hg.Plan(n, n, B, kind, levels, hg.HG_GS, fresnel=c, modulated=True, pipeline=args.pipeline,
+                       autotune=args.autotune)
         plan.set_illumination(torch.from_numpy(A).to(dev), None)
         plan.set_roi(torch.from_numpy(roi).to(dev))
         for _ in range(args.warmup):

@@ -411,6 +411,7 @@ cudaError_t ensure_pipe_init(int dev, const PipeOps *o) {
         if (!g_pinited[dev][i]) {
             cudaError_t e = o->init(const_cast<PipeOps *>(o));
             if (e == cudaSuccess) g_pinited[dev][i] = o;
+            else cudaGetLastError();  // a candidate this device cannot run is skipped: clear its error
             return e;
         }
     }
@@ -484,6 +485,7 @@ struct hg_plan_s {
     int tc_blocks = 1, ppt_tc = 0;
     CUtensorMap cmap;                                // field as [chains*ny][2*nx] floats
     CUtensorMap cmap_herm;                           // same field, tiles of the column-pair Hermitian pass
+    CUtensorMap emap;                                // modulated: E as [ny][2*nx] floats, tiles as cmap's
     bool use_herm_col = false;                       // Hermitian loop: column pairs share transforms
     const PipeOps *hops = nullptr;                   // variant providing the column-pair pass
     bool ospr_herm = false;                          // binary OSPR in Hermitian form
@@ -737,12 +739,16 @@ void launch_col_herm(hg_plan p, const ColArgs &a, cudaStream_t s) {
     p->launches++;
 }
 
+int col_blocks(const PipeOps *pc, int role) {
+    return role == COL_GS_MOD ? pc->col_mod_blocks_per_sm : pc->col_blocks_per_sm;
+}
+
 void launch_col_gs(hg_plan p, int role, const ColArgs &a, cudaStream_t s) {
     ProfScope ps(p, s, 1);
     if (p->pcol) {
         const long work = (long)a.items * ((p->nx + p->pcol->col_c - 1) / p->pcol->col_c);
-        p->pcol->col_gs(role, a, pipe_args(p), p->cmap,
-                        grid_for(p->pcol->col_blocks_per_sm, p->nsm, work), s);
+        p->pcol->col_gs(role, a, pipe_args(p), p->cmap, p->emap, grid_for(col_blocks(p->pcol, role), p->nsm, work),
+                        s);
         p->launches++;
     } else {
         launch_col(p, role, a, s);
@@ -1062,6 +1068,24 @@ bool make_cmap(hg_plan p, const PipeOps *pc, CUtensorMap *m) {
                CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
+// The column pass's tensor maps: the field, and for a modulated plan whose
+// variant stages E in shared memory, the illumination with the same boxes
+// (otherwise em repeats m, unused).
+bool make_col_maps(hg_plan p, const PipeOps *pc, CUtensorMap *m, CUtensorMap *em) {
+    if (!make_cmap(p, pc, m)) return false;
+    *em = *m;
+    if (!(p->mod && pc->col_emap)) return true;
+    EncodeTiledFn enc = encode_tiled();
+    if (!enc || !p->illum) return false;
+    const cuuint64_t gdim[2] = {(cuuint64_t)2 * p->nx, (cuuint64_t)p->ny};
+    const cuuint64_t gstride[1] = {(cuuint64_t)p->nx * 8};
+    const cuuint32_t box[2] = {(cuuint32_t)(2 * pc->col_c), (cuuint32_t)pc->col_boxr};
+    const cuuint32_t estr[2] = {1, 1};
+    return enc(em, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, p->illum, gdim, gstride, box, estr,
+               CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
 // Best-of-3 launch time (ms, after one warm-up launch) of one pass variant on
 // the plan's own zeroed buffers, on the private capture stream.
 float time_variant(hg_plan p, const PipeOps *o, bool row, bool herm = false, bool herm_pairs = false) {
@@ -1072,17 +1096,18 @@ float time_variant(hg_plan p, const PipeOps *o, bool row, bool herm = false, boo
     ra.part = nullptr;
     ra.herm = herm;
     ColArgs ca = col_args(p);
-    CUtensorMap m;
+    CUtensorMap m, em;
     if (herm_pairs) {
         if (!o->col_herm || !make_cmap_box(p, o->herm_c, o->herm_boxr, &m)) return 1e30f;
-    } else if (!row && !make_cmap(p, o, &m)) {
+    } else if (!row && !make_col_maps(p, o, &m, &em)) {
         return 1e30f;
     }
+    const int role = p->mod ? COL_GS_MOD : p->kind == HG_SLM_BINARY ? COL_GS_BIN : COL_GS_LVL;
     if (!row && herm) ca.half = ca.half_in = 1;
     const int ppt = row ? row_panels(o, p->ny) : (p->nx + (herm_pairs ? o->herm_c : o->col_c) - 1) /
                                                      (herm_pairs ? o->herm_c : o->col_c);
     const int grid = grid_for(row ? o->row_blocks_per_sm
-                                  : herm_pairs ? o->herm_blocks_per_sm : o->col_blocks_per_sm,
+                                  : herm_pairs ? o->herm_blocks_per_sm : col_blocks(o, role),
                               p->nsm, (long)p->batch * ppt);
     PipeArgs pa = pipe_args(p);
     cudaEvent_t e0, e1;
@@ -1098,7 +1123,7 @@ float time_variant(hg_plan p, const PipeOps *o, bool row, bool herm = false, boo
         cudaEventRecord(e0, s);
         if (row) o->row_iter(ra, pa, grid, s);
         else if (herm_pairs) o->col_herm(ca, pa, m, grid, s);
-        else o->col_gs(p->mod ? COL_GS_MOD : p->kind == HG_SLM_BINARY ? COL_GS_BIN : COL_GS_LVL, ca, pa, m, grid, s);
+        else o->col_gs(role, ca, pa, m, em, grid, s);
         cudaEventRecord(e1, s);
         if (cudaEventSynchronize(e1) != cudaSuccess) break;
         float ms = 0;
@@ -1329,10 +1354,11 @@ hg_status hg_plan_create(hg_plan *out, int ny, int nx, int batch, hg_slm slm, hg
     }
     // Pass variants are chosen (and timed) only once every buffer they touch exists;
     // search plans run the generic passes.  Modulated plans take unpaired TMA-fed rows (the
-    // light leaving the SLM, E e^{iH}, is complex, so no Hermitian symmetry) and the generic
-    // column pass, which measured faster than their TMA-fed one at 1024^2 x 64 (pipeline 1
-    // forces both TMA-fed passes).
-    const bool mod_col_generic = mod && o.pipeline != 1;
+    // light leaving the SLM, E e^{iH}, is complex, so no Hermitian symmetry) and, among the
+    // TMA-fed column passes, only those that stage E in shared memory (the others measured
+    // slower than the generic column pass at 1024^2 x 64); pipeline 1 admits every
+    // TMA-fed column pass.
+    const bool mod_any_col = mod && o.pipeline == 1;
     if (o.pipeline != 0 && !search) {
         // TMA-fed passes: row panels need 16-byte aligned rows of T (nx % 4 == 0);
         // the column tiles need a 16-byte multiple row pitch (nx even).
@@ -1352,10 +1378,10 @@ hg_status hg_plan_create(hg_plan *out, int ny, int nx, int batch, hg_slm slm, hg
         {
             const PipeOps *all[8];
             const int k = pipe_candidates(ny, all, 8);
-            CUtensorMap m;
-            for (int i = 0; i < k && !mod_col_generic; ++i)
-                if (!all[i]->paired && all[i]->col_gs && nx % 2 == 0 &&
-                    ensure_pipe_init(p->dev, all[i]) == cudaSuccess && make_cmap(p, all[i], &m))
+            CUtensorMap m, em;
+            for (int i = 0; i < k; ++i)
+                if (!all[i]->paired && all[i]->col_gs && nx % 2 == 0 && (!mod || mod_any_col || all[i]->col_emap) &&
+                    ensure_pipe_init(p->dev, all[i]) == cudaSuccess && make_col_maps(p, all[i], &m, &em))
                     cc[nc++] = all[i];
         }
         const PipeOps *row = nr ? rc[0] : nullptr, *col = nc ? cc[0] : nullptr;
@@ -1370,7 +1396,7 @@ hg_status hg_plan_create(hg_plan *out, int ny, int nx, int batch, hg_slm slm, hg
                 std::lock_guard<std::mutex> lk(g_tune_mu);
                 for (const TuneEntry &t : g_tune)
                     if (t.dev == p->dev && t.ny == ny && t.nx == nx && t.items == p->nchains &&
-                        t.kind == slm.kind + (mod ? (mod_col_generic ? 24 : 8) : 0)) {
+                        t.kind == slm.kind + (mod ? (mod_any_col ? 8 : 24) : 0)) {
                         row = t.row;
                         col = t.col;
                         cached = true;
@@ -1408,7 +1434,7 @@ hg_status hg_plan_create(hg_plan *out, int ny, int nx, int batch, hg_slm slm, hg
                     if (ms < best) best = ms, row = rc[i];
                 }
                 std::lock_guard<std::mutex> lk(g_tune_mu);
-                g_tune.push_back({p->dev, ny, nx, p->nchains, slm.kind + (mod ? (mod_col_generic ? 24 : 8) : 0), row,
+                g_tune.push_back({p->dev, ny, nx, p->nchains, slm.kind + (mod ? (mod_any_col ? 8 : 24) : 0), row,
                                   col});
             }
         }
@@ -1417,7 +1443,7 @@ hg_status hg_plan_create(hg_plan *out, int ny, int nx, int batch, hg_slm slm, hg
             p->ppt_pipe = row_panels(row, ny);
             if (p->ppt_pipe > p->ppt_max) p->ppt_max = p->ppt_pipe;
         }
-        if (col && make_cmap(p, col, &p->cmap)) p->pcol = col;
+        if (col && make_col_maps(p, col, &p->cmap, &p->emap)) p->pcol = col;
         if (o.pipeline == 1 && (!p->prow || !p->pcol)) return fail(HG_ERR_UNSUPPORTED_SIZE);
         // Hermitian loop: a column-pair pass of the column length, when it is at
         // least as fast as the per-column pass (a forced square candidate keeps

@@ -112,6 +112,17 @@ __device__ __forceinline__ void named_sync(int id, int nthreads) {
 // E terms each), the group total is stored as double by thread 0 and every
 // reduction across panels is done in double.  (Double shuffles or additions
 // here would occupy the FP64 pipe, which is narrow on this GPU.)
+// float -> double without the FP64 pipe: a normal float's biased exponent is
+// raised by 1023 - 127 = 896 and its 23 fraction bits become the top of the
+// 52-bit fraction, which is exact; zero, subnormals, infinities and NaN take
+// the conversion instruction.
+__device__ __forceinline__ double f2d_exact(float x) {
+    const uint32_t u = __float_as_uint(x), m = u & 0x7fffffffu;
+    if (m < 0x00800000u || m >= 0x7f800000u) return (double)x;
+    return __longlong_as_double((long long)((((unsigned long long)(u & 0x80000000u)) << 32) |
+                                            ((((unsigned long long)m) << 29) + (896ull << 52))));
+}
+
 template <int GT, class SYNC>
 __device__ __forceinline__ void group_sum4(float a0, float a1, float a2, float a3, double *red,
                                            double *dst, int gt, SYNC gsync) {
@@ -123,7 +134,7 @@ __device__ __forceinline__ void group_sum4(float a0, float a1, float a2, float a
     if constexpr (GT == 32) {
         if (gt == 0)
 #pragma unroll
-            for (int m = 0; m < NMET; ++m) dst[m] = (double)d[m];
+            for (int m = 0; m < NMET; ++m) dst[m] = f2d_exact(d[m]);
     } else {
         float *redf = reinterpret_cast<float *>(red);
         const int lane = gt & 31, w = gt >> 5;
@@ -133,15 +144,15 @@ __device__ __forceinline__ void group_sum4(float a0, float a1, float a2, float a
         gsync();
         if (gt == 0) {
             // the group's few warp sums in float (one rounding each), then one
-            // conversion: this thread's FP64 work would hold the group's
-            // barrier on the narrow FP64 pipe
+            // exact conversion on the integer pipes: FP64 work here would hold
+            // the group's barrier on the narrow FP64 pipe
             float s[NMET] = {0.f, 0.f, 0.f, 0.f};
 #pragma unroll
             for (int q = 0; q < GT / 32; ++q)
 #pragma unroll
                 for (int m = 0; m < NMET; ++m) s[m] += redf[q * NMET + m];
 #pragma unroll
-            for (int m = 0; m < NMET; ++m) dst[m] = (double)s[m];
+            for (int m = 0; m < NMET; ++m) dst[m] = f2d_exact(s[m]);
         }
         gsync();
     }
@@ -156,12 +167,24 @@ struct RowPipeCfg {
     static constexpr int THREADS = NG * GT;
     static constexpr int SLOT_F = LINES * P::N * 8;
     static constexpr int SLOT_T = LINES * P::N * 4;
-    static constexpr int SLOT = (SLOT_F + SLOT_T + 127) / 128 * 128;
     static constexpr int RED = NG * GW * NMET * 8;
-    static constexpr size_t SMEM = 1024 + (size_t)NG * D * SLOT + RED + NG * D * 8 + 4 * (NG + 1) + 256;
+    static constexpr size_t smem_for(int slot) {
+        return 1024 + (size_t)NG * D * slot + RED + NG * D * 8 + 4 * (NG + 1) + 256;
+    }
+    // region-of-interest rows (1 B/px) come in with the panel when a row is a
+    // whole number of 16-byte units and the larger ring still fits in 227 KB;
+    // otherwise they are read from global memory
+    static constexpr int SLOT_FT = (SLOT_F + SLOT_T + 127) / 128 * 128;
+    static constexpr int SLOT_FTR = (SLOT_F + SLOT_T + LINES * P::N + 127) / 128 * 128;
+    static constexpr bool ROI_SM = P::N % 16 == 0 && smem_for(SLOT_FTR) <= 227 * 1024;
+    static constexpr int SLOT = ROI_SM ? SLOT_FTR : SLOT_FT;
+    static constexpr size_t SMEM = smem_for(SLOT);
 };
 
-template <class P, int LINES, int NG, int D, int SWZ>
+// GEN: the modulated plans' row pass (a.gen: eight metric sums, region of
+// interest, no weights, a window that covers the field); otherwise the plain
+// GS / WGS / LT pass (four sums, no region of interest).
+template <class P, int LINES, int NG, int D, int SWZ, bool GEN>
 __global__ void __launch_bounds__(RowPipeCfg<P, LINES, NG, D, SWZ>::THREADS, 1)
     k_row_pipe(const RowArgs a, const PipeArgs pa) {
     using Cfg = RowPipeCfg<P, LINES, NG, D, SWZ>;
@@ -194,16 +217,18 @@ __global__ void __launch_bounds__(RowPipeCfg<P, LINES, NG, D, SWZ>::THREADS, 1)
         else named_sync(1 + g, GT);
     };
     auto job = [&](int k) { return (int)blockIdx.x + (g + NG * k) * (int)gridDim.x; };
-    auto issue = [&](int k) {  // copy the group's k-th panel (field rows + target rows)
+    auto issue = [&](int k) {  // copy the group's k-th panel (field, target and ROI rows)
         const int j = job(k);
         if (j >= J || j == pa.drop_job) return;
         const int item = j / ppt, pan = j - item * ppt, y0 = pan * LINES;
         const int nl = min(LINES, ny - y0);
         const uint32_t bf = (uint32_t)(nl * NX * 8), bt = (uint32_t)(nl * NX * 4);
+        const uint32_t br = GEN && Cfg::ROI_SM && a.roi ? (uint32_t)(nl * NX) : 0u;
         unsigned char *sl = ring + (size_t)(k % D) * Cfg::SLOT;
-        mbar_expect_tx(gfull + k % D, bf + bt);
+        mbar_expect_tx(gfull + k % D, bf + bt + br);
         bulk_g2s(sl, a.field + ((size_t)item * ny + y0) * NX, bf, gfull + k % D);
         bulk_g2s(sl + Cfg::SLOT_F, a.T + ((size_t)item * ny + y0) * NX, bt, gfull + k % D);
+        if (br) bulk_g2s(sl + Cfg::SLOT_F + Cfg::SLOT_T, a.roi + (size_t)y0 * NX, br, gfull + k % D);
     };
     auto drain = [&](int k0, int k1) {
         for (int q = k0; q < k1; ++q) {
@@ -242,8 +267,19 @@ __global__ void __launch_bounds__(RowPipeCfg<P, LINES, NG, D, SWZ>::THREADS, 1)
             v[e] = sf[t + TL * e];
         });
         line_fft<P, -1, 1, LAY>(v, sf, a.tw, t, gsync);
-        float *wr = a.w ? a.w + ((size_t)item * ny + (act ? y : ny - 1)) * NX : nullptr;
-        const uint8_t *roir = a.roi ? a.roi + (size_t)(act ? y : ny - 1) * NX : nullptr;
+        float *wr = !GEN && a.w ? a.w + ((size_t)item * ny + (act ? y : ny - 1)) * NX : nullptr;
+        // region-of-interest flags of this thread's E samples, one bit each
+        static_assert(E <= 32, "one flag bit per sample");
+        uint32_t inm = 0xffffffffu;
+        if (GEN && a.roi) {
+            const uint8_t *roir = Cfg::ROI_SM ? sl + Cfg::SLOT_F + Cfg::SLOT_T + line * NX
+                                              : a.roi + (size_t)(act ? y : ny - 1) * NX;
+            inm = 0u;
+            static_for<0, E>([&](auto ec) {
+                constexpr int e = decltype(ec)::value;
+                inm |= (roir[t + TL * e] != 0 ? 1u : 0u) << e;
+            });
+        }
         float acc0 = 0.f, acc1 = 0.f, acc2 = 0.f, acc3 = 0.f;
         float acc4 = 0.f, acc5 = 0.f, acc6 = 0.f, acc7 = 0.f;
         static_for<0, E>([&](auto ec) {
@@ -254,8 +290,8 @@ __global__ void __launch_bounds__(RowPipeCfg<P, LINES, NG, D, SWZ>::THREADS, 1)
             const float m2 = fmaf(r.x, r.x, r.y * r.y);
             const float rs = m2 > 0.f ? rsqrtf(m2) : 0.f;
             const float e2 = m2 * a.invN;
-            const bool in = !roir || roir[x] != 0;
-            if (a.gen) {  // modulated plan: the eight sums of the generic row pass
+            const bool in = (inm >> e) & 1u;
+            if constexpr (GEN) {  // modulated plan: the eight sums of the generic row pass
                 if (act) {
                     acc5 += e2;
                     if (in) {
@@ -286,8 +322,13 @@ __global__ void __launch_bounds__(RowPipeCfg<P, LINES, NG, D, SWZ>::THREADS, 1)
                 if (Tv > 0.f && m2 > 0.f) wv = wv * Tv * (a.NN * rs);
                 if (act) wr[x] = wv;
             }
-            const float gm = (a.lt_amp > 0.f ? a.lt_amp : 1.f) * Tv * wv;
-            if (a.lt_amp > 0.f && (!in || !lt_in(a, y, x))) v[e] = r;  // outside the window / ROI: left free
+            // a modulated plan scales T by its lt_amp (the replay energy of a
+            // unit-modulus hologram) with a window that covers the field, and
+            // leaves pixels outside the region of interest free; LT scales T
+            // the same way and leaves pixels outside its window free
+            const bool lt = GEN || a.lt_amp > 0.f;
+            const float gm = (lt ? a.lt_amp : 1.f) * Tv * wv;
+            if (lt && (!in || (!GEN && !lt_in(a, y, x)))) v[e] = r;
             else v[e] = m2 > 0.f ? make_float2(gm * r.x * rs, gm * r.y * rs) : make_float2(gm, 0.f);
         });
         line_fft<P, +1, 1, LAY>(v, sf, a.tw, t, gsync);
@@ -301,7 +342,7 @@ __global__ void __launch_bounds__(RowPipeCfg<P, LINES, NG, D, SWZ>::THREADS, 1)
             });
         }
         if (a.part) {
-            if (a.gen) {
+            if constexpr (GEN) {
                 double *dst = a.part + ((size_t)item * ppt + pan) * NMET_GEN;
                 group_sum4<GT>(acc0, acc1, acc2, acc3, red + (size_t)g * Cfg::GW * NMET, dst, gt, gsync);
                 group_sum4<GT>(acc4, acc5, acc6, acc7, red + (size_t)g * Cfg::GW * NMET, dst + NMET, gt, gsync);
@@ -856,31 +897,44 @@ __global__ void __launch_bounds__(PairPipeCfg<P, NG, D, SWZ>::THREADS, MINB)
 }
 
 // ----------------------------------------------------------- column pass
-template <class P, int C, int NG, int D, int SWZ, int BOXR>
+template <class P, int C, int NG, int D, int SWZ, int BOXR, bool EB = false>
 struct ColPipeCfg {
     static constexpr int GT = P::TL * C;
     static_assert(GT % 32 == 0, "column group must be whole warps");
     static_assert(P::N % BOXR == 0 && BOXR <= 256, "box rows must tile the column");
     static constexpr int THREADS = NG * GT;
     static constexpr int SLOT = P::N * C * 8;
-    static constexpr size_t SMEM = 1024 + (size_t)NG * D * SLOT + NG * D * 8 + 4 * (NG + 1) + 256;
+    // EB: each group also holds the illumination tile of its panel
+    static constexpr int NE = EB ? NG : 0;
+    static constexpr size_t SMEM = 1024 + (size_t)(NG * D + NE) * SLOT + (NG * D + NE) * 8 + 4 * (NG + 1) + 256;
 };
 
-template <class P, int ROLE, int C, int NG, int D, int SWZ, int BOXR>
-__global__ void __launch_bounds__(ColPipeCfg<P, C, NG, D, SWZ, BOXR>::THREADS, 1)
-    k_col_pipe(const ColArgs a, const PipeArgs pa, const __grid_constant__ CUtensorMap tmap) {
-    using Cfg = ColPipeCfg<P, C, NG, D, SWZ, BOXR>;
+// Column pass of the GS loop (binary, L-level or modulated quantiser): each
+// group of TL x C threads transforms C columns of one target per job, with the
+// panels brought in by tensor copies through a ring of D slots.  EB (modulated
+// plans): the illumination tile of the job's panel (C columns x all rows of E,
+// a second tensor map over [ny][nx] float2) is copied into the group's own
+// buffer at the start of the job, so the quantiser reads E from shared memory;
+// the copy overlaps the inverse transform.
+template <class P, int ROLE, int C, int NG, int D, int SWZ, int BOXR, int MINB = 1, bool EB = false>
+__global__ void __launch_bounds__(ColPipeCfg<P, C, NG, D, SWZ, BOXR, EB>::THREADS, MINB)
+    k_col_pipe(const ColArgs a, const PipeArgs pa, const __grid_constant__ CUtensorMap tmap,
+               const __grid_constant__ CUtensorMap emap) {
+    static_assert(!EB || ROLE == COL_GS_MOD, "illumination tiles serve the modulated quantiser");
+    using Cfg = ColPipeCfg<P, C, NG, D, SWZ, BOXR, EB>;
     using LAY = Swz<SWZ>;
     constexpr int TL = P::TL, E = P::E, NY = P::N, GT = Cfg::GT;
     extern __shared__ unsigned char smraw[];
     unsigned char *base = smraw + ((1024 - (smem_addr(smraw) & 1023)) & 1023);
-    uint64_t *full = reinterpret_cast<uint64_t *>(base + (size_t)NG * D * Cfg::SLOT);
-    volatile int *flags = reinterpret_cast<volatile int *>(full + NG * D);
+    unsigned char *ebuf = base + (size_t)NG * D * Cfg::SLOT;
+    uint64_t *full = reinterpret_cast<uint64_t *>(ebuf + (size_t)Cfg::NE * Cfg::SLOT);
+    uint64_t *ebar = full + NG * D;
+    volatile int *flags = reinterpret_cast<volatile int *>(ebar + Cfg::NE);
     volatile int *abort = flags + NG;
 
     const int tid = threadIdx.x;
     if (tid == 0) {
-        for (int i = 0; i < NG * D; ++i) mbar_init(full + i, 1);
+        for (int i = 0; i < NG * D + Cfg::NE; ++i) mbar_init(full + i, 1);
         *abort = 0;
         fence_mbar_init();
     }
@@ -943,6 +997,18 @@ __global__ void __launch_bounds__(ColPipeCfg<P, C, NG, D, SWZ, BOXR>::THREADS, 1
         const int item = j / ppt, pan = j - item * ppt;
         const int x = pan * C + c;
         const bool act = x < nx;
+        const float2 *se = reinterpret_cast<const float2 *>(ebuf + (size_t)g * Cfg::SLOT);
+        if constexpr (EB) {
+            // the previous job's readers of this buffer passed the group
+            // barriers of its forward transform
+            if (gt == 0) {
+                mbar_expect_tx(ebar + g, (uint32_t)(NY * C * 8));
+#pragma unroll 1
+                for (int r = 0; r < NY / BOXR; ++r)
+                    tma_load_2d(ebuf + (size_t)g * Cfg::SLOT + (size_t)r * BOXR * C * 8, &emap, 2 * pan * C,
+                                r * BOXR, ebar + g);
+            }
+        }
         float2 *sl = reinterpret_cast<float2 *>(ring + (size_t)(k % D) * Cfg::SLOT);
         float2 v[E];
         static_for<0, E>([&](auto ec) {
@@ -956,6 +1022,22 @@ __global__ void __launch_bounds__(ColPipeCfg<P, C, NG, D, SWZ, BOXR>::THREADS, 1
             }
         });
         line_fft<P, +1, C, LAY>(v, sl + c, a.tw, t, gsync);
+        if constexpr (EB) {
+            if (gt == 0) {
+                bool ok = !*abort && mbar_wait(ebar + g, k & 1, pa.wait_ns, abort);
+                if (!ok) {
+                    atomicOr(pa.err, ERR_TIMEOUT_BIT);
+                    *abort = 1;
+                    mbar_wait(ebar + g, k & 1, pa.wait_ns, nullptr);  // the copy still lands here
+                }
+                flags[g] = ok;
+            }
+            gsync();
+            if (!flags[g]) {
+                if (gt == 0) drain(k + 1, k + D);
+                break;
+            }
+        }
         const size_t base_o = (size_t)item * NY * nx;
         static_for<0, E>([&](auto ec) {
             constexpr int e = decltype(ec)::value;
@@ -965,7 +1047,8 @@ __global__ void __launch_bounds__(ColPipeCfg<P, C, NG, D, SWZ, BOXR>::THREADS, 1
             float2 ph;
             if constexpr (ROLE == COL_GS_MOD) {
                 // as the generic column pass: the level nearest h / E, light E x level
-                const float2 E = __ldg(a.illum + (size_t)(t + TL * e) * nx + (act ? x : nx - 1));
+                const float2 E = EB ? se[(t + TL * e) * C + c]
+                                    : __ldg(a.illum + (size_t)(t + TL * e) * nx + (act ? x : nx - 1));
                 const float hr = fmaf(h.x, E.x, h.y * E.y), hi = fmaf(h.y, E.x, -h.x * E.y);
                 if (a.kind == 2) {
                     const float e2 = fmaf(E.x, E.x, E.y * E.y);
@@ -1162,11 +1245,13 @@ struct PipeOps {
     int row_threads, col_threads, col_c, col_boxr, row_lines;
     size_t row_smem, col_smem;
     int row_blocks_per_sm, col_blocks_per_sm;
+    int col_mod_blocks_per_sm;  // CTAs per SM of the modulated column pass
+    int col_emap;               // the modulated column pass reads E through a tensor map
     int paired;  // row pass is k_row_pipe_pair (binary SLM, even ny, half-row column stores)
     cudaError_t (*init)(PipeOps *self);
     void (*row_iter)(const RowArgs &a, const PipeArgs &pa, int grid, cudaStream_t s);  // may be null
-    void (*col_gs)(int role, const ColArgs &a, const PipeArgs &pa, const CUtensorMap &m, int grid,
-                   cudaStream_t s);  // may be null
+    void (*col_gs)(int role, const ColArgs &a, const PipeArgs &pa, const CUtensorMap &m, const CUtensorMap &em,
+                   int grid, cudaStream_t s);  // may be null
     // column pass of the Hermitian binary loop, two columns per transform (may be null);
     // its tensor map has boxes of herm_c columns x herm_boxr rows
     void (*col_herm)(const ColArgs &a, const PipeArgs &pa, const CUtensorMap &m, int grid, cudaStream_t s);
@@ -1183,54 +1268,65 @@ struct PipeOps {
 
 // Row pass: plan P, LINES rows per group, NGR groups, ring depth DR, swizzle
 // SWZR (LINES == 0: no TMA-fed row pass).  Column pass: plan PC, C columns per
-// group, NGC groups, ring depth DC, swizzle SWZC, BOXR rows per tensor copy.
+// group, NGC groups, ring depth DC, swizzle SWZC, BOXR rows per tensor copy,
+// at least MINBC CTAs per SM (the register budget); EBC: the modulated
+// quantiser reads the illumination from a shared-memory tile per group.
 template <class P, int LINES, int NGR, int DR, int SWZR, class PC, int C, int NGC, int DC, int SWZC,
-          int BOXR>
+          int BOXR, int MINBC = 1, bool EBC = false>
 struct PipeImpl {
     using CC = ColPipeCfg<PC, C, NGC, DC, SWZC, BOXR>;
+    using CCM = ColPipeCfg<PC, C, NGC, DC, SWZC, BOXR, EBC>;  // the modulated pass
+    template <int ROLE, bool EB = false>
+    static constexpr auto col_kernel() { return k_col_pipe<PC, ROLE, C, NGC, DC, SWZC, BOXR, MINBC, EB>; }
     static cudaError_t init(PipeOps *self) {
         cudaError_t e = cudaSuccess;
-        int rb = 1, cb = 0;
+        int rb = 1, cb = 0, mb = 0;
         if constexpr (LINES > 0) {
             using RC = RowPipeCfg<P, LINES, NGR, DR, SWZR>;
-            e = cudaFuncSetAttribute((const void *)k_row_pipe<P, LINES, NGR, DR, SWZR>,
-                                     cudaFuncAttributeMaxDynamicSharedMemorySize, (int)RC::SMEM);
+            for (const void *f : {(const void *)k_row_pipe<P, LINES, NGR, DR, SWZR, false>,
+                                  (const void *)k_row_pipe<P, LINES, NGR, DR, SWZR, true>})
+                if (e == cudaSuccess)
+                    e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)RC::SMEM);
             if (e == cudaSuccess)
                 e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-                    &rb, k_row_pipe<P, LINES, NGR, DR, SWZR>, RC::THREADS, RC::SMEM);
+                    &rb, k_row_pipe<P, LINES, NGR, DR, SWZR, false>, RC::THREADS, RC::SMEM);
         }
+        for (const void *f : {(const void *)col_kernel<COL_GS_BIN>(), (const void *)col_kernel<COL_GS_LVL>()})
+            if (e == cudaSuccess)
+                e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)CC::SMEM);
         if (e == cudaSuccess)
-            e = cudaFuncSetAttribute((const void *)k_col_pipe<PC, COL_GS_BIN, C, NGC, DC, SWZC, BOXR>,
-                                     cudaFuncAttributeMaxDynamicSharedMemorySize, (int)CC::SMEM);
+            e = cudaFuncSetAttribute((const void *)col_kernel<COL_GS_MOD, EBC>(),
+                                     cudaFuncAttributeMaxDynamicSharedMemorySize, (int)CCM::SMEM);
         if (e == cudaSuccess)
-            e = cudaFuncSetAttribute((const void *)k_col_pipe<PC, COL_GS_LVL, C, NGC, DC, SWZC, BOXR>,
-                                     cudaFuncAttributeMaxDynamicSharedMemorySize, (int)CC::SMEM);
+            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&cb, col_kernel<COL_GS_BIN>(), CC::THREADS,
+                                                              CC::SMEM);
         if (e == cudaSuccess)
-            e = cudaFuncSetAttribute((const void *)k_col_pipe<PC, COL_GS_MOD, C, NGC, DC, SWZC, BOXR>,
-                                     cudaFuncAttributeMaxDynamicSharedMemorySize, (int)CC::SMEM);
-        if (e == cudaSuccess)
-            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-                &cb, k_col_pipe<PC, COL_GS_BIN, C, NGC, DC, SWZC, BOXR>, CC::THREADS, CC::SMEM);
+            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&mb, col_kernel<COL_GS_MOD, EBC>(), CCM::THREADS,
+                                                              CCM::SMEM);
         if (e != cudaSuccess) return e;
-        if (rb < 1 || cb < 1) return cudaErrorInvalidConfiguration;
+        if (rb < 1 || cb < 1 || mb < 1) return cudaErrorInvalidConfiguration;
         self->row_blocks_per_sm = rb;
         self->col_blocks_per_sm = cb;
+        self->col_mod_blocks_per_sm = mb;
         return cudaSuccess;
     }
     static void row_iter(const RowArgs &a, const PipeArgs &pa, int grid, cudaStream_t s) {
         if constexpr (LINES > 0) {
             using RC = RowPipeCfg<P, LINES, NGR, DR, SWZR>;
-            k_row_pipe<P, LINES, NGR, DR, SWZR><<<grid, RC::THREADS, RC::SMEM, s>>>(a, pa);
+            if (a.gen) k_row_pipe<P, LINES, NGR, DR, SWZR, true><<<grid, RC::THREADS, RC::SMEM, s>>>(a, pa);
+            else k_row_pipe<P, LINES, NGR, DR, SWZR, false><<<grid, RC::THREADS, RC::SMEM, s>>>(a, pa);
         }
     }
-    static void col_gs(int role, const ColArgs &a, const PipeArgs &pa, const CUtensorMap &m, int grid,
-                       cudaStream_t s) {
+    // em: the illumination's tensor map (boxes as the field's), read by the
+    // modulated pass of an EBC variant
+    static void col_gs(int role, const ColArgs &a, const PipeArgs &pa, const CUtensorMap &m, const CUtensorMap &em,
+                       int grid, cudaStream_t s) {
         if (role == COL_GS_BIN)
-            k_col_pipe<PC, COL_GS_BIN, C, NGC, DC, SWZC, BOXR><<<grid, CC::THREADS, CC::SMEM, s>>>(a, pa, m);
+            col_kernel<COL_GS_BIN>()<<<grid, CC::THREADS, CC::SMEM, s>>>(a, pa, m, m);
         else if (role == COL_GS_MOD)
-            k_col_pipe<PC, COL_GS_MOD, C, NGC, DC, SWZC, BOXR><<<grid, CC::THREADS, CC::SMEM, s>>>(a, pa, m);
+            col_kernel<COL_GS_MOD, EBC>()<<<grid, CCM::THREADS, CCM::SMEM, s>>>(a, pa, m, em);
         else
-            k_col_pipe<PC, COL_GS_LVL, C, NGC, DC, SWZC, BOXR><<<grid, CC::THREADS, CC::SMEM, s>>>(a, pa, m);
+            col_kernel<COL_GS_LVL>()<<<grid, CC::THREADS, CC::SMEM, s>>>(a, pa, m, m);
     }
     static PipeOps make(const char *name) {
         PipeOps o{};
@@ -1240,6 +1336,7 @@ struct PipeImpl {
         o.col_c = C;
         o.col_boxr = BOXR;
         o.col_smem = CC::SMEM;
+        o.col_emap = EBC;
         o.row_lines = LINES;
         if constexpr (LINES > 0) {
             using RC = RowPipeCfg<P, LINES, NGR, DR, SWZR>;
@@ -1343,6 +1440,7 @@ struct PairedOps {
         if (rb < 1) return cudaErrorInvalidConfiguration;
         self->row_blocks_per_sm = rb;
         self->col_blocks_per_sm = COL->col_blocks_per_sm;
+        self->col_mod_blocks_per_sm = COL->col_mod_blocks_per_sm;
         self->herm_blocks_per_sm = hb;
         if (hb < 1) self->col_herm = nullptr;
         return cudaSuccess;
@@ -1379,6 +1477,7 @@ struct WithHerm {
         if (e != cudaSuccess) return e;
         self->row_blocks_per_sm = BASE->row_blocks_per_sm;
         self->col_blocks_per_sm = BASE->col_blocks_per_sm;
+        self->col_mod_blocks_per_sm = BASE->col_mod_blocks_per_sm;
         self->herm_blocks_per_sm = hb;
         if (hb < 1) self->col_herm = nullptr;
         return cudaSuccess;

@@ -97,7 +97,9 @@ def run_gpu(c, t, ph0, iters, amp, ph, roi, f32, pipe=-1):
         ev = plan.evaluate(holo, T)
         plan.sync()
         assert "pair" not in hg.hg_plan_variant(plan.h, 0)
-        want = {0: 0, 1: 3, -1: 1 if nx >= 256 else 0}[pipe]  # auto: TMA-fed rows of >= 256 samples
+        # auto: TMA-fed rows of >= 256 samples; TMA-fed columns where a column pass
+        # that stages E exists (1024 samples)
+        want = {0: 0, 1: 3, -1: (1 if nx >= 256 else 0) | (2 if ny == 1024 else 0)}[pipe]
         assert hg.hg_pipelined(plan.h) == want, (hg.hg_pipelined(plan.h), want)
         return holo.cpu().numpy(), mse.cpu().numpy(), met, ev.cpu().numpy()
     finally:
@@ -268,6 +270,24 @@ def test_modulated_loop_step_from_oracle_state(c):
     relative L2 1e-5); H_{k+1} bit-exact except decision-boundary pixels; the
     column pass's field against the column DFT of E e^{iH_{k+1}} of the GPU's
     own hologram (relative L2 1e-5)."""
+    loop_step_case(c, {}, (0, 2))
+
+
+MOD_1024 = [(1024, 1024, hg.HG_SLM_BINARY, 2, 0.002, "gauss", "disc"),
+            (1024, 1024, hg.HG_SLM_LLEVEL, 8, 0.002, "gauss+tilt", "rect")]
+
+
+@pytest.mark.parametrize("cand", range(4))
+@pytest.mark.parametrize("c", MOD_1024, ids=case_id)
+def test_modulated_loop_step_every_pipelined_variant(c, cand):
+    """The same loop step at 1024^2 on each unpaired TMA-fed row and column
+    candidate, forced in turn: three that read E from global memory (panels
+    of 8 columns) and the one the autotuner picks from for modulated plans,
+    which stages E per group in shared memory (panels of 4 columns)."""
+    loop_step_case(c, dict(pipeline=1, autotune=2 + cand), (0,))
+
+
+def loop_step_case(c, plan_kw, ks):
     ny, nx, kind, levels = c[:4]
     if kind == hg.HG_SLM_AMPLITUDE and levels != 2:
         pytest.skip("boundary rule stated for phase and binary amplitude SLMs")
@@ -276,12 +296,15 @@ def test_modulated_loop_step_from_oracle_state(c):
     batch, N = 2, ny * nx
     t = synth.targets(batch, ny, nx, 5200)
     ph0 = synth.init_phases(batch, ny, nx, 5200)
-    plan = hg.Plan(ny, nx, batch, kind, levels, hg.HG_GS, modulated=True, fresnel=f32)
+    plan = hg.Plan(ny, nx, batch, kind, levels, hg.HG_GS, modulated=True, fresnel=f32, **plan_kw)
     try:
+        if plan_kw:
+            assert hg.hg_pipelined(plan.h) == 3
+        print("variants", hg.hg_plan_variant(plan.h, 0), hg.hg_plan_variant(plan.h, 1))
         plan.set_illumination(None if amp is None else torch.from_numpy(amp).to(DEV),
                               None if ph is None else torch.from_numpy(ph).to(DEV))
         plan.set_roi(None if roi is None else torch.from_numpy(roi).to(DEV))
-        for k in (0, 2):
+        for k in ks:
             runs = [oracle.modulated_run(t[b], ph0[b].astype(np.float64), k + 1, ok, levels, E=E, roi=roi)
                     for b in range(batch)]
             holos = np.stack([r["holo"] for r in runs]).astype(np.uint8)
