@@ -137,9 +137,11 @@ typedef struct {
                           the energy on the target's support over all replay
                           energy.  GS only (not precision > 0), no
                           hg_debug_step, else HG_ERR_INVALID_ARG.  TMA-fed
-                          row passes without paired rows where the size has them
-                          and the generic column pass (pipeline 0: generic
-                          passes only; 1: both TMA-fed).  Default 0. */
+                          row passes without paired rows where the size has them;
+                          a TMA-fed column pass where the size has one that
+                          stages E in shared memory, else the generic one
+                          (pipeline 0: generic passes only; 1: both TMA-fed).
+                          Default 0. */
     float fresnel;     /* Fresnel (mid-field) hologram, Section 2: the SLM-plane
                           field gains the quadratic phase fresnel * ((x - nx/2)^2
                           + (y - ny/2)^2) radians (pi dx^2 / (lambda z) for
@@ -149,6 +151,12 @@ typedef struct {
     float sa_temp;     /* SA: initial temperature relative to the initial guess's
                           MSE (> 0, default 1e-3) */
     float sa_cool;     /* SA: temperature factor per sweep, in (0, 1] (default 0.9) */
+    int host_chunks;   /* hg_run with host buffers (GS, WGS, LT, modulated): the batch
+                          runs in this many chunks, one chunk's copies overlapping
+                          another's iterations, with results identical to a
+                          whole-batch run; 0 (default) picks up to 4 chunks of at
+                          least 2^23 pixels each, 1 copies the whole batch first;
+                          >= 0 */
 } hg_opts;
 
 /* sizeof(hg_opts) as this library was built: a binding that lays the
@@ -158,7 +166,7 @@ size_t hg_opts_size(void);
 
 /* Fills *opts with the defaults: stream NULL, seed 0, subframes 24, lt_start
  * 0.25, lt_grow 10, modulated 0, fresnel 0, amp_clip 2, sa_temp 1e-3, sa_cool 0.9,
- * precision 0, use_graph 1, pipeline -1, autotune 1. */
+ * precision 0, use_graph 1, pipeline -1, autotune 1, host_chunks 0. */
 void hg_opts_default(hg_opts *opts);
 
 /* 1 if a line of n samples (a row of nx or a column of ny) has a compiled

@@ -533,6 +533,16 @@ struct hg_plan_s {
     int g_iters = -1;
     double *g_part = nullptr;
     char vname[2][128] = {};
+    // hg_run with host buffers: the batch runs as chunks, each a view of this
+    // plan (its own batch size, pointers into this plan's per-target buffers,
+    // its own loop graph), so that one chunk's copies overlap another's
+    // iterations; the copies go on two streams of their own
+    bool is_view = false;
+    int item0 = 0;  // a view: index of its first target in the plan's batch (Philox counters)
+    int host_chunks = 0;
+    std::vector<hg_plan_s *> views;
+    cudaStream_t h2d_stream = nullptr, d2h_stream = nullptr;
+    std::vector<cudaEvent_t> chunk_ev;  // per chunk: inputs copied, iterations done
 };
 
 namespace {
@@ -619,6 +629,7 @@ RowArgs row_args(hg_plan p) {
     a.seed_lo = (uint32_t)p->seed;
     a.seed_hi = (uint32_t)(p->seed >> 32);
     a.stream_id = 1;
+    a.item0 = p->item0;
     a.tw = p->twx;
     const double N = (double)p->npx;
     a.invN = (float)(1.0 / N);
@@ -1154,6 +1165,146 @@ struct DevGuard {
     }
 };
 
+// Chunks of a run with host buffers: 1 (the whole batch at once) for OSPR,
+// search, profiled plans and single targets; else opts.host_chunks, or (0)
+// up to 4 while every chunk keeps at least 2^23 pixels, so that each pass
+// still fills the GPU.
+int host_chunk_count(hg_plan p) {
+    if (is_ospr(p->algo) || is_search(p->algo) || p->prof_on || p->batch < 2) return 1;
+    long long k = p->host_chunks;
+    if (k == 0) k = std::min<long long>(4, ((long long)p->npx * p->batch) >> 23);
+    return (int)std::max<long long>(1, std::min<long long>(k, p->batch));
+}
+
+// A view of targets [first, first + count) of p: p's passes, tensor-map boxes
+// and settings on pointers into p's per-target buffers (field, prepared
+// targets, weights, prep partials, scales).  Its metric partials and metrics
+// are pointed into p's before each run; it owns only its loop graph.
+hg_status make_view(hg_plan p, int first, int count, hg_plan *out) {
+    hg_plan_s *v = new (std::nothrow) hg_plan_s(*p);
+    if (!v) return HG_ERR_OOM;
+    v->is_view = true;
+    v->item0 = p->item0 + first;
+    v->views.clear();
+    v->chunk_ev.clear();
+    v->prof_ev.clear();
+    v->prof_kind.clear();
+    v->prof_on = false;
+    v->prof_used = 0;
+    v->h2d_stream = v->d2h_stream = nullptr;
+    v->batch = v->nchains = count;
+    const size_t off = (size_t)first * p->npx;
+    v->field = p->field + off;
+    v->tf = p->tf + off;
+    v->w = p->w ? p->w + off : nullptr;
+    v->sum_part = p->sum_part + (size_t)first * PREP_BLOCKS;
+    v->scale = p->scale + first;
+    v->part = nullptr;
+    v->part_iters = 0;
+    v->metrics = nullptr;
+    v->metrics_iters = 0;
+    v->stage = nullptr;
+    v->stage_bytes = 0;
+    v->gexec = nullptr;
+    v->g_iters = -1;
+    v->g_part = nullptr;
+    v->ev_part = nullptr;
+    v->ev_buf = nullptr;
+    v->rbuf = nullptr;
+    v->sholo = nullptr;
+    v->acc = nullptr;
+    v->holo_tmp = nullptr;
+    v->launches = 0;
+    bool ok = true;
+    if (v->pcol) ok = make_col_maps(v, v->pcol, &v->cmap, &v->emap);
+    if (ok && v->use_herm_col && v->hops) ok = make_cmap_box(v, v->hops->herm_c, v->hops->herm_boxr, &v->cmap_herm);
+    if (!ok) {
+        delete v;
+        return HG_ERR_CUDA;
+    }
+    *out = v;
+    return HG_OK;
+}
+
+// hg_run with host buffers in K chunks: chunk c's inputs are copied on the
+// H2D stream while chunk c - 1 iterates on the plan's stream, and its outputs
+// are copied back on the D2H stream while chunk c + 1 iterates.  Every chunk
+// runs the same kernels on its targets as a whole-batch run, so holograms,
+// MSE and metrics are identical.  d_* point into the staging buffer (host
+// sides) or at the caller's device buffers.
+hg_status run_chunked(hg_plan p, int K, const float *target, const float *d_t, const float *init_phase,
+                      const float *d_ph, int iters, uint8_t *holo_out, uint8_t *d_ho, double *mse_out,
+                      double *d_mo) {
+    const int cs = (p->batch + K - 1) / K;
+    K = (p->batch + cs - 1) / cs;
+    hg_status st;
+    if ((int)p->views.size() != K || p->views[0]->batch != cs) {
+        for (hg_plan v : p->views) hg_plan_destroy(v);
+        p->views.clear();
+        for (int c = 0; c < K; ++c) {
+            hg_plan v = nullptr;
+            if ((st = make_view(p, c * cs, std::min(cs, p->batch - c * cs), &v)) != HG_OK) return st;
+            p->views.push_back(v);
+        }
+    }
+    for (cudaStream_t *cs_ : {&p->h2d_stream, &p->d2h_stream})
+        if (!*cs_) HG_CK(cudaStreamCreateWithFlags(cs_, cudaStreamNonBlocking));
+    while ((int)p->chunk_ev.size() < 2 * K + 1) {
+        cudaEvent_t e;
+        HG_CK(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+        p->chunk_ev.push_back(e);
+    }
+    cudaEvent_t *ev_in = p->chunk_ev.data(), *ev_done = ev_in + K, ev_start = ev_in[2 * K];
+    // the copies follow whatever the plan's stream already holds
+    HG_CK(cudaEventRecord(ev_start, p->stream));
+    HG_CK(cudaStreamWaitEvent(p->h2d_stream, ev_start, 0));
+    HG_CK(cudaStreamWaitEvent(p->d2h_stream, ev_start, 0));
+    const size_t npx = p->npx;
+    for (int c = 0; c < K; ++c) {
+        const size_t b0 = (size_t)c * cs, nb = p->views[c]->batch;
+        if (d_t != target)
+            HG_CK(cudaMemcpyAsync((void *)(d_t + b0 * npx), target + b0 * npx, sizeof(float) * nb * npx,
+                                  cudaMemcpyHostToDevice, p->h2d_stream));
+        if (d_ph && d_ph != init_phase)
+            HG_CK(cudaMemcpyAsync((void *)(d_ph + b0 * npx), init_phase + b0 * npx, sizeof(float) * nb * npx,
+                                  cudaMemcpyHostToDevice, p->h2d_stream));
+        HG_CK(cudaEventRecord(ev_in[c], p->h2d_stream));
+    }
+    int launches = 0;
+    for (int c = 0; c < K; ++c) {
+        hg_plan v = p->views[c];
+        const size_t b0 = (size_t)c * cs, nb = v->batch;
+        v->part = p->part;  // the chunks run one after another on the plan's stream
+        v->part_iters = p->part_iters;
+        v->metrics = p->metrics + b0 * iters * NMET;
+        v->metrics_iters = iters;
+        v->weights_preset = p->weights_preset;
+        v->wait_ns = p->wait_ns;
+        v->drop_job = p->drop_job;
+        HG_CK(cudaStreamWaitEvent(p->stream, ev_in[c], 0));
+        v->launches = 0;
+        if ((st = enqueue_run(v, d_t + b0 * npx, d_ph ? d_ph + b0 * npx : nullptr, iters,
+                              d_ho ? d_ho + b0 * npx : nullptr, d_mo ? d_mo + b0 * iters : nullptr, false)) != HG_OK)
+            return st;
+        launches += v->launches;
+        HG_CK(cudaEventRecord(ev_done[c], p->stream));
+        HG_CK(cudaStreamWaitEvent(p->d2h_stream, ev_done[c], 0));
+        if (d_ho && d_ho != holo_out)
+            HG_CK(cudaMemcpyAsync(holo_out + b0 * npx, d_ho + b0 * npx, nb * npx, cudaMemcpyDeviceToHost,
+                                  p->d2h_stream));
+        if (d_mo && d_mo != mse_out)
+            HG_CK(cudaMemcpyAsync(mse_out + b0 * iters, d_mo + b0 * iters, sizeof(double) * nb * iters,
+                                  cudaMemcpyDeviceToHost, p->d2h_stream));
+    }
+    p->launches = launches;
+    p->weights_preset = false;
+    p->have_run = true;
+    p->field_from_run = true;
+    p->last_iters = iters;
+    HG_CK(cudaStreamSynchronize(p->d2h_stream));
+    return hg_sync(p);
+}
+
 }  // namespace
 
 // ------------------------------------------------------------------- ABI
@@ -1174,6 +1325,7 @@ void hg_opts_default(hg_opts *o) {
     o->amp_clip = 2.f;
     o->sa_temp = 1e-3f;
     o->sa_cool = 0.9f;
+    o->host_chunks = 0;
 }
 
 int hg_supported_length(int n) { return find_ops(n) != nullptr; }
@@ -1196,6 +1348,18 @@ void hg_plan_destroy(hg_plan p) {
     if (!p) return;
     DevGuard g(p->dev);
     if (p->stream || p->cap_stream) cudaStreamSynchronize(p->stream);
+    if (p->is_view) {  // owns its loop graph only
+        if (p->gexec) cudaGraphExecDestroy(p->gexec);
+        delete p;
+        return;
+    }
+    for (hg_plan v : p->views) hg_plan_destroy(v);
+    for (cudaStream_t cs : {p->h2d_stream, p->d2h_stream})
+        if (cs) {
+            cudaStreamSynchronize(cs);
+            cudaStreamDestroy(cs);
+        }
+    for (cudaEvent_t e : p->chunk_ev) cudaEventDestroy(e);
     if (p->gexec) cudaGraphExecDestroy(p->gexec);
     if (p->cap_stream) cudaStreamDestroy(p->cap_stream);
     for (cudaEvent_t e : p->prof_ev) cudaEventDestroy(e);
@@ -1214,7 +1378,7 @@ hg_status hg_plan_create(hg_plan *out, int ny, int nx, int batch, hg_slm slm, hg
     hg_opts o;
     hg_opts_default(&o);
     if (opts) o = *opts;
-    if (batch < 1 || ny < 1 || nx < 1) return HG_ERR_INVALID_ARG;
+    if (batch < 1 || ny < 1 || nx < 1 || o.host_chunks < 0) return HG_ERR_INVALID_ARG;
     if (algo != HG_GS && algo != HG_WGS && algo != HG_OSPR && algo != HG_ADOSPR && algo != HG_LT &&
         algo != HG_DS && algo != HG_SA)
         return HG_ERR_INVALID_ARG;
@@ -1265,6 +1429,7 @@ hg_status hg_plan_create(hg_plan *out, int ny, int nx, int batch, hg_slm slm, hg
         p->sa_cool = o.sa_cool;
     }
     p->fresnel = o.fresnel;
+    p->host_chunks = o.host_chunks;
     p->amp_clip = o.amp_clip;
 
     p->nsub = nsub;
@@ -1631,12 +1796,14 @@ hg_status hg_run(hg_plan p, const float *target, const float *init_phase, int it
     const float *d_t = target, *d_ph = init_phase;
     uint8_t *d_ho = holo_out;
     double *d_mo = mse_out;
+    const bool chunked = any_host && host_chunk_count(p) > 1;  // copies by chunk, see run_chunked
     if (t_host) {
-        HG_CK(cudaMemcpyAsync(sb, target, fbytes, cudaMemcpyHostToDevice, p->stream));
+        if (!chunked) HG_CK(cudaMemcpyAsync(sb, target, fbytes, cudaMemcpyHostToDevice, p->stream));
         d_t = (const float *)sb;
     }
     if (ph_host) {
-        HG_CK(cudaMemcpyAsync(sb + al(fbytes), init_phase, fbytes, cudaMemcpyHostToDevice, p->stream));
+        if (!chunked)
+            HG_CK(cudaMemcpyAsync(sb + al(fbytes), init_phase, fbytes, cudaMemcpyHostToDevice, p->stream));
         d_ph = (const float *)(sb + al(fbytes));
     }
     if (ho_host) d_ho = (uint8_t *)(sb + 2 * al(fbytes));
@@ -1644,6 +1811,8 @@ hg_status hg_run(hg_plan p, const float *target, const float *init_phase, int it
 
     if ((st = ensure_part(p, iters)) != HG_OK) return st;
     if ((st = ensure_metrics(p, iters)) != HG_OK) return st;
+    const int K = any_host ? host_chunk_count(p) : 1;
+    if (K > 1) return run_chunked(p, K, target, d_t, init_phase, d_ph, iters, holo_out, d_ho, mse_out, d_mo);
     if ((st = enqueue_run(p, d_t, d_ph, iters, d_ho, d_mo, false)) != HG_OK) return st;
     if (ho_host)
         HG_CK(cudaMemcpyAsync(holo_out, d_ho, hbytes, cudaMemcpyDeviceToHost, p->stream));

@@ -34,6 +34,7 @@ struct RowArgs {
     float *w;              // weighted-GS weights [targets][ny][nx] DFT order, or null
     const float *phase;    // HEAD: initial replay phase (replay order) or null = Philox
     uint32_t seed_lo, seed_hi, stream_id;
+    int item0;  // Philox target index of item 0 (a chunk of a larger batch starts past 0)
     double *part;          // metric partials [targets][panels][NMET] or null
     float *phase_out;      // TAIL: arg R, replay order, or null
     float2 *R_out;         // TAIL: replay field, replay order, unitary scale, or null
@@ -176,8 +177,8 @@ __device__ __forceinline__ void row_body(const RowArgs &a) {
                     sincospif(__ldg(a.phase + ((size_t)b * ny + iy) * NX + ix) * 0.318309886183790672f,
                               &s, &c);
                 } else {
-                    sincospif(philox_phase2u((uint32_t)(iy * NX + ix), (uint32_t)sub, (uint32_t)b, a.stream_id,
-                                             a.seed_lo, a.seed_hi),
+                    sincospif(philox_phase2u((uint32_t)(iy * NX + ix), (uint32_t)sub, (uint32_t)(a.item0 + b),
+                                             a.stream_id, a.seed_lo, a.seed_hi),
                               &s, &c);  // pi * 2u
                 }
                 v[e] = make_float2(amp * c, amp * s);
@@ -189,7 +190,7 @@ __device__ __forceinline__ void row_body(const RowArgs &a) {
                         sincospif(__ldg(a.phase + ((size_t)b * ny + iym) * NX + ixm) * 0.318309886183790672f,
                                   &snm, &csm);
                     } else {
-                        sincospif(philox_phase2u((uint32_t)(iym * NX + ixm), (uint32_t)sub, (uint32_t)b,
+                        sincospif(philox_phase2u((uint32_t)(iym * NX + ixm), (uint32_t)sub, (uint32_t)(a.item0 + b),
                                                  a.stream_id, a.seed_lo, a.seed_hi),
                                   &snm, &csm);
                     }
@@ -324,7 +325,7 @@ __device__ __forceinline__ void row_body(const RowArgs &a) {
                     const float amp = sqrtf(fmaxf(fmaf((float)(a.sub + 1), Tv * Tv, -sum), 0.f));
                     const int ix = (x + NX / 2) % NX;
                     float s, c;
-                    sincospif(philox_phase2u((uint32_t)(iy * NX + ix), (uint32_t)a.sub, (uint32_t)item,
+                    sincospif(philox_phase2u((uint32_t)(iy * NX + ix), (uint32_t)a.sub, (uint32_t)(a.item0 + item),
                                              a.stream_id, a.seed_lo, a.seed_hi),
                               &s, &c);  // pi * 2u
                     v[e] = make_float2(amp * c, amp * s);

@@ -112,15 +112,29 @@ __device__ __forceinline__ void named_sync(int id, int nthreads) {
 // E terms each), the group total is stored as double by thread 0 and every
 // reduction across panels is done in double.  (Double shuffles or additions
 // here would occupy the FP64 pipe, which is narrow on this GPU.)
-// float -> double without the FP64 pipe: a normal float's biased exponent is
-// raised by 1023 - 127 = 896 and its 23 fraction bits become the top of the
-// 52-bit fraction, which is exact; zero, subnormals, infinities and NaN take
-// the conversion instruction.
+// float -> double on the integer pipes (IEEE 754 binary32 -> binary64, exact):
+// a normal float's biased exponent is raised by 1023 - 127 = 896 and its 23
+// fraction bits become the top of the 52-bit fraction; a subnormal m 2^-149
+// is renormalised at its leading bit p (exponent p - 149); zeros keep their
+// sign and infinities / NaNs keep exponent all-ones and the payload.  The
+// group totals would otherwise hold their group's barrier on the narrow FP64
+// pipe (a select between two paths still executes the conversion).
 __device__ __forceinline__ double f2d_exact(float x) {
     const uint32_t u = __float_as_uint(x), m = u & 0x7fffffffu;
-    if (m < 0x00800000u || m >= 0x7f800000u) return (double)x;
-    return __longlong_as_double((long long)((((unsigned long long)(u & 0x80000000u)) << 32) |
-                                            ((((unsigned long long)m) << 29) + (896ull << 52))));
+    const unsigned long long sgn = ((unsigned long long)(u & 0x80000000u)) << 32;
+    unsigned long long d;
+    if (m >= 0x00800000u && m < 0x7f800000u) {
+        d = (((unsigned long long)m) << 29) + (896ull << 52);
+    } else if (m >= 0x7f800000u) {
+        d = (0x7ffull << 52) | (((unsigned long long)(m & 0x007fffffu)) << 29);
+    } else if (m == 0u) {
+        d = 0ull;
+    } else {
+        const int pb = 31 - __clz((int)m);  // leading bit, 0 .. 22
+        d = ((unsigned long long)(pb + 874) << 52) |
+            ((((unsigned long long)m) << (52 - pb)) & ((1ull << 52) - 1));
+    }
+    return __longlong_as_double((long long)(sgn | d));
 }
 
 template <int GT, class SYNC>
@@ -628,7 +642,7 @@ __global__ void __launch_bounds__(PairPipeCfg<P, NG, D, SWZ>::THREADS, MINB)
                 const int nrow = partner ? 2 : 1;
                 for (int gi = t; gi < nrow * (NX / 4); gi += TL) {
                     const int rr = gi / (NX / 4), g4 = gi - rr * (NX / 4);
-                    const uint4 w = philox4((uint32_t)((rr ? iym : iy) * (NX / 4) + g4), (uint32_t)sub, (uint32_t)b,
+                    const uint4 w = philox4((uint32_t)((rr ? iym : iy) * (NX / 4) + g4), (uint32_t)sub, (uint32_t)(a.item0 + b),
                                             a.stream_id, a.seed_lo, a.seed_hi);
                     constexpr float k = 1.0f / 8388608.0f;
                     wP[gi] = make_float4((float)(w.x >> 8) * k, (float)(w.y >> 8) * k, (float)(w.z >> 8) * k,
@@ -739,7 +753,7 @@ __global__ void __launch_bounds__(PairPipeCfg<P, NG, D, SWZ>::THREADS, MINB)
                 for (int gi = t; gi < (partner ? 2 : 1) * (NX / 4); gi += TL) {
                     const int rr = gi / (NX / 4), g4 = gi - rr * (NX / 4);
                     const uint4 w = philox4((uint32_t)((rr ? iym : iy) * (NX / 4) + g4), (uint32_t)a.sub,
-                                            (uint32_t)item, a.stream_id, a.seed_lo, a.seed_hi);
+                                            (uint32_t)(a.item0 + item), a.stream_id, a.seed_lo, a.seed_hi);
                     constexpr float kk = 1.0f / 8388608.0f;
                     wP[gi] = make_float4((float)(w.x >> 8) * kk, (float)(w.y >> 8) * kk, (float)(w.z >> 8) * kk,
                                          (float)(w.w >> 8) * kk);

@@ -36,7 +36,7 @@ class hg_opts(ctypes.Structure):
                 ("precision", ctypes.c_int), ("use_graph", ctypes.c_int), ("pipeline", ctypes.c_int),
                 ("autotune", ctypes.c_int), ("lt_start", ctypes.c_float), ("lt_grow", ctypes.c_int),
                 ("modulated", ctypes.c_int), ("fresnel", ctypes.c_float), ("amp_clip", ctypes.c_float),
-                ("sa_temp", ctypes.c_float), ("sa_cool", ctypes.c_float)]
+                ("sa_temp", ctypes.c_float), ("sa_cool", ctypes.c_float), ("host_chunks", ctypes.c_int)]
 
 
 class hg_slm(ctypes.Structure):
@@ -166,7 +166,7 @@ def hg_status_string(st: int) -> str:
 def hg_plan_create(ny, nx, batch, slm_kind=HG_SLM_BINARY, levels=2, algo=HG_GS, stream=None,
                    seed=0, subframes=24, precision=0, use_graph=True, pipeline=-1, autotune=True,
                    lt_start=None, lt_grow=None, modulated=False, fresnel=0.0, amp_clip=None, sa_temp=None,
-                   sa_cool=None):
+                   sa_cool=None, host_chunks=0):
     o = hg_opts()
     lib().hg_opts_default(ctypes.byref(o))
     if stream is None and torch.cuda.is_available():
@@ -184,6 +184,7 @@ def hg_plan_create(ny, nx, batch, slm_kind=HG_SLM_BINARY, levels=2, algo=HG_GS, 
         o.lt_grow = int(lt_grow)
     o.modulated = 1 if modulated else 0
     o.fresnel = float(fresnel)
+    o.host_chunks = int(host_chunks)
     if amp_clip is not None:
         o.amp_clip = float(amp_clip)
     if sa_temp is not None:

@@ -50,6 +50,7 @@ def test_defaults_and_status_strings(lib):
     o = hg.hg_opts()
     lib.hg_opts_default(ctypes.byref(o))
     assert (o.subframes, o.use_graph, o.pipeline, o.autotune, o.precision, o.seed) == (24, 1, -1, 1, 0, 0)
+    assert o.host_chunks == 0
     seen = set()
     for st in range(8):
         s = hg.hg_status_string(st)
@@ -123,6 +124,7 @@ def test_plain_c_client_builds_and_runs(tmp_path):
     (64, 64, 2, 257, 0, None, None, 1),        # amplitude SLM with L > 256
     (1024, 1024, 0, 2, 0, "precision", 5, 1),  # precision outside 0..4
     (64, 64, 0, 2, 4, "lt_start", 0.0, 1),     # Liu-Taghizadeh window fraction in (0, 1]
+    (64, 64, 0, 2, 0, "host_chunks", -1, 1),   # chunk count >= 0
 ])
 def test_variant_options_rejected_before_device_work(lib, ny, nx, kind, levels, algo, opt, value, want):
     from paper_2008_12214_gb300 import hologen as hg
