@@ -152,11 +152,13 @@ typedef struct {
                           MSE (> 0, default 1e-3) */
     float sa_cool;     /* SA: temperature factor per sweep, in (0, 1] (default 0.9) */
     int host_chunks;   /* hg_run with host buffers (GS, WGS, LT, modulated): the batch
-                          runs in this many chunks, one chunk's copies overlapping
-                          another's iterations, with results identical to a
-                          whole-batch run; 0 (default) picks up to 4 chunks of at
-                          least 2^23 pixels each, 1 copies the whole batch first;
-                          >= 0 */
+                          runs in this many even chunks, one chunk's copies
+                          overlapping another's iterations, with results identical
+                          to a whole-batch run; 0 (default): batches of 2^24 pixels
+                          and more run a short lead chunk, about batch * 8 /
+                          (iters + 8) targets, whose iterations hide the input copy
+                          of one chunk holding the rest; 1 copies the whole batch
+                          first; >= 0 */
 } hg_opts;
 
 /* sizeof(hg_opts) as this library was built: a binding that lays the

@@ -1169,11 +1169,32 @@ struct DevGuard {
 // search, profiled plans and single targets; else opts.host_chunks, or (0)
 // up to 4 while every chunk keeps at least 2^23 pixels, so that each pass
 // still fills the GPU.
-int host_chunk_count(hg_plan p) {
-    if (is_ospr(p->algo) || is_search(p->algo) || p->prof_on || p->batch < 2) return 1;
-    long long k = p->host_chunks;
-    if (k == 0) k = std::min<long long>(4, ((long long)p->npx * p->batch) >> 23);
-    return (int)std::max<long long>(1, std::min<long long>(k, p->batch));
+// First target of each chunk of an hg_run with host buffers, then the batch
+// size (one chunk: {0, batch}).  hg_opts.host_chunks = K > 0 splits the batch
+// evenly.  The default (0) runs a short lead chunk and one chunk for the
+// rest: only the lead's input copy and the rest's output copy are exposed,
+// and the rest's input copy is hidden while the lead iterates if
+//   lead * iters * c_iter >= (batch - lead) * c_in,
+// where c_in / c_iter, one target's input copy over one of its iterations,
+// is about 8 B/px at ~200 GB/s over 36 B/px at ~6 TB/s, i.e. r = 8 / iters.
+// More chunks hide little more and cost more: each runs the persistent
+// passes on fewer targets, with relatively longer tails (measured at 1024^2
+// x 64 x 50 iterations with pinned buffers, even chunks: 1 -> 21.92 ms,
+// 2 -> 21.65, 4 -> 21.90, 8 -> 22.10; device buffers 19.02).  Small batches
+// (under 2^24 pixels) run as one chunk.
+std::vector<int> host_chunk_starts(hg_plan p, int iters) {
+    std::vector<int> st{0};
+    const bool one = is_ospr(p->algo) || is_search(p->algo) || p->prof_on || p->batch < 2;
+    if (!one && p->host_chunks > 0) {
+        const int K = std::min(p->host_chunks, p->batch), cs = (p->batch + K - 1) / K;
+        for (int b = cs; b < p->batch; b += cs) st.push_back(b);
+    } else if (!one && (long long)p->npx * p->batch >= (1ll << 24)) {
+        const double r = 8.0 / std::max(iters, 1);
+        const int lead = (int)std::ceil(p->batch * r / (1.0 + r));
+        if (lead < p->batch) st.push_back(std::max(lead, 1));
+    }
+    st.push_back(p->batch);
+    return st;
 }
 
 // A view of targets [first, first + count) of p: p's passes, tensor-map boxes
@@ -1232,18 +1253,20 @@ hg_status make_view(hg_plan p, int first, int count, hg_plan *out) {
 // runs the same kernels on its targets as a whole-batch run, so holograms,
 // MSE and metrics are identical.  d_* point into the staging buffer (host
 // sides) or at the caller's device buffers.
-hg_status run_chunked(hg_plan p, int K, const float *target, const float *d_t, const float *init_phase,
-                      const float *d_ph, int iters, uint8_t *holo_out, uint8_t *d_ho, double *mse_out,
-                      double *d_mo) {
-    const int cs = (p->batch + K - 1) / K;
-    K = (p->batch + cs - 1) / cs;
+hg_status run_chunked(hg_plan p, const std::vector<int> &cst, const float *target, const float *d_t,
+                      const float *init_phase, const float *d_ph, int iters, uint8_t *holo_out, uint8_t *d_ho,
+                      double *mse_out, double *d_mo) {
+    const int K = (int)cst.size() - 1;
     hg_status st;
-    if ((int)p->views.size() != K || p->views[0]->batch != cs) {
+    bool same = (int)p->views.size() == K;
+    for (int c = 0; same && c < K; ++c)
+        same = p->views[c]->item0 == p->item0 + cst[c] && p->views[c]->batch == cst[c + 1] - cst[c];
+    if (!same) {
         for (hg_plan v : p->views) hg_plan_destroy(v);
         p->views.clear();
         for (int c = 0; c < K; ++c) {
             hg_plan v = nullptr;
-            if ((st = make_view(p, c * cs, std::min(cs, p->batch - c * cs), &v)) != HG_OK) return st;
+            if ((st = make_view(p, cst[c], cst[c + 1] - cst[c], &v)) != HG_OK) return st;
             p->views.push_back(v);
         }
     }
@@ -1261,7 +1284,7 @@ hg_status run_chunked(hg_plan p, int K, const float *target, const float *d_t, c
     HG_CK(cudaStreamWaitEvent(p->d2h_stream, ev_start, 0));
     const size_t npx = p->npx;
     for (int c = 0; c < K; ++c) {
-        const size_t b0 = (size_t)c * cs, nb = p->views[c]->batch;
+        const size_t b0 = (size_t)cst[c], nb = p->views[c]->batch;
         if (d_t != target)
             HG_CK(cudaMemcpyAsync((void *)(d_t + b0 * npx), target + b0 * npx, sizeof(float) * nb * npx,
                                   cudaMemcpyHostToDevice, p->h2d_stream));
@@ -1273,7 +1296,7 @@ hg_status run_chunked(hg_plan p, int K, const float *target, const float *d_t, c
     int launches = 0;
     for (int c = 0; c < K; ++c) {
         hg_plan v = p->views[c];
-        const size_t b0 = (size_t)c * cs, nb = v->batch;
+        const size_t b0 = (size_t)cst[c], nb = v->batch;
         v->part = p->part;  // the chunks run one after another on the plan's stream
         v->part_iters = p->part_iters;
         v->metrics = p->metrics + b0 * iters * NMET;
@@ -1796,7 +1819,8 @@ hg_status hg_run(hg_plan p, const float *target, const float *init_phase, int it
     const float *d_t = target, *d_ph = init_phase;
     uint8_t *d_ho = holo_out;
     double *d_mo = mse_out;
-    const bool chunked = any_host && host_chunk_count(p) > 1;  // copies by chunk, see run_chunked
+    const std::vector<int> cst = any_host ? host_chunk_starts(p, iters) : std::vector<int>{0, p->batch};
+    const bool chunked = cst.size() > 2;  // copies by chunk, see run_chunked
     if (t_host) {
         if (!chunked) HG_CK(cudaMemcpyAsync(sb, target, fbytes, cudaMemcpyHostToDevice, p->stream));
         d_t = (const float *)sb;
@@ -1811,8 +1835,7 @@ hg_status hg_run(hg_plan p, const float *target, const float *init_phase, int it
 
     if ((st = ensure_part(p, iters)) != HG_OK) return st;
     if ((st = ensure_metrics(p, iters)) != HG_OK) return st;
-    const int K = any_host ? host_chunk_count(p) : 1;
-    if (K > 1) return run_chunked(p, K, target, d_t, init_phase, d_ph, iters, holo_out, d_ho, mse_out, d_mo);
+    if (chunked) return run_chunked(p, cst, target, d_t, init_phase, d_ph, iters, holo_out, d_ho, mse_out, d_mo);
     if ((st = enqueue_run(p, d_t, d_ph, iters, d_ho, d_mo, false)) != HG_OK) return st;
     if (ho_host)
         HG_CK(cudaMemcpyAsync(holo_out, d_ho, hbytes, cudaMemcpyDeviceToHost, p->stream));

@@ -2,8 +2,9 @@
 overlapping another chunk's iterations (hg_opts.host_chunks).  Every chunk
 runs the whole-batch run's kernels on its own targets, so the results must be
 bit-identical to a run of the same plan on device buffers: holograms, MSE,
-hg_get_metrics and hg_get_phase, for even and uneven chunks, GS, WGS, LT and
-a modulated plan, and across repeated calls with other iteration counts."""
+hg_get_metrics and hg_get_phase, for even and uneven chunks and the default
+lead-chunk schedule, GS, WGS, LT and a modulated plan, and across repeated
+calls with other iteration counts (which change the default's lead chunk)."""
 import numpy as np
 import pytest
 import torch
@@ -21,6 +22,9 @@ CASES = [
     (512, 512, 5, hg.HG_SLM_BINARY, 2, hg.HG_LT, 2, {}),
     (1024, 1024, 4, hg.HG_SLM_BINARY, 2, hg.HG_GS, 3, dict(modulated=True, fresnel=0.002)),
     (256, 512, 7, hg.HG_SLM_LLEVEL, 4, hg.HG_GS, 0, {}),
+    # the default schedule on 2^24 pixels: a lead chunk whose size follows the
+    # iteration count (10 targets at 5 iterations, 12 at 3), then the rest
+    (1024, 1024, 16, hg.HG_SLM_BINARY, 2, hg.HG_GS, 0, {}),
 ]
 
 
