@@ -60,7 +60,9 @@ def parse():
     ap.add_argument("--precision", type=int, default=0,
                     help="0 FP32 engine; 1..4 tensor-core row pass (FP16 hi+lo, FP16, BF16 hi+lo, BF16); "
                          "fresnel workload: 0 binary phase SLM, 1 16-level amplitude SLM")
-    ap.add_argument("--batch", type=int, default=BATCH, help="targets per rank (profiling runs)")
+    ap.add_argument("--batch", type=int, default=None,
+                    help="targets per rank (profiling runs; default: the workload's own, 64 for the headline; "
+                         "mixed: targets per size)")
     ap.add_argument("--quick", action="store_true", help="skip the e2e and CPU-baseline legs")
     ap.add_argument("--pairs", type=int, default=2048, help="warmstart: training pairs")
     ap.add_argument("--search-waves", type=int, default=1, help="search: targets = waves x 4 x SMs")
@@ -169,7 +171,7 @@ def run_reference(args):
     if args.warmup:
         oracle_per_core(cores, 1)
     rate = oracle_per_core(cores, args.steps)
-    B = args.batch
+    B = args.batch or BATCH
     value = rate / B
     per = cores / rate  # wall seconds per step (one iteration on every core)
     line = dict(impl="reference", metric=METRIC, value=value, unit=UNIT, n_gpus=world, steps=args.steps,
@@ -310,7 +312,7 @@ def run_side_workload(args):
     s0 = torch.cuda.current_stream(dev)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     if args.workload in ("ospr", "adospr"):
-        B, NS = 8, 24
+        B, NS = args.batch or 8, 24
         T = torch.from_numpy(synth.targets(B, NY, NX)).to(dev)
         holo = torch.empty((B, NS, NY, NX), dtype=torch.uint8, device=dev)
         mse = torch.empty(B, dtype=torch.float64, device=dev)
@@ -325,7 +327,7 @@ def run_side_workload(args):
         e1.record(s0)
         plan.sync()
         ms = e0.elapsed_time(e1) / args.steps
-        out = dict(workload="%s_8x24_1024x1024" % args.workload, ms_per_step=ms, subframes_per_s=B * NS / (ms / 1e3),
+        out = dict(workload="%s_%dx24_1024x1024" % (args.workload, B), ms_per_step=ms, subframes_per_s=B * NS / (ms / 1e3),
                    algorithmic_gbs=36.0 * B * NS * NY * NX / (ms / 1e3) / 1e9,
                    mse=mse.cpu().numpy().tolist(), column_variant=hg.hg_plan_variant(plan.h, 1))
         plan.close()
@@ -391,7 +393,7 @@ def run_side_workload(args):
         plan.close()
     elif args.workload == "lt":
         # Liu-Taghizadeh GS, 64 binary holograms of 1024^2, window 0.25 -> 1 over 10 constraints
-        B, n = 64, 1024
+        B, n = args.batch or 64, 1024
         T = torch.from_numpy(synth.targets(B, n, n, 7100)).to(dev)
         P = torch.from_numpy(synth.init_phases(B, n, n, 7100)).to(dev)
         mse = torch.empty((B, args.iters), dtype=torch.float64, device=dev)
@@ -406,7 +408,7 @@ def run_side_workload(args):
         plan.sync()
         ms = e0.elapsed_time(e1) / args.steps
         it_ms = ms / args.iters
-        out = dict(workload="lt_binary_1024x1024_batch64", ms_per_step=ms, iters_per_step=args.iters,
+        out = dict(workload="lt_binary_1024x1024_batch%d" % B, ms_per_step=ms, iters_per_step=args.iters,
                    batched_iterations_per_s=1e3 / it_ms, gbs_at_36=36.0 * B * n * n / (it_ms / 1e3) / 1e9,
                    final_mse_mean=float(mse[:, -1].mean().item()),
                    row_variant=hg.hg_plan_variant(plan.h, 0), column_variant=hg.hg_plan_variant(plan.h, 1))
@@ -415,7 +417,7 @@ def run_side_workload(args):
         # modulated GS: 64 Fresnel holograms of 1024^2 (quadratic phase pi dx^2 / (lambda z) for
         # 8 um pixels, 532 nm, 0.5 m), Gaussian illumination, disc region of interest, binary
         # phase or 16-level amplitude SLM (--precision 0 / 1 selects), 50 iterations
-        B, n = 64, 1024
+        B, n = args.batch or 64, 1024
         c = float(np.pi * (8e-6) ** 2 / (532e-9 * 0.5))
         amp_slm = args.precision == 1
         kind, levels = (hg.HG_SLM_AMPLITUDE, 16) if amp_slm else (hg.HG_SLM_BINARY, 2)
@@ -447,7 +449,7 @@ def run_side_workload(args):
         it_ms = ms / args.iters
         px = B * n * n
         # generic passes: row 8 + 8 (field) + 4 (T) + 1 (ROI); column 8 + 8 (field) + 8 (illumination)
-        out = dict(workload="fresnel_%s_1024x1024_batch64" % ("amplitude16" if amp_slm else "binary"),
+        out = dict(workload="fresnel_%s_1024x1024_batch%d" % ("amplitude16" if amp_slm else "binary", B),
                    ms_per_step=ms, iters_per_step=args.iters, batched_iterations_per_s=1e3 / it_ms,
                    algorithmic_gbs_at_45=45.0 * px / (it_ms / 1e3) / 1e9,
                    final_roi_mse_mean=float(mse[:, -1].mean().item()), roi_ssim_mean=float(ev[:, 3].mean()),
@@ -456,7 +458,7 @@ def run_side_workload(args):
                    row_variant=hg.hg_plan_variant(plan.h, 0), column_variant=hg.hg_plan_variant(plan.h, 1))
         plan.close()
     elif args.workload == "gs2048":
-        B, n = 16, 2048
+        B, n = args.batch or 16, 2048
         T = torch.from_numpy(synth.targets(B, n, n, 5000)).to(dev)
         P = torch.from_numpy(synth.init_phases(B, n, n, 5000)).to(dev)
         mse = torch.empty((B, args.iters), dtype=torch.float64, device=dev)
@@ -472,19 +474,20 @@ def run_side_workload(args):
         ms = e0.elapsed_time(e1) / args.steps
         px = B * n * n
         it_ms = ms / args.iters
-        out = dict(workload="gs_binary_2048x2048_batch16", precision=args.precision, ms_per_step=ms,
+        out = dict(workload="gs_binary_2048x2048_batch%d" % B, precision=args.precision, ms_per_step=ms,
                    iters_per_step=args.iters, final_mse_mean=float(mse[:, -1].mean().item()),
                    batched_iterations_per_s=1e3 / it_ms, gbs_at_36=36.0 * px / (it_ms / 1e3) / 1e9,
                    row_variant=hg.hg_plan_variant(plan.h, 0), column_variant=hg.hg_plan_variant(plan.h, 1))
         plan.close()
     else:
         shapes = [(512, 512), (1024, 1024), (2048, 2048), (1080, 1920)]
+        nb = args.batch or 16
         plans, Ts, Ps, Ms = [], [], [], []
         for i, (ny, nx) in enumerate(shapes):
-            plans.append(hg.Plan(ny, nx, 16))
-            Ts.append(torch.from_numpy(synth.targets(16, ny, nx, 3000 + 16 * i)).to(dev))
-            Ps.append(torch.from_numpy(synth.init_phases(16, ny, nx, 3000 + 16 * i)).to(dev))
-            Ms.append(torch.empty((16, args.iters), dtype=torch.float64, device=dev))
+            plans.append(hg.Plan(ny, nx, nb))
+            Ts.append(torch.from_numpy(synth.targets(nb, ny, nx, 3000 + 16 * i)).to(dev))
+            Ps.append(torch.from_numpy(synth.init_phases(nb, ny, nx, 3000 + 16 * i)).to(dev))
+            Ms.append(torch.empty((nb, args.iters), dtype=torch.float64, device=dev))
         g = hg.hg_group_create(plans)
         sched_ms = {}
         for name, sched in (("concurrent", hg.HG_GROUP_CONCURRENT), ("serial", hg.HG_GROUP_SERIAL)):
@@ -499,7 +502,7 @@ def run_side_workload(args):
             hg.hg_group_sync(g)
             sched_ms[name] = e0.elapsed_time(e1) / args.steps
         ms = sched_ms["serial"]  # the default schedule
-        px = 16 * sum(a * b for a, b in shapes)
+        px = nb * sum(a * b for a, b in shapes)
         # each size alone (its plan's own hg_run), and its loop passes one by one
         alone = []
         for i, p in enumerate(plans):
@@ -518,8 +521,8 @@ def run_side_workload(args):
             hg.hg_profile_enable(p.h, 0)
             alone.append(dict(shape="%dx%d" % shapes[i], ms_per_run=ms_i,
                               row_ms=prof[0] / max(prof[1], 1), column_ms=prof[2] / max(prof[3], 1),
-                              gbs_at_36=36.0 * 16 * shapes[i][0] * shapes[i][1] * args.iters / (ms_i / 1e3) / 1e9))
-        out = dict(workload="mixed_64_targets_one_graph", ms_per_step=ms, iters_per_step=args.iters,
+                              gbs_at_36=36.0 * nb * shapes[i][0] * shapes[i][1] * args.iters / (ms_i / 1e3) / 1e9))
+        out = dict(workload="mixed_%d_targets_one_graph" % (4 * nb), ms_per_step=ms, iters_per_step=args.iters,
                    batched_iterations_per_s=args.iters / (ms / 1e3),
                    algorithmic_gbs_at_36=36.0 * px * args.iters / (ms / 1e3) / 1e9,
                    ms_per_step_by_schedule=sched_ms,
@@ -559,7 +562,7 @@ def main():
         dist.barrier()
     __graft_entry__.build()
 
-    B = args.batch
+    B = args.batch or BATCH
     base = shard.target_seeds(rank, B)[0]
     t_host = synth.targets(B, NY, NX, base)
     p_host = synth.init_phases(B, NY, NX, base)

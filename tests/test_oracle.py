@@ -507,3 +507,54 @@ def test_ospr_mean_intensity_follows_the_arcsine_law():
         err.append(np.linalg.norm(I - E) / np.linalg.norm(E))
     assert err[0] < 0.03 and err[1] < 0.015, err
     assert err[1] < 0.7 * err[0]  # the subframe noise averages out
+
+
+# --------------------------------------------- GS labels for the warm start
+
+
+@pytest.mark.parametrize("kind,levels", [(oracle.SLM_BINARY, 2), (oracle.SLM_LLEVEL, 256)])
+def test_gs_phase_keeps_the_memory_of_its_start(kind, levels):
+    """The warm start's labels are replay phases after 200 GS iterations
+    (Section 3.2) grown from one seeded start phase shared by every target.
+    GS changes the phase only partly: on the target's support, weighted by
+    T^2, the phasor exp(i(phi_200 - phi_0)) still averages to a magnitude near
+    0.7, while the GS-200 phases grown from two independent starts are
+    uncorrelated (as are the starts themselves).  A label is therefore
+    dominated by the shared start, a fixed position-dependent random field
+    that a translation-equivariant network cannot produce from the target."""
+    n = 128
+    a = synth.init_phase(n, n, 1).astype(np.float64)
+    b = synth.init_phase(n, n, 2).astype(np.float64)
+    t = synth.target(n, n, 1000)
+    T = oracle.prepare_target(t)
+    w = T * T / np.sum(T * T)
+
+    def corr(x, y):
+        return abs(np.sum(w * np.exp(1j * (x - y))))
+
+    pa = oracle.gs_run(t, a, 200, kind, levels)["phase"]
+    pb = oracle.gs_run(t, b, 200, kind, levels)["phase"]
+    assert corr(pa, a) > 0.6 and corr(pb, b) > 0.6, (corr(pa, a), corr(pb, b))
+    assert corr(pa, pb) < 0.1 and corr(a, b) < 0.1, (corr(pa, pb), corr(a, b))
+
+
+def test_a_useful_gs_start_carries_the_labels_pixel_scale_detail():
+    """What a warm start would have to predict (256-level SLM, 128^2): GS
+    started from a target's own GS-200 phase (grown from the shared start
+    phi_0) is below the GS-100 MSE of a random start after one iteration,
+    while phi_0 corrected only by the label's remainder exp(i(phi_200 - phi_0))
+    averaged over 2 x 2 blocks needs more than half of those 100 iterations:
+    the part of the label that GS adds to phi_0 is pixel-scale."""
+    n, kind, levels = 128, oracle.SLM_LLEVEL, 256
+    phi0 = synth.init_phase(n, n, 1).astype(np.float64)
+    for s in range(2):
+        t = synth.target(n, n, 1000 + s)
+        T = oracle.prepare_target(t)
+        goal = oracle.gs_run(t, synth.init_phase(n, n, 5000 + s).astype(np.float64), 100, kind, levels)["mse"][-1]
+        label = oracle.gs_run(t, phi0, 200, kind, levels)["phase"]
+        assert oracle.gs_run(t, label, 1, kind, levels)["mse"][0] < 0.99 * goal
+        r = np.exp(1j * (label - phi0)) * (T > 0)
+        r2 = np.repeat(np.repeat(r.reshape(n // 2, 2, n // 2, 2).mean(axis=(1, 3)), 2, 0), 2, 1)
+        mse = oracle.gs_run(t, phi0 + np.angle(r2 + 1e-30), 100, kind, levels)["mse"]
+        hit = np.nonzero(mse <= goal)[0]
+        assert len(hit) == 0 or hit[0] >= 50, hit[:1]
