@@ -157,8 +157,12 @@ typedef struct {
                           to a whole-batch run; 0 (default): batches of 2^24 pixels
                           and more run a short lead chunk, about batch * 8 /
                           (iters + 8) targets, whose iterations hide the input copy
-                          of one chunk holding the rest; 1 copies the whole batch
-                          first; >= 0 */
+                          of one chunk holding the rest, and that call times its
+                          copies and iterations; later calls with the same
+                          iteration count take the chunk sizes this timing says
+                          are fastest (two chunks when host copies are fast, a
+                          growing sequence when they are slow); 1 copies the whole
+                          batch first; >= 0 */
 } hg_opts;
 
 /* sizeof(hg_opts) as this library was built: a binding that lays the

@@ -543,6 +543,13 @@ struct hg_plan_s {
     std::vector<hg_plan_s *> views;
     cudaStream_t h2d_stream = nullptr, d2h_stream = nullptr;
     std::vector<cudaEvent_t> chunk_ev;  // per chunk: inputs copied, iterations done
+    // the default schedule's model, measured on the first chunked call with
+    // x_iters iterations: per target, the input copy (x_in), the iterations
+    // (x_it) and the output copy (x_out), and the fixed cost of one chunk
+    // (x_fix), all in ms; timing events of that call
+    int x_iters = 0;
+    double x_in = 0, x_it = 0, x_out = 0, x_fix = 0;
+    std::vector<cudaEvent_t> x_ev;
 };
 
 namespace {
@@ -1169,31 +1176,79 @@ struct DevGuard {
 // search, profiled plans and single targets; else opts.host_chunks, or (0)
 // up to 4 while every chunk keeps at least 2^23 pixels, so that each pass
 // still fills the GPU.
+// Time of a chunk schedule under the plan's measured model: chunk k's inputs
+// are copied after chunk k - 1's on one stream, its iterations start when
+// both its inputs and chunk k - 1's iterations are done, and the last
+// chunk's outputs are copied after its iterations.
+double chunk_schedule_ms(hg_plan p, const std::vector<int> &st) {
+    double copied = 0, done = 0;
+    for (size_t k = 0; k + 1 < st.size(); ++k) {
+        const int n = st[k + 1] - st[k];
+        copied += n * p->x_in;
+        done = std::max(done, copied) + n * p->x_it + p->x_fix;
+    }
+    return done + (st.size() > 1 ? (st[st.size() - 1] - st[st.size() - 2]) * p->x_out : 0.0);
+}
+
 // First target of each chunk of an hg_run with host buffers, then the batch
 // size (one chunk: {0, batch}).  hg_opts.host_chunks = K > 0 splits the batch
-// evenly.  The default (0) runs a short lead chunk and one chunk for the
-// rest: only the lead's input copy and the rest's output copy are exposed,
-// and the rest's input copy is hidden while the lead iterates if
+// evenly.  The default (0), for batches of 2^24 pixels and more: the first
+// call with a given iteration count runs a short lead chunk and one chunk for
+// the rest.  Only the lead's input copy and the rest's output copy are then
+// exposed, and the rest's input copy is hidden while the lead iterates if
 //   lead * iters * c_iter >= (batch - lead) * c_in,
 // where c_in / c_iter, one target's input copy over one of its iterations,
 // is about 8 B/px at ~200 GB/s over 36 B/px at ~6 TB/s, i.e. r = 8 / iters.
-// More chunks hide little more and cost more: each runs the persistent
-// passes on fewer targets, with relatively longer tails (measured at 1024^2
-// x 64 x 50 iterations with pinned buffers, even chunks: 1 -> 21.92 ms,
-// 2 -> 21.65, 4 -> 21.90, 8 -> 22.10; device buffers 19.02).  Small batches
-// (under 2^24 pixels) run as one chunk.
+// That call times its copies and its two chunks' iterations (per target, and
+// the fixed cost of a chunk: launch tails of fewer targets, head and tail
+// passes); later calls with the same iteration count take the schedule
+// that this model says is fastest: a lead of n0 targets, then each next chunk
+// either the rest (if waiting for its copy costs less than another chunk's
+// fixed cost) or as many targets as are copied by the time the chunk before
+// it finishes.  With fast host copies that is the two-chunk schedule; with
+// slow ones a growing sequence of chunks.  (Measured at 1024^2 x 64 x 50
+// iterations with pinned buffers, even chunks: 1 -> 21.92 ms, 2 -> 21.65,
+// 4 -> 21.90, 8 -> 22.10; device buffers 19.02; lead of 9 then 55: 20.3.)
+// Small batches (under 2^24 pixels) run as one chunk.
 std::vector<int> host_chunk_starts(hg_plan p, int iters) {
     std::vector<int> st{0};
-    const bool one = is_ospr(p->algo) || is_search(p->algo) || p->prof_on || p->batch < 2;
+    const int B = p->batch;
+    const bool one = is_ospr(p->algo) || is_search(p->algo) || p->prof_on || B < 2;
     if (!one && p->host_chunks > 0) {
-        const int K = std::min(p->host_chunks, p->batch), cs = (p->batch + K - 1) / K;
-        for (int b = cs; b < p->batch; b += cs) st.push_back(b);
-    } else if (!one && (long long)p->npx * p->batch >= (1ll << 24)) {
+        const int K = std::min(p->host_chunks, B), cs = (B + K - 1) / K;
+        for (int b = cs; b < B; b += cs) st.push_back(b);
+    } else if (!one && (long long)p->npx * B >= (1ll << 24)) {
+        if (p->x_iters == iters && p->x_it > 0) {
+            // chunks of at least 2^23 pixels, so that each still fills the GPU
+            // (the model's cost per target holds for chunks of that size)
+            const long long px_min = ((1ll << 23) + p->npx - 1) / p->npx;
+            const int nmin = (int)std::min<long long>(B / 2, std::max<long long>(1, px_min));
+            std::vector<int> best{0, B}, cand;
+            double best_ms = chunk_schedule_ms(p, best);
+            const int step = std::max(1, B / 256);
+            for (int n0 = nmin; n0 <= B - nmin; n0 += step) {
+                cand.assign({0, n0});
+                double done = p->x_in * n0 + p->x_it * n0 + p->x_fix;
+                int S = n0;
+                while (S < B) {
+                    int n = B - S;
+                    if (p->x_in > 0 && B * p->x_in - done > p->x_fix)
+                        n = std::min(n, std::max(nmin, (int)std::floor(done / p->x_in) - S));
+                    if (B - S - n < nmin) n = B - S;
+                    done = std::max(done, (S + n) * p->x_in) + n * p->x_it + p->x_fix;
+                    S += n;
+                    cand.push_back(S);
+                }
+                const double ms = chunk_schedule_ms(p, cand);
+                if (ms < best_ms) best_ms = ms, best = cand;
+            }
+            return best;
+        }
         const double r = 8.0 / std::max(iters, 1);
-        const int lead = (int)std::ceil(p->batch * r / (1.0 + r));
-        if (lead < p->batch) st.push_back(std::max(lead, 1));
+        const int lead = (int)std::ceil(B * r / (1.0 + r));
+        if (lead < B) st.push_back(std::max(lead, 1));
     }
-    st.push_back(p->batch);
+    st.push_back(B);
     return st;
 }
 
@@ -1208,6 +1263,7 @@ hg_status make_view(hg_plan p, int first, int count, hg_plan *out) {
     v->item0 = p->item0 + first;
     v->views.clear();
     v->chunk_ev.clear();
+    v->x_ev.clear();
     v->prof_ev.clear();
     v->prof_kind.clear();
     v->prof_on = false;
@@ -1278,10 +1334,21 @@ hg_status run_chunked(hg_plan p, const std::vector<int> &cst, const float *targe
         p->chunk_ev.push_back(e);
     }
     cudaEvent_t *ev_in = p->chunk_ev.data(), *ev_done = ev_in + K, ev_start = ev_in[2 * K];
+    // the default schedule's first call with this iteration count times its
+    // copies and chunks: input copies, then per chunk its iterations and its
+    // output copies
+    const bool measure = p->host_chunks == 0 && p->x_iters != iters;
+    while (measure && (int)p->x_ev.size() < 2 + 4 * K) {
+        cudaEvent_t e;
+        HG_CK(cudaEventCreate(&e));
+        p->x_ev.push_back(e);
+    }
+    cudaEvent_t *xe = measure ? p->x_ev.data() : nullptr;
     // the copies follow whatever the plan's stream already holds
     HG_CK(cudaEventRecord(ev_start, p->stream));
     HG_CK(cudaStreamWaitEvent(p->h2d_stream, ev_start, 0));
     HG_CK(cudaStreamWaitEvent(p->d2h_stream, ev_start, 0));
+    if (measure) HG_CK(cudaEventRecord(xe[0], p->h2d_stream));
     const size_t npx = p->npx;
     for (int c = 0; c < K; ++c) {
         const size_t b0 = (size_t)cst[c], nb = p->views[c]->batch;
@@ -1293,6 +1360,7 @@ hg_status run_chunked(hg_plan p, const std::vector<int> &cst, const float *targe
                                   cudaMemcpyHostToDevice, p->h2d_stream));
         HG_CK(cudaEventRecord(ev_in[c], p->h2d_stream));
     }
+    if (measure) HG_CK(cudaEventRecord(xe[1], p->h2d_stream));
     int launches = 0;
     for (int c = 0; c < K; ++c) {
         hg_plan v = p->views[c];
@@ -1305,19 +1373,23 @@ hg_status run_chunked(hg_plan p, const std::vector<int> &cst, const float *targe
         v->wait_ns = p->wait_ns;
         v->drop_job = p->drop_job;
         HG_CK(cudaStreamWaitEvent(p->stream, ev_in[c], 0));
+        if (measure) HG_CK(cudaEventRecord(xe[2 + 4 * c], p->stream));
         v->launches = 0;
         if ((st = enqueue_run(v, d_t + b0 * npx, d_ph ? d_ph + b0 * npx : nullptr, iters,
                               d_ho ? d_ho + b0 * npx : nullptr, d_mo ? d_mo + b0 * iters : nullptr, false)) != HG_OK)
             return st;
         launches += v->launches;
         HG_CK(cudaEventRecord(ev_done[c], p->stream));
+        if (measure) HG_CK(cudaEventRecord(xe[3 + 4 * c], p->stream));
         HG_CK(cudaStreamWaitEvent(p->d2h_stream, ev_done[c], 0));
+        if (measure) HG_CK(cudaEventRecord(xe[4 + 4 * c], p->d2h_stream));
         if (d_ho && d_ho != holo_out)
             HG_CK(cudaMemcpyAsync(holo_out + b0 * npx, d_ho + b0 * npx, nb * npx, cudaMemcpyDeviceToHost,
                                   p->d2h_stream));
         if (d_mo && d_mo != mse_out)
             HG_CK(cudaMemcpyAsync(mse_out + b0 * iters, d_mo + b0 * iters, sizeof(double) * nb * iters,
                                   cudaMemcpyDeviceToHost, p->d2h_stream));
+        if (measure) HG_CK(cudaEventRecord(xe[5 + 4 * c], p->d2h_stream));
     }
     p->launches = launches;
     p->weights_preset = false;
@@ -1325,7 +1397,36 @@ hg_status run_chunked(hg_plan p, const std::vector<int> &cst, const float *targe
     p->field_from_run = true;
     p->last_iters = iters;
     HG_CK(cudaStreamSynchronize(p->d2h_stream));
-    return hg_sync(p);
+    hg_status sst = hg_sync(p);
+    if (measure && sst == HG_OK) {
+        // per-target copy and iteration times; the fixed cost of a chunk from
+        // the two chunk sizes (iteration time = n x_it + x_fix)
+        float ms = 0;
+        double in_ms = 0, out_ms = 0, n[2] = {0, 0}, it_ms[2] = {0, 0};
+        HG_CK(cudaEventElapsedTime(&ms, xe[0], xe[1]));
+        in_ms = ms;
+        for (int c = 0; c < K; ++c) {
+            HG_CK(cudaEventElapsedTime(&ms, xe[2 + 4 * c], xe[3 + 4 * c]));
+            const int i = c == 0 ? 0 : 1;
+            n[i] += cst[c + 1] - cst[c];
+            it_ms[i] += ms;
+            HG_CK(cudaEventElapsedTime(&ms, xe[4 + 4 * c], xe[5 + 4 * c]));
+            out_ms += ms;
+        }
+        const double B = p->batch;
+        p->x_in = in_ms / B;
+        p->x_out = out_ms / B;
+        double it = (it_ms[0] + it_ms[1]) / B, fix = 0;
+        if (K == 2 && n[0] != n[1]) {
+            it = (it_ms[1] - it_ms[0]) / (n[1] - n[0]);
+            fix = it_ms[0] - n[0] * it;
+            if (it <= 0 || fix < 0) it = (it_ms[0] + it_ms[1]) / B, fix = 0;
+        }
+        p->x_it = it;
+        p->x_fix = fix;
+        p->x_iters = iters;
+    }
+    return sst;
 }
 
 }  // namespace
@@ -1383,6 +1484,7 @@ void hg_plan_destroy(hg_plan p) {
             cudaStreamDestroy(cs);
         }
     for (cudaEvent_t e : p->chunk_ev) cudaEventDestroy(e);
+    for (cudaEvent_t e : p->x_ev) cudaEventDestroy(e);
     if (p->gexec) cudaGraphExecDestroy(p->gexec);
     if (p->cap_stream) cudaStreamDestroy(p->cap_stream);
     for (cudaEvent_t e : p->prof_ev) cudaEventDestroy(e);
