@@ -67,6 +67,10 @@ def parse():
     ap.add_argument("--pairs", type=int, default=2048, help="warmstart: training pairs")
     ap.add_argument("--search-waves", type=int, default=1, help="search: targets = waves x 4 x SMs")
     ap.add_argument("--heldout", type=int, default=64, help="warmstart: held-out targets")
+    ap.add_argument("--residual", action="store_true",
+                    help="warmstart: the shared start phase as the network's base phase (residual labels)")
+    ap.add_argument("--warm-slm", choices=["both", "llevel256", "binary"], default="both",
+                    help="warmstart: SLMs to train and evaluate")
     ap.add_argument("--workload", choices=["headline", "ospr", "adospr", "mixed", "warmstart", "gs2048", "wgs256", "fresnel", "lt", "search"],
                     default="headline",
                     help="headline: binary GS 1024^2 x 64 (the benchmark line); ospr: 8 targets x 24 "
@@ -79,10 +83,11 @@ def dist_env():
         os.environ.get("WORLD_SIZE", 1))
 
 
-# Sources of the GS passes that the roofline and the committed DRAM traffic
-# describe: the line engine, the passes, their instantiations and their
-# launches.  A change to any of them makes the committed traffic stale.
-GS_SOURCES = ("hg_fft.cuh", "hg_kernels.cuh", "hg_pipe.cuh", "hg_api.cu", "ops_*.cu")
+# Sources of the 1024-sample GS passes that the roofline and the committed
+# DRAM traffic describe: the line engine, the passes, their 1024-sample
+# instantiations and their launches.  A change to any of them makes the
+# committed traffic stale.
+GS_SOURCES = ("hg_fft.cuh", "hg_kernels.cuh", "hg_pipe.cuh", "hg_api.cu", "ops_1024.cu")
 
 
 def src_hash():
@@ -282,10 +287,12 @@ def run_warmstart(args, dev, s0):
                           frac_of_sustained_bf16=tf / peak if peak else None))
         del x, w, y
     res = dict(workload="warmstart_cnn_1024x1024", pairs=args.pairs, heldout=args.heldout, label_iters=200,
-               conv_kernel_k_conv_fwd=convs, peak_bf16_tflops_sustained=peak)
+               residual=args.residual, conv_kernel_k_conv_fwd=convs, peak_bf16_tflops_sustained=peak)
     for name, kind, L in (("llevel256", hg.HG_SLM_LLEVEL, 256), ("binary", hg.HG_SLM_BINARY, 2)):
+        if args.warm_slm not in ("both", name):
+            continue
         net, losses, secs = ws.train(NY, NX, args.pairs, batch=4, lr=1e-3, chunk=64, label_iters=200,
-                                     label_start="fixed", slm_kind=kind, levels=L)
+                                     label_start="fixed", slm_kind=kind, levels=L, residual=args.residual)
         ev = ws.evaluate(net, NY, NX, args.heldout, ref_iters=100, max_iters=100, chunk=4, slm_kind=kind, levels=L)
         net.close()
         pick = (0, 9, 49, 99)
@@ -616,7 +623,8 @@ def main():
         pp = torch.from_numpy(p_host).pin_memory()
         hp = torch.empty((B, NY, NX), dtype=torch.uint8).pin_memory()
         mp = torch.empty((B, args.iters), dtype=torch.float64).pin_memory()
-        plan.run(tp, pp, args.iters, hp, mp)
+        for _ in range(2):  # the first call times the copies, the second takes its chunk sizes
+            plan.run(tp, pp, args.iters, hp, mp)
         e2e_steps = max(2, min(args.steps, 5))
         if world > 1:
             dist.barrier()

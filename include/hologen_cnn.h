@@ -75,7 +75,8 @@ hg_status hg_cnn_set_state(hg_cnn net, const float *state, int64_t step);
 hg_status hg_cnn_get_grads(hg_cnn net, float *grads);
 
 /* Forward pass of `batch` targets [batch][H][W]: cs_out [batch][H][W][2]
- * (c, s) and/or phase_out [batch][H][W] = atan2(s, c), either may be NULL. */
+ * (c, s) and/or phase_out [batch][H][W] = atan2(s, c) (+ the base phase, see
+ * hg_cnn_set_base_phase), either may be NULL. */
 hg_status hg_cnn_forward(hg_cnn net, const float *target, int batch, float *cs_out, float *phase_out);
 
 /* Loss and gradients for (target, phase label) without updating the
@@ -97,6 +98,21 @@ hg_status hg_cnn_train_step(hg_cnn net, const float *target, const float *phase_
  * no counterpart there.  Errors: HG_ERR_INVALID_ARG (NULL, lr <= 0),
  * HG_ERR_CUDA. */
 hg_status hg_cnn_apply_grads(hg_cnn net, const float *grads, float lr);
+
+/* A base phase phi_b [H][W] float radians (device or host pointer; NULL
+ * removes it), the same for every image: with it the network models the
+ * remainder of a label over the base, e^{i(phi - phi_b)}.  The loss of
+ * hg_cnn_gradients / hg_cnn_train_step compares (c, s) with
+ * e^{i(phi - phi_b)}, and hg_cnn_forward's phase_out is atan2(s, c) + phi_b
+ * (not wrapped).  GS labels grown from one shared start phase keep a large
+ * part of that start (Section 3.2's loop changes the replay phase only
+ * partly), a fixed random field that a convolutional network cannot produce
+ * from the target; with the start as the base, the network is asked only for
+ * what GS added.  The paper has no network, so no counterpart there.  Copies
+ * the field into the net's own device buffer (allocated at the first call)
+ * and waits for the copy.  Errors: HG_ERR_INVALID_ARG (NULL net),
+ * HG_ERR_OOM, HG_ERR_CUDA. */
+hg_status hg_cnn_set_base_phase(hg_cnn net, const float *base);
 
 /* Waits for the net's stream; HG_ERR_TIMEOUT if a bounded device wait gave
  * up, HG_ERR_INVALID_ARG if a target held a negative / NaN / infinite value,

@@ -220,15 +220,18 @@ def backward(p, a, dc, ds, store=keep):
     return g
 
 
-def loss_and_grads(p, T, phi):
+def loss_and_grads(p, T, phi, base=None):
+    """Loss and parameter gradients for labels phi; with a base phase [H][W]
+    (shared by the images) (c, s) is compared with e^{i(phi - base)}."""
     c, s, a = forward(p, net_input(T))
-    L, dc, ds = phase_loss(c, s, T, phi)
+    L, dc, ds = phase_loss(c, s, T, phi if base is None else phi - base)
     return L, backward(p, a, dc, ds)
 
 
-def predict_phase(p, T):
+def predict_phase(p, T, base=None):
+    """Phase of the network's (c, s), plus the base phase if one is given."""
     c, s, _ = forward(p, net_input(T))
-    return np.arctan2(s, c)
+    return np.arctan2(s, c) + (0.0 if base is None else base)
 
 
 # ------------------------------------------------------------------- Adam

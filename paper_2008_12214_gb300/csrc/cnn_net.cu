@@ -334,15 +334,17 @@ __global__ void k_pool_bwd_add(const __nv_bfloat16 *__restrict__ dpool, const __
 }
 
 // Head: (c, s) = Wh h + bh per pixel.  With a label phi: the loss
-// wT |(c, s) - e^{i phi}|^2 / (2 B), wT = T^2 / sum T^2, its gradient
-// through the head (dpre of the last convolution, masked by h > 0) and
-// block partials {sum dc h[32], sum ds h[32], sum dc, sum ds, loss}.
+// wT |(c, s) - e^{i (phi - phi_b)}|^2 / (2 B), wT = T^2 / sum T^2 (phi_b:
+// the optional base phase [H][W], else 0), its gradient through the head
+// (dpre of the last convolution, masked by h > 0) and block partials
+// {sum dc h[32], sum ds h[32], sum dc, sum ds, loss}.  phase_out gets
+// atan2(s, c) + phi_b.
 constexpr int HEAD_THREADS = 256;
 __global__ void __launch_bounds__(HEAD_THREADS)
     k_head(const __nv_bfloat16 *__restrict__ h, const float *__restrict__ theta, const float *__restrict__ T,
            const float *__restrict__ phi, const float *__restrict__ inv_sumsq, int B, long npx_img, float invB,
            __nv_bfloat16 *__restrict__ dpre, float2 *__restrict__ cs_out, float *__restrict__ phase_out,
-           float *__restrict__ part) {
+           float *__restrict__ part, const float *__restrict__ base) {
     __shared__ float sw[66];
     __shared__ float red[HEAD_THREADS / 32][kHeadPartN];
     if (threadIdx.x < 66) sw[threadIdx.x] = theta[c_tab.head_w + threadIdx.x];
@@ -369,13 +371,14 @@ __global__ void __launch_bounds__(HEAD_THREADS)
             s = fmaf(sw[32 + j], hv[j], s);
         }
         if (cs_out) cs_out[p] = make_float2(c, s);
-        if (phase_out) phase_out[p] = atan2f(s, c);
+        const float pb = base ? base[p % npx_img] : 0.f;
+        if (phase_out) phase_out[p] = atan2f(s, c) + pb;
         if (!train) continue;
         const int b = (int)(p / npx_img);
         const float t = T[p];
         const float wT = t * t * inv_sumsq[b];
         float sp, cp;
-        sincosf(phi[p], &sp, &cp);
+        sincosf(phi[p] - pb, &sp, &cp);
         const float ec = c - cp, es = s - sp;
         g[66] += 0.5f * wT * (ec * ec + es * es) * invB;
         const float dc = wT * ec * invB, ds = wT * es * invB;
@@ -522,6 +525,8 @@ struct hg_cnn_s {
     size_t ws_bytes = 0;
     unsigned *err = nullptr;
     double *loss = nullptr;
+    float *base = nullptr;       // optional base phase [H][W] (see hg_cnn_set_base_phase)
+    float *base_buf = nullptr;   // its storage, allocated at the first set
     std::vector<void *> owned;
 };
 
@@ -627,7 +632,7 @@ cudaError_t enqueue_backward(hg_cnn n, const float *T, const float *phi, int B, 
     const long npx0 = lvl_px(n, B, 0);
     const int hb = head_blocks(n, npx0);
     k_head<<<hb, HEAD_THREADS, 0, n->s>>>(n->D[0][1], n->theta, T, phi, n->inv_sumsq, B, (long)n->H * n->W,
-                                          1.f / (float)B, n->G[0][0], nullptr, nullptr, n->head_part);
+                                          1.f / (float)B, n->G[0][0], nullptr, nullptr, n->head_part, n->base);
     k_head_final<<<1, 96, 0, n->s>>>(n->head_part, hb, n->grad, loss_out ? loss_out : n->loss);
     n->launches += 2;
     cudaError_t e;
@@ -801,6 +806,22 @@ hg_status hg_cnn_set_state(hg_cnn n, const float *state, int64_t step) {
     return HG_OK;
 }
 
+hg_status hg_cnn_set_base_phase(hg_cnn n, const float *base) {
+    if (!n) return HG_ERR_INVALID_ARG;
+    CnnGuard g(n->dev);
+    if (!base) {
+        CN_CK(cudaStreamSynchronize(n->s));
+        n->base = nullptr;
+        return HG_OK;
+    }
+    const long npx = (long)n->H * n->W;
+    if (!n->base_buf) CN_CK(alloc(n, &n->base_buf, npx));
+    CN_CK(cudaMemcpyAsync(n->base_buf, base, sizeof(float) * npx, cudaMemcpyDefault, n->s));
+    CN_CK(cudaStreamSynchronize(n->s));
+    n->base = n->base_buf;
+    return HG_OK;
+}
+
 hg_status hg_cnn_get_grads(hg_cnn n, float *grads) {
     if (!n || !grads) return HG_ERR_INVALID_ARG;
     CnnGuard g(n->dev);
@@ -820,7 +841,7 @@ hg_status hg_cnn_forward(hg_cnn n, const float *T, int B, float *cs_out, float *
     const long npx0 = lvl_px(n, B, 0);
     k_head<<<head_blocks(n, npx0), HEAD_THREADS, 0, n->s>>>(n->D[0][1], n->theta, nullptr, nullptr, nullptr, B,
                                                             (long)n->H * n->W, 1.f, nullptr, (float2 *)cs_out,
-                                                            phase_out, nullptr);
+                                                            phase_out, nullptr, n->base);
     n->launches++;
     CN_CK(cudaGetLastError());
     return HG_OK;

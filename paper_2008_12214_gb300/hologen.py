@@ -112,7 +112,7 @@ def lib():
                            ("hg_cnn_gradients", [P, P, P, I, P]),
                            ("hg_cnn_train_step", [P, P, P, I, ctypes.c_float, P]), ("hg_cnn_sync", [P]),
                            ("hg_cnn_apply_grads", [P, P, ctypes.c_float]),
-                           ("hg_cnn_launch_count", [P]),
+                           ("hg_cnn_launch_count", [P]), ("hg_cnn_set_base_phase", [P, P]),
                            ("hg_conv3x3_forward", [P, I, I, I, I, P, I, P, I, P, P, P]),
                            ("hg_conv3x3_dgrad", [P, I, I, I, I, P, I, P, P, P]),
                            ("hg_conv3x3_wgrad", [P, P, I, I, I, I, I, P, P, P, Z, P]),
@@ -481,6 +481,11 @@ def hg_cnn_train_step(net, target, phase_label, batch, lr, loss_out=None):
 def hg_cnn_apply_grads(net, grads, lr):
     _ck(lib().hg_cnn_apply_grads(net, _ptr(grads, torch.float32, HG_CNN_NPARAMS, name="grads"), float(lr)),
         "hg_cnn_apply_grads")
+
+
+def hg_cnn_set_base_phase(net, base):
+    """base: float32 [H][W] radians (device or host tensor) or None to remove it."""
+    _ck(lib().hg_cnn_set_base_phase(net, _ptr(base, torch.float32, name="base")), "hg_cnn_set_base_phase")
 
 
 def hg_cnn_sync(net):

@@ -9,7 +9,11 @@ Labels.  The label of a target is the replay phase after `label_iters` GS
 iterations (Section 3.2) from a starting phase chosen by `label_start`:
 "flat" (phase 0), "fixed" (one seeded random phase shared by every target)
 or "random" (GS's own seeded random phase per target).  The first two make
-the label a deterministic function of the target.
+the label a deterministic function of the target.  With `residual` (fixed
+starts only) the shared start phase becomes the network's base phase
+(hg_cnn_set_base_phase): the network then models e^{i(phi - phi_0)}, the
+part of the label that GS added to its start, and its phase output is that
+remainder's phase plus phi_0.
 
 Evaluation.  For held-out targets (seeds from 10^6), plain GS from the
 seeded random phase runs `ref_iters` iterations; its last MSE is the
@@ -55,12 +59,16 @@ def gs_labels(plan, T, label_iters=200, label_start="flat"):
 
 
 def train(H, W, pairs, batch=8, lr=1e-3, seed=0, chunk=64, label_iters=200, epochs=1, net=None,
-          base_seed=1, log=None, label_start="flat", slm_kind=hg.HG_SLM_BINARY, levels=2):
+          base_seed=1, log=None, label_start="flat", slm_kind=hg.HG_SLM_BINARY, levels=2, residual=False):
     """Trains on `pairs` (target, GS phase) pairs, generated `chunk` at a time
     (target seeds base_seed ...).  Returns (net, losses per step, seconds)."""
     dev = torch.device("cuda", torch.cuda.current_device())
     if net is None:
         net = hg.CNN(H, W, batch, seed=seed)
+    if residual:
+        if label_start != "fixed":
+            raise ValueError("residual labels need the one shared start phase (label_start='fixed')")
+        hg.hg_cnn_set_base_phase(net.h, start_phase("fixed", torch.zeros((1, H, W), device=dev))[0].contiguous())
     plan = hg.Plan(H, W, chunk, slm_kind, levels)
     losses = []
     loss = torch.zeros(1, dtype=torch.float64, device=dev)

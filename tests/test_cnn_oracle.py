@@ -5,6 +5,7 @@ import numpy as np
 import pytest
 
 from oracle import cnn_oracle as cn
+from paper_2008_12214_gb300 import synth
 
 
 def direct_conv(x, W, b):
@@ -170,3 +171,23 @@ def test_adam_first_step_closed_form_and_second_step():
     mh = (0.9 * 0.1 * g + 0.1 * g2) / (1 - 0.81)
     vh = (0.999 * 0.001 * g * g + 0.001 * g2 * g2) / (1 - 0.999 ** 2)
     assert np.allclose(th2, th1 - 0.01 * mh / (np.sqrt(vh) + 1e-8), rtol=1e-13)
+
+
+def test_base_phase_reads_the_label_as_its_remainder():
+    """With a base phase phi_b the network's (c, s) is compared with the
+    label's remainder e^{i(phi - phi_b)}, and the predicted phase is the
+    phase of (c, s) plus phi_b: the loss equals the plain loss on the labels
+    phi - phi_b, the gradients too, and the phase is shifted by phi_b."""
+    H = W = 16
+    p = cn.init_params(2)
+    T = np.stack([synth.target(H, W, 70 + b) for b in range(2)])
+    rng = np.random.default_rng(3)
+    phi = rng.uniform(-np.pi, np.pi, (2, H, W))
+    base = rng.uniform(0, 2 * np.pi, (H, W))
+    L1, g1 = cn.loss_and_grads(p, T, phi, base)
+    L2, g2 = cn.loss_and_grads(p, T, phi - base)
+    assert L1 == L2 and all(np.array_equal(g1[k], g2[k]) for k in g1)
+    # a label equal to the base is a remainder of phase 0: (c, s) = (1, 0) scores 0
+    c, s, _ = cn.forward(p, cn.net_input(T))
+    assert cn.phase_loss(np.ones_like(c), np.zeros_like(s), T, (base + 0 * phi) - base)[0] == 0.0
+    assert np.allclose(cn.predict_phase(p, T, base), cn.predict_phase(p, T) + base, atol=1e-15)

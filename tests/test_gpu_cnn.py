@@ -320,3 +320,37 @@ def test_data_parallel_step_with_one_rank_is_the_fused_step():
         b.close()
     assert ka == kb == 3
     assert torch.equal(sa, sb) and torch.equal(la, lb)
+
+
+def test_base_phase_equals_labels_minus_base():
+    """hg_cnn_set_base_phase: with a base phase phi_b the loss and gradients
+    equal those of the plain net on the labels phi - phi_b (the same float
+    subtraction as in the kernel), bit for bit; the forward phase is the
+    plain one plus phi_b; removing the base restores the plain net."""
+    B, H, W = 2, 128, 128
+    T, phi = net_inputs(B, H, W, 500)
+    base = np.random.default_rng(8).uniform(0, 2 * np.pi, (H, W)).astype(np.float32)
+    resid = (phi - base[None]).astype(np.float32)
+    net = hg.CNN(H, W, B, seed=4)
+    try:
+        Td = torch.from_numpy(T).to(DEV)
+
+        def run(label, with_base):
+            hg.hg_cnn_set_base_phase(net.h, torch.from_numpy(base).to(DEV) if with_base else None)
+            loss = torch.zeros(1, dtype=torch.float64, device=DEV)
+            hg.hg_cnn_gradients(net.h, Td, torch.from_numpy(label).to(DEV), B, loss)
+            g = torch.empty(hg.HG_CNN_NPARAMS, dtype=torch.float32, device=DEV)
+            hg.hg_cnn_get_grads(net.h, g)
+            ph = torch.empty((B, H, W), dtype=torch.float32, device=DEV)
+            hg.hg_cnn_forward(net.h, Td, B, None, ph)
+            hg.hg_cnn_sync(net.h)
+            return loss.item(), g.cpu().numpy(), ph.cpu().numpy()
+
+        Lb, gb, pb = run(phi, True)
+        Lr, gr, pr = run(resid, False)
+        L0, _, p0 = run(phi, False)
+    finally:
+        net.close()
+    assert Lb == Lr and np.array_equal(gb, gr), (Lb, Lr)
+    assert np.array_equal(pb, (pr + base[None]).astype(np.float32))
+    assert np.array_equal(p0, pr) and L0 != Lb
