@@ -10,8 +10,9 @@
 // per launch at 16 fields, against 0.161 for 2 lines of two slots).
 // Measured at 16 fields of 1080 x 1920 (ms per launch): column pairs at two
 // CTAs per SM 0.155 against 0.171 at one; 4 row lines at 128 registers (0.6 KB
-// of spill per thread) lost to 3 lines, and 16-column pairs (96 registers)
-// lost to the two-CTA 8-column pass.  The 30-samples-per-thread plans spill
+// of spill per thread) and 2 lines at two CTAs per SM (128 registers, 0.9 KB
+// of spill) lost to 3 lines, and 16-column pairs (96 registers) lost to the
+// two-CTA 8-column pass.  The 30-samples-per-thread plans spill
 // as TMA-fed paired or column-pair passes (255 and 168 registers plus 0.8-0.9
 // KB per thread) and measured 1.6x (rows) and 1.2x (column pairs) slower.
 #include "hg_pipe.cuh"
